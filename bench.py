@@ -1,0 +1,339 @@
+"""Benchmark: k-eigenpair solves/sec of ARRABIT-MPM (Algorithm 8) on one GB300.
+
+Workload (default): 3D 7-point Dirichlet Laplacian on a 128^3 grid (n = 2,097,152,
+nnz = 14,581,760), k = 200 smallest eigenpairs (largest of 12 I - A), block p = 240,
+Chebyshev-interpolant degree d = 20, q = 2 augmentation blocks, relative residual 1e-8,
+plain FP64 path.  One step = one whole solve (every step of the hot path) with A and the
+Gaussian start block already resident in HBM.
+
+Printed JSON line: value (solves/s, device-timed), e2e (same metric through the C ABI with
+host buffers: A and X0 uploaded from pinned host memory, eigenpairs read back), roofline of
+the dominant kernel (the fused filter SpMM), the CPU oracle baseline, clocks, launches.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1507_06078_gb300 import inputs as I  # noqa: E402
+
+METRIC = "k-eigenpair solves/sec at rel. residual 1e-8"
+UNIT = "solves/s"
+# SpMV-equivalent columns (sum of block widths over all products with A) of one solve of
+# the 128^3 workload, as counted by the CUDA path (arb_info.spmm_cols); the reference arm
+# converts its per-column oracle time into solves/s with it.
+WORKLOAD_SPMM_COLS = None  # filled from the GPU run's info when available
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=128, help="3D grid side (128 = the benchmark workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(m):
+    if m == 128:
+        return I.workload_3d128()
+    k = max(8, int(round(200 * (m / 128) ** 3)))
+    p = int(round(1.2 * k))
+    return I.workload_3d(m, k, p)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_dev{device}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sms if s > 0.5 * max(sms)] or sms
+        return {"sm_mhz": float(np.median(busy)), "sm_max_mhz": float(max(maxs)), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def filter_algorithmic_bytes(n, nnz, p, d, s=8):
+    """Algorithmic HBM bytes of one Clenshaw filter application (d fused SpMM passes):
+    every pass reads A once (nnz*(8+4) + 4(n+1)); the block traffic is 2 n p s for the
+    first pass (read X, write b_{d-1}), 3 n p s for the second (read b_{d-1}, X; write) and
+    4 n p s for every later pass (read b_{j+1}, b_{j+2}, X; write b_j)."""
+    a_bytes = nnz * (8 + 4) + 4 * (n + 1)
+    blocks = 2 + (3 if d >= 2 else 0) + 4 * max(d - 2, 0)
+    return d * a_bytes + blocks * n * p * s
+
+
+def cpu_oracle_sample(W, spmm_cols_per_solve, budget_s=20.0, degree=3):
+    """Time the oracle's own Clenshaw filter (oracle.poly_clenshaw: scipy CSR x dense
+    block, FP64, one thread) on the full workload for about budget_s seconds, and convert
+    the time per SpMV-equivalent column into solves/s with the count of one solve.  The
+    oracle's dense Rayleigh-Ritz work is left out (a lower bound on its time), so the
+    baseline errs in the CPU's favour."""
+    import scipy.sparse as sp
+    from oracle import arrabit_oracle as O
+    A = O.csr_to_scipy(W.A.n, W.A.rowptr, W.A.col, W.A.val)
+    sigma = O.gershgorin_bounds(A)[1]
+    B = (sigma * sp.identity(W.A.n, format="csr") - A).tocsr()
+    X = I.gaussian_block(W.A.n, W.p, W.seed)
+    coef = O.interpolant_cheb_coeffs(degree)
+    t0 = time.perf_counter()
+    calls = 0
+    while True:
+        O.poly_clenshaw(B, X, 0.0, 0.99 * sigma, coef)
+        calls += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    t_col = (time.perf_counter() - t0) / (calls * degree * W.p)
+    solve_s = t_col * spmm_cols_per_solve
+    return {"value": 1.0 / solve_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{calls} calls of oracle.poly_clenshaw (degree {degree}, {calls * degree} full-size "
+                      f"SpMM steps of width {W.p}, {t_col * W.p:.2f} s/step) scaled by {spmm_cols_per_solve} "
+                      "SpMV-equivalent columns per solve; dense RR work excluded"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    W = workload(args.grid)
+    cols = int(os.environ.get("ARB_SPMM_COLS_PER_SOLVE", "0")) or default_spmm_cols(args.grid)
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(W, cols, budget_s=8.0)
+        if i >= args.warmup:
+            samples.append(r["value"])
+    v = float(np.mean(samples))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W.name, "n": W.A.n, "nnz": W.A.nnz, "k": W.k, "p": W.p, "q": W.q,
+                       "degree": W.degree, "tol": W.tol},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def default_spmm_cols(m):
+    # SpMV-equivalent columns per solve recorded from the CUDA path's arb_info for this
+    # workload (profiles/bench_laplace3d_128.md); used only to scale the CPU sample
+    return {128: 2_000_000}.get(m, 200_000)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1507_06078_gb300 import arrabit as arb
+    from paper_1507_06078_gb300 import build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    torch.cuda.set_device(local)
+    build.build()
+    W = workload(args.grid)
+    ctx = arb.Context(local)
+    stream = ctx.stream
+    mat = arb.Matrix.from_csr(ctx, W.A)
+    X0h = I.gaussian_block(W.A.n, W.p, W.seed + rank)
+    X0 = torch.from_numpy(X0h).cuda(local)
+    opts = arb.arb_options_default(W.k)
+    opts.p, opts.q, opts.degree = W.p, W.q, W.degree
+
+    def step():
+        return arb.arb_solve(ctx, mat, W.k, arb.ARB_SMALLEST, W.tol, opts, x0=X0, evecs="device")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        r = step()
+    barrier()
+    launches0 = ctx.launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = step()
+            infos.append(r.info)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = (ctx.launches() - launches0) // max(args.steps, 1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per = ms / args.steps
+    value = world * args.steps / (ms * 1e-3)
+    # correctness of the timed solves: closed-form spectrum and residuals
+    from tests.conftest import laplacian_3d_eigs  # closed form, no oracle involved
+    lam = laplacian_3d_eigs(args.grid)[:W.k]
+    eig_err = float(np.max(np.abs(r.evals - lam) / np.maximum(1.0, np.abs(lam))))
+
+    # dominant kernel: the fused filter SpMM, timed live on the context's stream
+    coef = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, W.degree)
+    Xf = X0
+    Yf = torch.empty_like(X0)
+    nrep = 3
+    for _ in range(1):
+        arb.arb_filter(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, Xf, Y=Yf)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nrep):
+        arb.arb_filter(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, Xf, Y=Yf)
+    e1.record(stream)
+    barrier()
+    f_ms = e0.elapsed_time(e1) / nrep
+    fbytes = filter_algorithmic_bytes(W.A.n, W.A.nnz, W.p, W.degree)
+    fflops = W.degree * (2.0 * W.A.nnz * W.p + 6.0 * W.A.n * W.p)
+    peak, peak_src = measured_peaks()
+    achieved = fbytes / (f_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "spmm_fused_kernel (Clenshaw filter step, FP64)",
+            "launch_ms": f_ms / W.degree, "algorithmic_bytes_per_launch": fbytes / W.degree,
+            "fp64_tflops": fflops / (f_ms * 1e-3) / 1e12, "peak_source": peak_src}
+
+    e2e = None
+    if not args.no_e2e:
+        pin_rowptr = torch.from_numpy(W.A.rowptr).pin_memory()
+        pin_col = torch.from_numpy(W.A.col).pin_memory()
+        pin_val = torch.from_numpy(W.A.val).pin_memory()
+        pin_x0 = torch.from_numpy(X0h).pin_memory()
+        out_vecs = torch.empty((W.k, W.A.n), dtype=torch.float64).pin_memory()
+        import ctypes as C
+        lib = arb.load()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h = C.c_void_p()
+            st = lib.arb_matrix_create_csr(ctx.handle, W.A.n, W.A.nnz, pin_rowptr.data_ptr(), pin_col.data_ptr(),
+                                           pin_val.data_ptr(), 0, C.byref(h))
+            assert st == 0
+            ev = np.zeros(W.k)
+            info = arb.arb_info()
+            st = lib.arb_solve(ctx.handle, h, W.k, arb.ARB_SMALLEST, W.tol, C.byref(opts), pin_x0.data_ptr(), 0,
+                               ev.ctypes.data, out_vecs.data_ptr(), W.A.n, 0, C.byref(info))
+            lib.arb_matrix_destroy(h)
+            assert st in (0, 1)
+        barrier()
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        h2d = W.A.rowptr.nbytes + W.A.col.nbytes + W.A.val.nbytes + X0h.nbytes
+        d2h = W.k * W.A.n * 8 + W.k * 8
+        e2e = {"value": world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_sample(W, int(np.mean([i["spmm_cols"] for i in infos])))
+
+    if rank == 0:
+        info = infos[-1]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": W.name, "n": W.A.n, "nnz": W.A.nnz, "k": W.k, "p": W.p, "q": W.q,
+                           "degree": W.degree, "tol": W.tol, "precision": "fp64",
+                           "l2": "inputs larger than L2 (A 175 MB, X0 4 GB, work blocks ~50 GB)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "gpu_launches": int(launches),
+                "solve": {"eig_rel_err_vs_closed_form": eig_err, "maxres": info["maxres"],
+                          "outer_iters": info["outer_iters"], "n_filters": info["n_filters"],
+                          "spmm_cols": info["spmm_cols"], "t_filter_s": info["t_filter"],
+                          "t_arr_s": info["t_arr"], "stop": info["stop_reason"]}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

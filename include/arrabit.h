@@ -1,0 +1,210 @@
+/*
+ * arrabit.h - C ABI of a GB300 (sm_103a) implementation of the subspace-update +
+ * augmented Rayleigh-Ritz hot path of ARRABIT (Wen & Zhang, "Block algorithms with
+ * augmented Rayleigh-Ritz projections for large-scale eigenpair computation",
+ * arXiv 1507.06078).
+ *
+ * Problem statement (Section 1; Section 2 "our task is to compute k largest
+ * eigenpairs"): given a sparse symmetric A in R^{n x n}, an integer k and a tolerance,
+ * return (Lambda_k, Q_k) with A Q_k = Q_k Lambda_k and Q_k^T Q_k = I for the k
+ * algebraically largest, or (by running on sigma I - A) smallest, eigenvalues.
+ *
+ * Conventions for every call:
+ *  - Return value: an arb_status.  Nothing aborts, traps or exits; a failing CUDA call
+ *    returns ARB_CUDA_ERROR and arb_last_error() describes it.
+ *  - Dense blocks ("multivectors") on the device are ROW-MAJOR n x ncols float64 with a
+ *    leading dimension ld >= ncols counted in elements (row i starts at ptr + i*ld).
+ *  - Device pointers must point into memory of the context's device; "host" pointers
+ *    are ordinary (preferably pinned) host memory.
+ *  - The caller owns every buffer it passes; the library owns its workspaces (allocated
+ *    per context on first use and kept until arb_ctx_destroy).
+ *  - All device work runs on the context's stream.  Calls that return host values
+ *    synchronise that stream; the others are asynchronous with respect to the host.
+ *  - One context per host thread at a time; contexts are not thread-safe.
+ */
+#ifndef ARRABIT_H
+#define ARRABIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct arb_ctx_s* arb_ctx;
+typedef struct arb_mat_s* arb_mat;
+
+typedef enum {
+  ARB_OK = 0,
+  ARB_NOT_CONVERGED = 1,  /* outputs hold the best pairs found; info->maxres says how good */
+  ARB_INVALID_ARG = -1,
+  ARB_OUT_OF_MEMORY = -2,
+  ARB_NOT_SYMMETRIC = -3,
+  ARB_BREAKDOWN = -4,     /* the iterate lost all numerical rank */
+  ARB_CUDA_ERROR = -5,
+  ARB_TIMEOUT = -6,
+  ARB_REJECTED = -7
+} arb_status;
+
+typedef enum { ARB_LARGEST = 0, ARB_SMALLEST = 1 } arb_which;
+typedef enum { ARB_FP64 = 0, ARB_MIXED = 1 } arb_precision;
+/* Section 5: Chebyshev interpolant of max(0,t)^(10d) (the paper's choice) or the
+ * classic Chebyshev polynomial T_d (eq. cheby-poly, the paper's comparison filter). */
+typedef enum { ARB_FILTER_CHEBINTERP = 0, ARB_FILTER_CHEBYSHEV = 1 } arb_filter_kind;
+
+/* Why the outer loop of Algorithm 8 ended (Section 5, "Outer loop stop rule"). */
+typedef enum {
+  ARB_STOP_CONVERGED = 0, /* maxres <= tol (eq. out-stop) */
+  ARB_STOP_NEAR_TOL = 1,  /* case (iii): maxres < (1 + 9h/k) tol */
+  ARB_STOP_STALLED = 2,   /* case (ii): no maxres decrease for 3 outer iterations */
+  ARB_STOP_MAXIT = 3,     /* case (i) */
+  ARB_STOP_ALL_LOCKED = 4
+} arb_stop_reason;
+
+/* Solver parameters (Section 5 and Algorithm 8).  Names follow the paper except that the
+ * block width k+q is called p here and the paper's augmentation count p is called q. */
+typedef struct {
+  int32_t p;            /* block width = k + guard vectors (Section 5 "Guard vectors"); 0: k + round(0.1 k) */
+  int32_t q;            /* augmentation blocks in [X, AX, ..., A^q X] (Alg. 5; default 1) */
+  int32_t degree;       /* polynomial degree d (Section 5; default 3) */
+  int32_t maxit;        /* outer iterations (default 30) */
+  int32_t maxit1;       /* inner stop-rule checks per outer iteration (default 10) */
+  int32_t maxit2;       /* filter applications between checks (default 5) */
+  int32_t inner_fixed;  /* > 0: exactly this many filters per outer iteration, no rcond rule */
+  int32_t filter;       /* arb_filter_kind */
+  int32_t precision;    /* arb_precision; only ARB_FP64 is implemented, others -> ARB_INVALID_ARG */
+  int32_t reserved0;
+  double tol1;          /* first continuation tolerance; 0: max(1e-6, tol) if tol <= 1e-8 else tol */
+  double shift_sigma;   /* sigma of sigma I - A for ARB_SMALLEST; NaN: Gershgorin upper bound of A */
+  uint64_t seed;        /* stream for padding columns (Philox4x32-10 + Box-Muller) */
+} arb_options;
+
+typedef struct {
+  double maxres;        /* max_{i<=k} res_i, eq. resi */
+  double a, b0, b_final;/* filter interval ends: a, the first and the last b (Section 5) */
+  double sigma;         /* shift used for ARB_SMALLEST (0 for ARB_LARGEST) */
+  double t_total, t_filter, t_arr; /* seconds spent in the call / inner loops / ARR steps */
+  int64_t spmm_cols;    /* SpMV-equivalents: sum of block widths over all products with A */
+  int32_t outer_iters;
+  int32_t n_filters;    /* filter applications, all outer iterations */
+  int32_t n_locked;     /* size of the locked set at exit */
+  int32_t stop_reason;  /* arb_stop_reason */
+  int32_t last_rank;    /* dimension of the last Rayleigh-Ritz subspace */
+  int32_t reserved0;
+} arb_info;
+
+/* ---------------------------------------------------------------- context, matrices */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to run on,
+ * or NULL for a stream the context creates and owns. */
+arb_status arb_ctx_create(arb_ctx* out, int device, void* cuda_stream);
+arb_status arb_ctx_destroy(arb_ctx ctx);
+/* Description of the last error seen by this context (static storage, never NULL). */
+const char* arb_last_error(arb_ctx ctx);
+const char* arb_status_string(arb_status s);
+/* Number of kernels this context has launched since it was created. */
+int64_t arb_kernel_launches(arb_ctx ctx);
+
+/* Defaults of Section 5 for k wanted pairs: p = k + round(0.1 k), q = 1, d = 3,
+ * maxit = 30, maxit1 = 10, maxit2 = 5. */
+void arb_options_default(arb_options* opts, int32_t k);
+
+/* Copy a symmetric matrix in CSR form into library-owned device memory.
+ * rowptr: int32[n+1] (rowptr[0] = 0, nondecreasing, rowptr[n] = nnz); col: int32[nnz]
+ * with 0 <= col < n; val: float64[nnz].  ptr_on_device != 0 means the three arrays are
+ * device pointers, else host pointers.  Symmetry is the caller's promise (it is not
+ * checked); rowptr/col ranges are checked for host inputs -> ARB_INVALID_ARG. */
+arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                 const int32_t* col, const double* val, int ptr_on_device,
+                                 arb_mat* out);
+arb_status arb_matrix_destroy(arb_mat mat);
+/* Gershgorin interval [lo, hi] of A (host outputs); stands in for the paper's eigs
+ * estimate of lambda_n (Section 5, "Estimation of lambda_n and lambda_{k+q}"). */
+arb_status arb_matrix_gershgorin(arb_ctx ctx, arb_mat mat, double* lo, double* hi);
+
+/* ---------------------------------------------------------------- the whole method */
+
+/* ARRABIT with the multi-power inner solver (Algorithm 8) for the k largest or smallest
+ * eigenpairs of A.
+ *  x0:     n x p row-major float64 start block (ld = p), host or device per x0_on_device;
+ *          NULL draws it from opts->seed with the library's Philox generator.
+ *  evals:  host float64[k]: eigenvalues of A, descending for ARB_LARGEST, ascending for
+ *          ARB_SMALLEST (Rayleigh quotients x_i^T A x_i).
+ *  evecs:  n x k COLUMN-major float64 with leading dimension ldq >= n, host or device per
+ *          evecs_on_device; may be NULL.  Each column has unit norm and its largest-
+ *          magnitude entry positive.
+ *  info:   may be NULL.
+ * Requires 0 < k <= p and (q+1) p < n.  Returns ARB_OK when the outer stop rule (or its
+ * near-tolerance case) is met, ARB_NOT_CONVERGED otherwise (outputs still filled). */
+arb_status arb_solve(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol,
+                     const arb_options* opts, const double* x0, int x0_on_device,
+                     double* evals, double* evecs, int64_t ldq, int evecs_on_device,
+                     arb_info* info);
+
+/* ---------------------------------------------------------------- hot-path steps
+ * All pointers below are DEVICE pointers.  B denotes op_scale * A + op_shift * I. */
+
+/* Y = psi_d(S) X diag(xscale), S = (2/(b-a)) (B - aI) - I: the filter of Algorithm 7 (the
+ * map of eq. rhod with Alg. 8's call poly(A - aI, X, 0, b - a, Gamma_d)), evaluated in
+ * the Chebyshev basis by Clenshaw's recurrence, d fused SpMM passes.
+ * coef: HOST float64[degree+1], Chebyshev coefficients c_0..c_d of psi_d.
+ * X, Y: n x ncols (ldx, ldy); Y must not overlap X.  xscale: float64[ncols] or NULL (1).
+ * colss: float64[ncols] or NULL; receives the column sums of squares of Y (the MPM
+ * normalisation of Section 3 needs 1/sqrt of these). */
+arb_status arb_filter(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, double a,
+                      double b, int32_t degree, const double* coef, const double* X,
+                      int64_t ldx, int32_t ncols, const double* xscale, double* Y, int64_t ldy,
+                      double* colss);
+
+/* Host-side coefficients c_0..c_d (float64[degree+1]) of the degree-d Chebyshev
+ * interpolant of max(0,t)^(10 d) at t_j = -cos(j pi/d) (Section 5, eq. chebfun-f), or of
+ * T_d for ARB_FILTER_CHEBYSHEV. */
+arb_status arb_filter_coefficients(int32_t filter, int32_t degree, double* coef);
+
+/* Y = B X (one block product with A; Alg. 5 augmentation and Alg. 1's U^T A U). */
+arb_status arb_spmm(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift,
+                    const double* X, int64_t ldx, int32_t ncols, double* Y, int64_t ldy);
+
+/* C = X^T Y (na x nb, row-major, ldc): the tall-skinny Gram product used by the inner
+ * stop rule (eq. inn-stop, X^T X), orth(Z) and H = U^T A U.  Deterministic. */
+arb_status arb_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
+                    const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
+
+/* Eigen-decomposition H = V diag(w) V^T of a symmetric m x m matrix (row-major, ldh) by
+ * parallel cyclic Jacobi on the device (Alg. 1 step 3, reading H = V Sigma V^T).
+ * w: float64[m] descending; V: m x m row-major (ldv), column j the eigenvector of w[j].
+ * H is not modified.  sweeps (host, may be NULL) receives the sweep count. */
+arb_status arb_syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w,
+                     double* V, int64_t ldv, int32_t* sweeps);
+
+/* Reciprocal 1-norm condition number of the symmetric Gram matrix G = X^T X
+ * (eq. inn-stop); host output; 0 when G is not numerically positive definite. */
+arb_status arb_rcond_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx,
+                          int32_t ncols, const double* xscale, double* rc);
+
+/* U = an orthonormal basis of the numerical range of Z (Alg. 1 step 1, "orthonormalize
+ * Z"): two passes of eigen-truncated Gram orthonormalisation with unit-column scaling.
+ * U: n x m capacity (ldu); *rank (host) receives the number of columns written. */
+arb_status arb_orth(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz, int32_t m,
+                    double* U, int64_t ldu, int32_t* rank);
+
+/* (Y, w) = RR(B, Z), Algorithm 1.  Y: n x m capacity (ldy), w: float64[m] device,
+ * descending; *rank (host) = number of Ritz pairs produced (= rank of Z). */
+arb_status arb_rayleigh_ritz(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift,
+                             int64_t n, const double* Z, int64_t ldz, int32_t m, double* Y,
+                             int64_t ldy, double* w, int32_t* rank);
+
+/* (Y, w) = ARR(B, X, q), Algorithm 5: Rayleigh-Ritz on span[X, BX, ..., B^q X] (built as
+ * an orthonormal block Krylov basis), leading `npairs` Ritz pairs kept.
+ * X: n x ncols; Y: n x npairs (ldy); w: float64[npairs] device; *rank (host) = subspace
+ * dimension.  Fewer than npairs directions -> ARB_BREAKDOWN. */
+arb_status arb_arr(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, int64_t n,
+                   const double* X, int64_t ldx, int32_t ncols, int32_t q, int32_t npairs,
+                   double* Y, int64_t ldy, double* w, int32_t* rank);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARRABIT_H */

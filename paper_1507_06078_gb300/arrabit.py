@@ -1,0 +1,344 @@
+"""Thin ctypes binding of the C ABI declared in include/arrabit.h.
+
+Every function here only marshals arguments (tensor pointers, leading dimensions, host
+arrays) and calls the library of the same name; all arithmetic runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the stream: a Context runs its kernels on
+the torch stream that was current when it was created.
+
+The library must have been built (``paper_1507_06078_gb300.build.build()``); loading
+fails loudly otherwise - there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "lib", "libarrabit.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "arrabit.h")
+
+ARB_OK, ARB_NOT_CONVERGED, ARB_INVALID_ARG, ARB_OUT_OF_MEMORY = 0, 1, -1, -2
+ARB_NOT_SYMMETRIC, ARB_BREAKDOWN, ARB_CUDA_ERROR, ARB_TIMEOUT, ARB_REJECTED = -3, -4, -5, -6, -7
+ARB_LARGEST, ARB_SMALLEST = 0, 1
+ARB_FP64, ARB_MIXED = 0, 1
+ARB_FILTER_CHEBINTERP, ARB_FILTER_CHEBYSHEV = 0, 1
+STOP_REASONS = {0: "converged", 1: "near_tol", 2: "stalled", 3: "maxit", 4: "all_locked"}
+
+
+class ArbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"arrabit status {status}: {msg}")
+        self.status = status
+
+
+class arb_options(C.Structure):
+    _fields_ = [("p", C.c_int32), ("q", C.c_int32), ("degree", C.c_int32), ("maxit", C.c_int32),
+                ("maxit1", C.c_int32), ("maxit2", C.c_int32), ("inner_fixed", C.c_int32),
+                ("filter", C.c_int32), ("precision", C.c_int32), ("reserved0", C.c_int32),
+                ("tol1", C.c_double), ("shift_sigma", C.c_double), ("seed", C.c_uint64)]
+
+
+class arb_info(C.Structure):
+    _fields_ = [("maxres", C.c_double), ("a", C.c_double), ("b0", C.c_double), ("b_final", C.c_double),
+                ("sigma", C.c_double), ("t_total", C.c_double), ("t_filter", C.c_double),
+                ("t_arr", C.c_double), ("spmm_cols", C.c_int64), ("outer_iters", C.c_int32),
+                ("n_filters", C.c_int32), ("n_locked", C.c_int32), ("stop_reason", C.c_int32),
+                ("last_rank", C.c_int32), ("reserved0", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
+        d["stop_reason"] = STOP_REASONS.get(self.stop_reason, str(self.stop_reason))
+        return d
+
+
+_lib = None
+_vp, _i32, _i64, _dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_PROTOS = {
+    "arb_ctx_create": (_i32, [C.POINTER(_vp), C.c_int, _vp]),
+    "arb_ctx_destroy": (_i32, [_vp]),
+    "arb_last_error": (C.c_char_p, [_vp]),
+    "arb_status_string": (C.c_char_p, [_i32]),
+    "arb_kernel_launches": (_i64, [_vp]),
+    "arb_options_default": (None, [C.POINTER(arb_options), _i32]),
+    "arb_matrix_create_csr": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, C.c_int, C.POINTER(_vp)]),
+    "arb_matrix_destroy": (_i32, [_vp]),
+    "arb_matrix_gershgorin": (_i32, [_vp, _vp, C.POINTER(_dbl), C.POINTER(_dbl)]),
+    "arb_solve": (_i32, [_vp, _vp, _i32, _i32, _dbl, C.POINTER(arb_options), _vp, C.c_int, _vp, _vp, _i64,
+                         C.c_int, C.POINTER(arb_info)]),
+    "arb_filter": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _dbl, _i32, _vp, _vp, _i64, _i32, _vp, _vp, _i64, _vp]),
+    "arb_filter_coefficients": (_i32, [_i32, _i32, _vp]),
+    "arb_spmm": (_i32, [_vp, _vp, _dbl, _dbl, _vp, _i64, _i32, _vp, _i64]),
+    "arb_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
+    "arb_syevj": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _i64, C.POINTER(_i32)]),
+    "arb_rcond_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, C.POINTER(_dbl)]),
+    "arb_orth": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, C.POINTER(_i32)]),
+    "arb_rayleigh_ritz": (_i32, [_vp, _vp, _dbl, _dbl, _i64, _vp, _i64, _i32, _vp, _i64, _vp, C.POINTER(_i32)]),
+    "arb_arr": (_i32, [_vp, _vp, _dbl, _dbl, _i64, _vp, _i64, _i32, _i32, _i32, _vp, _i64, _vp, C.POINTER(_i32)]),
+}
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/arrabit.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(arb_\w+)\s*\(", txt)))
+
+
+def load():
+    """Load the built library (raises if it is missing: no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIBPATH):
+        raise RuntimeError(f"CUDA library not built: {LIBPATH} missing "
+                           "(run paper_1507_06078_gb300.build.build())")
+    lib = C.CDLL(LIBPATH)
+    for name, (res, args) in _PROTOS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, st: int, what: str):
+    if st not in (ARB_OK, ARB_NOT_CONVERGED):
+        msg = load().arb_last_error(ctx.handle if ctx is not None else None)
+        raise ArbError(st, f"{what}: {load().arb_status_string(st).decode()} ({msg.decode() if msg else ''})")
+    return st
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _dev2d(t, name: str):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2
+            and t.stride(1) == 1):
+        raise ValueError(f"{name}: expected a row-major 2D float64 CUDA tensor")
+    return t.stride(0)
+
+
+class Context:
+    """A library context bound to a CUDA device and the current torch stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.device = device
+        h = _vp()
+        st = lib.arb_ctx_create(C.byref(h), device, _vp(stream.cuda_stream))
+        if st != ARB_OK:
+            raise ArbError(st, "arb_ctx_create failed")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().arb_ctx_destroy(self.handle)
+            self.handle = None
+
+    def launches(self) -> int:
+        return int(load().arb_kernel_launches(self.handle))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Matrix:
+    """A CSR matrix copied into library-owned device memory."""
+
+    def __init__(self, ctx: Context, n: int, rowptr, col, val):
+        lib = load()
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        h = _vp()
+        st = lib.arb_matrix_create_csr(ctx.handle, n, col.shape[0], rowptr.ctypes.data, col.ctypes.data,
+                                       val.ctypes.data, 0, C.byref(h))
+        _check(ctx, st, "arb_matrix_create_csr")
+        self.ctx, self.handle, self.n, self.nnz = ctx, h, n, col.shape[0]
+
+    @classmethod
+    def from_csr(cls, ctx: Context, A) -> "Matrix":
+        return cls(ctx, A.n, A.rowptr, A.col, A.val)
+
+    def close(self):
+        if self.handle:
+            load().arb_matrix_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def arb_options_default(k: int) -> arb_options:
+    o = arb_options()
+    load().arb_options_default(C.byref(o), k)
+    return o
+
+
+def arb_matrix_gershgorin(ctx: Context, mat: Matrix) -> tuple[float, float]:
+    lo, hi = _dbl(), _dbl()
+    _check(ctx, load().arb_matrix_gershgorin(ctx.handle, mat.handle, C.byref(lo), C.byref(hi)), "gershgorin")
+    return lo.value, hi.value
+
+
+def arb_filter_coefficients(kind: int, degree: int) -> np.ndarray:
+    c = np.zeros(degree + 1, dtype=np.float64)
+    st = load().arb_filter_coefficients(kind, degree, c.ctypes.data)
+    if st != ARB_OK:
+        raise ArbError(st, "arb_filter_coefficients")
+    return c
+
+
+@dataclass
+class SolveResult:
+    status: int
+    evals: np.ndarray
+    evecs: object
+    info: dict
+
+
+def arb_solve(ctx: Context, mat: Matrix, k: int, which: int, tol: float, opts: arb_options | None = None,
+              x0=None, evecs: str | None = "host") -> SolveResult:
+    """Algorithm 8 end to end.  x0: numpy (host) or torch CUDA n x p float64, or None.
+    evecs: "host" (numpy, n x k), "device" (torch CUDA tensor holding the column-major
+    n x k block as a k x n row-major view), or None."""
+    import torch
+    lib = load()
+    if opts is None:
+        opts = arb_options_default(k)
+    x0_ptr, x0_dev = 0, 0
+    if x0 is not None:
+        if isinstance(x0, np.ndarray):
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            x0_ptr = x0.ctypes.data
+        else:
+            _dev2d(x0, "x0")
+            if x0.stride(0) != x0.shape[1]:
+                raise ValueError("x0 must be contiguous")
+            x0_ptr, x0_dev = _ptr(x0), 1
+    ev = np.zeros(k, dtype=np.float64)
+    out, optr, odev = None, 0, 0
+    if evecs == "host":
+        out = np.zeros((k, mat.n), dtype=np.float64)  # column-major n x k == row-major k x n
+        optr = out.ctypes.data
+    elif evecs == "device":
+        out = torch.empty((k, mat.n), dtype=torch.float64, device=f"cuda:{ctx.device}")
+        optr, odev = _ptr(out), 1
+    info = arb_info()
+    st = lib.arb_solve(ctx.handle, mat.handle, k, which, tol, C.byref(opts), _vp(x0_ptr), x0_dev,
+                       ev.ctypes.data, _vp(optr), mat.n, odev, C.byref(info))
+    _check(ctx, st, "arb_solve")
+    vecs = None
+    if out is not None:
+        vecs = out.T
+    return SolveResult(st, ev, vecs, info.as_dict())
+
+
+def arb_filter(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, a: float, b: float,
+               coef: np.ndarray, X, xscale=None, Y=None, colss=None):
+    """Y = psi_d(S) X diag(xscale); returns Y (torch, n x ncols)."""
+    import torch
+    ldx = _dev2d(X, "X")
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    if Y is None:
+        Y = torch.empty_like(X)
+    ldy = _dev2d(Y, "Y")
+    st = load().arb_filter(ctx.handle, mat.handle, op_scale, op_shift, a, b, len(coef) - 1, coef.ctypes.data,
+                           _vp(_ptr(X)), ldx, X.shape[1], _vp(_ptr(xscale)), _vp(_ptr(Y)), ldy,
+                           _vp(_ptr(colss)))
+    _check(ctx, st, "arb_filter")
+    return Y
+
+
+def arb_spmm(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, X, Y=None):
+    import torch
+    ldx = _dev2d(X, "X")
+    if Y is None:
+        Y = torch.empty_like(X)
+    ldy = _dev2d(Y, "Y")
+    _check(ctx, load().arb_spmm(ctx.handle, mat.handle, op_scale, op_shift, _vp(_ptr(X)), ldx, X.shape[1],
+                                _vp(_ptr(Y)), ldy), "arb_spmm")
+    return Y
+
+
+def arb_gram(ctx: Context, X, Y, C_out=None):
+    import torch
+    ldx = _dev2d(X, "X")
+    ldy = _dev2d(Y, "Y")
+    if C_out is None:
+        C_out = torch.empty((X.shape[1], Y.shape[1]), dtype=torch.float64, device=X.device)
+    ldc = _dev2d(C_out, "C")
+    _check(ctx, load().arb_gram(ctx.handle, X.shape[0], _vp(_ptr(X)), ldx, X.shape[1], _vp(_ptr(Y)), ldy,
+                                Y.shape[1], _vp(_ptr(C_out)), ldc), "arb_gram")
+    return C_out
+
+
+def arb_syevj(ctx: Context, H):
+    import torch
+    ldh = _dev2d(H, "H")
+    m = H.shape[0]
+    w = torch.empty(m, dtype=torch.float64, device=H.device)
+    V = torch.empty((m, m), dtype=torch.float64, device=H.device)
+    sweeps = _i32()
+    _check(ctx, load().arb_syevj(ctx.handle, m, _vp(_ptr(H)), ldh, _vp(_ptr(w)), _vp(_ptr(V)), m,
+                                 C.byref(sweeps)), "arb_syevj")
+    return w, V, sweeps.value
+
+
+def arb_rcond_gram(ctx: Context, X, xscale=None) -> float:
+    ldx = _dev2d(X, "X")
+    rc = _dbl()
+    _check(ctx, load().arb_rcond_gram(ctx.handle, X.shape[0], _vp(_ptr(X)), ldx, X.shape[1],
+                                      _vp(_ptr(xscale)), C.byref(rc)), "arb_rcond_gram")
+    return rc.value
+
+
+def arb_orth(ctx: Context, Z):
+    import torch
+    ldz = _dev2d(Z, "Z")
+    U = torch.empty_like(Z)
+    r = _i32()
+    _check(ctx, load().arb_orth(ctx.handle, Z.shape[0], _vp(_ptr(Z)), ldz, Z.shape[1], _vp(_ptr(U)),
+                                U.stride(0), C.byref(r)), "arb_orth")
+    return U[:, :r.value]
+
+
+def arb_rayleigh_ritz(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, Z):
+    import torch
+    ldz = _dev2d(Z, "Z")
+    Y = torch.empty_like(Z)
+    w = torch.empty(Z.shape[1], dtype=torch.float64, device=Z.device)
+    r = _i32()
+    _check(ctx, load().arb_rayleigh_ritz(ctx.handle, mat.handle, op_scale, op_shift, Z.shape[0], _vp(_ptr(Z)),
+                                         ldz, Z.shape[1], _vp(_ptr(Y)), Y.stride(0), _vp(_ptr(w)), C.byref(r)),
+           "arb_rayleigh_ritz")
+    return Y[:, :r.value], w[:r.value]
+
+
+def arb_arr(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, X, q: int, npairs: int | None = None):
+    import torch
+    ldx = _dev2d(X, "X")
+    npairs = X.shape[1] if npairs is None else npairs
+    Y = torch.empty((X.shape[0], npairs), dtype=torch.float64, device=X.device)
+    w = torch.empty(npairs, dtype=torch.float64, device=X.device)
+    r = _i32()
+    _check(ctx, load().arb_arr(ctx.handle, mat.handle, op_scale, op_shift, X.shape[0], _vp(_ptr(X)), ldx,
+                               X.shape[1], q, npairs, _vp(_ptr(Y)), Y.stride(0), _vp(_ptr(w)), C.byref(r)),
+           "arb_arr")
+    return Y, w, r.value

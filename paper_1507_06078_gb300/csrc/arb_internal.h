@@ -1,0 +1,246 @@
+// Internal declarations shared by the CUDA translation units of the ARRABIT library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "arrabit.h"
+
+namespace arb {
+
+// Workspace slots owned by a context.  Each slot is one device allocation that grows on
+// demand; contents are not preserved across calls that request a larger size.
+enum WsSlot : int {
+  WS_GRAM_PART = 0,   // split-K partial sums of Gram products
+  WS_SS_PART,         // per-block column sums of squares from the fused SpMM
+  WS_COEF,            // per-step per-column filter coefficients
+  WS_SMALL0,          // small dense matrices (Gram, eigenvectors, ...)
+  WS_SMALL1,
+  WS_SMALL2,
+  WS_SMALL3,
+  WS_VEC0,            // short vectors
+  WS_VEC1,
+  WS_VEC2,
+  WS_INT0,
+  WS_JACOBI,          // Jacobi rotation table + reduction scratch
+  WS_FILT_W1,         // filter work blocks (step-level entry point)
+  WS_FILT_W2,
+  WS_TALL0,           // n x w temporaries of orth / RR / ARR entry points
+  WS_TALL1,
+  WS_TALL2,
+  WS_SOLVER_X,        // solver state (iterate, work blocks, bases)
+  WS_SOLVER_Y,
+  WS_SOLVER_W1,
+  WS_SOLVER_W2,
+  WS_SOLVER_QC,
+  WS_SOLVER_XALL,
+  WS_SOLVER_U,
+  WS_SOLVER_AU,
+  WS_SOLVER_T,
+  WS_SOLVER_T2,
+  WS_S_V,             // solver: eigenvectors of H, selected columns
+  WS_S_VSEL,
+  WS_S_VEC,           // solver: short per-column vectors
+  WS_NUM_SLOTS
+};
+
+}  // namespace arb
+
+struct arb_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  int64_t launches = 0;
+  std::string last_error = "no error";
+  void* ws[arb::WS_NUM_SLOTS] = {};
+  size_t ws_bytes[arb::WS_NUM_SLOTS] = {};
+  void* host_pinned = nullptr;  // small staging area for read-backs
+  size_t host_pinned_bytes = 0;
+  int jacobi_max_blocks = 0;    // co-resident blocks for the cooperative Jacobi kernel
+};
+
+struct arb_mat_s {
+  arb_ctx ctx = nullptr;
+  int64_t n = 0, nnz = 0;
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  bool gersh_valid = false;
+  double gersh_lo = 0.0, gersh_hi = 0.0;
+};
+
+namespace arb {
+
+// ---------------------------------------------------------------- error plumbing
+arb_status set_error(arb_ctx ctx, arb_status st, const std::string& msg);
+arb_status cuda_error(arb_ctx ctx, cudaError_t e, const char* what, const char* file, int line);
+
+#define ARB_CUDA(ctx, expr)                                                   \
+  do {                                                                        \
+    cudaError_t e__ = (expr);                                                 \
+    if (e__ != cudaSuccess) return ::arb::cuda_error((ctx), e__, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+// Check the launch just made and count it.
+#define ARB_LAUNCHED(ctx)                                                     \
+  do {                                                                        \
+    (ctx)->launches++;                                                        \
+    cudaError_t e__ = cudaGetLastError();                                     \
+    if (e__ != cudaSuccess) return ::arb::cuda_error((ctx), e__, "kernel launch", __FILE__, __LINE__); \
+  } while (0)
+
+#define ARB_TRY(expr)                        \
+  do {                                       \
+    arb_status s__ = (expr);                 \
+    if (s__ != ARB_OK) return s__;           \
+  } while (0)
+
+// Device workspace of at least `bytes` for `slot`.
+arb_status ws_get(arb_ctx ctx, int slot, size_t bytes, void** out);
+template <typename T>
+inline arb_status ws(arb_ctx ctx, int slot, size_t count, T** out) {
+  return ws_get(ctx, slot, count * sizeof(T) + 256, reinterpret_cast<void**>(out));
+}
+// Pinned host staging of at least `bytes`.
+arb_status host_stage(arb_ctx ctx, size_t bytes, void** out);
+// Copy `bytes` from device to a host pointer through the stream and wait.
+arb_status d2h_sync(arb_ctx ctx, void* host, const void* dev, size_t bytes);
+
+// ---------------------------------------------------------------- kernels (spmm.cu)
+// out = sy[c] * (alpha * (A Yin) + beta * Yin) + sx[c] * X + sz[c] * Z, row-major blocks.
+// Optional outputs: `out` (skipped when NULL) and per-column reductions into `colred`
+// (sum over rows of out^2, or of out * Yin when dot_with_yin).
+struct SpmmArgs {
+  const arb_mat_s* A = nullptr;
+  int32_t ncols = 0;
+  const double* Yin = nullptr;
+  int64_t ldy = 0;
+  double alpha = 1.0, beta = 0.0;
+  const double* sy = nullptr;  // NULL: 1
+  const double* X = nullptr;
+  int64_t ldx = 0;
+  const double* sx = nullptr;  // required when X != NULL
+  const double* Z = nullptr;
+  int64_t ldz = 0;
+  const double* sz = nullptr;  // required when Z != NULL
+  double* out = nullptr;
+  int64_t ldo = 0;
+  double* colred = nullptr;    // float64[ncols] result of the column reduction, or NULL
+  bool dot_with_yin = false;
+};
+arb_status spmm_fused(arb_ctx ctx, const SpmmArgs& a);
+
+// Gershgorin lower/upper bound of A into host doubles.
+arb_status gershgorin(arb_ctx ctx, arb_mat mat, double* lo, double* hi);
+
+// Column sums of squares of a block (ncols results, device).
+arb_status col_sumsq(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
+                     double* out);
+
+// ---------------------------------------------------------------- kernels (dense.cu)
+// C (na x nb, ldc) = X^T Y over n rows; deterministic split-K.  symmetric: X == Y.
+arb_status gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
+                const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
+// Out (n x nb) = alpha * In (n x na) * W (na x nb, ldw) + beta * Out.  Out must not alias In.
+arb_status gemm_tall(arb_ctx ctx, int64_t n, const double* In, int64_t ldi, int32_t na,
+                     const double* W, int64_t ldw, int32_t nb, double alpha, double beta,
+                     double* Out, int64_t ldo);
+// dst[:, j] = src[:, idx[j]] for j < ncols (idx on device)
+arb_status gather_cols(arb_ctx ctx, int64_t n, const double* src, int64_t lds,
+                       const int32_t* idx, int32_t ncols, double* dst, int64_t ldd);
+// dst[:, j] = idx[j] >= 0 ? srcA[:, idx[j]] : srcB[:, -idx[j]-1]
+arb_status gather_cols2(arb_ctx ctx, int64_t n, const double* srcA, int64_t ldA, const double* srcB,
+                        int64_t ldB, const int32_t* idx, int32_t ncols, double* dst, int64_t ldd);
+// res[c] = sqrt(ss[c]) / max(1, |lambda_c|), lambda_c = smallest ? sigma - mu_c : mu_c
+arb_status residual_finish(arb_ctx ctx, int32_t p, const double* ss, const double* mu, int smallest,
+                           double sigma, double* res);
+// Per-column index of the largest |x| (ties: smallest row) -> sign[c] = +-1.
+arb_status column_signs(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
+                        double* sign);
+// evecs[c * ldq + i] = sign[c] * X[i * ldx + perm[c]]  (column-major output)
+arb_status write_colmajor(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, const int32_t* perm,
+                          const double* sign, int32_t k, double* out, int64_t ldq);
+// dst = src (n x ncols)
+arb_status copy_block(arb_ctx ctx, int64_t n, const double* src, int64_t lds, int32_t ncols,
+                      double* dst, int64_t ldd);
+arb_status fill(arb_ctx ctx, double* p, int64_t count, double v);
+// H <- (H + H^T)/2 for an m x m row-major matrix
+arb_status symmetrize(arb_ctx ctx, int32_t m, double* H, int64_t ldh);
+// G <- diag(s) G diag(s)
+arb_status scale_sym(arb_ctx ctx, int32_t m, double* G, int64_t ldg, const double* s);
+// s[c] = 1/sqrt(ss[c]) (0 when ss[c] == 0)
+arb_status inv_sqrt(arb_ctx ctx, int32_t m, const double* ss, double* s);
+// Ghat = D G D with D = diag(1/sqrt(G_ii)); d gets the diagonal of D.
+arb_status svqb_prep(arb_ctx ctx, int32_t m, const double* G, int64_t ldg, double* Ghat,
+                     double* d);
+// M[:, j] = d .* W[:, j] / sqrt(theta_j) for theta_j > tau * theta_0 (else 0); *rank_dev.
+arb_status svqb_finish(arb_ctx ctx, int32_t m, const double* theta, const double* W,
+                       int64_t ldw, const double* d, double tau, double* M, int32_t* rank_dev);
+// rc = 1/(||G||_1 ||G^{-1}||_1) from G and its eigen-decomposition, into rc_dev.
+arb_status rcond_from_eig(arb_ctx ctx, int32_t m, const double* G, int64_t ldg,
+                          const double* theta, const double* W, int64_t ldw, double* rc_dev);
+// Largest p of the concatenation [vlock (nl), vnew (nn)] (descending, stable): map[s] and
+// val[s]; map < nl -> locked index, else nl + index into vnew.  *count = min(p, nl+nn).
+arb_status select_top(arb_ctx ctx, const double* vlock, int32_t nl, const double* vnew,
+                      int32_t nn, int32_t p, int32_t* map, double* val);
+// Gaussian fill from the Philox4x32-10 stream `seed` (row-major n x ncols, element
+// i*ncols + j), same numbering as the input generators.
+arb_status gaussian_fill(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, double* X,
+                         int64_t ldx);
+
+// ---------------------------------------------------------------- Jacobi (jacobi.cu)
+// w (descending), V (row-major, column j = eigenvector) of symmetric H (not modified).
+arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
+                 int64_t ldv, int32_t* sweeps);
+
+// ---------------------------------------------------------------- composite steps (steps.cu)
+struct FilterPlan {
+  double alpha = 1.0, beta = 0.0;  // S = alpha A + beta I
+  int32_t degree = 0;
+  double coef[64] = {};            // Chebyshev coefficients c_0..c_d
+};
+// S from B = op_scale A + op_shift I and the interval [a, b] of Algorithm 8's call
+// poly(B - aI, X, 0, b - a, Gamma_d).
+FilterPlan make_filter_plan(double op_scale, double op_shift, double a, double b, int32_t degree,
+                            const double* coef);
+// Y = psi_d(S) (X diag(xscale)); W1, W2: n x ncols work blocks (ldw); Y may be NULL, in
+// which case the result overwrites one of W1/W2 and *result points at it.  colss: column
+// sums of squares of the result (device, may be NULL).
+arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const double* X,
+                        int64_t ldx, int32_t ncols, const double* xscale, double* W1,
+                        double* W2, int64_t ldw, double* Y, int64_t ldy, double* colss,
+                        double** result);
+
+// Orthonormal basis of range(Z) (two eigen-truncated Gram passes).  U must not alias Z.
+// tmp: n x m work block.  *rank on host.
+arb_status orth(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz, int32_t m, double* U,
+                int64_t ldu, double* tmp, int64_t ldt, int32_t* rank);
+
+// Reciprocal 1-norm condition number of diag(xs) X^T X diag(xs) (host result).
+arb_status rcond_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
+                      const double* xs, double* rc);
+
+// X <- X - Q (Q^T X)
+arb_status project_out(arb_ctx ctx, int64_t n, const double* Q, int64_t ldq, int32_t nq,
+                       double* X, int64_t ldx, int32_t ncols);
+
+// Block-Krylov Rayleigh-Ritz: U holds an orthonormal basis of span[X, BX, ..., B^q X]
+// (projected against Qc), AU = B U, then H = U^T AU is diagonalised.
+// Outputs: *m (subspace dimension, host), theta (device, m, descending), V (device m x m,
+// row-major with leading dimension m; column j is the eigenvector of theta_j).
+struct ArrWork {
+  double* U = nullptr;  int64_t ldu = 0;   // n x mcap
+  double* AU = nullptr; int64_t ldau = 0;  // n x mcap
+  double* T = nullptr;  int64_t ldt = 0;   // n x w
+  double* T2 = nullptr; int64_t ldt2 = 0;  // n x w
+};
+arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift,
+                             int64_t n, double* X, int64_t ldx, int32_t w, const double* Qc,
+                             int64_t ldqc, int32_t nl, int32_t q, const ArrWork& wk,
+                             int32_t* m_out, double* theta, double* V);
+
+}  // namespace arb

@@ -1,0 +1,553 @@
+// Dense FP64 kernels of the subspace step: tall-skinny Gram products X^T Y (inner stop
+// rule eq. inn-stop, orth(Z) and H = U^T A U of Algorithm 1), tall-skinny products
+// X W (projection X - Q_c(Q_c^T X) of Algorithm 8, basis change in orth, Ritz rotation
+// Y = U V of Algorithm 1), and the small helpers around the dense eigensolver.
+//
+// GB300 executes FP64 at a small fraction of its FP32/tensor rate, so these FP64 kernels
+// are bound by the FP64 pipe; they are register-tiled (4x4 outputs per thread, operands
+// staged in shared memory) so that the pipe, not memory, is the limit.
+#include <algorithm>
+#include <cmath>
+
+#include "arb_internal.h"
+
+namespace arb {
+namespace {
+
+constexpr int TILE = 64;
+constexpr int KSTEP = 16;
+
+// part[s][i][j] = sum over rows of split s of X[r][i] * Y[r][j], one 64x64 tile per CTA.
+__global__ void __launch_bounds__(256)
+gram_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int na,
+            const double* __restrict__ Y, int64_t ldy, int nb, int64_t rows_per_split,
+            int symmetric, double* __restrict__ part) {
+  const int ti = blockIdx.x, tj = blockIdx.y, s = blockIdx.z;
+  if (symmetric && tj < ti) return;
+  __shared__ double Xs[KSTEP][TILE + 1];
+  __shared__ double Ys[KSTEP][TILE + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = ti * TILE, j0 = tj * TILE;
+  const int64_t r0 = s * rows_per_split;
+  const int64_t r1 = min(n, r0 + rows_per_split);
+  double acc[4][4] = {};
+  for (int64_t rb = r0; rb < r1; rb += KSTEP) {
+    for (int t = threadIdx.x; t < KSTEP * TILE; t += 256) {
+      const int rr = t / TILE, cc = t % TILE;
+      const int64_t r = rb + rr;
+      const bool rok = r < r1;
+      Xs[rr][cc] = (rok && i0 + cc < na) ? X[r * ldx + i0 + cc] : 0.0;
+      Ys[rr][cc] = (rok && j0 + cc < nb) ? Y[r * ldy + j0 + cc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KSTEP; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = Xs[k][ty + 16 * u];
+        b[u] = Ys[k][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double* P = part + static_cast<size_t>(s) * na * nb;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + ty + 16 * u;
+    if (i >= na) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + tx + 16 * v;
+      if (j < nb) P[static_cast<size_t>(i) * nb + j] = acc[u][v];
+    }
+  }
+}
+
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int nsplit, int na, int nb,
+                                   int symmetric, double* __restrict__ C, int64_t ldc) {
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (idx >= static_cast<int64_t>(na) * nb) return;
+  int i = static_cast<int>(idx / nb), j = static_cast<int>(idx % nb);
+  int si = i, sj = j;
+  if (symmetric && (j / TILE) < (i / TILE)) {
+    si = j;
+    sj = i;
+  }
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += part[static_cast<size_t>(k) * na * nb + static_cast<size_t>(si) * nb + sj];
+  C[static_cast<int64_t>(i) * ldc + j] = s;
+}
+
+// Out[r][c] = alpha * sum_k In[r][k] W[k][c] + beta * Out[r][c]; 64x64 output tile per CTA.
+__global__ void __launch_bounds__(256)
+gemm_tall_kernel(int64_t n, const double* __restrict__ In, int64_t ldi, int na,
+                 const double* __restrict__ W, int64_t ldw, int nb, double alpha, double beta,
+                 double* __restrict__ Out, int64_t ldo) {
+  __shared__ double Is[KSTEP][TILE + 1];
+  __shared__ double Ws[KSTEP][TILE + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TILE;
+  const int c0 = blockIdx.y * TILE;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < na; k0 += KSTEP) {
+    for (int t = threadIdx.x; t < KSTEP * TILE; t += 256) {
+      const int kk = t % KSTEP, rr = t / KSTEP;
+      const int64_t r = r0 + rr;
+      Is[kk][rr] = (r < n && k0 + kk < na) ? In[r * ldi + k0 + kk] : 0.0;
+      const int kw = t / TILE, cw = t % TILE;
+      Ws[kw][cw] = (k0 + kw < na && c0 + cw < nb) ? W[static_cast<int64_t>(k0 + kw) * ldw + c0 + cw] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KSTEP; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = Is[k][ty + 16 * u];
+        b[u] = Ws[k][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t r = r0 + ty + 16 * u;
+    if (r >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = c0 + tx + 16 * v;
+      if (c >= nb) continue;
+      double* o = Out + r * ldo + c;
+      const double val = alpha * acc[u][v];
+      *o = (beta == 0.0) ? val : fma(beta, *o, val);
+    }
+  }
+}
+
+__global__ void gather_cols_kernel(int64_t n, const double* __restrict__ src, int64_t lds,
+                                   const int32_t* __restrict__ idx, int ncols,
+                                   double* __restrict__ dst, int64_t ldd) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * ncols) return;
+  const int64_t r = t / ncols;
+  const int c = static_cast<int>(t % ncols);
+  dst[r * ldd + c] = src[r * lds + idx[c]];
+}
+
+__global__ void gather_cols2_kernel(int64_t n, const double* __restrict__ srcA, int64_t ldA,
+                                    const double* __restrict__ srcB, int64_t ldB,
+                                    const int32_t* __restrict__ idx, int ncols,
+                                    double* __restrict__ dst, int64_t ldd) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * ncols) return;
+  const int64_t r = t / ncols;
+  const int c = static_cast<int>(t % ncols);
+  const int s = idx[c];
+  dst[r * ldd + c] = s >= 0 ? srcA[r * ldA + s] : srcB[r * ldB + (-s - 1)];
+}
+
+__global__ void residual_finish_kernel(int p, const double* __restrict__ ss, const double* __restrict__ mu,
+                                       int smallest, double sigma, double* __restrict__ res) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p) return;
+  const double lam = smallest ? sigma - mu[c] : mu[c];
+  res[c] = sqrt(fmax(ss[c], 0.0)) / fmax(1.0, fabs(lam));
+}
+
+// one block per column: largest |x| and its (smallest) row index
+__global__ void column_signs_kernel(int64_t n, const double* __restrict__ X, int64_t ldx,
+                                    double* __restrict__ sign) {
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  const int c = blockIdx.x;
+  double best = -1.0;
+  int64_t bi = 0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double v = fabs(X[r * ldx + c]);
+    if (v > best) {
+      best = v;
+      bi = r;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double v2 = sv[threadIdx.x + s];
+      const int64_t i2 = si[threadIdx.x + s];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sign[c] = X[si[0] * ldx + c] < 0.0 ? -1.0 : 1.0;
+}
+
+__global__ void write_colmajor_kernel(int64_t n, const double* __restrict__ X, int64_t ldx,
+                                      const int32_t* __restrict__ perm, const double* __restrict__ sign,
+                                      int k, double* __restrict__ out, int64_t ldq) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * k) return;
+  const int c = static_cast<int>(t / n);
+  const int64_t r = t % n;
+  out[c * ldq + r] = sign[c] * X[r * ldx + perm[c]];
+}
+
+__global__ void copy_block_kernel(int64_t n, const double* __restrict__ src, int64_t lds, int ncols,
+                                  double* __restrict__ dst, int64_t ldd) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * ncols) return;
+  const int64_t r = t / ncols;
+  const int c = static_cast<int>(t % ncols);
+  dst[r * ldd + c] = src[r * lds + c];
+}
+
+__global__ void fill_kernel(double* p, int64_t count, double v) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t < count) p[t] = v;
+}
+
+__global__ void symmetrize_kernel(int m, double* H, int64_t ldh) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(m) * m) return;
+  const int i = static_cast<int>(t / m), j = static_cast<int>(t % m);
+  if (j <= i) return;
+  const double v = 0.5 * (H[static_cast<int64_t>(i) * ldh + j] + H[static_cast<int64_t>(j) * ldh + i]);
+  H[static_cast<int64_t>(i) * ldh + j] = v;
+  H[static_cast<int64_t>(j) * ldh + i] = v;
+}
+
+__global__ void scale_sym_kernel(int m, double* G, int64_t ldg, const double* __restrict__ s) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(m) * m) return;
+  const int i = static_cast<int>(t / m), j = static_cast<int>(t % m);
+  G[static_cast<int64_t>(i) * ldg + j] *= s[i] * s[j];
+}
+
+__global__ void inv_sqrt_kernel(int m, const double* __restrict__ ss, double* __restrict__ s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) s[i] = ss[i] > 0.0 ? 1.0 / sqrt(ss[i]) : 0.0;
+}
+
+__global__ void svqb_prep_kernel(int m, const double* __restrict__ G, int64_t ldg,
+                                 double* __restrict__ Gh, double* __restrict__ d) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(m) * m) return;
+  const int i = static_cast<int>(t / m), j = static_cast<int>(t % m);
+  const double gi = G[static_cast<int64_t>(i) * ldg + i];
+  const double gj = G[static_cast<int64_t>(j) * ldg + j];
+  const double di = gi > 0.0 ? 1.0 / sqrt(gi) : 0.0;
+  const double dj = gj > 0.0 ? 1.0 / sqrt(gj) : 0.0;
+  Gh[static_cast<int64_t>(i) * m + j] = G[static_cast<int64_t>(i) * ldg + j] * di * dj;
+  if (j == 0) d[i] = di;
+}
+
+// number of leading theta_j > tau * theta_0 (theta descending)
+__device__ int svqb_rank(int m, const double* theta, double tau) {
+  const double t0 = theta[0];
+  if (!(t0 > 0.0)) return 0;
+  const double thr = tau * t0;
+  int lo = 0, hi = m;  // first index with !(theta > thr)
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (theta[mid] > thr) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void svqb_finish_kernel(int m, const double* __restrict__ theta, const double* __restrict__ W,
+                                   int64_t ldw, const double* __restrict__ d, double tau,
+                                   double* __restrict__ M, int32_t* rank_dev) {
+  __shared__ int r_s;
+  if (threadIdx.x == 0) r_s = svqb_rank(m, theta, tau);
+  __syncthreads();
+  const int r = r_s;
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t == 0) *rank_dev = r;
+  if (t >= static_cast<int64_t>(m) * m) return;
+  const int i = static_cast<int>(t / m), j = static_cast<int>(t % m);
+  M[static_cast<int64_t>(i) * m + j] = (j < r) ? d[i] * W[static_cast<int64_t>(i) * ldw + j] / sqrt(theta[j]) : 0.0;
+}
+
+// Ginv[i][j] = sum_k W[i][k] W[j][k] / theta_k
+__global__ void inverse_from_eig_kernel(int m, const double* __restrict__ theta,
+                                        const double* __restrict__ W, int64_t ldw,
+                                        double* __restrict__ Ginv) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(m) * m) return;
+  const int i = static_cast<int>(t / m), j = static_cast<int>(t % m);
+  double s = 0.0;
+  for (int k = 0; k < m; ++k)
+    s = fma(W[static_cast<int64_t>(i) * ldw + k] * W[static_cast<int64_t>(j) * ldw + k], 1.0 / theta[k], s);
+  Ginv[t] = s;
+}
+
+__global__ void rcond_final_kernel(int m, const double* __restrict__ G, int64_t ldg,
+                                   const double* __restrict__ Ginv, const double* __restrict__ theta,
+                                   double* __restrict__ rc) {
+  __shared__ double sg[256], si[256];
+  double mg = 0.0, mi = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double cg = 0.0, ci = 0.0;
+    for (int i = 0; i < m; ++i) {
+      cg += fabs(G[static_cast<int64_t>(i) * ldg + j]);
+      ci += fabs(Ginv[static_cast<int64_t>(i) * m + j]);
+    }
+    mg = fmax(mg, cg);
+    mi = fmax(mi, ci);
+  }
+  sg[threadIdx.x] = mg;
+  si[threadIdx.x] = mi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sg[threadIdx.x] = fmax(sg[threadIdx.x], sg[threadIdx.x + s]);
+      si[threadIdx.x] = fmax(si[threadIdx.x], si[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double tmin = theta[m - 1];
+    double r = 0.0;
+    if (tmin > 0.0 && isfinite(si[0]) && si[0] > 0.0 && sg[0] > 0.0) r = 1.0 / (sg[0] * si[0]);
+    *rc = r;
+  }
+}
+
+__device__ __forceinline__ double nan_to_neginf(double v) { return isnan(v) ? -INFINITY : v; }
+
+__global__ void select_top_kernel(const double* __restrict__ vl, int nl, const double* __restrict__ vn,
+                                  int nn, int p, int32_t* __restrict__ map, double* __restrict__ val) {
+  const int N = nl + nn;
+  for (int s = threadIdx.x; s < p; s += blockDim.x) map[s] = -1;
+  __syncthreads();
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const double ve = nan_to_neginf(e < nl ? vl[e] : vn[e - nl]);
+    int rank = 0;
+    for (int f = 0; f < N; ++f) {
+      const double vf = nan_to_neginf(f < nl ? vl[f] : vn[f - nl]);
+      rank += (vf > ve) || (vf == ve && f < e);
+    }
+    if (rank < p) {
+      map[rank] = e;
+      val[rank] = ve;
+    }
+  }
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) on counter (c0, c1, 0, 0).
+__device__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t k0, uint32_t k1, uint32_t out[4]) {
+  uint32_t c[4] = {c0, c1, 0u, 0u};
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+  out[0] = c[0];
+  out[1] = c[1];
+  out[2] = c[2];
+  out[3] = c[3];
+}
+
+__global__ void gaussian_fill_kernel(int64_t n, int ncols, uint64_t seed, double* X, int64_t ldx) {
+  const int64_t pair = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t total = n * ncols;
+  if (2 * pair >= total) return;
+  uint32_t o[4];
+  philox4x32_10(static_cast<uint32_t>(pair & 0xffffffffu), static_cast<uint32_t>(pair >> 32),
+                static_cast<uint32_t>(seed & 0xffffffffu), static_cast<uint32_t>(seed >> 32), o);
+  const double two53 = 9007199254740992.0;
+  const double u1 = ((double)(o[0] >> 5) * 67108864.0 + (double)(o[1] >> 6) + 0.5) / two53;
+  const double u2 = ((double)(o[2] >> 5) * 67108864.0 + (double)(o[3] >> 6)) / two53;
+  const double r = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  const int64_t e0 = 2 * pair;
+  X[(e0 / ncols) * ldx + (e0 % ncols)] = r * cs;
+  if (e0 + 1 < total) X[((e0 + 1) / ncols) * ldx + ((e0 + 1) % ncols)] = r * sn;
+}
+
+inline int blocks_for(int64_t count, int threads) {
+  return static_cast<int>(std::max<int64_t>(1, (count + threads - 1) / threads));
+}
+
+}  // namespace
+
+arb_status gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
+                const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc) {
+  if (na <= 0 || nb <= 0) return ARB_OK;
+  const int symmetric = (X == Y && ldx == ldy && na == nb) ? 1 : 0;
+  const int gi = (na + TILE - 1) / TILE, gj = (nb + TILE - 1) / TILE;
+  const int tiles = symmetric ? gi * (gi + 1) / 2 : gi * gj;
+  const int64_t target = static_cast<int64_t>(ctx->num_sms) * 3;
+  int64_t nsplit = std::max<int64_t>(1, (target + tiles - 1) / tiles);
+  nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, n / (4 * KSTEP)));
+  nsplit = std::min<int64_t>(nsplit, 4096);
+  int64_t rows = (n + nsplit - 1) / nsplit;
+  rows = ((rows + KSTEP - 1) / KSTEP) * KSTEP;
+  nsplit = std::max<int64_t>(1, (n + rows - 1) / rows);
+  double* part;
+  ARB_TRY(ws<double>(ctx, WS_GRAM_PART, static_cast<size_t>(nsplit) * na * nb, &part));
+  dim3 grid(gi, gj, static_cast<unsigned>(nsplit));
+  gram_kernel<<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+  ARB_LAUNCHED(ctx);
+  gram_reduce_kernel<<<blocks_for(static_cast<int64_t>(na) * nb, 256), 256, 0, ctx->stream>>>(
+      part, static_cast<int>(nsplit), na, nb, symmetric, C, ldc);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status gemm_tall(arb_ctx ctx, int64_t n, const double* In, int64_t ldi, int32_t na,
+                     const double* W, int64_t ldw, int32_t nb, double alpha, double beta,
+                     double* Out, int64_t ldo) {
+  if (n <= 0 || nb <= 0) return ARB_OK;
+  if (na <= 0) {
+    if (beta == 1.0) return ARB_OK;
+    return set_error(ctx, ARB_INVALID_ARG, "gemm_tall: empty inner dimension with beta != 1");
+  }
+  dim3 grid(static_cast<unsigned>((n + TILE - 1) / TILE), static_cast<unsigned>((nb + TILE - 1) / TILE));
+  gemm_tall_kernel<<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status gather_cols(arb_ctx ctx, int64_t n, const double* src, int64_t lds, const int32_t* idx,
+                       int32_t ncols, double* dst, int64_t ldd) {
+  if (ncols <= 0 || n <= 0) return ARB_OK;
+  gather_cols_kernel<<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, idx, ncols, dst, ldd);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status gather_cols2(arb_ctx ctx, int64_t n, const double* srcA, int64_t ldA, const double* srcB,
+                        int64_t ldB, const int32_t* idx, int32_t ncols, double* dst, int64_t ldd) {
+  if (ncols <= 0 || n <= 0) return ARB_OK;
+  gather_cols2_kernel<<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, srcA, ldA, srcB, ldB, idx,
+                                                                           ncols, dst, ldd);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status residual_finish(arb_ctx ctx, int32_t p, const double* ss, const double* mu, int smallest,
+                           double sigma, double* res) {
+  if (p <= 0) return ARB_OK;
+  residual_finish_kernel<<<blocks_for(p, 128), 128, 0, ctx->stream>>>(p, ss, mu, smallest, sigma, res);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status column_signs(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
+                        double* sign) {
+  if (ncols <= 0) return ARB_OK;
+  column_signs_kernel<<<ncols, 256, 0, ctx->stream>>>(n, X, ldx, sign);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status write_colmajor(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, const int32_t* perm,
+                          const double* sign, int32_t k, double* out, int64_t ldq) {
+  if (k <= 0 || n <= 0) return ARB_OK;
+  write_colmajor_kernel<<<blocks_for(n * k, 256), 256, 0, ctx->stream>>>(n, X, ldx, perm, sign, k, out, ldq);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status copy_block(arb_ctx ctx, int64_t n, const double* src, int64_t lds, int32_t ncols,
+                      double* dst, int64_t ldd) {
+  if (ncols <= 0 || n <= 0) return ARB_OK;
+  copy_block_kernel<<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status fill(arb_ctx ctx, double* p, int64_t count, double v) {
+  if (count <= 0) return ARB_OK;
+  fill_kernel<<<blocks_for(count, 256), 256, 0, ctx->stream>>>(p, count, v);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status symmetrize(arb_ctx ctx, int32_t m, double* H, int64_t ldh) {
+  if (m <= 1) return ARB_OK;
+  symmetrize_kernel<<<blocks_for(static_cast<int64_t>(m) * m, 256), 256, 0, ctx->stream>>>(m, H, ldh);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status scale_sym(arb_ctx ctx, int32_t m, double* G, int64_t ldg, const double* s) {
+  if (m <= 0) return ARB_OK;
+  scale_sym_kernel<<<blocks_for(static_cast<int64_t>(m) * m, 256), 256, 0, ctx->stream>>>(m, G, ldg, s);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status inv_sqrt(arb_ctx ctx, int32_t m, const double* ss, double* s) {
+  if (m <= 0) return ARB_OK;
+  inv_sqrt_kernel<<<blocks_for(m, 256), 256, 0, ctx->stream>>>(m, ss, s);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status svqb_prep(arb_ctx ctx, int32_t m, const double* G, int64_t ldg, double* Ghat, double* d) {
+  svqb_prep_kernel<<<blocks_for(static_cast<int64_t>(m) * m, 256), 256, 0, ctx->stream>>>(m, G, ldg, Ghat, d);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status svqb_finish(arb_ctx ctx, int32_t m, const double* theta, const double* W, int64_t ldw,
+                       const double* d, double tau, double* M, int32_t* rank_dev) {
+  svqb_finish_kernel<<<blocks_for(static_cast<int64_t>(m) * m, 256), 256, 0, ctx->stream>>>(
+      m, theta, W, ldw, d, tau, M, rank_dev);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status rcond_from_eig(arb_ctx ctx, int32_t m, const double* G, int64_t ldg, const double* theta,
+                          const double* W, int64_t ldw, double* rc_dev) {
+  double* Ginv;
+  ARB_TRY(ws<double>(ctx, WS_SMALL3, static_cast<size_t>(m) * m, &Ginv));
+  inverse_from_eig_kernel<<<blocks_for(static_cast<int64_t>(m) * m, 256), 256, 0, ctx->stream>>>(
+      m, theta, W, ldw, Ginv);
+  ARB_LAUNCHED(ctx);
+  rcond_final_kernel<<<1, 256, 0, ctx->stream>>>(m, G, ldg, Ginv, theta, rc_dev);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status select_top(arb_ctx ctx, const double* vlock, int32_t nl, const double* vnew, int32_t nn,
+                      int32_t p, int32_t* map, double* val) {
+  select_top_kernel<<<1, 1024, 0, ctx->stream>>>(vlock, nl, vnew, nn, p, map, val);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status gaussian_fill(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, double* X, int64_t ldx) {
+  const int64_t pairs = (n * ncols + 1) / 2;
+  gaussian_fill_kernel<<<blocks_for(pairs, 256), 256, 0, ctx->stream>>>(n, ncols, seed, X, ldx);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+}  // namespace arb

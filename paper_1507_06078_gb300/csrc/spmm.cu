@@ -1,0 +1,328 @@
+// Fused CSR block SpMM: the A-product of the filter recurrence (Algorithm 7 / Clenshaw),
+// of the augmentation [X, AX, ..., A^q X] (Algorithm 5), of U^T A U (Algorithm 1) and
+// of the residuals A x_i - mu_i x_i (eq. resi), with the per-step vector update and the
+// column reductions fused into the epilogue.
+//
+// Layout: A in CSR (int32 rowptr/col, float64 val); every block is row-major with a
+// leading dimension, so the row of the iterate that a nonzero a_ij gathers is one
+// contiguous run of `ncols` doubles.  One warp owns one row at a time; its 32 lanes
+// cover 32*VEC consecutive columns per chunk, so each gathered row segment is a fully
+// coalesced 256/512-byte transaction.  Column indices and values of a row are loaded
+// once per 32 nonzeros (one per lane) and broadcast with shuffles.
+#include <algorithm>
+
+#include "arb_internal.h"
+
+namespace arb {
+namespace {
+
+constexpr int SPMM_THREADS = 256;
+constexpr int SPMM_WARPS = SPMM_THREADS / 32;
+
+struct KParams {
+  int64_t n;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  int32_t ncols;
+  const double* Yin;
+  int64_t ldy;
+  double alpha, beta;
+  const double* sy;
+  const double* X;
+  int64_t ldx;
+  const double* sx;
+  const double* Z;
+  int64_t ldz;
+  const double* sz;
+  double* out;
+  int64_t ldo;
+  double* red_part;  // [gridDim.x][ncols] per-block partial column reductions, or NULL
+  int dot_with_yin;
+};
+
+template <int VEC>
+__device__ __forceinline__ void load_vec(const double* __restrict__ p, double (&r)[VEC]) {
+  if constexpr (VEC == 2) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    r[0] = t.x;
+    r[1] = t.y;
+  } else {
+    r[0] = *p;
+  }
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_vec(double* __restrict__ p, const double (&r)[VEC]) {
+  if constexpr (VEC == 2) {
+    *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+  } else {
+    *p = r[0];
+  }
+}
+
+template <int VEC>
+__global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams P) {
+  extern __shared__ double s_red[];  // [SPMM_WARPS][ncols]
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int ncols = P.ncols;
+  double* my_red = s_red + static_cast<size_t>(warp) * ncols;
+  if (P.red_part)
+    for (int c = lane; c < ncols; c += 32) my_red[c] = 0.0;
+  __syncwarp();
+  constexpr int CH = 32 * VEC;
+  const int64_t first = static_cast<int64_t>(blockIdx.x) * SPMM_WARPS + warp;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * SPMM_WARPS;
+  for (int64_t row = first; row < P.n; row += stride) {
+    const int beg = __ldg(P.rowptr + row);
+    const int end = __ldg(P.rowptr + row + 1);
+    for (int c0 = 0; c0 < ncols; c0 += CH) {
+      const int c = c0 + lane * VEC;
+      const bool act = c < ncols;
+      double acc[VEC];
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) acc[u] = 0.0;
+      for (int base = beg; base < end; base += 32) {
+        const int e = base + lane;
+        int jc = 0;
+        double av = 0.0;
+        if (e < end) {
+          jc = __ldg(P.col + e);
+          av = __ldg(P.val + e);
+        }
+        const int cnt = min(32, end - base);
+#pragma unroll 4
+        for (int t = 0; t < cnt; ++t) {
+          const int j = __shfl_sync(0xffffffffu, jc, t);
+          const double v = __shfl_sync(0xffffffffu, av, t);
+          if (act) {
+            double y[VEC];
+            load_vec<VEC>(P.Yin + static_cast<int64_t>(j) * P.ldy + c, y);
+#pragma unroll
+            for (int u = 0; u < VEC; ++u) acc[u] = fma(v, y[u], acc[u]);
+          }
+        }
+      }
+      if (act) {
+        double yi[VEC], o[VEC];
+        if (P.beta != 0.0 || P.dot_with_yin) {
+          load_vec<VEC>(P.Yin + row * P.ldy + c, yi);
+        } else {
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) yi[u] = 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          const double s = P.alpha * acc[u] + P.beta * yi[u];
+          o[u] = P.sy ? P.sy[c + u] * s : s;
+        }
+        if (P.X) {
+          double x[VEC];
+          load_vec<VEC>(P.X + row * P.ldx + c, x);
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) o[u] = fma(P.sx[c + u], x[u], o[u]);
+        }
+        if (P.Z) {
+          double z[VEC];
+          load_vec<VEC>(P.Z + row * P.ldz + c, z);
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) o[u] = fma(P.sz[c + u], z[u], o[u]);
+        }
+        if (P.out) store_vec<VEC>(P.out + row * P.ldo + c, o);
+        if (P.red_part) {
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) my_red[c + u] += P.dot_with_yin ? o[u] * yi[u] : o[u] * o[u];
+        }
+      }
+    }
+  }
+  if (P.red_part) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+      double s = 0.0;
+      for (int w = 0; w < SPMM_WARPS; ++w) s += s_red[static_cast<size_t>(w) * ncols + c];
+      P.red_part[static_cast<size_t>(blockIdx.x) * ncols + c] = s;
+    }
+  }
+}
+
+// out[c] = sum_b part[b][c], b in order (deterministic).
+__global__ void reduce_partials_kernel(const double* __restrict__ part, int nb, int ncols,
+                                       double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[static_cast<size_t>(b) * ncols + c];
+  out[c] = s;
+}
+
+// Per-block Gershgorin bounds: lo = min(a_ii - r_i), hi = max(a_ii + r_i).
+__global__ void gershgorin_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                  const int32_t* __restrict__ col, const double* __restrict__ val,
+                                  double* __restrict__ part) {
+  __shared__ double slo[256], shi[256];
+  double lo = 1e308, hi = -1e308;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double d = 0.0, r = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      if (col[e] == i) d += val[e];
+      else r += fabs(val[e]);
+    }
+    lo = fmin(lo, d - r);
+    hi = fmax(hi, d + r);
+  }
+  slo[threadIdx.x] = lo;
+  shi[threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = slo[0];
+    part[2 * blockIdx.x + 1] = shi[0];
+  }
+}
+
+__global__ void gershgorin_final_kernel(const double* __restrict__ part, int nb,
+                                        double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double lo = 1e308, hi = -1e308;
+  for (int b = 0; b < nb; ++b) {
+    lo = fmin(lo, part[2 * b]);
+    hi = fmax(hi, part[2 * b + 1]);
+  }
+  out[0] = lo;
+  out[1] = hi;
+}
+
+// Per-block column sums of squares of rows [b*rows, (b+1)*rows).
+__global__ void col_sumsq_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int ncols,
+                                 int64_t rows_per_block, double* __restrict__ part) {
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_block;
+  const int64_t r1 = min(n, r0 + rows_per_block);
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+    double s = 0.0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const double x = X[r * ldx + c];
+      s = fma(x, x, s);
+    }
+    part[static_cast<size_t>(blockIdx.x) * ncols + c] = s;
+  }
+}
+
+template <int VEC>
+arb_status launch_spmm(arb_ctx ctx, const KParams& P, int grid, size_t smem) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    ARB_CUDA(ctx, cudaFuncSetAttribute(spmm_fused_kernel<VEC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr_set = true;
+  }
+  spmm_fused_kernel<VEC><<<grid, SPMM_THREADS, smem, ctx->stream>>>(P);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+arb_status spmm_fused(arb_ctx ctx, const SpmmArgs& a) {
+  const arb_mat_s* A = a.A;
+  if (a.ncols <= 0 || A->n <= 0) return ARB_OK;
+  if (a.ncols > 6000) return set_error(ctx, ARB_INVALID_ARG, "spmm: ncols too large");
+  KParams P;
+  P.n = A->n;
+  P.rowptr = A->rowptr;
+  P.col = A->col;
+  P.val = A->val;
+  P.ncols = a.ncols;
+  P.Yin = a.Yin;
+  P.ldy = a.ldy;
+  P.alpha = a.alpha;
+  P.beta = a.beta;
+  P.sy = a.sy;
+  P.X = a.X;
+  P.ldx = a.ldx;
+  P.sx = a.sx;
+  P.Z = a.Z;
+  P.ldz = a.ldz;
+  P.sz = a.sz;
+  P.out = a.out;
+  P.ldo = a.ldo;
+  P.dot_with_yin = a.dot_with_yin ? 1 : 0;
+  P.red_part = nullptr;
+  // rows spread over a fixed grid so the per-block partial sums are deterministic
+  const int64_t want = (A->n + SPMM_WARPS - 1) / SPMM_WARPS;
+  int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(ctx->num_sms) * 8));
+  grid = std::max(grid, 1);
+  size_t smem = 0;
+  if (a.colred) {
+    smem = static_cast<size_t>(SPMM_WARPS) * a.ncols * sizeof(double);
+    if (smem > 200 * 1024) return set_error(ctx, ARB_INVALID_ARG, "spmm: too many columns for reduction");
+    ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * a.ncols, &P.red_part));
+  }
+  // vector width 2 needs even column counts, even leading dimensions and 16-byte bases
+  bool v2 = (a.ncols % 2 == 0) && (a.ldy % 2 == 0) && aligned16(a.Yin);
+  if (a.X) v2 = v2 && (a.ldx % 2 == 0) && aligned16(a.X);
+  if (a.Z) v2 = v2 && (a.ldz % 2 == 0) && aligned16(a.Z);
+  if (a.out) v2 = v2 && (a.ldo % 2 == 0) && aligned16(a.out);
+  if (a.ncols <= 32) v2 = false;  // one 32-lane chunk already covers the row
+  if (v2) {
+    ARB_TRY(launch_spmm<2>(ctx, P, grid, smem));
+  } else {
+    ARB_TRY(launch_spmm<1>(ctx, P, grid, smem));
+  }
+  if (a.colred) {
+    reduce_partials_kernel<<<(a.ncols + 127) / 128, 128, 0, ctx->stream>>>(P.red_part, grid, a.ncols,
+                                                                           a.colred);
+    ARB_LAUNCHED(ctx);
+  }
+  return ARB_OK;
+}
+
+arb_status gershgorin(arb_ctx ctx, arb_mat mat, double* lo, double* hi) {
+  if (mat->gersh_valid) {
+    *lo = mat->gersh_lo;
+    *hi = mat->gersh_hi;
+    return ARB_OK;
+  }
+  const int grid = std::max(1, std::min(ctx->num_sms * 4, static_cast<int>((mat->n + 255) / 256)));
+  double* part;
+  ARB_TRY(ws<double>(ctx, WS_VEC2, 2 * static_cast<size_t>(grid) + 2, &part));
+  gershgorin_kernel<<<grid, 256, 0, ctx->stream>>>(mat->n, mat->rowptr, mat->col, mat->val, part);
+  ARB_LAUNCHED(ctx);
+  gershgorin_final_kernel<<<1, 32, 0, ctx->stream>>>(part, grid, part + 2 * grid);
+  ARB_LAUNCHED(ctx);
+  double h[2];
+  ARB_TRY(d2h_sync(ctx, h, part + 2 * grid, sizeof(h)));
+  mat->gersh_lo = h[0];
+  mat->gersh_hi = h[1];
+  mat->gersh_valid = true;
+  *lo = h[0];
+  *hi = h[1];
+  return ARB_OK;
+}
+
+arb_status col_sumsq(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
+                     double* out) {
+  if (ncols <= 0) return ARB_OK;
+  const int64_t target = static_cast<int64_t>(ctx->num_sms) * 4;
+  int64_t rows = std::max<int64_t>(1, (n + target - 1) / target);
+  const int grid = static_cast<int>((n + rows - 1) / rows);
+  double* part;
+  ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * ncols, &part));
+  col_sumsq_kernel<<<grid, 256, 0, ctx->stream>>>(n, X, ldx, ncols, rows, part);
+  ARB_LAUNCHED(ctx);
+  reduce_partials_kernel<<<(ncols + 127) / 128, 128, 0, ctx->stream>>>(part, grid, ncols, out);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+}  // namespace arb

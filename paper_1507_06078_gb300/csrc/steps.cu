@@ -1,0 +1,295 @@
+// Composite steps of the subspace update and of the augmented Rayleigh-Ritz projection,
+// built from the kernels of spmm.cu, dense.cu and jacobi.cu.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "arb_internal.h"
+
+namespace arb {
+namespace {
+
+struct ChebCoef {
+  double c[64];
+};
+
+// Per-step per-column multipliers of the fused Clenshaw step (see filter_apply).
+//   table[(3 t + 0) * ncols + c] = sy, [(3 t + 1) ...] = sx, [(3 t + 2) ...] = sz
+__global__ void filter_table_kernel(int d, ChebCoef cc, const double* __restrict__ xs, int ncols,
+                                    double* __restrict__ table) {
+  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int nsteps = d;
+  if (idx >= static_cast<int64_t>(nsteps) * ncols) return;
+  const int t = static_cast<int>(idx / ncols), c = static_cast<int>(idx % ncols);
+  const double s = xs ? xs[c] : 1.0;
+  const int j = d - 1 - t;  // step t produces b_j (b_0 at the last step means Y)
+  double sy, sx, sz;
+  if (d == 1) {
+    sy = cc.c[1] * s;
+    sx = cc.c[0] * s;
+    sz = 0.0;
+  } else {
+    sy = (t == 0) ? 2.0 * cc.c[d] * s : (t == d - 1 ? 1.0 : 2.0);
+    sx = cc.c[j] * s;
+    sz = (j + 2 == d) ? -cc.c[d] * s : -1.0;
+  }
+  table[(3 * static_cast<int64_t>(t) + 0) * ncols + c] = sy;
+  table[(3 * static_cast<int64_t>(t) + 1) * ncols + c] = sx;
+  table[(3 * static_cast<int64_t>(t) + 2) * ncols + c] = sz;
+}
+
+inline double orth_tau(int m) { return 32.0 * std::max(m, 1) * 2.220446049250313e-16; }
+
+}  // namespace
+
+FilterPlan make_filter_plan(double op_scale, double op_shift, double a, double b, int32_t degree,
+                            const double* coef) {
+  // Algorithm 8 calls poly(B - aI, X, 0, b - a, Gamma_d); Algorithm 7 with interval
+  // [0, b - a] has c0 = (0 + (b-a))/(0 - (b-a)) = -1 and c1 = 2/(b - a), so the recurrence
+  // variable is S = c1 (B - aI) - I = alpha A + beta I with B = op_scale A + op_shift I.
+  FilterPlan p;
+  const double c1 = 2.0 / (b - a);
+  p.alpha = c1 * op_scale;
+  p.beta = c1 * (op_shift - a) - 1.0;
+  p.degree = degree;
+  for (int i = 0; i <= degree && i < 64; ++i) p.coef[i] = coef[i];
+  return p;
+}
+
+// Clenshaw's recurrence for Y = sum_k c_k T_k(S) X~ (X~ = X diag(xs)):
+//   b_{d-1} = c_{d-1} X~ + 2 S (c_d X~)
+//   b_j     = c_j X~ + 2 S b_{j+1} - b_{j+2}      (j = d-2 .. 1; b_d = c_d X~)
+//   Y       = c_0 X~ + S b_1 - b_2
+// Each line is one fused pass of spmm_fused (one product with A); b_j overwrites b_{j+2}
+// in place, so two work blocks suffice.  The same polynomial psi_d of Section 5 is
+// evaluated as Algorithm 7 does in the monomial basis, but with bounded coefficients.
+arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const double* X,
+                        int64_t ldx, int32_t ncols, const double* xscale, double* W1,
+                        double* W2, int64_t ldw, double* Y, int64_t ldy, double* colss,
+                        double** result) {
+  const int d = plan.degree;
+  if (d < 1 || d > 60) return set_error(ctx, ARB_INVALID_ARG, "filter: degree must be in [1, 60]");
+  if (ncols <= 0) return ARB_OK;
+  double* table;
+  ARB_TRY(ws<double>(ctx, WS_COEF, static_cast<size_t>(3) * d * ncols, &table));
+  ChebCoef cc;
+  for (int i = 0; i < 64; ++i) cc.c[i] = (i <= d) ? plan.coef[i] : 0.0;
+  {
+    const int64_t cnt = static_cast<int64_t>(d) * ncols;
+    filter_table_kernel<<<static_cast<int>((cnt + 255) / 256), 256, 0, ctx->stream>>>(d, cc, xscale, ncols,
+                                                                                    table);
+    ARB_LAUNCHED(ctx);
+  }
+  auto sy_of = [&](int t) { return table + (3 * static_cast<int64_t>(t) + 0) * ncols; };
+  auto sx_of = [&](int t) { return table + (3 * static_cast<int64_t>(t) + 1) * ncols; };
+  auto sz_of = [&](int t) { return table + (3 * static_cast<int64_t>(t) + 2) * ncols; };
+
+  SpmmArgs a;
+  a.A = mat;
+  a.ncols = ncols;
+  a.alpha = plan.alpha;
+  a.beta = plan.beta;
+  if (d == 1) {
+    a.Yin = X;
+    a.ldy = ldx;
+    a.sy = sy_of(0);
+    if (cc.c[0] != 0.0) {
+      a.X = X;
+      a.ldx = ldx;
+      a.sx = sx_of(0);
+    }
+    double* out = Y ? Y : W1;
+    a.out = out;
+    a.ldo = Y ? ldy : ldw;
+    a.colred = colss;
+    ARB_TRY(spmm_fused(ctx, a));
+    if (result) *result = out;
+    return ARB_OK;
+  }
+  // step 0: b_{d-1} -> W1
+  a.Yin = X;
+  a.ldy = ldx;
+  a.sy = sy_of(0);
+  if (cc.c[d - 1] != 0.0) {
+    a.X = X;
+    a.ldx = ldx;
+    a.sx = sx_of(0);
+  }
+  a.out = W1;
+  a.ldo = ldw;
+  ARB_TRY(spmm_fused(ctx, a));
+  double* cur = W1;        // holds b_{j+1}
+  double* prev = nullptr;  // holds b_{j+2}; nullptr means b_d = c_d X~ (read from X)
+  for (int t = 1; t < d; ++t) {
+    const int j = d - 1 - t;
+    const bool last = (t == d - 1);
+    SpmmArgs s;
+    s.A = mat;
+    s.ncols = ncols;
+    s.alpha = plan.alpha;
+    s.beta = plan.beta;
+    s.Yin = cur;
+    s.ldy = ldw;
+    s.sy = sy_of(t);
+    if (cc.c[j] != 0.0) {
+      s.X = X;
+      s.ldx = ldx;
+      s.sx = sx_of(t);
+    }
+    if (prev) {
+      s.Z = prev;
+      s.ldz = ldw;
+    } else if (cc.c[d] != 0.0) {
+      s.Z = X;
+      s.ldz = ldx;
+    }
+    if (s.Z) s.sz = sz_of(t);
+    double* out;
+    int64_t ldo;
+    if (last && Y) {
+      out = Y;
+      ldo = ldy;
+    } else {
+      out = prev ? prev : W2;
+      ldo = ldw;
+    }
+    s.out = out;
+    s.ldo = ldo;
+    if (last) s.colred = colss;
+    ARB_TRY(spmm_fused(ctx, s));
+    prev = cur;
+    cur = out;
+  }
+  if (result) *result = cur;
+  return ARB_OK;
+}
+
+arb_status project_out(arb_ctx ctx, int64_t n, const double* Q, int64_t ldq, int32_t nq, double* X,
+                       int64_t ldx, int32_t ncols) {
+  if (nq <= 0 || ncols <= 0) return ARB_OK;
+  double* W;
+  ARB_TRY(ws<double>(ctx, WS_SMALL3, static_cast<size_t>(nq) * ncols, &W));
+  ARB_TRY(gram(ctx, n, Q, ldq, nq, X, ldx, ncols, W, ncols));
+  ARB_TRY(gemm_tall(ctx, n, Q, ldq, nq, W, ncols, ncols, -1.0, 1.0, X, ldx));
+  return ARB_OK;
+}
+
+// One eigen-truncated Gram pass (SVQB, Stathopoulos & Wu 2002): scale the columns of Z to
+// unit norm, G = D Z^T Z D = W Theta W^T, keep theta_j > tau theta_0, and map
+// Z -> Z D W_r Theta_r^{-1/2}.
+static arb_status svqb_pass(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz, int32_t m,
+                            double* out, int64_t ldo, int32_t* rank) {
+  double *G, *Gh, *W, *d, *theta;
+  int32_t* r_dev;
+  const size_t mm = static_cast<size_t>(m) * m;
+  ARB_TRY(ws<double>(ctx, WS_SMALL0, mm, &G));
+  ARB_TRY(ws<double>(ctx, WS_SMALL1, mm, &Gh));
+  ARB_TRY(ws<double>(ctx, WS_SMALL2, mm, &W));
+  ARB_TRY(ws<double>(ctx, WS_VEC0, m, &d));
+  ARB_TRY(ws<double>(ctx, WS_VEC1, m, &theta));
+  ARB_TRY(ws<int32_t>(ctx, WS_INT0, 4, &r_dev));
+  ARB_TRY(gram(ctx, n, Z, ldz, m, Z, ldz, m, G, m));
+  ARB_TRY(svqb_prep(ctx, m, G, m, Gh, d));
+  ARB_TRY(syevj(ctx, m, Gh, m, theta, W, m, nullptr));
+  ARB_TRY(svqb_finish(ctx, m, theta, W, m, d, orth_tau(m), Gh, r_dev));
+  int32_t r = 0;
+  ARB_TRY(d2h_sync(ctx, &r, r_dev, sizeof(int32_t)));
+  *rank = r;
+  if (r > 0) ARB_TRY(gemm_tall(ctx, n, Z, ldz, m, Gh, m, r, 1.0, 0.0, out, ldo));
+  return ARB_OK;
+}
+
+arb_status orth(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz, int32_t m, double* U,
+                int64_t ldu, double* tmp, int64_t ldt, int32_t* rank) {
+  *rank = 0;
+  if (m <= 0) return ARB_OK;
+  int32_t r1 = 0, r2 = 0;
+  ARB_TRY(svqb_pass(ctx, n, Z, ldz, m, tmp, ldt, &r1));
+  if (r1 == 0) return ARB_OK;
+  ARB_TRY(svqb_pass(ctx, n, tmp, ldt, r1, U, ldu, &r2));
+  *rank = r2;
+  return ARB_OK;
+}
+
+arb_status rcond_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
+                      const double* xs, double* rc) {
+  double *G, *W, *theta, *rc_dev;
+  const size_t mm = static_cast<size_t>(ncols) * ncols;
+  ARB_TRY(ws<double>(ctx, WS_SMALL0, mm, &G));
+  ARB_TRY(ws<double>(ctx, WS_SMALL2, mm, &W));
+  ARB_TRY(ws<double>(ctx, WS_VEC1, ncols + 2, &theta));
+  rc_dev = theta + ncols;
+  ARB_TRY(gram(ctx, n, X, ldx, ncols, X, ldx, ncols, G, ncols));
+  if (xs) ARB_TRY(scale_sym(ctx, ncols, G, ncols, xs));
+  ARB_TRY(syevj(ctx, ncols, G, ncols, theta, W, ncols, nullptr));
+  ARB_TRY(rcond_from_eig(ctx, ncols, G, ncols, theta, W, ncols, rc_dev));
+  ARB_TRY(d2h_sync(ctx, rc, rc_dev, sizeof(double)));
+  return ARB_OK;
+}
+
+// span[X, BX, ..., B^q X] as an orthonormal block Krylov basis: U_0 = orth(X); for
+// i = 1..q, W = B U_{i-1} (kept as the block AU_{i-1}), W is projected against Q_c and
+// U_0..U_{i-1} twice (block classical Gram-Schmidt with reorthogonalisation), and
+// U_i = orth(W).  In exact arithmetic span{U_0..U_q} = span{X, BX, ..., B^q X} of
+// Algorithm 5; building it block by block keeps the small residual directions that
+// columns of [X, BX, ...] carry at full relative accuracy.  Then AU_q = B U_q and
+// H = U^T (B U) (Algorithm 1) is diagonalised.
+arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, int64_t n,
+                             double* X, int64_t ldx, int32_t w, const double* Qc, int64_t ldqc,
+                             int32_t nl, int32_t q, const ArrWork& wk, int32_t* m_out,
+                             double* theta, double* V) {
+  *m_out = 0;
+  if (nl > 0) ARB_TRY(project_out(ctx, n, Qc, ldqc, nl, X, ldx, w));
+  int32_t r0 = 0;
+  ARB_TRY(orth(ctx, n, X, ldx, w, wk.U, wk.ldu, wk.T, wk.ldt, &r0));
+  if (r0 == 0) return set_error(ctx, ARB_BREAKDOWN, "ARR: iterate has no numerical rank");
+  std::vector<int32_t> off{0}, rk{r0};
+  int32_t m = r0;
+  for (int i = 1; i <= q; ++i) {
+    const int32_t o = off.back(), r = rk.back();
+    SpmmArgs s;
+    s.A = mat;
+    s.ncols = r;
+    s.Yin = wk.U + o;
+    s.ldy = wk.ldu;
+    s.alpha = op_scale;
+    s.beta = op_shift;
+    s.out = wk.AU + o;
+    s.ldo = wk.ldau;
+    ARB_TRY(spmm_fused(ctx, s));
+    ARB_TRY(copy_block(ctx, n, wk.AU + o, wk.ldau, r, wk.T2, wk.ldt2));
+    for (int pass = 0; pass < 2; ++pass) {
+      if (nl > 0) ARB_TRY(project_out(ctx, n, Qc, ldqc, nl, wk.T2, wk.ldt2, r));
+      ARB_TRY(project_out(ctx, n, wk.U, wk.ldu, m, wk.T2, wk.ldt2, r));
+    }
+    int32_t ri = 0;
+    ARB_TRY(orth(ctx, n, wk.T2, wk.ldt2, r, wk.U + m, wk.ldu, wk.T, wk.ldt, &ri));
+    if (ri == 0) break;  // the Krylov space is exhausted
+    off.push_back(m);
+    rk.push_back(ri);
+    m += ri;
+  }
+  {
+    // B U for the last block (the earlier blocks were formed during the augmentation)
+    const int32_t o = off.back(), r = rk.back();
+    SpmmArgs s;
+    s.A = mat;
+    s.ncols = r;
+    s.Yin = wk.U + o;
+    s.ldy = wk.ldu;
+    s.alpha = op_scale;
+    s.beta = op_shift;
+    s.out = wk.AU + o;
+    s.ldo = wk.ldau;
+    ARB_TRY(spmm_fused(ctx, s));
+  }
+  double* H;
+  ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(m) * m, &H));
+  ARB_TRY(gram(ctx, n, wk.U, wk.ldu, m, wk.AU, wk.ldau, m, H, m));
+  ARB_TRY(symmetrize(ctx, m, H, m));
+  ARB_TRY(syevj(ctx, m, H, m, theta, V, m, nullptr));
+  *m_out = m;
+  return ARB_OK;
+}
+
+}  // namespace arb

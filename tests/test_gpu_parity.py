@@ -1,0 +1,317 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (FP64 throughout): a fused step reorders the sums of the oracle only within a
+row (at most 7 nonzeros here) and across Clenshaw steps, so filter outputs agree to a few
+ulps of the largest intermediate; 1e-12 relative to max|Y| is the bar.  Gram products
+reduce over n rows in a different order: 1e-13 relative to ||X|| ||Y||.  Eigenvalues of
+the dense Jacobi solver: 1e-13 relative to ||H||.  End-to-end eigenvalues: 1e-10 relative
+to max(1, |lambda|), the target the method is run to; residuals <= tol.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import arrabit_oracle as O
+from paper_1507_06078_gb300 import inputs as I
+
+from conftest import laplacian_2d_eigs, laplacian_3d_eigs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def arb():
+    from paper_1507_06078_gb300 import arrabit, build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return arrabit
+
+
+@pytest.fixture(scope="module")
+def ctx(arb):
+    c = arb.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def scipy_of(A):
+    return O.csr_to_scipy(A.n, A.rowptr, A.col, A.val)
+
+
+# ------------------------------------------------------------------ SpMM and filter
+@pytest.mark.parametrize("ncols", [1, 2, 7, 30, 33, 64, 65, 130])
+def test_spmm_matches_oracle(arb, ctx, ncols):
+    A = I.laplacian_2d(37)  # n = 1369: not a multiple of any tile
+    mat = arb.Matrix.from_csr(ctx, A)
+    X = I.gaussian_block(A.n, ncols, 11)
+    B = -1.0 * scipy_of(A) + 8.0 * sp.identity(A.n)
+    Y = host(arb.arb_spmm(ctx, mat, -1.0, 8.0, dev(X)))
+    ref = B @ X
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_spmm_strided_views(arb, ctx):
+    A = I.laplacian_3d(9)
+    mat = arb.Matrix.from_csr(ctx, A)
+    big = dev(I.gaussian_block(A.n, 50, 3))
+    X = big[:, 3:40]  # odd offset, leading dimension 50
+    Yb = torch.zeros((A.n, 41), dtype=torch.float64, device="cuda")
+    arb.arb_spmm(ctx, mat, 1.0, 0.0, X, Yb[:, 1:38])
+    ref = scipy_of(A) @ host(big)[:, 3:40]
+    np.testing.assert_allclose(host(Yb)[:, 1:38], ref, atol=1e-13 * np.abs(ref).max())
+    assert np.all(host(Yb)[:, 0] == 0) and np.all(host(Yb)[:, 38:] == 0)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 10, 20])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_filter_matches_oracle(arb, ctx, d, kind):
+    A = I.laplacian_2d(40)
+    mat = arb.Matrix.from_csr(ctx, A)
+    B = 8.0 * sp.identity(A.n, format="csr") - scipy_of(A)
+    ncols = 30
+    X = I.gaussian_block(A.n, ncols, 5)
+    xs = np.linspace(0.5, 2.0, ncols)
+    a, b = 0.0, 3.7
+    coef = O.interpolant_cheb_coeffs(d) if kind == 0 else O.chebyshev_T_coeffs(d)
+    colss = torch.zeros(ncols, dtype=torch.float64, device="cuda")
+    Y = host(arb.arb_filter(ctx, mat, -1.0, 8.0, a, b, arb.arb_filter_coefficients(kind, d), dev(X),
+                            xscale=dev(xs), colss=colss))
+    Bs = B - a * sp.identity(A.n, format="csr")
+    ref = O.poly_clenshaw(Bs, X * xs[None, :], 0.0, b - a, coef)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(host(colss), np.sum(ref * ref, axis=0), rtol=1e-11)
+    if d <= 10:  # Algorithm 7 as printed (monomial Horner) agrees at moderate degree
+        ref7 = O.poly_alg7(Bs, X * xs[None, :], 0.0, b - a, O.cheb_to_monomial(coef))
+        np.testing.assert_allclose(Y, ref7, rtol=0, atol=1e-9 * scale)
+
+
+def test_filter_on_closed_form_eigenvectors(arb, ctx):
+    # spectral mapping (eq. poly-A): rho(A) v = rho(lambda) v for the sin-product eigenvectors
+    m = 20
+    A = I.laplacian_3d(m)
+    mat = arb.Matrix.from_csr(ctx, A)
+    x = np.arange(1, m + 1)
+    modes = [(1, 1, 1), (2, 1, 1), (3, 2, 1), (5, 5, 5), (20, 1, 7)]
+    cols, lams = [], []
+    for (i, j, l) in modes:
+        v = np.einsum("a,b,c->cba", np.sin(np.pi * i * x / (m + 1)), np.sin(np.pi * j * x / (m + 1)),
+                      np.sin(np.pi * l * x / (m + 1))).ravel()
+        cols.append(v / np.linalg.norm(v))
+        lams.append(6 - 2 * np.cos(np.pi * i / (m + 1)) - 2 * np.cos(np.pi * j / (m + 1))
+                    - 2 * np.cos(np.pi * l / (m + 1)))
+    V = np.stack(cols, axis=1)
+    np.testing.assert_allclose(scipy_of(A) @ V, V * np.array(lams)[None, :], atol=1e-12)
+    coef = O.interpolant_cheb_coeffs(20)
+    a, b = 0.0, 11.5
+    Y = host(arb.arb_filter(ctx, mat, -1.0, 12.0, a, b, coef, dev(V)))
+    rho = O.rho_d(coef, 12.0 - np.array(lams), a, b)
+    np.testing.assert_allclose(Y, V * rho[None, :], atol=1e-12 * np.abs(rho).max())
+
+
+# ------------------------------------------------------------------ dense kernels
+@pytest.mark.parametrize("n,na,nb", [(1, 1, 1), (17, 3, 5), (1000, 30, 30), (4099, 65, 130), (20000, 64, 64)])
+def test_gram_matches_numpy(arb, ctx, n, na, nb):
+    X = I.gaussian_block(n, na, 1)
+    Y = I.gaussian_block(n, nb, 2)
+    C = host(arb.arb_gram(ctx, dev(X), dev(Y)))
+    ref = X.T @ Y
+    np.testing.assert_allclose(C, ref, atol=1e-13 * np.sqrt(n) * 4)
+    G = host(arb.arb_gram(ctx, dev(X), dev(X)))  # symmetric path
+    np.testing.assert_allclose(G, X.T @ X, atol=1e-13 * np.sqrt(n) * 4)
+    assert np.array_equal(G, G.T)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 10, 31, 64, 65, 200])
+def test_syevj_matches_oracle_jacobi(arb, ctx, m):
+    rng = np.random.default_rng(m)
+    H = rng.standard_normal((m, m))
+    H = 0.5 * (H + H.T)
+    w, V, sweeps = arb.arb_syevj(ctx, dev(H))
+    w, V = host(w), host(V)
+    if m <= 65:
+        wo, _ = O.jacobi_eigh(H)
+        np.testing.assert_allclose(w, wo, atol=1e-13 * np.linalg.norm(H))
+    np.testing.assert_allclose(w, np.sort(np.linalg.eigvalsh(H))[::-1], atol=1e-13 * np.linalg.norm(H))
+    np.testing.assert_allclose(V.T @ V, np.eye(m), atol=1e-13 * m)
+    np.testing.assert_allclose(H @ V, V * w[None, :], atol=1e-12 * np.linalg.norm(H))
+    assert sweeps < 60
+
+
+def test_syevj_clusters_and_zero(arb, ctx):
+    w0 = np.array([5.0, 5.0, 5.0, 2.0, 2.0, 1e-9, 0.0, -3.0, -3.0, 7.5, 7.5])
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((11, 11)))
+    H = Q @ np.diag(w0) @ Q.T
+    w, V, _ = arb.arb_syevj(ctx, dev(H))
+    np.testing.assert_allclose(host(w), np.sort(w0)[::-1], atol=1e-13 * 15)
+    w, V, s = arb.arb_syevj(ctx, dev(np.zeros((4, 4))))
+    assert np.all(host(w) == 0) and s == 0
+
+
+def test_rcond_matches_oracle(arb, ctx):
+    rng = np.random.default_rng(9)
+    X = rng.standard_normal((3000, 12)) @ np.diag(np.logspace(0, -3, 12))
+    xs = np.linspace(1.0, 3.0, 12)
+    rc = arb.arb_rcond_gram(ctx, dev(X), xscale=dev(xs))
+    Xs = X * xs[None, :]
+    ref = O.rcond_spd(Xs.T @ Xs)
+    assert abs(rc - ref) <= 1e-8 * ref
+    Xd = np.hstack([X, X[:, :1]])
+    assert arb.arb_rcond_gram(ctx, dev(Xd)) < 1e-14
+
+
+def test_orth_spans_and_rank(arb, ctx):
+    rng = np.random.default_rng(4)
+    Z = rng.standard_normal((5000, 20))
+    Z[:, 15:] = Z[:, :5] @ rng.standard_normal((5, 5))  # rank 15
+    U = host(arb.arb_orth(ctx, dev(Z)))
+    assert U.shape[1] == 15
+    np.testing.assert_allclose(U.T @ U, np.eye(15), atol=1e-13)
+    Uo = O.orth(Z)
+    assert Uo.shape[1] == 15
+    np.testing.assert_allclose(U @ (U.T @ Uo), Uo, atol=1e-11)
+
+
+def test_rayleigh_ritz_matches_oracle(arb, ctx):
+    A = I.laplacian_2d(30)
+    mat = arb.Matrix.from_csr(ctx, A)
+    B = 8.0 * sp.identity(A.n, format="csr") - scipy_of(A)
+    Z = I.gaussian_block(A.n, 24, 3)
+    Y, w = arb.arb_rayleigh_ritz(ctx, mat, -1.0, 8.0, dev(Z))
+    Yo, wo = O.rayleigh_ritz(B, Z)
+    np.testing.assert_allclose(host(w), wo, atol=1e-12 * 8)
+    Y = host(Y)
+    np.testing.assert_allclose(Y.T @ Y, np.eye(24), atol=1e-12)
+    P, Po = Y @ Y.T, Yo @ Yo.T
+    assert np.abs(P - Po).max() < 1e-10
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_arr_matches_oracle(arb, ctx, q):
+    A = I.laplacian_2d(32)
+    mat = arb.Matrix.from_csr(ctx, A)
+    B = 8.0 * sp.identity(A.n, format="csr") - scipy_of(A)
+    X = I.gaussian_block(A.n, 16, 8)
+    # a few oracle filter steps so X is the kind of block ARR sees
+    coef = O.interpolant_cheb_coeffs(6)
+    for _ in range(3):
+        X = O.normalize_columns(O.poly_clenshaw(B, X, 0.0, 4.0, coef))
+    Y, w, rank = arb.arb_arr(ctx, mat, -1.0, 8.0, dev(X), q)
+    Yo, wo = O.arr(B, X, q)
+    assert rank == (q + 1) * 16
+    np.testing.assert_allclose(host(w), wo, atol=1e-11 * 8)
+    Y = host(Y)
+    res = O.residual_norms(B, Y, host(w), host(w))
+    reso = O.residual_norms(B, Yo, wo, wo)
+    np.testing.assert_allclose(res, reso, atol=1e-9)
+
+
+# ------------------------------------------------------------------ whole method
+def _solve(arb, ctx, A, k, p, q, d, tol, X0, which=1, **kw):
+    mat = arb.Matrix.from_csr(ctx, A)
+    o = arb.arb_options_default(k)
+    o.p, o.q, o.degree = p, q, d
+    for key, v in kw.items():
+        setattr(o, key, v)
+    return arb.arb_solve(ctx, mat, k, which, tol, o, x0=X0, evecs="host")
+
+
+def _projector_distance(Q1, Q2):
+    return np.abs(Q1 @ Q1.T - Q2 @ Q2.T).max()
+
+
+def test_solve_2d64_against_oracle_and_closed_form(arb, ctx):
+    W = I.workload_2d64()
+    X0 = I.gaussian_block(W.A.n, W.p, W.seed)
+    r = _solve(arb, ctx, W.A, W.k, W.p, W.q, W.degree, W.tol, X0)
+    assert r.status == arb.ARB_OK, r.info
+    ref = O.arrabit_mpm(scipy_of(W.A), W.k, X0, which="smallest", tol=W.tol, q=W.q, degree=W.degree)
+    lam = laplacian_2d_eigs(64)[:W.k]
+    denom = np.maximum(1.0, np.abs(lam))
+    assert np.max(np.abs(r.evals - ref.evals) / denom) <= 1e-10
+    assert np.max(np.abs(r.evals - lam) / denom) <= 1e-10
+    Q = r.evecs
+    A = scipy_of(W.A)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(W.k), atol=1e-12)
+    R = A @ Q - Q * r.evals[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= W.tol * 8.0
+    # the first 20 eigenvalues end on a complete cluster: compare spectral projectors
+    assert _projector_distance(Q, ref.evecs) < 1e-8
+    assert r.info["maxres"] <= W.tol
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_solve_bruteforce_random_sparse(arb, ctx, which):
+    from paper_1507_06078_gb300.inputs import CSR
+    n, k, p = 400, 8, 12
+    rng = np.random.default_rng(77)
+    M = sp.random(n, n, density=0.02, random_state=rng, format="csr")
+    M = (M + M.T + sp.diags(rng.uniform(0, 3, n))).tocsr()
+    M.sort_indices()
+    A = CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+    X0 = I.gaussian_block(n, p, 31)
+    r = _solve(arb, ctx, A, k, p, 1, 10, 1e-10, X0, which=which)
+    wref = np.linalg.eigvalsh(M.toarray())
+    want = wref[:k] if which == 1 else wref[::-1][:k]
+    np.testing.assert_allclose(r.evals, want, atol=1e-9 * np.abs(wref).max())
+
+
+def test_solve_lockstep_fixed_schedule(arb, ctx):
+    A = I.laplacian_2d(16)
+    X0 = I.gaussian_block(A.n, 12, 10)
+    r = _solve(arb, ctx, A, 10, 12, 1, 6, 1e-9, X0, inner_fixed=4, maxit=20)
+    ref = O.arrabit_mpm(scipy_of(A), 10, X0, which="smallest", tol=1e-9, q=1, degree=6, inner_fixed=4,
+                        maxit=20)
+    assert r.info["n_filters"] == 4 * r.info["outer_iters"]
+    np.testing.assert_allclose(r.evals, ref.evals, atol=1e-9)
+    np.testing.assert_allclose(r.evals, laplacian_2d_eigs(16)[:10], atol=1e-9)
+
+
+def test_solve_3d_scaled(arb, ctx):
+    m, k, p = 24, 30, 36
+    A = I.laplacian_3d(m)
+    X0 = I.gaussian_block(A.n, p, 99)
+    r = _solve(arb, ctx, A, k, p, 2, 12, 1e-8, X0)
+    assert r.status == arb.ARB_OK, r.info
+    lam = laplacian_3d_eigs(m)[:k]
+    np.testing.assert_allclose(r.evals, lam, atol=1e-9)
+
+
+def test_solve_rejects_bad_arguments(arb, ctx):
+    A = I.laplacian_2d(8)
+    X0 = I.gaussian_block(A.n, 12, 1)
+    with pytest.raises(arb.ArbError) as e:
+        _solve(arb, ctx, A, 20, 12, 1, 5, 1e-8, X0)  # k > p
+    assert e.value.status == arb.ARB_INVALID_ARG
+    with pytest.raises(arb.ArbError):
+        _solve(arb, ctx, A, 10, 12, 5, 5, 1e-8, X0)  # (q+1) p >= n
+    with pytest.raises(arb.ArbError):
+        _solve(arb, ctx, A, 10, 12, 1, 0, 1e-8, X0)  # degree 0
+    with pytest.raises(arb.ArbError):
+        arb.Matrix(ctx, 4, np.array([0, 1, 2, 3, 5]), np.array([0, 1, 2, 3, 9]), np.ones(5))
+
+
+def test_device_start_block_matches_host_generator(arb, ctx):
+    # x0 = NULL draws X0 on the device from the same Philox stream as the input generator
+    A = I.laplacian_2d(20)
+    k, p = 8, 10
+    o = arb.arb_options_default(k)
+    o.p, o.q, o.degree, o.seed = p, 1, 8, 4242
+    mat = arb.Matrix.from_csr(ctx, A)
+    r_dev = arb.arb_solve(ctx, mat, k, 1, 1e-10, o, x0=None)
+    r_host = arb.arb_solve(ctx, mat, k, 1, 1e-10, o, x0=I.gaussian_block(A.n, p, 4242))
+    np.testing.assert_allclose(r_dev.evals, r_host.evals, atol=1e-12)
+    assert r_dev.info["n_filters"] == r_host.info["n_filters"]

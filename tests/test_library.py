@@ -1,0 +1,52 @@
+"""Host-side checks of the C ABI library (no GPU needed): it builds for sm_103a, loads, and
+exports every function that include/arrabit.h declares."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1507_06078_gb300 import arrabit as arb
+from paper_1507_06078_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return arb.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = arb.header_functions()
+    assert "arb_solve" in names and "arb_filter" in names and len(names) >= 18
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding declares a prototype for each of them
+    assert set(names) <= set(arb._PROTOS)
+
+
+def test_status_strings_and_defaults(lib):
+    assert lib.arb_status_string(0) == b"ok"
+    assert lib.arb_status_string(-4) == b"iterate lost numerical rank"
+    o = arb.arb_options_default(20)
+    assert (o.p, o.q, o.degree, o.maxit, o.maxit1, o.maxit2) == (22, 1, 3, 30, 10, 5)
+    assert np.isnan(o.shift_sigma)
+    assert ctypes.sizeof(arb.arb_options) == 4 * 10 + 8 * 3
+    assert ctypes.sizeof(arb.arb_info) == 8 * 8 + 8 + 4 * 6
+
+
+@pytest.mark.parametrize("d", [1, 3, 10, 15, 20])
+def test_host_filter_coefficients_match_oracle(lib, d):
+    # the library's host-side coefficients (cosine-sum formula) against the oracle's
+    # collocation solve: two independent derivations of the Section 5 interpolant
+    from oracle import arrabit_oracle as O
+    c = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, d)
+    np.testing.assert_allclose(c, O.interpolant_cheb_coeffs(d), atol=2e-15)
+    e = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBYSHEV, d)
+    np.testing.assert_array_equal(e, O.chebyshev_T_coeffs(d))
+
+
+def test_bad_coefficient_requests_rejected(lib):
+    buf = np.zeros(70)
+    assert lib.arb_filter_coefficients(0, 0, buf.ctypes.data) == arb.ARB_INVALID_ARG
+    assert lib.arb_filter_coefficients(0, 61, buf.ctypes.data) == arb.ARB_INVALID_ARG
+    assert lib.arb_filter_coefficients(7, 3, buf.ctypes.data) == arb.ARB_INVALID_ARG
