@@ -142,6 +142,14 @@ arb_status arb_solve(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doubl
                      double* evals, double* evecs, int64_t ldq, int evecs_on_device,
                      arb_info* info);
 
+/* The i.i.d. Gaussian start block of Algorithm 8 ("initialize an i.i.d. Gaussian random
+ * matrix X"): X (device, n x ncols row-major, ldx) gets element (i, j) = sample i*ncols + j
+ * of the stream `seed` - Philox4x32-10 (Salmon et al., SC'11) on counter (e/2, 0, 0, 0)
+ * with key (seed), two 53-bit uniforms, Box-Muller (cos for even e, sin for odd e).
+ * arb_solve draws its start block this way when x0 is NULL. */
+arb_status arb_gaussian_block(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, double* X,
+                              int64_t ldx);
+
 /* ---------------------------------------------------------------- hot-path steps
  * All pointers below are DEVICE pointers.  B denotes op_scale * A + op_shift * I. */
 

@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import re
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -69,6 +70,7 @@ _PROTOS = {
     "arb_matrix_gershgorin": (_i32, [_vp, _vp, C.POINTER(_dbl), C.POINTER(_dbl)]),
     "arb_solve": (_i32, [_vp, _vp, _i32, _i32, _dbl, C.POINTER(arb_options), _vp, C.c_int, _vp, _vp, _i64,
                          C.c_int, C.POINTER(arb_info)]),
+    "arb_gaussian_block": (_i32, [_vp, _i64, _i32, C.c_uint64, _vp, _i64]),
     "arb_filter": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _dbl, _i32, _vp, _vp, _i64, _i32, _vp, _vp, _i64, _vp]),
     "arb_filter_coefficients": (_i32, [_i32, _i32, _vp]),
     "arb_spmm": (_i32, [_vp, _vp, _dbl, _dbl, _vp, _i64, _i32, _vp, _i64]),
@@ -139,9 +141,12 @@ class Context:
         if st != ARB_OK:
             raise ArbError(st, "arb_ctx_create failed")
         self.handle = h
+        self._mats = weakref.WeakSet()
 
     def close(self):
         if self.handle:
+            for m in list(self._mats):
+                m.close()
             load().arb_ctx_destroy(self.handle)
             self.handle = None
 
@@ -168,6 +173,7 @@ class Matrix:
                                        val.ctypes.data, 0, C.byref(h))
         _check(ctx, st, "arb_matrix_create_csr")
         self.ctx, self.handle, self.n, self.nnz = ctx, h, n, col.shape[0]
+        ctx._mats.add(self)
 
     @classmethod
     def from_csr(cls, ctx: Context, A) -> "Matrix":
@@ -248,6 +254,17 @@ def arb_solve(ctx: Context, mat: Matrix, k: int, which: int, tol: float, opts: a
     if out is not None:
         vecs = out.T
     return SolveResult(st, ev, vecs, info.as_dict())
+
+
+def arb_gaussian_block(ctx: Context, n: int, ncols: int, seed: int, X=None):
+    """Device start block from the library's Philox stream (same numbering as the input
+    generator)."""
+    import torch
+    if X is None:
+        X = torch.empty((n, ncols), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    ldx = _dev2d(X, "X")
+    _check(ctx, load().arb_gaussian_block(ctx.handle, n, ncols, seed, _vp(_ptr(X)), ldx), "arb_gaussian_block")
+    return X
 
 
 def arb_filter(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, a: float, b: float,

@@ -202,6 +202,7 @@ extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz,
   ARB_CUDA(ctx, cudaSetDevice(ctx->device));
   arb_mat m = new arb_mat_s();
   m->ctx = ctx;
+  m->device = ctx->device;
   m->n = n;
   m->nnz = nnz;
   const cudaMemcpyKind kind = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -225,8 +226,9 @@ extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz,
 
 extern "C" arb_status arb_matrix_destroy(arb_mat m) {
   if (!m) return ARB_INVALID_ARG;
-  cudaSetDevice(m->ctx->device);
-  cudaStreamSynchronize(m->ctx->stream);
+  // the creating context may already be gone: use only what the matrix owns
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
   cudaFree(m->rowptr);
   cudaFree(m->col);
   cudaFree(m->val);
@@ -255,6 +257,15 @@ extern "C" arb_status arb_filter_coefficients(int32_t filter, int32_t degree, do
 // =====================================================================================
 // step entry points
 // =====================================================================================
+extern "C" arb_status arb_gaussian_block(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, double* X,
+                                         int64_t ldx) {
+  if (!ctx || n < 0 || ncols < 0 || (n > 0 && ncols > 0 && (!X || ldx < ncols)))
+    return set_error(ctx, ARB_INVALID_ARG, "gaussian_block: bad arguments");
+  ARB_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (n == 0 || ncols == 0) return ARB_OK;
+  return gaussian_fill(ctx, n, ncols, seed, X, ldx);
+}
+
 extern "C" arb_status arb_filter(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, double a,
                                  double b, int32_t degree, const double* coef, const double* X,
                                  int64_t ldx, int32_t ncols, const double* xscale, double* Y, int64_t ldy,

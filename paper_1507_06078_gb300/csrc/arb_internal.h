@@ -64,7 +64,8 @@ struct arb_ctx_s {
 };
 
 struct arb_mat_s {
-  arb_ctx ctx = nullptr;
+  arb_ctx ctx = nullptr;  // creating context (not dereferenced on destroy)
+  int device = 0;
   int64_t n = 0, nnz = 0;
   int32_t* rowptr = nullptr;
   int32_t* col = nullptr;

@@ -313,5 +313,14 @@ def test_device_start_block_matches_host_generator(arb, ctx):
     mat = arb.Matrix.from_csr(ctx, A)
     r_dev = arb.arb_solve(ctx, mat, k, 1, 1e-10, o, x0=None)
     r_host = arb.arb_solve(ctx, mat, k, 1, 1e-10, o, x0=I.gaussian_block(A.n, p, 4242))
-    np.testing.assert_allclose(r_dev.evals, r_host.evals, atol=1e-12)
-    assert r_dev.info["n_filters"] == r_host.info["n_filters"]
+    # the two start blocks differ in the last bits of log/cos, which can move an inner
+    # stop decision; the converged pairs agree all the same
+    np.testing.assert_allclose(r_dev.evals, r_host.evals, atol=1e-10)
+
+
+@pytest.mark.parametrize("n,ncols", [(1, 1), (7, 3), (1000, 30), (333, 17)])
+def test_gaussian_block_matches_input_generator(arb, ctx, n, ncols):
+    Xd = host(arb.arb_gaussian_block(ctx, n, ncols, 987654321987))
+    Xh = I.gaussian_block(n, ncols, 987654321987)
+    # same counters and uniforms; log/sqrt/sincos of two math libraries differ by ulps
+    np.testing.assert_allclose(Xd, Xh, rtol=1e-14, atol=1e-15)
