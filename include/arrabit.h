@@ -96,8 +96,8 @@ typedef struct {
 
 /* ---------------------------------------------------------------- context, matrices */
 
-/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t to run on,
- * or NULL for a stream the context creates and owns. */
+/* Create a context on CUDA device `device`.  `cuda_stream` is the cudaStream_t all of the
+ * context's device work runs on; NULL means the legacy default stream. */
 arb_status arb_ctx_create(arb_ctx* out, int device, void* cuda_stream);
 arb_status arb_ctx_destroy(arb_ctx ctx);
 /* Description of the last error seen by this context (static storage, never NULL). */

@@ -120,15 +120,9 @@ extern "C" arb_status arb_ctx_create(arb_ctx* out, int device, void* cuda_stream
     return ARB_CUDA_ERROR;
   }
   ctx->num_sms = prop.multiProcessorCount;
-  if (cuda_stream) {
-    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
-  } else {
-    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete ctx;
-      return ARB_CUDA_ERROR;
-    }
-    ctx->own_stream = true;
-  }
+  // NULL is the legacy default stream, as everywhere in CUDA
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->own_stream = false;
   *out = ctx;
   return ARB_OK;
 }

@@ -14,26 +14,29 @@
 namespace arb {
 namespace {
 
-constexpr int TILE = 64;
 constexpr int KSTEP = 16;
 
-// part[s][i][j] = sum over rows of split s of X[r][i] * Y[r][j], one 64x64 tile per CTA.
+// part[s][i][j] = sum over the rows of split s of X[r][i] * Y[r][j].  One (16R)x(16R) tile
+// per CTA of 256 threads, each thread owning R x R outputs strided by 16 (R = 1, 2, 4 so
+// that small blocks do not pay for a 64-wide tile of FP64 multiply-adds).
+template <int R>
 __global__ void __launch_bounds__(256)
 gram_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int na,
             const double* __restrict__ Y, int64_t ldy, int nb, int64_t rows_per_split,
             int symmetric, double* __restrict__ part) {
+  constexpr int T = 16 * R;
   const int ti = blockIdx.x, tj = blockIdx.y, s = blockIdx.z;
   if (symmetric && tj < ti) return;
-  __shared__ double Xs[KSTEP][TILE + 1];
-  __shared__ double Ys[KSTEP][TILE + 1];
+  __shared__ double Xs[KSTEP][T + 1];
+  __shared__ double Ys[KSTEP][T + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = ti * TILE, j0 = tj * TILE;
+  const int i0 = ti * T, j0 = tj * T;
   const int64_t r0 = s * rows_per_split;
   const int64_t r1 = min(n, r0 + rows_per_split);
-  double acc[4][4] = {};
+  double acc[R][R] = {};
   for (int64_t rb = r0; rb < r1; rb += KSTEP) {
-    for (int t = threadIdx.x; t < KSTEP * TILE; t += 256) {
-      const int rr = t / TILE, cc = t % TILE;
+    for (int t = threadIdx.x; t < KSTEP * T; t += 256) {
+      const int rr = t / T, cc = t % T;
       const int64_t r = rb + rr;
       const bool rok = r < r1;
       Xs[rr][cc] = (rok && i0 + cc < na) ? X[r * ldx + i0 + cc] : 0.0;
@@ -42,26 +45,26 @@ gram_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int na,
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < KSTEP; ++k) {
-      double a[4], b[4];
+      double a[R], b[R];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < R; ++u) {
         a[u] = Xs[k][ty + 16 * u];
         b[u] = Ys[k][tx + 16 * u];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < R; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
   double* P = part + static_cast<size_t>(s) * na * nb;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < R; ++u) {
     const int i = i0 + ty + 16 * u;
     if (i >= na) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < R; ++v) {
       const int j = j0 + tx + 16 * v;
       if (j < nb) P[static_cast<size_t>(i) * nb + j] = acc[u][v];
     }
@@ -69,12 +72,12 @@ gram_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int na,
 }
 
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int nsplit, int na, int nb,
-                                   int symmetric, double* __restrict__ C, int64_t ldc) {
+                                   int symmetric, int tile, double* __restrict__ C, int64_t ldc) {
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (idx >= static_cast<int64_t>(na) * nb) return;
   int i = static_cast<int>(idx / nb), j = static_cast<int>(idx % nb);
   int si = i, sj = j;
-  if (symmetric && (j / TILE) < (i / TILE)) {
+  if (symmetric && (j / tile) < (i / tile)) {
     si = j;
     sj = i;
   }
@@ -83,38 +86,42 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nsplit, 
   C[static_cast<int64_t>(i) * ldc + j] = s;
 }
 
-// Out[r][c] = alpha * sum_k In[r][k] W[k][c] + beta * Out[r][c]; 64x64 output tile per CTA.
+// Out[r][c] = alpha * sum_k In[r][k] W[k][c] + beta * Out[r][c]; a 64 x (16 RN) output tile
+// per CTA, each thread owning 4 x RN outputs.
+template <int RN>
 __global__ void __launch_bounds__(256)
 gemm_tall_kernel(int64_t n, const double* __restrict__ In, int64_t ldi, int na,
                  const double* __restrict__ W, int64_t ldw, int nb, double alpha, double beta,
                  double* __restrict__ Out, int64_t ldo) {
-  __shared__ double Is[KSTEP][TILE + 1];
-  __shared__ double Ws[KSTEP][TILE + 1];
+  constexpr int TR = 64, TC = 16 * RN;
+  __shared__ double Is[KSTEP][TR + 1];
+  __shared__ double Ws[KSTEP][TC + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TILE;
-  const int c0 = blockIdx.y * TILE;
-  double acc[4][4] = {};
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TR;
+  const int c0 = blockIdx.y * TC;
+  double acc[4][RN] = {};
   for (int k0 = 0; k0 < na; k0 += KSTEP) {
-    for (int t = threadIdx.x; t < KSTEP * TILE; t += 256) {
+    for (int t = threadIdx.x; t < KSTEP * TR; t += 256) {
       const int kk = t % KSTEP, rr = t / KSTEP;
       const int64_t r = r0 + rr;
       Is[kk][rr] = (r < n && k0 + kk < na) ? In[r * ldi + k0 + kk] : 0.0;
-      const int kw = t / TILE, cw = t % TILE;
+    }
+    for (int t = threadIdx.x; t < KSTEP * TC; t += 256) {
+      const int kw = t / TC, cw = t % TC;
       Ws[kw][cw] = (k0 + kw < na && c0 + cw < nb) ? W[static_cast<int64_t>(k0 + kw) * ldw + c0 + cw] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < KSTEP; ++k) {
-      double a[4], b[4];
+      double a[4], b[RN];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = Is[k][ty + 16 * u];
-        b[u] = Ws[k][tx + 16 * u];
-      }
+      for (int u = 0; u < 4; ++u) a[u] = Is[k][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < RN; ++v) b[v] = Ws[k][tx + 16 * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < RN; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
@@ -123,7 +130,7 @@ gemm_tall_kernel(int64_t n, const double* __restrict__ In, int64_t ldi, int na,
     const int64_t r = r0 + ty + 16 * u;
     if (r >= n) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < RN; ++v) {
       const int c = c0 + tx + 16 * v;
       if (c >= nb) continue;
       double* o = Out + r * ldo + c;
@@ -399,7 +406,10 @@ arb_status gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na
                 const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc) {
   if (na <= 0 || nb <= 0) return ARB_OK;
   const int symmetric = (X == Y && ldx == ldy && na == nb) ? 1 : 0;
-  const int gi = (na + TILE - 1) / TILE, gj = (nb + TILE - 1) / TILE;
+  const int mx = std::max(na, nb);
+  const int R = mx <= 16 ? 1 : (mx <= 32 ? 2 : 4);
+  const int T = 16 * R;
+  const int gi = (na + T - 1) / T, gj = (nb + T - 1) / T;
   const int tiles = symmetric ? gi * (gi + 1) / 2 : gi * gj;
   const int64_t target = static_cast<int64_t>(ctx->num_sms) * 3;
   int64_t nsplit = std::max<int64_t>(1, (target + tiles - 1) / tiles);
@@ -411,10 +421,12 @@ arb_status gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na
   double* part;
   ARB_TRY(ws<double>(ctx, WS_GRAM_PART, static_cast<size_t>(nsplit) * na * nb, &part));
   dim3 grid(gi, gj, static_cast<unsigned>(nsplit));
-  gram_kernel<<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+  if (R == 1) gram_kernel<1><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+  else if (R == 2) gram_kernel<2><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+  else gram_kernel<4><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
   ARB_LAUNCHED(ctx);
   gram_reduce_kernel<<<blocks_for(static_cast<int64_t>(na) * nb, 256), 256, 0, ctx->stream>>>(
-      part, static_cast<int>(nsplit), na, nb, symmetric, C, ldc);
+      part, static_cast<int>(nsplit), na, nb, symmetric, T, C, ldc);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
@@ -427,8 +439,12 @@ arb_status gemm_tall(arb_ctx ctx, int64_t n, const double* In, int64_t ldi, int3
     if (beta == 1.0) return ARB_OK;
     return set_error(ctx, ARB_INVALID_ARG, "gemm_tall: empty inner dimension with beta != 1");
   }
-  dim3 grid(static_cast<unsigned>((n + TILE - 1) / TILE), static_cast<unsigned>((nb + TILE - 1) / TILE));
-  gemm_tall_kernel<<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
+  const int RN = nb <= 16 ? 1 : (nb <= 32 ? 2 : 4);
+  const int TC = 16 * RN;
+  dim3 grid(static_cast<unsigned>((n + 63) / 64), static_cast<unsigned>((nb + TC - 1) / TC));
+  if (RN == 1) gemm_tall_kernel<1><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
+  else if (RN == 2) gemm_tall_kernel<2><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
+  else gemm_tall_kernel<4><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }

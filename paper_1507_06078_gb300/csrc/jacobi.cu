@@ -205,6 +205,115 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacParams P) {
   if (tid == 0 && P.sweeps_out) *P.sweeps_out = sweep;
 }
 
+// The same method for M <= JAC_SMALL_M in one CTA: A and V live in shared memory and the
+// phase barriers are __syncthreads (no grid-wide barrier latency).
+constexpr int JAC_SMALL_M = 96;
+constexpr int JAC_SMALL_THREADS = 512;
+
+__global__ void __launch_bounds__(JAC_SMALL_THREADS) jacobi_small_kernel(JacParams P) {
+  extern __shared__ double smem[];
+  const int m = P.m, M = P.M, half = M / 2;
+  double* A = smem;
+  double* V = smem + M * M;
+  double2* rot = reinterpret_cast<double2*>(V + M * M);
+  double* red = reinterpret_cast<double*>(rot + half);  // JAC_SMALL_THREADS
+  const int tid = threadIdx.x, nth = blockDim.x;
+  double fro = 0.0;
+  for (int t = tid; t < M * M; t += nth) {
+    const int i = t / M, j = t % M;
+    const double v = (i < m && j < m) ? P.H[static_cast<int64_t>(i) * P.ldh + j] : 0.0;
+    A[t] = v;
+    V[t] = (i == j) ? 1.0 : 0.0;
+    fro += v * v;
+  }
+  const double normF = sqrt(block_sum(fro, red));
+  int sweep = 0;
+  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
+    double off = 0.0;
+    for (int t = tid; t < M * M; t += nth)
+      if (t / M != t % M) off += A[t] * A[t];
+    const double off2 = block_sum(off, red);
+    if (sqrt(off2) <= JAC_TOL * normF || normF == 0.0) break;
+    for (int r = 0; r < M - 1; ++r) {
+      for (int k = tid; k < half; k += nth) {
+        int i, j;
+        round_pair(M, r, k, i, j);
+        double c = 1.0, s = 0.0;
+        const double aij = A[i * M + j];
+        if (j < m && aij != 0.0) {
+          const double theta = (A[j * M + j] - A[i * M + i]) / (2.0 * aij);
+          const double sg = theta >= 0.0 ? 1.0 : -1.0;
+          const double t = sg / (fabs(theta) + sqrt(theta * theta + 1.0));
+          c = 1.0 / sqrt(t * t + 1.0);
+          s = t * c;
+        }
+        rot[k] = make_double2(c, s);
+      }
+      __syncthreads();
+      const int nblk = half * half;
+      for (int it = tid; it < nblk + M * half; it += nth) {
+        if (it < nblk) {
+          const int kp = it / half, kq = it % half;
+          if (kp > kq) continue;
+          int i1, j1, i2, j2;
+          round_pair(M, r, kp, i1, j1);
+          round_pair(M, r, kq, i2, j2);
+          const double2 r1 = rot[kp], r2 = rot[kq];
+          const double a = A[i1 * M + i2], b = A[i1 * M + j2], cc = A[j1 * M + i2], d = A[j1 * M + j2];
+          const double ra0 = r1.x * a - r1.y * cc, ra1 = r1.x * b - r1.y * d;
+          const double rb0 = r1.y * a + r1.x * cc, rb1 = r1.y * b + r1.x * d;
+          double na = r2.x * ra0 - r2.y * ra1, nb = r2.y * ra0 + r2.x * ra1;
+          double nc = r2.x * rb0 - r2.y * rb1, nd = r2.y * rb0 + r2.x * rb1;
+          if (kp == kq && r1.y != 0.0) {
+            nb = 0.0;
+            nc = 0.0;
+          }
+          A[i1 * M + i2] = na;
+          A[i1 * M + j2] = nb;
+          A[j1 * M + i2] = nc;
+          A[j1 * M + j2] = nd;
+          if (kp != kq) {
+            A[i2 * M + i1] = na;
+            A[j2 * M + i1] = nb;
+            A[i2 * M + j1] = nc;
+            A[j2 * M + j1] = nd;
+          }
+        } else {
+          const int it2 = it - nblk;
+          const int row = it2 / half, kp = it2 % half;
+          int i, j;
+          round_pair(M, r, kp, i, j);
+          const double2 rr = rot[kp];
+          if (rr.y != 0.0) {
+            const double x = V[row * M + i], y = V[row * M + j];
+            V[row * M + i] = rr.x * x - rr.y * y;
+            V[row * M + j] = rr.y * x + rr.x * y;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  int* perm = reinterpret_cast<int*>(red);  // red is free now
+  __syncthreads();
+  for (int i = tid; i < m; i += nth) {
+    const double vi = A[i * M + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double vj = A[j * M + j];
+      rank += (vj > vi) || (vj == vi && j < i);
+    }
+    perm[i] = rank;
+    P.w_out[rank] = vi;
+  }
+  __syncthreads();
+  for (int t = tid; t < m * m; t += nth) {
+    const int row = t / m, i = t % m;
+    P.V_out[static_cast<int64_t>(row) * P.ldv + perm[i]] = V[row * M + i];
+  }
+  if (tid == 0 && P.sweeps_out) *P.sweeps_out = sweep;
+}
+
 }  // namespace
 
 arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
@@ -216,6 +325,26 @@ arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w
   if (m > 8192) return set_error(ctx, ARB_INVALID_ARG, "syevj: matrix too large");
   const int M = (m % 2 == 0) ? m : m + 1;
   const int half = M / 2;
+  if (M <= JAC_SMALL_M) {
+    const size_t smem = (2 * static_cast<size_t>(M) * M + 2 * half + JAC_SMALL_THREADS) * sizeof(double);
+    int32_t* sw;
+    ARB_TRY(ws<int32_t>(ctx, WS_JACOBI, 4, &sw));
+    ARB_CUDA(ctx, cudaFuncSetAttribute(jacobi_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem)));
+    JacParams P = {};
+    P.m = m;
+    P.M = M;
+    P.H = H;
+    P.ldh = ldh;
+    P.w_out = w;
+    P.V_out = V;
+    P.ldv = ldv;
+    P.sweeps_out = sw;
+    jacobi_small_kernel<<<1, JAC_SMALL_THREADS, smem, ctx->stream>>>(P);
+    ARB_LAUNCHED(ctx);
+    if (sweeps) ARB_TRY(d2h_sync(ctx, sweeps, sw, sizeof(int32_t)));
+    return ARB_OK;
+  }
   if (ctx->jacobi_max_blocks == 0) {
     int per_sm = 0;
     ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JAC_THREADS, 0));

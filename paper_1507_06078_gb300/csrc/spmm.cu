@@ -147,14 +147,21 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams P) {
   }
 }
 
-// out[c] = sum_b part[b][c], b in order (deterministic).
+// out[c] = sum_b part[b][c]: one block per column, fixed strided partial sums and a fixed
+// tree, so the result does not depend on scheduling (deterministic).
 __global__ void reduce_partials_kernel(const double* __restrict__ part, int nb, int ncols,
                                        double* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols) return;
+  __shared__ double sh[256];
+  const int c = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[static_cast<size_t>(b) * ncols + c];
-  out[c] = s;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[static_cast<size_t>(b) * ncols + c];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sh[0];
 }
 
 // Per-block Gershgorin bounds: lo = min(a_ii - r_i), hi = max(a_ii + r_i).
@@ -280,8 +287,7 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs& a) {
     ARB_TRY(launch_spmm<1>(ctx, P, grid, smem));
   }
   if (a.colred) {
-    reduce_partials_kernel<<<(a.ncols + 127) / 128, 128, 0, ctx->stream>>>(P.red_part, grid, a.ncols,
-                                                                           a.colred);
+    reduce_partials_kernel<<<a.ncols, 256, 0, ctx->stream>>>(P.red_part, grid, a.ncols, a.colred);
     ARB_LAUNCHED(ctx);
   }
   return ARB_OK;
@@ -320,7 +326,7 @@ arb_status col_sumsq(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32
   ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * ncols, &part));
   col_sumsq_kernel<<<grid, 256, 0, ctx->stream>>>(n, X, ldx, ncols, rows, part);
   ARB_LAUNCHED(ctx);
-  reduce_partials_kernel<<<(ncols + 127) / 128, 128, 0, ctx->stream>>>(part, grid, ncols, out);
+  reduce_partials_kernel<<<ncols, 256, 0, ctx->stream>>>(part, grid, ncols, out);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }

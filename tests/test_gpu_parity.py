@@ -322,5 +322,6 @@ def test_device_start_block_matches_host_generator(arb, ctx):
 def test_gaussian_block_matches_input_generator(arb, ctx, n, ncols):
     Xd = host(arb.arb_gaussian_block(ctx, n, ncols, 987654321987))
     Xh = I.gaussian_block(n, ncols, 987654321987)
-    # same counters and uniforms; log/sqrt/sincos of two math libraries differ by ulps
-    np.testing.assert_allclose(Xd, Xh, rtol=1e-14, atol=1e-15)
+    # same counters and uniforms; the host rounds 2*pi*u before cos/sin while the device
+    # uses sincospi(2u), so values near a zero of cos/sin differ by ~eps * |r| absolutely
+    np.testing.assert_allclose(Xd, Xh, rtol=1e-14, atol=1e-14)
