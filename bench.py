@@ -2,9 +2,11 @@
 
 Workload (default): 3D 7-point Dirichlet Laplacian on a 128^3 grid (n = 2,097,152,
 nnz = 14,581,760), k = 200 smallest eigenpairs (largest of 12 I - A), block p = 240,
-Chebyshev-interpolant degree d = 20, q = 2 augmentation blocks, relative residual 1e-8,
-plain FP64 path.  One step = one whole solve (every step of the hot path) with A and the
-Gaussian start block already resident in HBM.
+Chebyshev-interpolant degree d = 20, q = 2 augmentation blocks, relative residual 1e-8.
+Default precision: the mixed path (FP32 filter and FP32 block-Krylov Rayleigh-Ritz, then
+an FP64 refinement phase to the same tolerance); --precision fp64 runs the plain FP64 path.
+One step = one whole solve (every step of the hot path) with A and the Gaussian start block
+already resident in HBM.
 
 Printed JSON line: value (solves/s, device-timed), e2e (same metric through the C ABI with
 host buffers: A and X0 uploaded from pinned host memory, eigenpairs read back), roofline of
@@ -43,6 +45,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=128, help="3D grid side (128 = the benchmark workload)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="also time one plain FP64 solve of the same workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -127,12 +132,12 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def filter_algorithmic_bytes(n, nnz, p, d, s=8):
+def filter_algorithmic_bytes(n, nnz, p, d, s=8, z=8):
     """Algorithmic HBM bytes of one Clenshaw filter application (d fused SpMM passes):
     every pass reads A once (nnz*(8+4) + 4(n+1)); the block traffic is 2 n p s for the
     first pass (read X, write b_{d-1}), 3 n p s for the second (read b_{d-1}, X; write) and
     4 n p s for every later pass (read b_{j+1}, b_{j+2}, X; write b_j)."""
-    a_bytes = nnz * (8 + 4) + 4 * (n + 1)
+    a_bytes = nnz * (z + 4) + 4 * (n + 1)
     blocks = 2 + (3 if d >= 2 else 0) + 4 * max(d - 2, 0)
     return d * a_bytes + blocks * n * p * s
 
@@ -214,6 +219,7 @@ def run_ours(args):
     X0 = torch.from_numpy(X0h).cuda(local)
     opts = arb.arb_options_default(W.k)
     opts.p, opts.q, opts.degree = W.p, W.q, W.degree
+    opts.precision = arb.ARB_MIXED if args.precision == "mixed" else arb.ARB_FP64
 
     def step():
         return arb.arb_solve(ctx, mat, W.k, arb.ARB_SMALLEST, W.tol, opts, x0=X0, evecs="device")
@@ -250,30 +256,55 @@ def run_ours(args):
     lam = laplacian_3d_eigs(args.grid)[:W.k]
     eig_err = float(np.max(np.abs(r.evals - lam) / np.maximum(1.0, np.abs(lam))))
 
-    # dominant kernel: the fused filter SpMM, timed live on the context's stream
+    # dominant kernel: the fused filter SpMM (one filter = W.degree launches), timed live
+    # with CUDA events on the context's stream, on the full n x p block of the workload
     coef = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, W.degree)
-    Xf = X0
-    Yf = torch.empty_like(X0)
-    nrep = 3
-    for _ in range(1):
-        arb.arb_filter(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, Xf, Y=Yf)
+    if args.precision == "mixed":
+        Xf = X0.float()
+        run_filter = lambda Y: arb.arb_filter_f32(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, Xf, Y=Y)  # noqa: E731
+        s_bytes, z_bytes, kname = 4, 4, "spmm_fused_kernel<float,4> (Clenshaw filter pass, FP32)"
+    else:
+        Xf = X0
+        run_filter = lambda Y: arb.arb_filter(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, Xf, Y=Y)  # noqa: E731
+        s_bytes, z_bytes, kname = 8, 8, "spmm_fused_kernel<double,2> (Clenshaw filter pass, FP64)"
+    Yf = torch.empty_like(Xf)
+    run_filter(Yf)
     barrier()
+    nrep = 3
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(nrep):
-        arb.arb_filter(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, Xf, Y=Yf)
+        run_filter(Yf)
     e1.record(stream)
     barrier()
     f_ms = e0.elapsed_time(e1) / nrep
-    fbytes = filter_algorithmic_bytes(W.A.n, W.A.nnz, W.p, W.degree)
+    del Yf
+    fbytes = filter_algorithmic_bytes(W.A.n, W.A.nnz, W.p, W.degree, s=s_bytes, z=z_bytes)
     fflops = W.degree * (2.0 * W.A.nnz * W.p + 6.0 * W.A.n * W.p)
     peak, peak_src = measured_peaks()
     achieved = fbytes / (f_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "spmm_fused_kernel (Clenshaw filter step, FP64)",
-            "launch_ms": f_ms / W.degree, "algorithmic_bytes_per_launch": fbytes / W.degree,
-            "fp64_tflops": fflops / (f_ms * 1e-3) / 1e12, "peak_source": peak_src}
+            "traffic": None, "kernel": kname, "launch_ms": f_ms / W.degree,
+            "algorithmic_bytes_per_launch": fbytes / W.degree, "flops_per_launch": fflops / W.degree,
+            "peak_source": peak_src + " hbm_gbs (STREAM-style copy)"}
+
+    fp64_cmp = None
+    if args.compare_fp64 and args.precision == "mixed":
+        o64 = arb.arb_options_default(W.k)
+        o64.p, o64.q, o64.degree, o64.precision = W.p, W.q, W.degree, arb.ARB_FP64
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        r64 = arb.arb_solve(ctx, mat, W.k, arb.ARB_SMALLEST, W.tol, o64, x0=X0, evecs="device")
+        t1.record(stream)
+        barrier()
+        ms64 = t0.elapsed_time(t1)
+        fp64_cmp = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "speedup_mixed_vs_fp64": ms64 / ms_per,
+                    "maxres": r64.info["maxres"], "outer_iters": r64.info["outer_iters"],
+                    "eig_rel_err_vs_closed_form": float(np.max(np.abs(r64.evals - lam) / np.maximum(1.0, np.abs(lam)))),
+                    "max_eig_diff_vs_mixed": float(np.max(np.abs(r64.evals - r.evals) / np.maximum(1.0, np.abs(lam))))}
 
     e2e = None
     if not args.no_e2e:
@@ -311,17 +342,19 @@ def run_ours(args):
         info = infos[-1]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+                "data": "synthetic",
                 "config": {"workload": W.name, "n": W.A.n, "nnz": W.A.nnz, "k": W.k, "p": W.p, "q": W.q,
-                           "degree": W.degree, "tol": W.tol, "precision": "fp64",
+                           "degree": W.degree, "tol": W.tol, "precision": args.precision,
                            "l2": "inputs larger than L2 (A 175 MB, X0 4 GB, work blocks ~50 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "gpu_launches": int(launches),
+                "gpu_launches": int(launches), "fp64_path": fp64_cmp,
                 "solve": {"eig_rel_err_vs_closed_form": eig_err, "maxres": info["maxres"],
                           "outer_iters": info["outer_iters"], "n_filters": info["n_filters"],
                           "spmm_cols": info["spmm_cols"], "t_filter_s": info["t_filter"],
-                          "t_arr_s": info["t_arr"], "stop": info["stop_reason"]}}
+                          "t_arr_s": info["t_arr"], "stop": info["stop_reason"],
+                          "outer_iters_fp32": info["outer_iters_fp32"]}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

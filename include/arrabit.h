@@ -73,10 +73,12 @@ typedef struct {
   int32_t maxit2;       /* filter applications between checks (default 5) */
   int32_t inner_fixed;  /* > 0: exactly this many filters per outer iteration, no rcond rule */
   int32_t filter;       /* arb_filter_kind */
-  int32_t precision;    /* arb_precision; only ARB_FP64 is implemented, others -> ARB_INVALID_ARG */
+  int32_t precision;    /* arb_precision: ARB_FP64, or ARB_MIXED (FP32 phase, then FP64 refinement) */
   int32_t reserved0;
   double tol1;          /* first continuation tolerance; 0: max(1e-6, tol) if tol <= 1e-8 else tol */
   double shift_sigma;   /* sigma of sigma I - A for ARB_SMALLEST; NaN: Gershgorin upper bound of A */
+  double tol_switch;    /* ARB_MIXED: relative residual at which the FP32 phase hands over to
+                           FP64 (one continuation step is taken there); 0: 1e-5 */
   uint64_t seed;        /* stream for padding columns (Philox4x32-10 + Box-Muller) */
 } arb_options;
 
@@ -91,7 +93,7 @@ typedef struct {
   int32_t n_locked;     /* size of the locked set at exit */
   int32_t stop_reason;  /* arb_stop_reason */
   int32_t last_rank;    /* dimension of the last Rayleigh-Ritz subspace */
-  int32_t reserved0;
+  int32_t outer_iters_fp32; /* ARB_MIXED: outer iterations of the FP32 phase */
 } arb_info;
 
 /* ---------------------------------------------------------------- context, matrices */
@@ -164,6 +166,14 @@ arb_status arb_filter(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift
                       double b, int32_t degree, const double* coef, const double* X,
                       int64_t ldx, int32_t ncols, const double* xscale, double* Y, int64_t ldy,
                       double* colss);
+
+/* The same filter with FP32 blocks and FP32 arithmetic (the mixed-precision path's
+ * filter; column sums of squares still accumulate in FP64).  X, Y: n x ncols FP32,
+ * row-major; A's values are rounded to FP32 once and kept with the matrix. */
+arb_status arb_filter_f32(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, double a,
+                          double b, int32_t degree, const double* coef, const float* X,
+                          int64_t ldx, int32_t ncols, const double* xscale, float* Y,
+                          int64_t ldy, double* colss);
 
 /* Host-side coefficients c_0..c_d (float64[degree+1]) of the degree-d Chebyshev
  * interpolant of max(0,t)^(10 d) at t_j = -cos(j pi/d) (Section 5, eq. chebfun-f), or of

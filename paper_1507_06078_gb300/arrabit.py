@@ -40,7 +40,8 @@ class arb_options(C.Structure):
     _fields_ = [("p", C.c_int32), ("q", C.c_int32), ("degree", C.c_int32), ("maxit", C.c_int32),
                 ("maxit1", C.c_int32), ("maxit2", C.c_int32), ("inner_fixed", C.c_int32),
                 ("filter", C.c_int32), ("precision", C.c_int32), ("reserved0", C.c_int32),
-                ("tol1", C.c_double), ("shift_sigma", C.c_double), ("seed", C.c_uint64)]
+                ("tol1", C.c_double), ("shift_sigma", C.c_double), ("tol_switch", C.c_double),
+                ("seed", C.c_uint64)]
 
 
 class arb_info(C.Structure):
@@ -48,7 +49,7 @@ class arb_info(C.Structure):
                 ("sigma", C.c_double), ("t_total", C.c_double), ("t_filter", C.c_double),
                 ("t_arr", C.c_double), ("spmm_cols", C.c_int64), ("outer_iters", C.c_int32),
                 ("n_filters", C.c_int32), ("n_locked", C.c_int32), ("stop_reason", C.c_int32),
-                ("last_rank", C.c_int32), ("reserved0", C.c_int32)]
+                ("last_rank", C.c_int32), ("outer_iters_fp32", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}
@@ -72,6 +73,8 @@ _PROTOS = {
                          C.c_int, C.POINTER(arb_info)]),
     "arb_gaussian_block": (_i32, [_vp, _i64, _i32, C.c_uint64, _vp, _i64]),
     "arb_filter": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _dbl, _i32, _vp, _vp, _i64, _i32, _vp, _vp, _i64, _vp]),
+    "arb_filter_f32": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _dbl, _i32, _vp, _vp, _i64, _i32, _vp, _vp, _i64,
+                              _vp]),
     "arb_filter_coefficients": (_i32, [_i32, _i32, _vp]),
     "arb_spmm": (_i32, [_vp, _vp, _dbl, _dbl, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
@@ -280,6 +283,22 @@ def arb_filter(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, a: f
                            _vp(_ptr(X)), ldx, X.shape[1], _vp(_ptr(xscale)), _vp(_ptr(Y)), ldy,
                            _vp(_ptr(colss)))
     _check(ctx, st, "arb_filter")
+    return Y
+
+
+def arb_filter_f32(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, a: float, b: float,
+                   coef: np.ndarray, X, xscale=None, Y=None, colss=None):
+    """FP32 variant of arb_filter (X, Y: row-major 2D float32 CUDA tensors)."""
+    import torch
+    if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1):
+        raise ValueError("X: expected a row-major 2D float32 CUDA tensor")
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    if Y is None:
+        Y = torch.empty_like(X)
+    st = load().arb_filter_f32(ctx.handle, mat.handle, op_scale, op_shift, a, b, len(coef) - 1, coef.ctypes.data,
+                               _vp(_ptr(X)), X.stride(0), X.shape[1], _vp(_ptr(xscale)), _vp(_ptr(Y)), Y.stride(0),
+                               _vp(_ptr(colss)))
+    _check(ctx, st, "arb_filter_f32")
     return Y
 
 

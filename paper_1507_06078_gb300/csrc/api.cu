@@ -226,6 +226,7 @@ extern "C" arb_status arb_matrix_destroy(arb_mat m) {
   cudaFree(m->rowptr);
   cudaFree(m->col);
   cudaFree(m->val);
+  if (m->val32) cudaFree(m->val32);
   delete m;
   return ARB_OK;
 }
@@ -274,7 +275,23 @@ extern "C" arb_status arb_filter(arb_ctx ctx, arb_mat mat, double op_scale, doub
   ARB_TRY(ws<double>(ctx, WS_FILT_W1, static_cast<size_t>(n) * ldw, &W1));
   ARB_TRY(ws<double>(ctx, WS_FILT_W2, static_cast<size_t>(n) * ldw, &W2));
   FilterPlan plan = make_filter_plan(op_scale, op_shift, a, b, degree, coef);
-  return filter_apply(ctx, mat, plan, X, ldx, ncols, xscale, W1, W2, ldw, Y, ldy, colss, nullptr);
+  return filter_apply<double>(ctx, mat, plan, X, ldx, ncols, xscale, W1, W2, ldw, Y, ldy, colss, nullptr);
+}
+
+extern "C" arb_status arb_filter_f32(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, double a,
+                                     double b, int32_t degree, const double* coef, const float* X, int64_t ldx,
+                                     int32_t ncols, const double* xscale, float* Y, int64_t ldy, double* colss) {
+  if (!ctx || !mat || !coef || !X || !Y || ncols < 0 || ldx < ncols || ldy < ncols || !(b > a))
+    return set_error(ctx, ARB_INVALID_ARG, "filter_f32: bad arguments");
+  if (degree < 1 || degree > 60) return set_error(ctx, ARB_INVALID_ARG, "filter_f32: degree must be in [1, 60]");
+  ARB_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int64_t n = mat->n;
+  const int64_t ldw = ((ncols + 3) / 4) * 4;
+  float *W1, *W2;
+  ARB_TRY(ws<float>(ctx, WS_F32_W1, static_cast<size_t>(n) * ldw, &W1));
+  ARB_TRY(ws<float>(ctx, WS_F32_W2, static_cast<size_t>(n) * ldw, &W2));
+  FilterPlan plan = make_filter_plan(op_scale, op_shift, a, b, degree, coef);
+  return filter_apply<float>(ctx, mat, plan, X, ldx, ncols, xscale, W1, W2, ldw, Y, ldy, colss, nullptr);
 }
 
 extern "C" arb_status arb_spmm(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, const double* X,
@@ -282,7 +299,7 @@ extern "C" arb_status arb_spmm(arb_ctx ctx, arb_mat mat, double op_scale, double
   if (!ctx || !mat || !X || !Y || ncols < 0 || ldx < ncols || ldy < ncols)
     return set_error(ctx, ARB_INVALID_ARG, "spmm: bad arguments");
   ARB_CUDA(ctx, cudaSetDevice(ctx->device));
-  SpmmArgs s;
+  SpmmArgs<double> s;
   s.A = mat;
   s.ncols = ncols;
   s.Yin = X;
@@ -291,7 +308,7 @@ extern "C" arb_status arb_spmm(arb_ctx ctx, arb_mat mat, double op_scale, double
   s.beta = op_shift;
   s.out = Y;
   s.ldo = ldy;
-  return spmm_fused(ctx, s);
+  return spmm_fused<double>(ctx, s);
 }
 
 extern "C" arb_status arb_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
@@ -303,7 +320,7 @@ extern "C" arb_status arb_gram(arb_ctx ctx, int64_t n, const double* X, int64_t 
     for (int32_t i = 0; i < na; ++i) ARB_TRY(fill(ctx, C + static_cast<int64_t>(i) * ldc, nb, 0.0));
     return ARB_OK;
   }
-  return gram(ctx, n, X, ldx, na, Y, ldy, nb, C, ldc);
+  return gram<double>(ctx, n, X, ldx, na, Y, ldy, nb, C, ldc);
 }
 
 extern "C" arb_status arb_syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
@@ -319,7 +336,7 @@ extern "C" arb_status arb_rcond_gram(arb_ctx ctx, int64_t n, const double* X, in
   if (!ctx || n <= 0 || !X || ncols <= 0 || ldx < ncols || !rc)
     return set_error(ctx, ARB_INVALID_ARG, "rcond_gram: bad arguments");
   ARB_CUDA(ctx, cudaSetDevice(ctx->device));
-  return rcond_gram(ctx, n, X, ldx, ncols, xscale, rc);
+  return rcond_gram<double>(ctx, n, X, ldx, ncols, xscale, rc);
 }
 
 extern "C" arb_status arb_orth(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz, int32_t m, double* U,
@@ -329,7 +346,7 @@ extern "C" arb_status arb_orth(arb_ctx ctx, int64_t n, const double* Z, int64_t 
   ARB_CUDA(ctx, cudaSetDevice(ctx->device));
   double* tmp;
   ARB_TRY(ws<double>(ctx, WS_TALL0, static_cast<size_t>(n) * std::max(m, 1), &tmp));
-  return orth(ctx, n, Z, ldz, m, U, ldu, tmp, std::max(m, 1), rank);
+  return orth<double>(ctx, n, Z, ldz, m, U, ldu, tmp, std::max(m, 1), rank);
 }
 
 extern "C" arb_status arb_rayleigh_ritz(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift,
@@ -343,10 +360,10 @@ extern "C" arb_status arb_rayleigh_ritz(arb_ctx ctx, arb_mat mat, double op_scal
   ARB_TRY(ws<double>(ctx, WS_TALL1, static_cast<size_t>(n) * m, &U));
   ARB_TRY(ws<double>(ctx, WS_TALL2, static_cast<size_t>(n) * m, &AU));
   int32_t r = 0;
-  ARB_TRY(orth(ctx, n, Z, ldz, m, U, m, tmp, m, &r));
+  ARB_TRY(orth<double>(ctx, n, Z, ldz, m, U, m, tmp, m, &r));
   *rank = r;
   if (r == 0) return ARB_OK;
-  SpmmArgs s;
+  SpmmArgs<double> s;
   s.A = mat;
   s.ncols = r;
   s.Yin = U;
@@ -355,13 +372,13 @@ extern "C" arb_status arb_rayleigh_ritz(arb_ctx ctx, arb_mat mat, double op_scal
   s.beta = op_shift;
   s.out = AU;
   s.ldo = m;
-  ARB_TRY(spmm_fused(ctx, s));
+  ARB_TRY(spmm_fused<double>(ctx, s));
   ARB_TRY(ws<double>(ctx, WS_S_V, static_cast<size_t>(r) * r, &H));
   ARB_TRY(ws<double>(ctx, WS_S_VSEL, static_cast<size_t>(r) * r, &V));
-  ARB_TRY(gram(ctx, n, U, m, r, AU, m, r, H, r));
+  ARB_TRY(gram<double>(ctx, n, U, m, r, AU, m, r, H, r));
   ARB_TRY(symmetrize(ctx, r, H, r));
   ARB_TRY(syevj(ctx, r, H, r, w, V, r, nullptr));
-  return gemm_tall(ctx, n, U, m, r, V, r, r, 1.0, 0.0, Y, ldy);
+  return gemm_tall<double>(ctx, n, U, m, r, V, r, r, 1.0, 0.0, Y, ldy);
 }
 
 extern "C" arb_status arb_arr(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, int64_t n,
@@ -374,26 +391,26 @@ extern "C" arb_status arb_arr(arb_ctx ctx, arb_mat mat, double op_scale, double 
   const int64_t ldw = ncols + (ncols & 1);
   const int64_t mcap = static_cast<int64_t>(q + 1) * ncols;
   const int64_t ldm = mcap + (mcap & 1);
-  ArrWork wk;
+  ArrWork<double> wk;
   double* Xc;
   ARB_TRY(ws<double>(ctx, WS_TALL0, static_cast<size_t>(n) * ldw, &Xc));
   ARB_TRY(ws<double>(ctx, WS_SOLVER_U, static_cast<size_t>(n) * ldm, &wk.U));
   ARB_TRY(ws<double>(ctx, WS_SOLVER_AU, static_cast<size_t>(n) * ldm, &wk.AU));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_T, static_cast<size_t>(n) * ldw, &wk.T));
+  ARB_TRY(ws<double>(ctx, WS_SOLVER_T, static_cast<size_t>(n) * ldw, &wk.T1));
   ARB_TRY(ws<double>(ctx, WS_SOLVER_T2, static_cast<size_t>(n) * ldw, &wk.T2));
   wk.ldu = wk.ldau = ldm;
   wk.ldt = wk.ldt2 = ldw;
-  ARB_TRY(copy_block(ctx, n, X, ldx, ncols, Xc, ldw));
+  ARB_TRY((copy_block<double, double>(ctx, n, X, ldx, ncols, Xc, ldw)));
   double *theta, *V;
   ARB_TRY(ws<double>(ctx, WS_S_VEC, static_cast<size_t>(mcap), &theta));
   ARB_TRY(ws<double>(ctx, WS_S_V, static_cast<size_t>(mcap) * mcap, &V));
   int32_t m = 0;
-  ARB_TRY(arr_basis_and_eig(ctx, mat, op_scale, op_shift, n, Xc, ldw, ncols, nullptr, 0, 0, q, wk, &m,
-                            theta, V));
+  ARB_TRY(arr_basis_and_eig<double>(ctx, mat, op_scale, op_shift, n, Xc, ldw, ncols, nullptr, 0, 0, q, wk, &m,
+                                    theta, V));
   *rank = m;
   if (m < npairs) return set_error(ctx, ARB_BREAKDOWN, "arr: subspace smaller than the requested pairs");
   ARB_CUDA(ctx, cudaMemcpyAsync(w, theta, npairs * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
-  return gemm_tall(ctx, n, wk.U, ldm, m, V, m, npairs, 1.0, 0.0, Y, ldy);
+  return gemm_tall<double>(ctx, n, wk.U, ldm, m, V, m, npairs, 1.0, 0.0, Y, ldy);
 }
 
 // =====================================================================================
@@ -412,315 +429,409 @@ arb_status upload_ints(arb_ctx ctx, int32_t* dev, const std::vector<int32_t>& h)
   return h2d(ctx, dev, h.data(), h.size() * sizeof(int32_t));
 }
 
-arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol, const arb_options& o,
-                      const double* x0, int x0_on_device, double* evals, double* evecs, int64_t ldq,
-                      int evecs_on_device, arb_info* info_out) {
-  Timer total;
-  arb_info info;
-  memset(&info, 0, sizeof(info));
-  const int64_t n = mat->n;
-  const int32_t p = o.p > 0 ? o.p : k + static_cast<int32_t>(std::lround(0.1 * k));
-  const int32_t q = o.q, d = o.degree;
-  if (k <= 0 || k > p || q < 0 || d < 1 || d > 60 || o.maxit < 1 || o.maxit1 < 1 || o.maxit2 < 1 ||
-      static_cast<int64_t>(q + 1) * p >= n || !(tol > 0.0))
-    return set_error(ctx, ARB_INVALID_ARG, "solve: need 0 < k <= p, (q+1) p < n, 1 <= degree <= 60, tol > 0");
-  if (o.precision != ARB_FP64) return set_error(ctx, ARB_INVALID_ARG, "solve: only ARB_FP64 is implemented");
-  if (which != ARB_LARGEST && which != ARB_SMALLEST) return set_error(ctx, ARB_INVALID_ARG, "solve: bad which");
-  if (evecs && ldq < n) return set_error(ctx, ARB_INVALID_ARG, "solve: ldq < n");
-  const bool smallest = (which == ARB_SMALLEST);
-
-  // operator B = op_scale A + op_shift I whose largest eigenpairs are wanted
-  double glo, ghi;
-  ARB_TRY(gershgorin(ctx, mat, &glo, &ghi));
-  double sigma = 0.0, op_scale = 1.0, op_shift = 0.0, a;
-  if (smallest) {
-    sigma = std::isnan(o.shift_sigma) ? ghi : o.shift_sigma;
-    op_scale = -1.0;
-    op_shift = sigma;
-    a = sigma - ghi;  // Gershgorin lower bound of sigma I - A
-  } else {
-    a = glo;
-  }
-
-  // device buffers
-  const int64_t ld = p + (p & 1);
-  const int64_t mcap = static_cast<int64_t>(q + 1) * p;
-  const int64_t ldm = mcap + (mcap & 1);
-  const size_t blk = static_cast<size_t>(n) * ld;
-  double *bufX, *bufW1, *bufW2, *Qc, *Xall;
-  ArrWork wk;
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_X, blk, &bufX));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_W1, blk, &bufW1));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_W2, blk, &bufW2));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_QC, blk, &Qc));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_XALL, blk, &Xall));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_U, static_cast<size_t>(n) * ldm, &wk.U));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_AU, static_cast<size_t>(n) * ldm, &wk.AU));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_T, blk, &wk.T));
-  ARB_TRY(ws<double>(ctx, WS_SOLVER_T2, blk, &wk.T2));
-  wk.ldu = wk.ldau = ldm;
-  wk.ldt = wk.ldt2 = ld;
-  double *V, *Vsel, *vec;
-  ARB_TRY(ws<double>(ctx, WS_S_V, static_cast<size_t>(mcap) * mcap, &V));
-  ARB_TRY(ws<double>(ctx, WS_S_VSEL, static_cast<size_t>(mcap) * p, &Vsel));
-  // vec layout: theta[mcap] | mu[p] | sigc[p] | ss[p] | res[p] | xs[p] | negmu... | ints
-  ARB_TRY(ws<double>(ctx, WS_S_VEC, static_cast<size_t>(mcap) + 8 * static_cast<size_t>(p) + 64, &vec));
-  double* theta = vec;
-  double* mu = theta + mcap;
-  double* sigc = mu + p;
-  double* ss = sigc + p;
-  double* res = ss + p;
-  double* xs = res + p;
-  int32_t* imap = reinterpret_cast<int32_t*>(xs + p);       // p ints
-  int32_t* iidx = imap + p + (p & 1);                          // p ints
-  double* sgn = reinterpret_cast<double*>(iidx + p + (p & 1)); // p doubles
-
-  // start block X0 (Algorithm 8: i.i.d. Gaussian n x (k+q))
-  if (x0) {
-    ARB_CUDA(ctx, cudaMemcpy2DAsync(bufX, ld * sizeof(double), x0, p * sizeof(double), p * sizeof(double), n,
-                                    x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                    ctx->stream));
-  } else {
-    ARB_TRY(gaussian_fill(ctx, n, p, o.seed, bufX, ld));
-  }
-
-  // b: smallest Ritz value of orth(X0) (Section 5, "Estimation of lambda_n and lambda_{k+q}")
-  double b;
-  {
-    int32_t r = 0;
-    ARB_TRY(orth(ctx, n, bufX, ld, p, wk.U, ldm, wk.T, ld, &r));
-    if (r == 0) return set_error(ctx, ARB_BREAKDOWN, "solve: start block has no numerical rank");
-    SpmmArgs s;
-    s.A = mat;
-    s.ncols = r;
-    s.Yin = wk.U;
-    s.ldy = ldm;
-    s.alpha = op_scale;
-    s.beta = op_shift;
-    s.out = wk.AU;
-    s.ldo = ldm;
-    ARB_TRY(spmm_fused(ctx, s));
-    double* H;
-    ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(r) * r, &H));
-    ARB_TRY(gram(ctx, n, wk.U, ldm, r, wk.AU, ldm, r, H, r));
-    ARB_TRY(symmetrize(ctx, r, H, r));
-    ARB_TRY(syevj(ctx, r, H, r, theta, V, r, nullptr));
-    ARB_TRY(d2h_sync(ctx, &b, theta + (r - 1), sizeof(double)));
-    info.spmm_cols += r;
-  }
-  info.a = a;
-  info.b0 = b;
-  info.sigma = sigma;
-  if (!(b > a)) b = a + 1e-3 * std::max(1.0, std::fabs(a));  // degenerate start: keep the map defined
-
-  double coef[64];
-  ARB_TRY(arb_filter_coefficients(o.filter, d, coef) == ARB_OK ? ARB_OK
-                                                                 : set_error(ctx, ARB_INVALID_ARG, "bad filter"));
-  const double tol1 = o.tol1 > 0.0 ? o.tol1 : (tol <= 1e-8 ? std::max(1e-6, tol) : tol);
-  double tol_t = std::max(tol1, tol);
-
-  double* X = bufX;
-  double* W1 = bufW1;
-  double* W2 = bufW2;
-  int32_t w = p, nl = 0;
-  std::vector<double> h_sigc;  // locked Ritz values (host mirror)
-  ARB_TRY(fill(ctx, xs, w, 1.0));
+// Everything of a solve that does not depend on the element type of the blocks.
+struct SolveState {
+  int64_t n = 0;
+  int32_t k = 0, p = 0, q = 0, d = 0;
+  bool smallest = false;
+  double sigma = 0.0, op_scale = 1.0, op_shift = 0.0, a = 0.0, b = 0.0, tol = 0.0, tol_t = 0.0;
+  arb_options o{};
+  double coef[64] = {};
+  int64_t mcap = 0;
+  // device vectors
+  double *theta = nullptr, *mu = nullptr, *sigc = nullptr, *ss = nullptr, *res = nullptr, *xs = nullptr;
+  double *sgn = nullptr, *V = nullptr, *Vsel = nullptr;
+  int32_t *imap = nullptr, *iidx = nullptr;
+  // host mirror
+  int32_t w = 0, nl = 0;
+  std::vector<double> h_mu, h_res, h_sigc;
+  std::vector<int32_t> h_map;
   double best = std::numeric_limits<double>::infinity();
   int best_iter = 0;
+  int outer = 0;  // outer iterations done in the current phase
   int stop = ARB_STOP_MAXIT;
-  std::vector<double> h_mu(p), h_res(p);
-  std::vector<int32_t> h_map(p);
-  int j = 0;
-  cudaEvent_t ev0, ev1;
-  ARB_CUDA(ctx, cudaEventCreate(&ev0));
-  ARB_CUDA(ctx, cudaEventCreate(&ev1));
-  for (j = 1; j <= o.maxit; ++j) {
+  arb_info info{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+template <typename T>
+struct BlockSet {
+  T *X = nullptr, *W1 = nullptr, *W2 = nullptr, *Qc = nullptr, *Xall = nullptr;
+  int64_t ld = 0, ldm = 0;
+  ArrWork<T> wk;
+};
+
+template <typename T>
+arb_status alloc_blocks(arb_ctx ctx, const SolveState& S, BlockSet<T>& B) {
+  const bool f32 = sizeof(T) == 4;
+  const int vec = f32 ? 4 : 2;  // keep rows 16-byte aligned
+  B.ld = ((S.p + vec - 1) / vec) * vec;
+  B.ldm = ((S.mcap + vec - 1) / vec) * vec;
+  const size_t blk = static_cast<size_t>(S.n) * B.ld;
+  const size_t big = static_cast<size_t>(S.n) * B.ldm;
+  ARB_TRY(ws<T>(ctx, f32 ? WS_F32_X : WS_SOLVER_X, blk, &B.X));
+  ARB_TRY(ws<T>(ctx, f32 ? WS_F32_W1 : WS_SOLVER_W1, blk, &B.W1));
+  ARB_TRY(ws<T>(ctx, f32 ? WS_F32_W2 : WS_SOLVER_W2, blk, &B.W2));
+  ARB_TRY(ws<T>(ctx, f32 ? WS_F32_XALL : WS_SOLVER_XALL, blk, &B.Xall));
+  if (!f32) ARB_TRY(ws<T>(ctx, WS_SOLVER_QC, blk, &B.Qc));
+  ARB_TRY(ws<T>(ctx, f32 ? WS_F32_U : WS_SOLVER_U, big, &B.wk.U));
+  ARB_TRY(ws<T>(ctx, f32 ? WS_F32_AU : WS_SOLVER_AU, big, &B.wk.AU));
+  ARB_TRY(ws<T>(ctx, f32 ? WS_F32_T : WS_SOLVER_T, blk, &B.wk.T1));
+  ARB_TRY(ws<T>(ctx, f32 ? WS_F32_T2 : WS_SOLVER_T2, blk, &B.wk.T2));
+  B.wk.ldu = B.wk.ldau = B.ldm;
+  B.wk.ldt = B.wk.ldt2 = B.ld;
+  return ARB_OK;
+}
+
+// Outer iterations of Algorithm 8 with blocks of type T until the outer stop rule holds for
+// `tol_phase` (or a stall / maxit / all-locked stop).  rc_floor bounds the inner-stop
+// threshold from below (reading c7: 100 u of the filter precision); lock = false disables
+// deflation (thresholds of eq. defl are below what FP32 blocks resolve).  When
+// continue_on_phase_tol is set, reaching tol_phase performs one continuation step (b and
+// tol_t updated as in eq. contin) before returning.
+template <typename T>
+arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, double tol_phase, double rc_floor,
+                     bool lock, bool continue_on_phase_tol) {
+  const int64_t n = S.n;
+  const int32_t p = S.p, k = S.k;
+  S.best = std::numeric_limits<double>::infinity();
+  S.best_iter = 0;
+  S.outer = 0;
+  S.stop = ARB_STOP_MAXIT;
+  float ms = 0.f;
+  for (int j = 1; j <= S.o.maxit; ++j) {
+    S.outer = j;
+    S.info.outer_iters++;
     // ---------------- inner loop: multi-power steps (Algorithm 8, MPM branch)
-    ARB_CUDA(ctx, cudaEventRecord(ev0, ctx->stream));
+    ARB_CUDA(ctx, cudaEventRecord(S.ev0, ctx->stream));
     double rc = std::numeric_limits<double>::infinity();
-    const int n_outer_checks = o.inner_fixed > 0 ? 1 : o.maxit1;
-    const int n_steps = o.inner_fixed > 0 ? o.inner_fixed : o.maxit2;
-    for (int i1 = 0; i1 < n_outer_checks; ++i1) {
+    const int n_checks = S.o.inner_fixed > 0 ? 1 : S.o.maxit1;
+    const int n_steps = S.o.inner_fixed > 0 ? S.o.inner_fixed : S.o.maxit2;
+    const double rc_thr = std::max(S.tol_t, rc_floor);
+    for (int i1 = 0; i1 < n_checks; ++i1) {
       for (int i2 = 0; i2 < n_steps; ++i2) {
-        const FilterPlan plan = make_filter_plan(op_scale, op_shift, a, b, d, coef);
-        double* result = nullptr;
-        ARB_TRY(filter_apply(ctx, mat, plan, X, ld, w, xs, W1, W2, ld, nullptr, 0, ss, &result));
-        // the result lives in W1 or W2: rotate the three buffers
-        if (result == W1) std::swap(X, W1);
-        else std::swap(X, W2);
-        ARB_TRY(inv_sqrt(ctx, w, ss, xs));  // column normalisation, applied lazily
-        if (nl > 0) ARB_TRY(project_out(ctx, n, Qc, ld, nl, X, ld, w));
-        info.n_filters++;
-        info.spmm_cols += static_cast<int64_t>(d) * w;
+        const FilterPlan plan = make_filter_plan(S.op_scale, S.op_shift, S.a, S.b, S.d, S.coef);
+        T* result = nullptr;
+        ARB_TRY(filter_apply<T>(ctx, mat, plan, B.X, B.ld, S.w, S.xs, B.W1, B.W2, B.ld, nullptr, 0, S.ss, &result));
+        if (result == B.W1) std::swap(B.X, B.W1);
+        else std::swap(B.X, B.W2);
+        ARB_TRY(inv_sqrt(ctx, S.w, S.ss, S.xs));  // column normalisation, applied lazily
+        if (S.nl > 0) ARB_TRY(project_out<T>(ctx, n, B.Qc, B.ld, S.nl, B.X, B.ld, S.w));
+        S.info.n_filters++;
+        S.info.spmm_cols += static_cast<int64_t>(S.d) * S.w;
       }
-      if (o.inner_fixed > 0) break;
+      if (S.o.inner_fixed > 0) break;
       const double rcp = rc;
-      ARB_TRY(rcond_gram(ctx, n, X, ld, w, xs, &rc));
-      if (rc <= tol_t || rc / rcp > 0.99) break;  // eq. inn-stop
+      ARB_TRY(rcond_gram<T>(ctx, n, B.X, B.ld, S.w, S.xs, &rc));
+      if (rc <= rc_thr || rc / rcp > 0.99) break;  // eq. inn-stop
     }
-    ARB_CUDA(ctx, cudaEventRecord(ev1, ctx->stream));
-    ARB_CUDA(ctx, cudaEventSynchronize(ev1));
-    float ms = 0.f;
-    ARB_CUDA(ctx, cudaEventElapsedTime(&ms, ev0, ev1));
-    info.t_filter += ms * 1e-3;
+    ARB_CUDA(ctx, cudaEventRecord(S.ev1, ctx->stream));
+    ARB_CUDA(ctx, cudaEventSynchronize(S.ev1));
+    ARB_CUDA(ctx, cudaEventElapsedTime(&ms, S.ev0, S.ev1));
+    S.info.t_filter += ms * 1e-3;
 
     // ---------------- augmentation + projection + RR (Algorithm 5 inside Algorithm 8)
-    ARB_CUDA(ctx, cudaEventRecord(ev0, ctx->stream));
+    ARB_CUDA(ctx, cudaEventRecord(S.ev0, ctx->stream));
     int32_t m = 0;
-    ARB_TRY(arr_basis_and_eig(ctx, mat, op_scale, op_shift, n, X, ld, w, Qc, ld, nl, q, wk, &m, theta, V));
-    info.last_rank = m;
-    info.spmm_cols += m;
+    ARB_TRY(arr_basis_and_eig<T>(ctx, mat, S.op_scale, S.op_shift, n, B.X, B.ld, S.w, B.Qc, B.ld, S.nl, S.q,
+                                 B.wk, &m, S.theta, S.V));
+    S.info.last_rank = m;
+    S.info.spmm_cols += m;
     // the p leading pairs of (Q_c, Sigma_c) and (U V, theta)
-    ARB_TRY(select_top(ctx, sigc, nl, theta, m, p, imap, mu));
-    ARB_TRY(d2h_sync(ctx, h_map.data(), imap, p * sizeof(int32_t)));
+    ARB_TRY(select_top(ctx, S.sigc, S.nl, S.theta, m, p, S.imap, S.mu));
+    ARB_TRY(d2h_sync(ctx, S.h_map.data(), S.imap, p * sizeof(int32_t)));
     for (int s = 0; s < p; ++s)
-      if (h_map[s] < 0) return set_error(ctx, ARB_BREAKDOWN, "solve: fewer Ritz pairs than the block width");
+      if (S.h_map[s] < 0) return set_error(ctx, ARB_BREAKDOWN, "solve: fewer Ritz pairs than the block width");
     std::vector<int32_t> newcols, src(p);
     for (int s = 0; s < p; ++s) {
-      if (h_map[s] < nl) {
-        src[s] = -h_map[s] - 1;  // locked column
+      if (S.h_map[s] < S.nl) {
+        src[s] = -S.h_map[s] - 1;  // locked column
       } else {
         src[s] = static_cast<int32_t>(newcols.size());
-        newcols.push_back(h_map[s] - nl);
+        newcols.push_back(S.h_map[s] - S.nl);
       }
     }
     const int32_t pn = static_cast<int32_t>(newcols.size());
     if (pn > 0) {
-      ARB_TRY(upload_ints(ctx, iidx, newcols));
-      // V is m x m with leading dimension m (see arr_basis_and_eig call: ldv = m)
-      ARB_TRY(gather_cols(ctx, m, V, m, iidx, pn, Vsel, pn));
-      ARB_TRY(gemm_tall(ctx, n, wk.U, ldm, m, Vsel, pn, pn, 1.0, 0.0, wk.T, ld));
+      ARB_TRY(upload_ints(ctx, S.iidx, newcols));
+      ARB_TRY(gather_cols<double>(ctx, m, S.V, m, S.iidx, pn, S.Vsel, pn));  // V: m x m, ld m
+      ARB_TRY(gemm_tall<T>(ctx, n, B.wk.U, B.ldm, m, S.Vsel, pn, pn, 1.0, 0.0, B.wk.T1, B.ld));
     }
-    ARB_TRY(upload_ints(ctx, imap, src));
-    ARB_TRY(gather_cols2(ctx, n, wk.T, ld, Qc, ld, imap, p, Xall, ld));
+    ARB_TRY(upload_ints(ctx, S.imap, src));
+    ARB_TRY(gather_cols2<T>(ctx, n, B.wk.T1, B.ld, B.Qc, B.ld, S.imap, p, B.Xall, B.ld));
     // residuals (eq. resi): ||B x - mu x|| with the sign folded (-B x + mu x)
     {
-      SpmmArgs s;
-      s.A = mat;
-      s.ncols = p;
-      s.Yin = Xall;
-      s.ldy = ld;
-      s.alpha = -op_scale;
-      s.beta = -op_shift;
-      s.X = Xall;
-      s.ldx = ld;
-      s.sx = mu;
-      s.colred = ss;
-      ARB_TRY(spmm_fused(ctx, s));
-      ARB_TRY(residual_finish(ctx, p, ss, mu, smallest ? 1 : 0, sigma, res));
-      info.spmm_cols += p;
+      SpmmArgs<T> sa;
+      sa.A = mat;
+      sa.ncols = p;
+      sa.Yin = B.Xall;
+      sa.ldy = B.ld;
+      sa.alpha = -S.op_scale;
+      sa.beta = -S.op_shift;
+      sa.X = B.Xall;
+      sa.ldx = B.ld;
+      sa.sx = S.mu;
+      sa.colred = S.ss;
+      ARB_TRY(spmm_fused<T>(ctx, sa));
+      ARB_TRY(residual_finish(ctx, p, S.ss, S.mu, S.smallest ? 1 : 0, S.sigma, S.res));
+      S.info.spmm_cols += p;
     }
-    ARB_TRY(d2h_sync(ctx, h_mu.data(), mu, p * sizeof(double)));
-    ARB_TRY(d2h_sync(ctx, h_res.data(), res, p * sizeof(double)));
-    ARB_CUDA(ctx, cudaEventRecord(ev1, ctx->stream));
-    ARB_CUDA(ctx, cudaEventSynchronize(ev1));
-    ARB_CUDA(ctx, cudaEventElapsedTime(&ms, ev0, ev1));
-    info.t_arr += ms * 1e-3;
+    ARB_TRY(d2h_sync(ctx, S.h_mu.data(), S.mu, p * sizeof(double)));
+    ARB_TRY(d2h_sync(ctx, S.h_res.data(), S.res, p * sizeof(double)));
+    ARB_CUDA(ctx, cudaEventRecord(S.ev1, ctx->stream));
+    ARB_CUDA(ctx, cudaEventSynchronize(S.ev1));
+    ARB_CUDA(ctx, cudaEventElapsedTime(&ms, S.ev0, S.ev1));
+    S.info.t_arr += ms * 1e-3;
 
     // ---------------- outer stop rules, continuation, deflation (Section 5)
     double maxres = 0.0;
     int h = 0;
     for (int i = 0; i < k; ++i) {
-      maxres = std::max(maxres, std::isnan(h_res[i]) ? std::numeric_limits<double>::infinity() : h_res[i]);
-      h += h_res[i] < 0.1 * tol;
+      maxres = std::max(maxres, std::isnan(S.h_res[i]) ? std::numeric_limits<double>::infinity() : S.h_res[i]);
+      h += S.h_res[i] < 0.1 * tol_phase;
     }
-    info.maxres = maxres;
-    if (maxres < best) {
-      best = maxres;
-      best_iter = j;
+    S.info.maxres = maxres;
+    if (maxres < S.best) {
+      S.best = maxres;
+      S.best_iter = j;
     }
-    if (maxres <= tol) {
-      stop = ARB_STOP_CONVERGED;
-      break;
+    if (maxres <= tol_phase) {
+      S.stop = ARB_STOP_CONVERGED;
+      if (continue_on_phase_tol && tol_phase > S.tol) {
+        S.tol_t = std::max(1e-2 * S.tol_t, S.tol);
+        S.b = S.h_mu[p - 1];
+        if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+      }
+      return ARB_OK;
     }
-    if (maxres < (1.0 + 9.0 * h / k) * tol) {
-      stop = ARB_STOP_NEAR_TOL;
-      break;
+    if (maxres < (1.0 + 9.0 * h / k) * tol_phase) {
+      S.stop = ARB_STOP_NEAR_TOL;
+      return ARB_OK;
     }
-    if (j - best_iter >= 3) {
-      stop = ARB_STOP_STALLED;
-      break;
+    if (j - S.best_iter >= 3) {
+      S.stop = ARB_STOP_STALLED;
+      return ARB_OK;
     }
-    if (maxres <= tol_t) {  // continuation, eq. contin
-      tol_t = std::max(1e-2 * tol_t, tol);
-      b = h_mu[p - 1];
-      if (!(b > a)) b = a + 1e-3 * std::max(1.0, std::fabs(a));
+    if (maxres <= S.tol_t) {  // continuation, eq. contin
+      S.tol_t = std::max(1e-2 * S.tol_t, S.tol);
+      S.b = S.h_mu[p - 1];
+      if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
     }
-    const double thr = std::max(1e-14, tol_t * tol_t);  // eq. defl
+    const double thr = std::max(1e-14, S.tol_t * S.tol_t);  // eq. defl
     std::vector<int32_t> lock_idx, free_idx;
-    h_sigc.clear();
+    S.h_sigc.clear();
     for (int s = 0; s < p; ++s) {
-      if (s < k && h_res[s] <= thr) {
+      if (lock && s < k && S.h_res[s] <= thr) {
         lock_idx.push_back(s);
-        h_sigc.push_back(h_mu[s]);
+        S.h_sigc.push_back(S.h_mu[s]);
       } else {
         free_idx.push_back(s);
       }
     }
-    nl = static_cast<int32_t>(lock_idx.size());
-    w = p - nl;
-    if (w == 0) {
-      stop = ARB_STOP_ALL_LOCKED;
-      break;
+    S.nl = static_cast<int32_t>(lock_idx.size());
+    S.w = p - S.nl;
+    if (S.w == 0) {
+      S.stop = ARB_STOP_ALL_LOCKED;
+      return ARB_OK;
     }
-    if (nl > 0) {
-      ARB_TRY(upload_ints(ctx, iidx, lock_idx));
-      ARB_TRY(gather_cols(ctx, n, Xall, ld, iidx, nl, Qc, ld));
-      ARB_TRY(h2d(ctx, sigc, h_sigc.data(), nl * sizeof(double)));
+    if (S.nl > 0) {
+      ARB_TRY(upload_ints(ctx, S.iidx, lock_idx));
+      ARB_TRY(gather_cols<T>(ctx, n, B.Xall, B.ld, S.iidx, S.nl, B.Qc, B.ld));
+      ARB_TRY(h2d(ctx, S.sigc, S.h_sigc.data(), S.nl * sizeof(double)));
     }
-    ARB_TRY(upload_ints(ctx, iidx, free_idx));
-    ARB_TRY(gather_cols(ctx, n, Xall, ld, iidx, w, X, ld));
-    ARB_TRY(fill(ctx, xs, w, 1.0));
+    ARB_TRY(upload_ints(ctx, S.iidx, free_idx));
+    ARB_TRY(gather_cols<T>(ctx, n, B.Xall, B.ld, S.iidx, S.w, B.X, B.ld));
+    ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
   }
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
-  info.outer_iters = std::min(j, o.maxit);
-  info.stop_reason = stop;
-  info.b_final = b;
-  info.n_locked = nl;
+  return ARB_OK;
+}
+
+arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol, const arb_options& o,
+                      const double* x0, int x0_on_device, double* evals, double* evecs, int64_t ldq,
+                      int evecs_on_device, arb_info* info_out) {
+  Timer total;
+  SolveState S;
+  S.o = o;
+  S.n = mat->n;
+  S.k = k;
+  S.p = o.p > 0 ? o.p : k + static_cast<int32_t>(std::lround(0.1 * k));
+  S.q = o.q;
+  S.d = o.degree;
+  S.tol = tol;
+  const int64_t n = S.n;
+  const int32_t p = S.p;
+  if (k <= 0 || k > p || S.q < 0 || S.d < 1 || S.d > 60 || o.maxit < 1 || o.maxit1 < 1 || o.maxit2 < 1 ||
+      static_cast<int64_t>(S.q + 1) * p >= n || !(tol > 0.0))
+    return set_error(ctx, ARB_INVALID_ARG, "solve: need 0 < k <= p, (q+1) p < n, 1 <= degree <= 60, tol > 0");
+  if (o.precision != ARB_FP64 && o.precision != ARB_MIXED)
+    return set_error(ctx, ARB_INVALID_ARG, "solve: unknown precision");
+  if (which != ARB_LARGEST && which != ARB_SMALLEST) return set_error(ctx, ARB_INVALID_ARG, "solve: bad which");
+  if (evecs && ldq < n) return set_error(ctx, ARB_INVALID_ARG, "solve: ldq < n");
+  S.smallest = (which == ARB_SMALLEST);
+  const bool mixed = (o.precision == ARB_MIXED);
+
+  // operator B = op_scale A + op_shift I whose largest eigenpairs are wanted
+  double glo, ghi;
+  ARB_TRY(gershgorin(ctx, mat, &glo, &ghi));
+  if (S.smallest) {
+    S.sigma = std::isnan(o.shift_sigma) ? ghi : o.shift_sigma;
+    S.op_scale = -1.0;
+    S.op_shift = S.sigma;
+    S.a = S.sigma - ghi;  // Gershgorin lower bound of sigma I - A
+  } else {
+    S.a = glo;
+  }
+
+  // device buffers
+  S.mcap = static_cast<int64_t>(S.q + 1) * p;
+  BlockSet<double> D;
+  BlockSet<float> F;
+  ARB_TRY(alloc_blocks<double>(ctx, S, D));
+  if (mixed) {
+    ARB_TRY(alloc_blocks<float>(ctx, S, F));
+    ARB_TRY(ensure_val32(ctx, mat));
+  }
+  ARB_TRY(ws<double>(ctx, WS_S_V, static_cast<size_t>(S.mcap) * S.mcap, &S.V));
+  ARB_TRY(ws<double>(ctx, WS_S_VSEL, static_cast<size_t>(S.mcap) * p, &S.Vsel));
+  double* vec;
+  ARB_TRY(ws<double>(ctx, WS_S_VEC, static_cast<size_t>(S.mcap) + 8 * static_cast<size_t>(p) + 64, &vec));
+  S.theta = vec;
+  S.mu = S.theta + S.mcap;
+  S.sigc = S.mu + p;
+  S.ss = S.sigc + p;
+  S.res = S.ss + p;
+  S.xs = S.res + p;
+  S.imap = reinterpret_cast<int32_t*>(S.xs + p);
+  S.iidx = S.imap + p + (p & 1);
+  S.sgn = reinterpret_cast<double*>(S.iidx + p + (p & 1));
+  S.h_mu.resize(p);
+  S.h_res.resize(p);
+  S.h_map.resize(p);
+
+  // start block X0 (Algorithm 8: i.i.d. Gaussian n x (k+q)), held in the FP64 iterate
+  if (x0) {
+    ARB_CUDA(ctx, cudaMemcpy2DAsync(D.X, D.ld * sizeof(double), x0, p * sizeof(double), p * sizeof(double), n,
+                                    x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    ctx->stream));
+  } else {
+    ARB_TRY(gaussian_fill(ctx, n, p, o.seed, D.X, D.ld));
+  }
+
+  // b: smallest Ritz value of orth(X0) (Section 5, "Estimation of lambda_n and lambda_{k+q}")
+  {
+    int32_t r = 0;
+    ARB_TRY(orth<double>(ctx, n, D.X, D.ld, p, D.wk.U, D.ldm, D.wk.T1, D.ld, &r));
+    if (r == 0) return set_error(ctx, ARB_BREAKDOWN, "solve: start block has no numerical rank");
+    SpmmArgs<double> sa;
+    sa.A = mat;
+    sa.ncols = r;
+    sa.Yin = D.wk.U;
+    sa.ldy = D.ldm;
+    sa.alpha = S.op_scale;
+    sa.beta = S.op_shift;
+    sa.out = D.wk.AU;
+    sa.ldo = D.ldm;
+    ARB_TRY(spmm_fused<double>(ctx, sa));
+    double* H;
+    ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(r) * r, &H));
+    ARB_TRY(gram<double>(ctx, n, D.wk.U, D.ldm, r, D.wk.AU, D.ldm, r, H, r));
+    ARB_TRY(symmetrize(ctx, r, H, r));
+    ARB_TRY(syevj(ctx, r, H, r, S.theta, S.V, r, nullptr));
+    ARB_TRY(d2h_sync(ctx, &S.b, S.theta + (r - 1), sizeof(double)));
+    S.info.spmm_cols += r;
+  }
+  S.info.a = S.a;
+  S.info.b0 = S.b;
+  S.info.sigma = S.sigma;
+  if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+
+  if (arb_filter_coefficients(o.filter, S.d, S.coef) != ARB_OK)
+    return set_error(ctx, ARB_INVALID_ARG, "solve: bad filter kind");
+  const double tol1 = o.tol1 > 0.0 ? o.tol1 : (tol <= 1e-8 ? std::max(1e-6, tol) : tol);
+  S.tol_t = std::max(tol1, tol);
+  S.w = p;
+  S.nl = 0;
+  ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
+  ARB_CUDA(ctx, cudaEventCreate(&S.ev0));
+  ARB_CUDA(ctx, cudaEventCreate(&S.ev1));
+  struct EvGuard {
+    SolveState& s;
+    ~EvGuard() {
+      if (s.ev0) cudaEventDestroy(s.ev0);
+      if (s.ev1) cudaEventDestroy(s.ev1);
+    }
+  } guard{S};
+
+  if (mixed) {
+    // Phase 1: FP32 blocks until the continuation tolerance of the FP32 phase is met
+    // (reading c7: inner-stop threshold >= 100 u32; precision switches when continuation
+    // tightens tol_t below what FP32 resolves).
+    const double sw = o.tol_switch > 0.0 ? o.tol_switch : 1e-5;
+    const double tol_phase = std::max(sw, tol);
+    S.tol_t = std::max(S.tol_t, tol_phase);
+    ARB_TRY((copy_block<double, float>(ctx, n, D.X, D.ld, p, F.X, F.ld)));
+    ARB_TRY(run_outer<float>(ctx, mat, S, F, tol_phase, 100.0 * 5.96e-8, false, true));
+    S.info.outer_iters_fp32 = S.info.outer_iters;
+    const bool done32 = (S.stop == ARB_STOP_CONVERGED || S.stop == ARB_STOP_NEAR_TOL) && tol_phase <= tol;
+    // Phase 2: FP64 refinement from the FP32 Ritz block (Algorithm 8 continued in FP64)
+    ARB_TRY((copy_block<float, double>(ctx, n, F.Xall, F.ld, p, D.Xall, D.ld)));
+    if (!done32) {
+      ARB_TRY((copy_block<double, double>(ctx, n, D.Xall, D.ld, p, D.X, D.ld)));
+      S.w = p;
+      S.nl = 0;
+      ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
+      ARB_TRY(run_outer<double>(ctx, mat, S, D, tol, 0.0, true, false));
+    }
+  } else {
+    ARB_TRY(run_outer<double>(ctx, mat, S, D, tol, 0.0, true, false));
+  }
+  S.info.stop_reason = S.stop;
+  S.info.b_final = S.b;
+  S.info.n_locked = S.nl;
 
   // ---------------- outputs: Rayleigh quotients on A, order, sign, column-major copy
   {
-    SpmmArgs s;
-    s.A = mat;
-    s.ncols = k;
-    s.Yin = Xall;
-    s.ldy = ld;
-    s.alpha = 1.0;
-    s.beta = 0.0;
-    s.colred = ss;
-    s.dot_with_yin = true;
-    ARB_TRY(spmm_fused(ctx, s));
-    info.spmm_cols += k;
+    SpmmArgs<double> sa;
+    sa.A = mat;
+    sa.ncols = k;
+    sa.Yin = D.Xall;
+    sa.ldy = D.ld;
+    sa.alpha = 1.0;
+    sa.beta = 0.0;
+    sa.colred = S.ss;
+    sa.dot_with_yin = true;
+    ARB_TRY(spmm_fused<double>(ctx, sa));
+    S.info.spmm_cols += k;
   }
   std::vector<double> rq(k);
-  ARB_TRY(d2h_sync(ctx, rq.data(), ss, k * sizeof(double)));
+  ARB_TRY(d2h_sync(ctx, rq.data(), S.ss, k * sizeof(double)));
   std::vector<int32_t> perm(k);
   for (int i = 0; i < k; ++i) perm[i] = i;
-  std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return smallest ? rq[x] < rq[y] : rq[x] > rq[y]; });
+  std::stable_sort(perm.begin(), perm.end(),
+                   [&](int x, int y) { return S.smallest ? rq[x] < rq[y] : rq[x] > rq[y]; });
   if (evals)
     for (int i = 0; i < k; ++i) evals[i] = rq[perm[i]];
   if (evecs) {
-    ARB_TRY(column_signs(ctx, n, Xall, ld, p, sgn));
+    ARB_TRY(column_signs(ctx, n, D.Xall, D.ld, p, S.sgn));
     std::vector<double> hs(p);
-    ARB_TRY(d2h_sync(ctx, hs.data(), sgn, p * sizeof(double)));
+    ARB_TRY(d2h_sync(ctx, hs.data(), S.sgn, p * sizeof(double)));
     std::vector<double> sgn_perm(k);
     for (int i = 0; i < k; ++i) sgn_perm[i] = hs[perm[i]];
-    ARB_TRY(upload_ints(ctx, iidx, perm));
-    ARB_TRY(h2d(ctx, res, sgn_perm.data(), k * sizeof(double)));
+    ARB_TRY(upload_ints(ctx, S.iidx, perm));
+    ARB_TRY(h2d(ctx, S.res, sgn_perm.data(), k * sizeof(double)));
     if (evecs_on_device) {
-      ARB_TRY(write_colmajor(ctx, n, Xall, ld, iidx, res, k, evecs, ldq));
+      ARB_TRY(write_colmajor(ctx, n, D.Xall, D.ld, S.iidx, S.res, k, evecs, ldq));
     } else {
       // stage through a device block (W1 is free now), then one strided copy to the host
-      ARB_TRY(write_colmajor(ctx, n, Xall, ld, iidx, res, k, W1, n));
-      ARB_CUDA(ctx, cudaMemcpy2DAsync(evecs, ldq * sizeof(double), W1, n * sizeof(double), n * sizeof(double), k,
+      ARB_TRY(write_colmajor(ctx, n, D.Xall, D.ld, S.iidx, S.res, k, D.W1, n));
+      ARB_CUDA(ctx, cudaMemcpy2DAsync(evecs, ldq * sizeof(double), D.W1, n * sizeof(double), n * sizeof(double), k,
                                       cudaMemcpyDeviceToHost, ctx->stream));
     }
   }
   ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  info.t_total = total.sec();
-  if (info_out) *info_out = info;
-  const bool ok = (stop == ARB_STOP_CONVERGED || stop == ARB_STOP_NEAR_TOL);
+  S.info.t_total = total.sec();
+  if (info_out) *info_out = S.info;
+  const bool ok = (S.stop == ARB_STOP_CONVERGED || S.stop == ARB_STOP_NEAR_TOL);
   return ok ? ARB_OK : ARB_NOT_CONVERGED;
 }
 

@@ -44,6 +44,14 @@ enum WsSlot : int {
   WS_S_V,             // solver: eigenvectors of H, selected columns
   WS_S_VSEL,
   WS_S_VEC,           // solver: short per-column vectors
+  WS_F32_X,           // mixed-precision solver: FP32 iterate, work blocks and bases
+  WS_F32_W1,
+  WS_F32_W2,
+  WS_F32_XALL,
+  WS_F32_U,
+  WS_F32_AU,
+  WS_F32_T,
+  WS_F32_T2,
   WS_NUM_SLOTS
 };
 
@@ -70,6 +78,7 @@ struct arb_mat_s {
   int32_t* rowptr = nullptr;
   int32_t* col = nullptr;
   double* val = nullptr;
+  float* val32 = nullptr;  // FP32 copy of val for the mixed-precision filter (made on demand)
   bool gersh_valid = false;
   double gersh_lo = 0.0, gersh_hi = 0.0;
 };
@@ -112,28 +121,33 @@ arb_status host_stage(arb_ctx ctx, size_t bytes, void** out);
 arb_status d2h_sync(arb_ctx ctx, void* host, const void* dev, size_t bytes);
 
 // ---------------------------------------------------------------- kernels (spmm.cu)
-// out = sy[c] * (alpha * (A Yin) + beta * Yin) + sx[c] * X + sz[c] * Z, row-major blocks.
+// out = sy[c] * (alpha * (A Yin) + beta * Yin) + sx[c] * X + sz[c] * Z, row-major blocks of
+// element type T (float64 path or the FP32 filter of the mixed path).
 // Optional outputs: `out` (skipped when NULL) and per-column reductions into `colred`
-// (sum over rows of out^2, or of out * Yin when dot_with_yin).
+// (FP64 sums over rows of out^2, or of out * Yin when dot_with_yin).
+template <typename T>
 struct SpmmArgs {
   const arb_mat_s* A = nullptr;
   int32_t ncols = 0;
-  const double* Yin = nullptr;
+  const T* Yin = nullptr;
   int64_t ldy = 0;
   double alpha = 1.0, beta = 0.0;
   const double* sy = nullptr;  // NULL: 1
-  const double* X = nullptr;
+  const T* X = nullptr;
   int64_t ldx = 0;
   const double* sx = nullptr;  // required when X != NULL
-  const double* Z = nullptr;
+  const T* Z = nullptr;
   int64_t ldz = 0;
   const double* sz = nullptr;  // required when Z != NULL
-  double* out = nullptr;
+  T* out = nullptr;
   int64_t ldo = 0;
   double* colred = nullptr;    // float64[ncols] result of the column reduction, or NULL
   bool dot_with_yin = false;
 };
-arb_status spmm_fused(arb_ctx ctx, const SpmmArgs& a);
+template <typename T>
+arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a);
+// FP32 copy of A's values (kept with the matrix).
+arb_status ensure_val32(arb_ctx ctx, arb_mat mat);
 
 // Gershgorin lower/upper bound of A into host doubles.
 arb_status gershgorin(arb_ctx ctx, arb_mat mat, double* lo, double* hi);
@@ -143,19 +157,29 @@ arb_status col_sumsq(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32
                      double* out);
 
 // ---------------------------------------------------------------- kernels (dense.cu)
-// C (na x nb, ldc) = X^T Y over n rows; deterministic split-K.  symmetric: X == Y.
-arb_status gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
-                const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
-// Out (n x nb) = alpha * In (n x na) * W (na x nb, ldw) + beta * Out.  Out must not alias In.
-arb_status gemm_tall(arb_ctx ctx, int64_t n, const double* In, int64_t ldi, int32_t na,
-                     const double* W, int64_t ldw, int32_t nb, double alpha, double beta,
-                     double* Out, int64_t ldo);
+// C (na x nb, ldc, FP64) = X^T Y over n rows of element type T; deterministic split-K.
+// FP32 inputs are multiplied and summed in FP32 over runs of 64 rows and the run sums are
+// added in FP64.  symmetric: X == Y.
+template <typename T>
+arb_status gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t na, const T* Y, int64_t ldy,
+                int32_t nb, double* C, int64_t ldc);
+// Out (n x nb) = alpha * In (n x na) * W (na x nb, FP64, ldw) + beta * Out, accumulated in T.
+// Out must not alias In.
+template <typename T>
+arb_status gemm_tall(arb_ctx ctx, int64_t n, const T* In, int64_t ldi, int32_t na, const double* W,
+                     int64_t ldw, int32_t nb, double alpha, double beta, T* Out, int64_t ldo);
 // dst[:, j] = src[:, idx[j]] for j < ncols (idx on device)
-arb_status gather_cols(arb_ctx ctx, int64_t n, const double* src, int64_t lds,
-                       const int32_t* idx, int32_t ncols, double* dst, int64_t ldd);
+template <typename T>
+arb_status gather_cols(arb_ctx ctx, int64_t n, const T* src, int64_t lds, const int32_t* idx,
+                       int32_t ncols, T* dst, int64_t ldd);
 // dst[:, j] = idx[j] >= 0 ? srcA[:, idx[j]] : srcB[:, -idx[j]-1]
-arb_status gather_cols2(arb_ctx ctx, int64_t n, const double* srcA, int64_t ldA, const double* srcB,
-                        int64_t ldB, const int32_t* idx, int32_t ncols, double* dst, int64_t ldd);
+template <typename T>
+arb_status gather_cols2(arb_ctx ctx, int64_t n, const T* srcA, int64_t ldA, const T* srcB, int64_t ldB,
+                        const int32_t* idx, int32_t ncols, T* dst, int64_t ldd);
+// dst = src (n x ncols), converting the element type
+template <typename Ti, typename To>
+arb_status copy_block(arb_ctx ctx, int64_t n, const Ti* src, int64_t lds, int32_t ncols, To* dst,
+                      int64_t ldd);
 // res[c] = sqrt(ss[c]) / max(1, |lambda_c|), lambda_c = smallest ? sigma - mu_c : mu_c
 arb_status residual_finish(arb_ctx ctx, int32_t p, const double* ss, const double* mu, int smallest,
                            double sigma, double* res);
@@ -165,9 +189,6 @@ arb_status column_signs(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, in
 // evecs[c * ldq + i] = sign[c] * X[i * ldx + perm[c]]  (column-major output)
 arb_status write_colmajor(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, const int32_t* perm,
                           const double* sign, int32_t k, double* out, int64_t ldq);
-// dst = src (n x ncols)
-arb_status copy_block(arb_ctx ctx, int64_t n, const double* src, int64_t lds, int32_t ncols,
-                      double* dst, int64_t ldd);
 arb_status fill(arb_ctx ctx, double* p, int64_t count, double v);
 // H <- (H + H^T)/2 for an m x m row-major matrix
 arb_status symmetrize(arb_ctx ctx, int32_t m, double* H, int64_t ldh);
@@ -211,37 +232,41 @@ FilterPlan make_filter_plan(double op_scale, double op_shift, double a, double b
 // Y = psi_d(S) (X diag(xscale)); W1, W2: n x ncols work blocks (ldw); Y may be NULL, in
 // which case the result overwrites one of W1/W2 and *result points at it.  colss: column
 // sums of squares of the result (device, may be NULL).
-arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const double* X,
-                        int64_t ldx, int32_t ncols, const double* xscale, double* W1,
-                        double* W2, int64_t ldw, double* Y, int64_t ldy, double* colss,
-                        double** result);
+template <typename T>
+arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const T* X, int64_t ldx,
+                        int32_t ncols, const double* xscale, T* W1, T* W2, int64_t ldw, T* Y,
+                        int64_t ldy, double* colss, T** result);
 
 // Orthonormal basis of range(Z) (two eigen-truncated Gram passes).  U must not alias Z.
 // tmp: n x m work block.  *rank on host.
-arb_status orth(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz, int32_t m, double* U,
-                int64_t ldu, double* tmp, int64_t ldt, int32_t* rank);
+template <typename T>
+arb_status orth(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* U, int64_t ldu, T* tmp,
+                int64_t ldt, int32_t* rank);
 
 // Reciprocal 1-norm condition number of diag(xs) X^T X diag(xs) (host result).
-arb_status rcond_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
-                      const double* xs, double* rc);
+template <typename T>
+arb_status rcond_gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t ncols, const double* xs,
+                      double* rc);
 
 // X <- X - Q (Q^T X)
-arb_status project_out(arb_ctx ctx, int64_t n, const double* Q, int64_t ldq, int32_t nq,
-                       double* X, int64_t ldx, int32_t ncols);
+template <typename T>
+arb_status project_out(arb_ctx ctx, int64_t n, const T* Q, int64_t ldq, int32_t nq, T* X, int64_t ldx,
+                       int32_t ncols);
 
 // Block-Krylov Rayleigh-Ritz: U holds an orthonormal basis of span[X, BX, ..., B^q X]
 // (projected against Qc), AU = B U, then H = U^T AU is diagonalised.
 // Outputs: *m (subspace dimension, host), theta (device, m, descending), V (device m x m,
 // row-major with leading dimension m; column j is the eigenvector of theta_j).
+template <typename T>
 struct ArrWork {
-  double* U = nullptr;  int64_t ldu = 0;   // n x mcap
-  double* AU = nullptr; int64_t ldau = 0;  // n x mcap
-  double* T = nullptr;  int64_t ldt = 0;   // n x w
-  double* T2 = nullptr; int64_t ldt2 = 0;  // n x w
+  T* U = nullptr;  int64_t ldu = 0;   // n x mcap
+  T* AU = nullptr; int64_t ldau = 0;  // n x mcap
+  T* T1 = nullptr; int64_t ldt = 0;   // n x w
+  T* T2 = nullptr; int64_t ldt2 = 0;  // n x w
 };
-arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift,
-                             int64_t n, double* X, int64_t ldx, int32_t w, const double* Qc,
-                             int64_t ldqc, int32_t nl, int32_t q, const ArrWork& wk,
-                             int32_t* m_out, double* theta, double* V);
+template <typename T>
+arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, int64_t n, T* X,
+                             int64_t ldx, int32_t w, const T* Qc, int64_t ldqc, int32_t nl, int32_t q,
+                             const ArrWork<T>& wk, int32_t* m_out, double* theta, double* V);
 
 }  // namespace arb

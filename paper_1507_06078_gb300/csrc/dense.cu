@@ -18,34 +18,39 @@ constexpr int KSTEP = 16;
 
 // part[s][i][j] = sum over the rows of split s of X[r][i] * Y[r][j].  One (16R)x(16R) tile
 // per CTA of 256 threads, each thread owning R x R outputs strided by 16 (R = 1, 2, 4 so
-// that small blocks do not pay for a 64-wide tile of FP64 multiply-adds).
-template <int R>
+// that small blocks do not pay for a 64-wide tile of FP64 multiply-adds).  For FP32
+// inputs the products are summed in FP32 over runs of 64 rows and the run sums in FP64:
+// a run's rounding error is ~64 u32 of its own (short) sum, so an n-row Gram entry is
+// accurate to ~64 u32 / sqrt(n) relative (~3e-9 at n = 2M) instead of ~u32 sqrt(n).
+template <typename T, int R>
 __global__ void __launch_bounds__(256)
-gram_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int na,
-            const double* __restrict__ Y, int64_t ldy, int nb, int64_t rows_per_split,
-            int symmetric, double* __restrict__ part) {
-  constexpr int T = 16 * R;
+gram_kernel(int64_t n, const T* __restrict__ X, int64_t ldx, int na, const T* __restrict__ Y,
+            int64_t ldy, int nb, int64_t rows_per_split, int symmetric, double* __restrict__ part) {
+  constexpr int TT = 16 * R;
+  constexpr int FLUSH = 4;  // k-steps (of 16 rows) per FP32 run
   const int ti = blockIdx.x, tj = blockIdx.y, s = blockIdx.z;
   if (symmetric && tj < ti) return;
-  __shared__ double Xs[KSTEP][T + 1];
-  __shared__ double Ys[KSTEP][T + 1];
+  __shared__ T Xs[KSTEP][TT + 1];
+  __shared__ T Ys[KSTEP][TT + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = ti * T, j0 = tj * T;
+  const int i0 = ti * TT, j0 = tj * TT;
   const int64_t r0 = s * rows_per_split;
   const int64_t r1 = min(n, r0 + rows_per_split);
   double acc[R][R] = {};
+  T accT[R][R] = {};
+  int steps = 0;
   for (int64_t rb = r0; rb < r1; rb += KSTEP) {
-    for (int t = threadIdx.x; t < KSTEP * T; t += 256) {
-      const int rr = t / T, cc = t % T;
+    for (int t = threadIdx.x; t < KSTEP * TT; t += 256) {
+      const int rr = t / TT, cc = t % TT;
       const int64_t r = rb + rr;
       const bool rok = r < r1;
-      Xs[rr][cc] = (rok && i0 + cc < na) ? X[r * ldx + i0 + cc] : 0.0;
-      Ys[rr][cc] = (rok && j0 + cc < nb) ? Y[r * ldy + j0 + cc] : 0.0;
+      Xs[rr][cc] = (rok && i0 + cc < na) ? X[r * ldx + i0 + cc] : T(0);
+      Ys[rr][cc] = (rok && j0 + cc < nb) ? Y[r * ldy + j0 + cc] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < KSTEP; ++k) {
-      double a[R], b[R];
+      T a[R], b[R];
 #pragma unroll
       for (int u = 0; u < R; ++u) {
         a[u] = Xs[k][ty + 16 * u];
@@ -54,10 +59,24 @@ gram_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int na,
 #pragma unroll
       for (int u = 0; u < R; ++u)
 #pragma unroll
-        for (int v = 0; v < R; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        for (int v = 0; v < R; ++v) accT[u][v] = fma(a[u], b[v], accT[u][v]);
     }
     __syncthreads();
+    if (sizeof(T) == 4 && ++steps == FLUSH) {
+      steps = 0;
+#pragma unroll
+      for (int u = 0; u < R; ++u)
+#pragma unroll
+        for (int v = 0; v < R; ++v) {
+          acc[u][v] += static_cast<double>(accT[u][v]);
+          accT[u][v] = T(0);
+        }
+    }
   }
+#pragma unroll
+  for (int u = 0; u < R; ++u)
+#pragma unroll
+    for (int v = 0; v < R; ++v) acc[u][v] += static_cast<double>(accT[u][v]);
   double* P = part + static_cast<size_t>(s) * na * nb;
 #pragma unroll
   for (int u = 0; u < R; ++u) {
@@ -87,33 +106,33 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nsplit, 
 }
 
 // Out[r][c] = alpha * sum_k In[r][k] W[k][c] + beta * Out[r][c]; a 64 x (16 RN) output tile
-// per CTA, each thread owning 4 x RN outputs.
-template <int RN>
+// per CTA, each thread owning 4 x RN outputs; W (FP64) is rounded to T as it is staged.
+template <typename T, int RN>
 __global__ void __launch_bounds__(256)
-gemm_tall_kernel(int64_t n, const double* __restrict__ In, int64_t ldi, int na,
-                 const double* __restrict__ W, int64_t ldw, int nb, double alpha, double beta,
-                 double* __restrict__ Out, int64_t ldo) {
+gemm_tall_kernel(int64_t n, const T* __restrict__ In, int64_t ldi, int na, const double* __restrict__ W,
+                 int64_t ldw, int nb, T alpha, T beta, T* __restrict__ Out, int64_t ldo) {
   constexpr int TR = 64, TC = 16 * RN;
-  __shared__ double Is[KSTEP][TR + 1];
-  __shared__ double Ws[KSTEP][TC + 1];
+  __shared__ T Is[KSTEP][TR + 1];
+  __shared__ T Ws[KSTEP][TC + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TR;
   const int c0 = blockIdx.y * TC;
-  double acc[4][RN] = {};
+  T acc[4][RN] = {};
   for (int k0 = 0; k0 < na; k0 += KSTEP) {
     for (int t = threadIdx.x; t < KSTEP * TR; t += 256) {
       const int kk = t % KSTEP, rr = t / KSTEP;
       const int64_t r = r0 + rr;
-      Is[kk][rr] = (r < n && k0 + kk < na) ? In[r * ldi + k0 + kk] : 0.0;
+      Is[kk][rr] = (r < n && k0 + kk < na) ? In[r * ldi + k0 + kk] : T(0);
     }
     for (int t = threadIdx.x; t < KSTEP * TC; t += 256) {
       const int kw = t / TC, cw = t % TC;
-      Ws[kw][cw] = (k0 + kw < na && c0 + cw < nb) ? W[static_cast<int64_t>(k0 + kw) * ldw + c0 + cw] : 0.0;
+      Ws[kw][cw] = (k0 + kw < na && c0 + cw < nb) ? static_cast<T>(W[static_cast<int64_t>(k0 + kw) * ldw + c0 + cw])
+                                                  : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < KSTEP; ++k) {
-      double a[4], b[RN];
+      T a[4], b[RN];
 #pragma unroll
       for (int u = 0; u < 4; ++u) a[u] = Is[k][ty + 16 * u];
 #pragma unroll
@@ -133,16 +152,17 @@ gemm_tall_kernel(int64_t n, const double* __restrict__ In, int64_t ldi, int na,
     for (int v = 0; v < RN; ++v) {
       const int c = c0 + tx + 16 * v;
       if (c >= nb) continue;
-      double* o = Out + r * ldo + c;
-      const double val = alpha * acc[u][v];
-      *o = (beta == 0.0) ? val : fma(beta, *o, val);
+      T* o = Out + r * ldo + c;
+      const T val = alpha * acc[u][v];
+      *o = (beta == T(0)) ? val : fma(beta, *o, val);
     }
   }
 }
 
-__global__ void gather_cols_kernel(int64_t n, const double* __restrict__ src, int64_t lds,
-                                   const int32_t* __restrict__ idx, int ncols,
-                                   double* __restrict__ dst, int64_t ldd) {
+template <typename T>
+__global__ void gather_cols_kernel(int64_t n, const T* __restrict__ src, int64_t lds,
+                                   const int32_t* __restrict__ idx, int ncols, T* __restrict__ dst,
+                                   int64_t ldd) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= n * ncols) return;
   const int64_t r = t / ncols;
@@ -150,10 +170,11 @@ __global__ void gather_cols_kernel(int64_t n, const double* __restrict__ src, in
   dst[r * ldd + c] = src[r * lds + idx[c]];
 }
 
-__global__ void gather_cols2_kernel(int64_t n, const double* __restrict__ srcA, int64_t ldA,
-                                    const double* __restrict__ srcB, int64_t ldB,
-                                    const int32_t* __restrict__ idx, int ncols,
-                                    double* __restrict__ dst, int64_t ldd) {
+template <typename T>
+__global__ void gather_cols2_kernel(int64_t n, const T* __restrict__ srcA, int64_t ldA,
+                                    const T* __restrict__ srcB, int64_t ldB,
+                                    const int32_t* __restrict__ idx, int ncols, T* __restrict__ dst,
+                                    int64_t ldd) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= n * ncols) return;
   const int64_t r = t / ncols;
@@ -212,13 +233,14 @@ __global__ void write_colmajor_kernel(int64_t n, const double* __restrict__ X, i
   out[c * ldq + r] = sign[c] * X[r * ldx + perm[c]];
 }
 
-__global__ void copy_block_kernel(int64_t n, const double* __restrict__ src, int64_t lds, int ncols,
-                                  double* __restrict__ dst, int64_t ldd) {
+template <typename Ti, typename To>
+__global__ void copy_block_kernel(int64_t n, const Ti* __restrict__ src, int64_t lds, int ncols,
+                                  To* __restrict__ dst, int64_t ldd) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= n * ncols) return;
   const int64_t r = t / ncols;
   const int c = static_cast<int>(t % ncols);
-  dst[r * ldd + c] = src[r * lds + c];
+  dst[r * ldd + c] = static_cast<To>(src[r * lds + c]);
 }
 
 __global__ void fill_kernel(double* p, int64_t count, double v) {
@@ -402,14 +424,15 @@ inline int blocks_for(int64_t count, int threads) {
 
 }  // namespace
 
-arb_status gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
-                const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc) {
+template <typename T>
+arb_status gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t na, const T* Y, int64_t ldy,
+                int32_t nb, double* C, int64_t ldc) {
   if (na <= 0 || nb <= 0) return ARB_OK;
   const int symmetric = (X == Y && ldx == ldy && na == nb) ? 1 : 0;
   const int mx = std::max(na, nb);
   const int R = mx <= 16 ? 1 : (mx <= 32 ? 2 : 4);
-  const int T = 16 * R;
-  const int gi = (na + T - 1) / T, gj = (nb + T - 1) / T;
+  const int TT = 16 * R;
+  const int gi = (na + TT - 1) / TT, gj = (nb + TT - 1) / TT;
   const int tiles = symmetric ? gi * (gi + 1) / 2 : gi * gj;
   const int64_t target = static_cast<int64_t>(ctx->num_sms) * 3;
   int64_t nsplit = std::max<int64_t>(1, (target + tiles - 1) / tiles);
@@ -421,19 +444,22 @@ arb_status gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na
   double* part;
   ARB_TRY(ws<double>(ctx, WS_GRAM_PART, static_cast<size_t>(nsplit) * na * nb, &part));
   dim3 grid(gi, gj, static_cast<unsigned>(nsplit));
-  if (R == 1) gram_kernel<1><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
-  else if (R == 2) gram_kernel<2><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
-  else gram_kernel<4><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+  if (R == 1)
+    gram_kernel<T, 1><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+  else if (R == 2)
+    gram_kernel<T, 2><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+  else
+    gram_kernel<T, 4><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
   ARB_LAUNCHED(ctx);
   gram_reduce_kernel<<<blocks_for(static_cast<int64_t>(na) * nb, 256), 256, 0, ctx->stream>>>(
-      part, static_cast<int>(nsplit), na, nb, symmetric, T, C, ldc);
+      part, static_cast<int>(nsplit), na, nb, symmetric, TT, C, ldc);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
 
-arb_status gemm_tall(arb_ctx ctx, int64_t n, const double* In, int64_t ldi, int32_t na,
-                     const double* W, int64_t ldw, int32_t nb, double alpha, double beta,
-                     double* Out, int64_t ldo) {
+template <typename T>
+arb_status gemm_tall(arb_ctx ctx, int64_t n, const T* In, int64_t ldi, int32_t na, const double* W,
+                     int64_t ldw, int32_t nb, double alpha, double beta, T* Out, int64_t ldo) {
   if (n <= 0 || nb <= 0) return ARB_OK;
   if (na <= 0) {
     if (beta == 1.0) return ARB_OK;
@@ -442,29 +468,67 @@ arb_status gemm_tall(arb_ctx ctx, int64_t n, const double* In, int64_t ldi, int3
   const int RN = nb <= 16 ? 1 : (nb <= 32 ? 2 : 4);
   const int TC = 16 * RN;
   dim3 grid(static_cast<unsigned>((n + 63) / 64), static_cast<unsigned>((nb + TC - 1) / TC));
-  if (RN == 1) gemm_tall_kernel<1><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
-  else if (RN == 2) gemm_tall_kernel<2><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
-  else gemm_tall_kernel<4><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
+  const T al = static_cast<T>(alpha), be = static_cast<T>(beta);
+  if (RN == 1)
+    gemm_tall_kernel<T, 1><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, al, be, Out, ldo);
+  else if (RN == 2)
+    gemm_tall_kernel<T, 2><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, al, be, Out, ldo);
+  else
+    gemm_tall_kernel<T, 4><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, al, be, Out, ldo);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
 
-arb_status gather_cols(arb_ctx ctx, int64_t n, const double* src, int64_t lds, const int32_t* idx,
-                       int32_t ncols, double* dst, int64_t ldd) {
+template <typename T>
+arb_status gather_cols(arb_ctx ctx, int64_t n, const T* src, int64_t lds, const int32_t* idx, int32_t ncols,
+                       T* dst, int64_t ldd) {
   if (ncols <= 0 || n <= 0) return ARB_OK;
-  gather_cols_kernel<<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, idx, ncols, dst, ldd);
+  gather_cols_kernel<T><<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, idx, ncols, dst, ldd);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
 
-arb_status gather_cols2(arb_ctx ctx, int64_t n, const double* srcA, int64_t ldA, const double* srcB,
-                        int64_t ldB, const int32_t* idx, int32_t ncols, double* dst, int64_t ldd) {
+template <typename T>
+arb_status gather_cols2(arb_ctx ctx, int64_t n, const T* srcA, int64_t ldA, const T* srcB, int64_t ldB,
+                        const int32_t* idx, int32_t ncols, T* dst, int64_t ldd) {
   if (ncols <= 0 || n <= 0) return ARB_OK;
-  gather_cols2_kernel<<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, srcA, ldA, srcB, ldB, idx,
-                                                                           ncols, dst, ldd);
+  gather_cols2_kernel<T><<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, srcA, ldA, srcB, ldB, idx,
+                                                                              ncols, dst, ldd);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
+
+template <typename Ti, typename To>
+arb_status copy_block(arb_ctx ctx, int64_t n, const Ti* src, int64_t lds, int32_t ncols, To* dst, int64_t ldd) {
+  if (ncols <= 0 || n <= 0) return ARB_OK;
+  copy_block_kernel<Ti, To><<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+template arb_status gram<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, const double*, int64_t,
+                                 int32_t, double*, int64_t);
+template arb_status gram<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, const float*, int64_t,
+                                int32_t, double*, int64_t);
+template arb_status gemm_tall<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, const double*, int64_t,
+                                      int32_t, double, double, double*, int64_t);
+template arb_status gemm_tall<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, const double*, int64_t,
+                                     int32_t, double, double, float*, int64_t);
+template arb_status gather_cols<double>(arb_ctx, int64_t, const double*, int64_t, const int32_t*, int32_t,
+                                        double*, int64_t);
+template arb_status gather_cols<float>(arb_ctx, int64_t, const float*, int64_t, const int32_t*, int32_t, float*,
+                                       int64_t);
+template arb_status gather_cols2<double>(arb_ctx, int64_t, const double*, int64_t, const double*, int64_t,
+                                         const int32_t*, int32_t, double*, int64_t);
+template arb_status gather_cols2<float>(arb_ctx, int64_t, const float*, int64_t, const float*, int64_t,
+                                        const int32_t*, int32_t, float*, int64_t);
+template arb_status copy_block<double, double>(arb_ctx, int64_t, const double*, int64_t, int32_t, double*,
+                                               int64_t);
+template arb_status copy_block<float, float>(arb_ctx, int64_t, const float*, int64_t, int32_t, float*, int64_t);
+template arb_status copy_block<float, double>(arb_ctx, int64_t, const float*, int64_t, int32_t, double*,
+                                              int64_t);
+template arb_status copy_block<double, float>(arb_ctx, int64_t, const double*, int64_t, int32_t, float*,
+                                              int64_t);
 
 arb_status residual_finish(arb_ctx ctx, int32_t p, const double* ss, const double* mu, int smallest,
                            double sigma, double* res) {
@@ -490,13 +554,6 @@ arb_status write_colmajor(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, 
   return ARB_OK;
 }
 
-arb_status copy_block(arb_ctx ctx, int64_t n, const double* src, int64_t lds, int32_t ncols,
-                      double* dst, int64_t ldd) {
-  if (ncols <= 0 || n <= 0) return ARB_OK;
-  copy_block_kernel<<<blocks_for(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
-  ARB_LAUNCHED(ctx);
-  return ARB_OK;
-}
 
 arb_status fill(arb_ctx ctx, double* p, int64_t count, double v) {
   if (count <= 0) return ARB_OK;

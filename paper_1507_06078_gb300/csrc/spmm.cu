@@ -19,50 +19,78 @@ namespace {
 constexpr int SPMM_THREADS = 256;
 constexpr int SPMM_WARPS = SPMM_THREADS / 32;
 
+template <typename T>
 struct KParams {
   int64_t n;
   const int32_t* rowptr;
   const int32_t* col;
-  const double* val;
+  const T* val;
   int32_t ncols;
-  const double* Yin;
+  const T* Yin;
   int64_t ldy;
-  double alpha, beta;
+  T alpha, beta;
   const double* sy;
-  const double* X;
+  const T* X;
   int64_t ldx;
   const double* sx;
-  const double* Z;
+  const T* Z;
   int64_t ldz;
   const double* sz;
-  double* out;
+  T* out;
   int64_t ldo;
   double* red_part;  // [gridDim.x][ncols] per-block partial column reductions, or NULL
   int dot_with_yin;
 };
 
-template <int VEC>
-__device__ __forceinline__ void load_vec(const double* __restrict__ p, double (&r)[VEC]) {
-  if constexpr (VEC == 2) {
+// VEC consecutive elements as one 8/16-byte access
+template <typename T, int VEC>
+struct VecIO;
+template <>
+struct VecIO<double, 1> {
+  __device__ static void ld(const double* p, double* r) { r[0] = *p; }
+  __device__ static void st(double* p, const double* r) { *p = r[0]; }
+};
+template <>
+struct VecIO<double, 2> {
+  __device__ static void ld(const double* p, double* r) {
     const double2 t = *reinterpret_cast<const double2*>(p);
     r[0] = t.x;
     r[1] = t.y;
-  } else {
-    r[0] = *p;
   }
-}
-
-template <int VEC>
-__device__ __forceinline__ void store_vec(double* __restrict__ p, const double (&r)[VEC]) {
-  if constexpr (VEC == 2) {
-    *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
-  } else {
-    *p = r[0];
+  __device__ static void st(double* p, const double* r) { *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]); }
+};
+template <>
+struct VecIO<float, 1> {
+  __device__ static void ld(const float* p, float* r) { r[0] = *p; }
+  __device__ static void st(float* p, const float* r) { *p = r[0]; }
+};
+template <>
+struct VecIO<float, 2> {
+  __device__ static void ld(const float* p, float* r) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    r[0] = t.x;
+    r[1] = t.y;
   }
-}
+  __device__ static void st(float* p, const float* r) { *reinterpret_cast<float2*>(p) = make_float2(r[0], r[1]); }
+};
+template <>
+struct VecIO<float, 4> {
+  __device__ static void ld(const float* p, float* r) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r[0] = t.x;
+    r[1] = t.y;
+    r[2] = t.z;
+    r[3] = t.w;
+  }
+  __device__ static void st(float* p, const float* r) {
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+};
 
-template <int VEC>
-__global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams P) {
+// T is the storage and arithmetic type of the blocks and of A's values (FP64 path or
+// the FP32 filter of the mixed path); column reductions always accumulate in FP64.
+template <typename T, int VEC>
+__global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) {
   extern __shared__ double s_red[];  // [SPMM_WARPS][ncols]
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -80,13 +108,13 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams P) {
     for (int c0 = 0; c0 < ncols; c0 += CH) {
       const int c = c0 + lane * VEC;
       const bool act = c < ncols;
-      double acc[VEC];
+      T acc[VEC];
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) acc[u] = 0.0;
+      for (int u = 0; u < VEC; ++u) acc[u] = T(0);
       for (int base = beg; base < end; base += 32) {
         const int e = base + lane;
         int jc = 0;
-        double av = 0.0;
+        T av = T(0);
         if (e < end) {
           jc = __ldg(P.col + e);
           av = __ldg(P.val + e);
@@ -95,44 +123,47 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams P) {
 #pragma unroll 4
         for (int t = 0; t < cnt; ++t) {
           const int j = __shfl_sync(0xffffffffu, jc, t);
-          const double v = __shfl_sync(0xffffffffu, av, t);
+          const T v = __shfl_sync(0xffffffffu, av, t);
           if (act) {
-            double y[VEC];
-            load_vec<VEC>(P.Yin + static_cast<int64_t>(j) * P.ldy + c, y);
+            T y[VEC];
+            VecIO<T, VEC>::ld(P.Yin + static_cast<int64_t>(j) * P.ldy + c, y);
 #pragma unroll
             for (int u = 0; u < VEC; ++u) acc[u] = fma(v, y[u], acc[u]);
           }
         }
       }
       if (act) {
-        double yi[VEC], o[VEC];
-        if (P.beta != 0.0 || P.dot_with_yin) {
-          load_vec<VEC>(P.Yin + row * P.ldy + c, yi);
+        T yi[VEC], o[VEC];
+        if (P.beta != T(0) || P.dot_with_yin) {
+          VecIO<T, VEC>::ld(P.Yin + row * P.ldy + c, yi);
         } else {
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) yi[u] = 0.0;
+          for (int u = 0; u < VEC; ++u) yi[u] = T(0);
         }
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-          const double s = P.alpha * acc[u] + P.beta * yi[u];
-          o[u] = P.sy ? P.sy[c + u] * s : s;
+          const T s = fma(P.alpha, acc[u], P.beta * yi[u]);
+          o[u] = P.sy ? static_cast<T>(P.sy[c + u]) * s : s;
         }
         if (P.X) {
-          double x[VEC];
-          load_vec<VEC>(P.X + row * P.ldx + c, x);
+          T x[VEC];
+          VecIO<T, VEC>::ld(P.X + row * P.ldx + c, x);
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) o[u] = fma(P.sx[c + u], x[u], o[u]);
+          for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sx[c + u]), x[u], o[u]);
         }
         if (P.Z) {
-          double z[VEC];
-          load_vec<VEC>(P.Z + row * P.ldz + c, z);
+          T z[VEC];
+          VecIO<T, VEC>::ld(P.Z + row * P.ldz + c, z);
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) o[u] = fma(P.sz[c + u], z[u], o[u]);
+          for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sz[c + u]), z[u], o[u]);
         }
-        if (P.out) store_vec<VEC>(P.out + row * P.ldo + c, o);
+        if (P.out) VecIO<T, VEC>::st(P.out + row * P.ldo + c, o);
         if (P.red_part) {
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) my_red[c + u] += P.dot_with_yin ? o[u] * yi[u] : o[u] * o[u];
+          for (int u = 0; u < VEC; ++u) {
+            const double od = static_cast<double>(o[u]);
+            my_red[c + u] += P.dot_with_yin ? od * static_cast<double>(yi[u]) : od * od;
+          }
         }
       }
     }
@@ -145,6 +176,11 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams P) {
       P.red_part[static_cast<size_t>(blockIdx.x) * ncols + c] = s;
     }
   }
+}
+
+__global__ void to_float_kernel(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t < n) dst[t] = static_cast<float>(src[t]);
 }
 
 // out[c] = sum_b part[b][c]: one block per column, fixed strided partial sums and a fixed
@@ -223,37 +259,57 @@ __global__ void col_sumsq_kernel(int64_t n, const double* __restrict__ X, int64_
   }
 }
 
-template <int VEC>
-arb_status launch_spmm(arb_ctx ctx, const KParams& P, int grid, size_t smem) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    ARB_CUDA(ctx, cudaFuncSetAttribute(spmm_fused_kernel<VEC>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
-  spmm_fused_kernel<VEC><<<grid, SPMM_THREADS, smem, ctx->stream>>>(P);
+template <typename T, int VEC>
+arb_status launch_spmm(arb_ctx ctx, const KParams<T>& P, int grid, size_t smem) {
+  ARB_CUDA(ctx, cudaFuncSetAttribute(spmm_fused_kernel<T, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     200 * 1024));
+  spmm_fused_kernel<T, VEC><<<grid, SPMM_THREADS, smem, ctx->stream>>>(P);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
 
-inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+template <typename T>
+const T* values_of(const arb_mat_s* A);
+template <>
+const double* values_of<double>(const arb_mat_s* A) {
+  return A->val;
+}
+template <>
+const float* values_of<float>(const arb_mat_s* A) {
+  return A->val32;
+}
 
 }  // namespace
 
-arb_status spmm_fused(arb_ctx ctx, const SpmmArgs& a) {
+arb_status ensure_val32(arb_ctx ctx, arb_mat mat) {
+  if (mat->val32) return ARB_OK;
+  ARB_CUDA(ctx, cudaMalloc(&mat->val32, std::max<int64_t>(mat->nnz, 1) * sizeof(float)));
+  if (mat->nnz > 0) {
+    to_float_kernel<<<static_cast<int>((mat->nnz + 255) / 256), 256, 0, ctx->stream>>>(mat->nnz, mat->val,
+                                                                                     mat->val32);
+    ARB_LAUNCHED(ctx);
+  }
+  return ARB_OK;
+}
+
+template <typename T>
+arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   const arb_mat_s* A = a.A;
   if (a.ncols <= 0 || A->n <= 0) return ARB_OK;
   if (a.ncols > 6000) return set_error(ctx, ARB_INVALID_ARG, "spmm: ncols too large");
-  KParams P;
+  if (!values_of<T>(A)) return set_error(ctx, ARB_INVALID_ARG, "spmm: matrix has no values of this precision");
+  KParams<T> P;
   P.n = A->n;
   P.rowptr = A->rowptr;
   P.col = A->col;
-  P.val = A->val;
+  P.val = values_of<T>(A);
   P.ncols = a.ncols;
   P.Yin = a.Yin;
   P.ldy = a.ldy;
-  P.alpha = a.alpha;
-  P.beta = a.beta;
+  P.alpha = static_cast<T>(a.alpha);
+  P.beta = static_cast<T>(a.beta);
   P.sy = a.sy;
   P.X = a.X;
   P.ldx = a.ldx;
@@ -275,16 +331,29 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs& a) {
     if (smem > 200 * 1024) return set_error(ctx, ARB_INVALID_ARG, "spmm: too many columns for reduction");
     ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * a.ncols, &P.red_part));
   }
-  // vector width 2 needs even column counts, even leading dimensions and 16-byte bases
-  bool v2 = (a.ncols % 2 == 0) && (a.ldy % 2 == 0) && aligned16(a.Yin);
-  if (a.X) v2 = v2 && (a.ldx % 2 == 0) && aligned16(a.X);
-  if (a.Z) v2 = v2 && (a.ldz % 2 == 0) && aligned16(a.Z);
-  if (a.out) v2 = v2 && (a.ldo % 2 == 0) && aligned16(a.out);
-  if (a.ncols <= 32) v2 = false;  // one 32-lane chunk already covers the row
-  if (v2) {
-    ARB_TRY(launch_spmm<2>(ctx, P, grid, smem));
+  // widest vector access that the column count, leading dimensions and bases allow
+  auto fits = [&](int v) {
+    const size_t bytes = v * sizeof(T);
+    bool ok = (a.ncols % v == 0) && (a.ldy % v == 0) && aligned(a.Yin, bytes);
+    if (a.X) ok = ok && (a.ldx % v == 0) && aligned(a.X, bytes);
+    if (a.Z) ok = ok && (a.ldz % v == 0) && aligned(a.Z, bytes);
+    if (a.out) ok = ok && (a.ldo % v == 0) && aligned(a.out, bytes);
+    return ok && a.ncols > 32 * (v / 2);
+  };
+  if constexpr (sizeof(T) == 4) {
+    if (fits(4)) {
+      ARB_TRY((launch_spmm<T, 4>(ctx, P, grid, smem)));
+    } else if (fits(2)) {
+      ARB_TRY((launch_spmm<T, 2>(ctx, P, grid, smem)));
+    } else {
+      ARB_TRY((launch_spmm<T, 1>(ctx, P, grid, smem)));
+    }
   } else {
-    ARB_TRY(launch_spmm<1>(ctx, P, grid, smem));
+    if (fits(2)) {
+      ARB_TRY((launch_spmm<T, 2>(ctx, P, grid, smem)));
+    } else {
+      ARB_TRY((launch_spmm<T, 1>(ctx, P, grid, smem)));
+    }
   }
   if (a.colred) {
     reduce_partials_kernel<<<a.ncols, 256, 0, ctx->stream>>>(P.red_part, grid, a.ncols, a.colred);
@@ -292,6 +361,9 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs& a) {
   }
   return ARB_OK;
 }
+
+template arb_status spmm_fused<double>(arb_ctx, const SpmmArgs<double>&);
+template arb_status spmm_fused<float>(arb_ctx, const SpmmArgs<float>&);
 
 arb_status gershgorin(arb_ctx ctx, arb_mat mat, double* lo, double* hi) {
   if (mat->gersh_valid) {

@@ -38,7 +38,13 @@ __global__ void filter_table_kernel(int d, ChebCoef cc, const double* __restrict
   table[(3 * static_cast<int64_t>(t) + 2) * ncols + c] = sz;
 }
 
-inline double orth_tau(int m) { return 32.0 * std::max(m, 1) * 2.220446049250313e-16; }
+// Gram truncation threshold relative to the largest eigenvalue of the unit-diagonal Gram
+// matrix, above the noise of the computed Gram entries: 64 m u for FP64 blocks; for FP32
+// blocks (FP32 products summed in FP64 over 64-row runs, entries good to ~3e-9) 2e-9 m.
+template <typename T>
+inline double orth_tau(int m) {
+  return sizeof(T) == 4 ? 2e-9 * std::max(m, 1) : 64.0 * std::max(m, 1) * 1.11e-16;
+}
 
 }  // namespace
 
@@ -63,10 +69,10 @@ FilterPlan make_filter_plan(double op_scale, double op_shift, double a, double b
 // Each line is one fused pass of spmm_fused (one product with A); b_j overwrites b_{j+2}
 // in place, so two work blocks suffice.  The same polynomial psi_d of Section 5 is
 // evaluated as Algorithm 7 does in the monomial basis, but with bounded coefficients.
-arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const double* X,
-                        int64_t ldx, int32_t ncols, const double* xscale, double* W1,
-                        double* W2, int64_t ldw, double* Y, int64_t ldy, double* colss,
-                        double** result) {
+template <typename T>
+arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const T* X, int64_t ldx,
+                        int32_t ncols, const double* xscale, T* W1, T* W2, int64_t ldw, T* Y,
+                        int64_t ldy, double* colss, T** result) {
   const int d = plan.degree;
   if (d < 1 || d > 60) return set_error(ctx, ARB_INVALID_ARG, "filter: degree must be in [1, 60]");
   if (ncols <= 0) return ARB_OK;
@@ -84,7 +90,8 @@ arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const 
   auto sx_of = [&](int t) { return table + (3 * static_cast<int64_t>(t) + 1) * ncols; };
   auto sz_of = [&](int t) { return table + (3 * static_cast<int64_t>(t) + 2) * ncols; };
 
-  SpmmArgs a;
+  if (sizeof(T) == 4) ARB_TRY(ensure_val32(ctx, mat));
+  SpmmArgs<T> a;
   a.A = mat;
   a.ncols = ncols;
   a.alpha = plan.alpha;
@@ -98,7 +105,7 @@ arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const 
       a.ldx = ldx;
       a.sx = sx_of(0);
     }
-    double* out = Y ? Y : W1;
+    T* out = Y ? Y : W1;
     a.out = out;
     a.ldo = Y ? ldy : ldw;
     a.colred = colss;
@@ -118,12 +125,12 @@ arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const 
   a.out = W1;
   a.ldo = ldw;
   ARB_TRY(spmm_fused(ctx, a));
-  double* cur = W1;        // holds b_{j+1}
-  double* prev = nullptr;  // holds b_{j+2}; nullptr means b_d = c_d X~ (read from X)
+  T* cur = W1;        // holds b_{j+1}
+  T* prev = nullptr;  // holds b_{j+2}; nullptr means b_d = c_d X~ (read from X)
   for (int t = 1; t < d; ++t) {
     const int j = d - 1 - t;
     const bool last = (t == d - 1);
-    SpmmArgs s;
+    SpmmArgs<T> s;
     s.A = mat;
     s.ncols = ncols;
     s.alpha = plan.alpha;
@@ -144,7 +151,7 @@ arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const 
       s.ldz = ldx;
     }
     if (s.Z) s.sz = sz_of(t);
-    double* out;
+    T* out;
     int64_t ldo;
     if (last && Y) {
       out = Y;
@@ -164,21 +171,23 @@ arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const 
   return ARB_OK;
 }
 
-arb_status project_out(arb_ctx ctx, int64_t n, const double* Q, int64_t ldq, int32_t nq, double* X,
-                       int64_t ldx, int32_t ncols) {
+template <typename T>
+arb_status project_out(arb_ctx ctx, int64_t n, const T* Q, int64_t ldq, int32_t nq, T* X, int64_t ldx,
+                       int32_t ncols) {
   if (nq <= 0 || ncols <= 0) return ARB_OK;
   double* W;
   ARB_TRY(ws<double>(ctx, WS_SMALL3, static_cast<size_t>(nq) * ncols, &W));
-  ARB_TRY(gram(ctx, n, Q, ldq, nq, X, ldx, ncols, W, ncols));
-  ARB_TRY(gemm_tall(ctx, n, Q, ldq, nq, W, ncols, ncols, -1.0, 1.0, X, ldx));
+  ARB_TRY(gram<T>(ctx, n, Q, ldq, nq, X, ldx, ncols, W, ncols));
+  ARB_TRY(gemm_tall<T>(ctx, n, Q, ldq, nq, W, ncols, ncols, -1.0, 1.0, X, ldx));
   return ARB_OK;
 }
 
 // One eigen-truncated Gram pass (SVQB, Stathopoulos & Wu 2002): scale the columns of Z to
 // unit norm, G = D Z^T Z D = W Theta W^T, keep theta_j > tau theta_0, and map
 // Z -> Z D W_r Theta_r^{-1/2}.
-static arb_status svqb_pass(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz, int32_t m,
-                            double* out, int64_t ldo, int32_t* rank) {
+template <typename T>
+static arb_status svqb_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* out, int64_t ldo,
+                            int32_t* rank) {
   double *G, *Gh, *W, *d, *theta;
   int32_t* r_dev;
   const size_t mm = static_cast<size_t>(m) * m;
@@ -188,38 +197,40 @@ static arb_status svqb_pass(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz
   ARB_TRY(ws<double>(ctx, WS_VEC0, m, &d));
   ARB_TRY(ws<double>(ctx, WS_VEC1, m, &theta));
   ARB_TRY(ws<int32_t>(ctx, WS_INT0, 4, &r_dev));
-  ARB_TRY(gram(ctx, n, Z, ldz, m, Z, ldz, m, G, m));
+  ARB_TRY(gram<T>(ctx, n, Z, ldz, m, Z, ldz, m, G, m));
   ARB_TRY(svqb_prep(ctx, m, G, m, Gh, d));
   ARB_TRY(syevj(ctx, m, Gh, m, theta, W, m, nullptr));
-  ARB_TRY(svqb_finish(ctx, m, theta, W, m, d, orth_tau(m), Gh, r_dev));
+  ARB_TRY(svqb_finish(ctx, m, theta, W, m, d, orth_tau<T>(m), Gh, r_dev));
   int32_t r = 0;
   ARB_TRY(d2h_sync(ctx, &r, r_dev, sizeof(int32_t)));
   *rank = r;
-  if (r > 0) ARB_TRY(gemm_tall(ctx, n, Z, ldz, m, Gh, m, r, 1.0, 0.0, out, ldo));
+  if (r > 0) ARB_TRY(gemm_tall<T>(ctx, n, Z, ldz, m, Gh, m, r, 1.0, 0.0, out, ldo));
   return ARB_OK;
 }
 
-arb_status orth(arb_ctx ctx, int64_t n, const double* Z, int64_t ldz, int32_t m, double* U,
-                int64_t ldu, double* tmp, int64_t ldt, int32_t* rank) {
+template <typename T>
+arb_status orth(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* U, int64_t ldu, T* tmp,
+                int64_t ldt, int32_t* rank) {
   *rank = 0;
   if (m <= 0) return ARB_OK;
   int32_t r1 = 0, r2 = 0;
-  ARB_TRY(svqb_pass(ctx, n, Z, ldz, m, tmp, ldt, &r1));
+  ARB_TRY(svqb_pass<T>(ctx, n, Z, ldz, m, tmp, ldt, &r1));
   if (r1 == 0) return ARB_OK;
-  ARB_TRY(svqb_pass(ctx, n, tmp, ldt, r1, U, ldu, &r2));
+  ARB_TRY(svqb_pass<T>(ctx, n, tmp, ldt, r1, U, ldu, &r2));
   *rank = r2;
   return ARB_OK;
 }
 
-arb_status rcond_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
-                      const double* xs, double* rc) {
+template <typename T>
+arb_status rcond_gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t ncols, const double* xs,
+                      double* rc) {
   double *G, *W, *theta, *rc_dev;
   const size_t mm = static_cast<size_t>(ncols) * ncols;
   ARB_TRY(ws<double>(ctx, WS_SMALL0, mm, &G));
   ARB_TRY(ws<double>(ctx, WS_SMALL2, mm, &W));
   ARB_TRY(ws<double>(ctx, WS_VEC1, ncols + 2, &theta));
   rc_dev = theta + ncols;
-  ARB_TRY(gram(ctx, n, X, ldx, ncols, X, ldx, ncols, G, ncols));
+  ARB_TRY(gram<T>(ctx, n, X, ldx, ncols, X, ldx, ncols, G, ncols));
   if (xs) ARB_TRY(scale_sym(ctx, ncols, G, ncols, xs));
   ARB_TRY(syevj(ctx, ncols, G, ncols, theta, W, ncols, nullptr));
   ARB_TRY(rcond_from_eig(ctx, ncols, G, ncols, theta, W, ncols, rc_dev));
@@ -234,20 +245,21 @@ arb_status rcond_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int3
 // Algorithm 5; building it block by block keeps the small residual directions that
 // columns of [X, BX, ...] carry at full relative accuracy.  Then AU_q = B U_q and
 // H = U^T (B U) (Algorithm 1) is diagonalised.
-arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, int64_t n,
-                             double* X, int64_t ldx, int32_t w, const double* Qc, int64_t ldqc,
-                             int32_t nl, int32_t q, const ArrWork& wk, int32_t* m_out,
-                             double* theta, double* V) {
+template <typename T>
+arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, int64_t n, T* X,
+                             int64_t ldx, int32_t w, const T* Qc, int64_t ldqc, int32_t nl, int32_t q,
+                             const ArrWork<T>& wk, int32_t* m_out, double* theta, double* V) {
   *m_out = 0;
-  if (nl > 0) ARB_TRY(project_out(ctx, n, Qc, ldqc, nl, X, ldx, w));
+  if (sizeof(T) == 4) ARB_TRY(ensure_val32(ctx, mat));
+  if (nl > 0) ARB_TRY(project_out<T>(ctx, n, Qc, ldqc, nl, X, ldx, w));
   int32_t r0 = 0;
-  ARB_TRY(orth(ctx, n, X, ldx, w, wk.U, wk.ldu, wk.T, wk.ldt, &r0));
+  ARB_TRY(orth(ctx, n, static_cast<const T*>(X), ldx, w, wk.U, wk.ldu, wk.T1, wk.ldt, &r0));
   if (r0 == 0) return set_error(ctx, ARB_BREAKDOWN, "ARR: iterate has no numerical rank");
   std::vector<int32_t> off{0}, rk{r0};
   int32_t m = r0;
   for (int i = 1; i <= q; ++i) {
     const int32_t o = off.back(), r = rk.back();
-    SpmmArgs s;
+    SpmmArgs<T> s;
     s.A = mat;
     s.ncols = r;
     s.Yin = wk.U + o;
@@ -257,13 +269,13 @@ arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double o
     s.out = wk.AU + o;
     s.ldo = wk.ldau;
     ARB_TRY(spmm_fused(ctx, s));
-    ARB_TRY(copy_block(ctx, n, wk.AU + o, wk.ldau, r, wk.T2, wk.ldt2));
+    ARB_TRY((copy_block<T, T>(ctx, n, wk.AU + o, wk.ldau, r, wk.T2, wk.ldt2)));
     for (int pass = 0; pass < 2; ++pass) {
-      if (nl > 0) ARB_TRY(project_out(ctx, n, Qc, ldqc, nl, wk.T2, wk.ldt2, r));
-      ARB_TRY(project_out(ctx, n, wk.U, wk.ldu, m, wk.T2, wk.ldt2, r));
+      if (nl > 0) ARB_TRY(project_out<T>(ctx, n, Qc, ldqc, nl, wk.T2, wk.ldt2, r));
+      ARB_TRY(project_out<T>(ctx, n, wk.U, wk.ldu, m, wk.T2, wk.ldt2, r));
     }
     int32_t ri = 0;
-    ARB_TRY(orth(ctx, n, wk.T2, wk.ldt2, r, wk.U + m, wk.ldu, wk.T, wk.ldt, &ri));
+    ARB_TRY(orth(ctx, n, static_cast<const T*>(wk.T2), wk.ldt2, r, wk.U + m, wk.ldu, wk.T1, wk.ldt, &ri));
     if (ri == 0) break;  // the Krylov space is exhausted
     off.push_back(m);
     rk.push_back(ri);
@@ -272,7 +284,7 @@ arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double o
   {
     // B U for the last block (the earlier blocks were formed during the augmentation)
     const int32_t o = off.back(), r = rk.back();
-    SpmmArgs s;
+    SpmmArgs<T> s;
     s.A = mat;
     s.ncols = r;
     s.Yin = wk.U + o;
@@ -285,11 +297,32 @@ arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double o
   }
   double* H;
   ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(m) * m, &H));
-  ARB_TRY(gram(ctx, n, wk.U, wk.ldu, m, wk.AU, wk.ldau, m, H, m));
+  ARB_TRY(gram<T>(ctx, n, wk.U, wk.ldu, m, wk.AU, wk.ldau, m, H, m));
   ARB_TRY(symmetrize(ctx, m, H, m));
   ARB_TRY(syevj(ctx, m, H, m, theta, V, m, nullptr));
   *m_out = m;
   return ARB_OK;
 }
+
+template arb_status filter_apply<double>(arb_ctx, arb_mat, const FilterPlan&, const double*, int64_t, int32_t,
+                                         const double*, double*, double*, int64_t, double*, int64_t, double*,
+                                         double**);
+template arb_status filter_apply<float>(arb_ctx, arb_mat, const FilterPlan&, const float*, int64_t, int32_t,
+                                        const double*, float*, float*, int64_t, float*, int64_t, double*, float**);
+template arb_status orth<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, double*, int64_t, double*,
+                                 int64_t, int32_t*);
+template arb_status orth<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, float*, int64_t, float*,
+                                int64_t, int32_t*);
+template arb_status rcond_gram<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, const double*, double*);
+template arb_status rcond_gram<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, const double*, double*);
+template arb_status project_out<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, double*, int64_t,
+                                        int32_t);
+template arb_status project_out<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, float*, int64_t, int32_t);
+template arb_status arr_basis_and_eig<double>(arb_ctx, arb_mat, double, double, int64_t, double*, int64_t,
+                                              int32_t, const double*, int64_t, int32_t, int32_t,
+                                              const ArrWork<double>&, int32_t*, double*, double*);
+template arb_status arr_basis_and_eig<float>(arb_ctx, arb_mat, double, double, int64_t, float*, int64_t, int32_t,
+                                             const float*, int64_t, int32_t, int32_t, const ArrWork<float>&,
+                                             int32_t*, double*, double*);
 
 }  // namespace arb

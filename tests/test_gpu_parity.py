@@ -98,6 +98,28 @@ def test_filter_matches_oracle(arb, ctx, d, kind):
         np.testing.assert_allclose(Y, ref7, rtol=0, atol=1e-9 * scale)
 
 
+@pytest.mark.parametrize("d,ncols", [(1, 7), (3, 30), (10, 64), (20, 130)])
+def test_filter_f32_against_oracle(arb, ctx, d, ncols):
+    # FP32 filter of the mixed path vs the FP64 oracle.  Each Clenshaw pass adds a few
+    # u32 of relative rounding, growing roughly linearly in d: an FP32 emulation of the same
+    # recurrence in numpy measures 1.2e-7 (d=1) .. 1.3e-6 (d=20) of max|Y| on these
+    # inputs, so 1e-5 of max|Y| is the bar.
+    A = I.laplacian_2d(40)
+    mat = arb.Matrix.from_csr(ctx, A)
+    B = 8.0 * sp.identity(A.n, format="csr") - scipy_of(A)
+    X = I.gaussian_block(A.n, ncols, 5)
+    xs = np.linspace(0.5, 2.0, ncols)
+    a, b = 0.0, 3.7
+    coef = O.interpolant_cheb_coeffs(d)
+    colss = torch.zeros(ncols, dtype=torch.float64, device="cuda")
+    X32 = dev(X).float()
+    Y = host(arb.arb_filter_f32(ctx, mat, -1.0, 8.0, a, b, coef, X32, xscale=dev(xs), colss=colss))
+    ref = O.poly_clenshaw(B, X.astype(np.float32).astype(np.float64) * xs[None, :], 0.0, b, coef)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=1e-5 * scale)
+    np.testing.assert_allclose(host(colss), np.sum(ref * ref, axis=0), rtol=1e-4)
+
+
 def test_filter_on_closed_form_eigenvectors(arb, ctx):
     # spectral mapping (eq. poly-A): rho(A) v = rho(lambda) v for the sin-product eigenvectors
     m = 20
@@ -325,3 +347,36 @@ def test_gaussian_block_matches_input_generator(arb, ctx, n, ncols):
     # same counters and uniforms; the host rounds 2*pi*u before cos/sin while the device
     # uses sincospi(2u), so values near a zero of cos/sin differ by ~eps * |r| absolutely
     np.testing.assert_allclose(Xd, Xh, rtol=1e-14, atol=1e-14)
+
+
+def test_solve_mixed_2d64_against_oracle(arb, ctx):
+    # FP32 phase + FP64 refinement must land on the FP64 oracle's pairs (spec bar:
+    # eigenvalue relative error <= 1e-10, relative residual <= tol)
+    W = I.workload_2d64()
+    X0 = I.gaussian_block(W.A.n, W.p, W.seed)
+    r = _solve(arb, ctx, W.A, W.k, W.p, W.q, W.degree, W.tol, X0, precision=arb.ARB_MIXED)
+    assert r.status == arb.ARB_OK, r.info
+    ref = json_golden()
+    lam = np.array(ref["evals"])
+    assert np.max(np.abs(r.evals - lam) / np.maximum(1.0, np.abs(lam))) <= 1e-10
+    Q = r.evecs
+    R = scipy_of(W.A) @ Q - Q * r.evals[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= W.tol * 8.0
+    np.testing.assert_allclose(Q.T @ Q, np.eye(W.k), atol=1e-12)
+    assert r.info["outer_iters_fp32"] >= 1
+
+
+def test_solve_mixed_3d_scaled(arb, ctx):
+    m, k, p = 24, 30, 36
+    A = I.laplacian_3d(m)
+    X0 = I.gaussian_block(A.n, p, 99)
+    r = _solve(arb, ctx, A, k, p, 2, 12, 1e-8, X0, precision=arb.ARB_MIXED)
+    assert r.status == arb.ARB_OK, r.info
+    np.testing.assert_allclose(r.evals, laplacian_3d_eigs(m)[:k], atol=1e-9)
+
+
+def json_golden():
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "laplace2d_64_oracle.json")
+    return json.load(open(here))
