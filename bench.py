@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--compare-fp64", action="store_true",
                     help="also time one plain FP64 solve of the same workload")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--filter-only", action="store_true",
+                    help="only apply the filter (--reps times) to an n x --ncols block: for profiling")
+    ap.add_argument("--ncols", type=int, default=0)
+    ap.add_argument("--degree", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -360,8 +365,47 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_filter_only(args):
+    """Apply the Chebyshev-interpolant filter to a Gaussian block of the workload matrix and
+    print the per-pass time (CUDA events on the context's stream)."""
+    import torch
+
+    from paper_1507_06078_gb300 import arrabit as arb
+    from paper_1507_06078_gb300 import build
+    build.build()
+    W = workload(args.grid)
+    ncols = args.ncols or W.p
+    d = args.degree or W.degree
+    ctx = arb.Context(0)
+    mat = arb.Matrix.from_csr(ctx, W.A)
+    X = arb.arb_gaussian_block(ctx, W.A.n, ncols, W.seed)
+    if args.precision == "mixed":
+        X = X.float()
+        f = arb.arb_filter_f32
+        s = 4
+    else:
+        f = arb.arb_filter
+        s = 8
+    Y = torch.empty_like(X)
+    coef = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, d)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    for _ in range(args.reps):
+        f(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, X, Y=Y)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (args.reps * d)
+    nb = filter_algorithmic_bytes(W.A.n, W.A.nnz, ncols, d, s=s, z=s) / d
+    print(json.dumps({"filter_only": True, "n": W.A.n, "ncols": ncols, "degree": d, "precision": args.precision,
+                      "ms_per_pass": ms, "algorithmic_GBps": nb / ms / 1e6}))
+
+
 def main():
     args = parse()
+    if args.filter_only:
+        run_filter_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <vector>
@@ -452,6 +453,7 @@ struct SolveState {
   int stop = ARB_STOP_MAXIT;
   arb_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool trace = false;  // ARB_TRACE set in the environment: one line per outer iteration on stderr
 };
 
 template <typename T>
@@ -590,6 +592,12 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
       maxres = std::max(maxres, std::isnan(S.h_res[i]) ? std::numeric_limits<double>::infinity() : S.h_res[i]);
       h += S.h_res[i] < 0.1 * tol_phase;
     }
+    if (S.trace)
+      fprintf(stderr,
+              "[arb] %s outer %d: filters %d (total %d) rc %.3e rank %d maxres %.3e b %.9g tol_t %.1e locked %d "
+              "t_filter %.3fs t_arr %.3fs\n",
+              sizeof(T) == 4 ? "fp32" : "fp64", j, S.o.inner_fixed > 0 ? S.o.inner_fixed : -1, S.info.n_filters, rc,
+              m, maxres, S.b, S.tol_t, S.nl, S.info.t_filter, S.info.t_arr);
     S.info.maxres = maxres;
     if (maxres < S.best) {
       S.best = maxres;
@@ -669,6 +677,7 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
   if (evecs && ldq < n) return set_error(ctx, ARB_INVALID_ARG, "solve: ldq < n");
   S.smallest = (which == ARB_SMALLEST);
   const bool mixed = (o.precision == ARB_MIXED);
+  S.trace = getenv("ARB_TRACE") != nullptr;
 
   // operator B = op_scale A + op_shift I whose largest eigenpairs are wanted
   double glo, ghi;

@@ -45,10 +45,15 @@ struct KParams {
 // VEC consecutive elements as one 8/16-byte access
 template <typename T, int VEC>
 struct VecIO;
+// ld/st: default caching (the gathered block, reused by neighbouring rows through L1/L2);
+// lds/sts: evict-first streaming access for the blocks each row touches once (X, the
+// b_{j+2} term and the output), so that they do not push the gathered block out of L2.
 template <>
 struct VecIO<double, 1> {
   __device__ static void ld(const double* p, double* r) { r[0] = *p; }
   __device__ static void st(double* p, const double* r) { *p = r[0]; }
+  __device__ static void lds(const double* p, double* r) { r[0] = __ldcs(p); }
+  __device__ static void sts(double* p, const double* r) { __stcs(p, r[0]); }
 };
 template <>
 struct VecIO<double, 2> {
@@ -58,11 +63,21 @@ struct VecIO<double, 2> {
     r[1] = t.y;
   }
   __device__ static void st(double* p, const double* r) { *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]); }
+  __device__ static void lds(const double* p, double* r) {
+    const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+    r[0] = t.x;
+    r[1] = t.y;
+  }
+  __device__ static void sts(double* p, const double* r) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(r[0], r[1]));
+  }
 };
 template <>
 struct VecIO<float, 1> {
   __device__ static void ld(const float* p, float* r) { r[0] = *p; }
   __device__ static void st(float* p, const float* r) { *p = r[0]; }
+  __device__ static void lds(const float* p, float* r) { r[0] = __ldcs(p); }
+  __device__ static void sts(float* p, const float* r) { __stcs(p, r[0]); }
 };
 template <>
 struct VecIO<float, 2> {
@@ -72,6 +87,12 @@ struct VecIO<float, 2> {
     r[1] = t.y;
   }
   __device__ static void st(float* p, const float* r) { *reinterpret_cast<float2*>(p) = make_float2(r[0], r[1]); }
+  __device__ static void lds(const float* p, float* r) {
+    const float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+    r[0] = t.x;
+    r[1] = t.y;
+  }
+  __device__ static void sts(float* p, const float* r) { __stcs(reinterpret_cast<float2*>(p), make_float2(r[0], r[1])); }
 };
 template <>
 struct VecIO<float, 4> {
@@ -84,6 +105,16 @@ struct VecIO<float, 4> {
   }
   __device__ static void st(float* p, const float* r) {
     *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  }
+  __device__ static void lds(const float* p, float* r) {
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    r[0] = t.x;
+    r[1] = t.y;
+    r[2] = t.z;
+    r[3] = t.w;
+  }
+  __device__ static void sts(float* p, const float* r) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(r[0], r[1], r[2], r[3]));
   }
 };
 
@@ -147,17 +178,17 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) 
         }
         if (P.X) {
           T x[VEC];
-          VecIO<T, VEC>::ld(P.X + row * P.ldx + c, x);
+          VecIO<T, VEC>::lds(P.X + row * P.ldx + c, x);
 #pragma unroll
           for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sx[c + u]), x[u], o[u]);
         }
         if (P.Z) {
           T z[VEC];
-          VecIO<T, VEC>::ld(P.Z + row * P.ldz + c, z);
+          VecIO<T, VEC>::lds(P.Z + row * P.ldz + c, z);
 #pragma unroll
           for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sz[c + u]), z[u], o[u]);
         }
-        if (P.out) VecIO<T, VEC>::st(P.out + row * P.ldo + c, o);
+        if (P.out) VecIO<T, VEC>::sts(P.out + row * P.ldo + c, o);
         if (P.red_part) {
 #pragma unroll
           for (int u = 0; u < VEC; ++u) {
