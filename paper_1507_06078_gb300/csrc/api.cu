@@ -504,6 +504,7 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
   for (int j = 1; j <= S.o.maxit; ++j) {
     S.outer = j;
     S.info.outer_iters++;
+    const int nf0 = S.info.n_filters;
     // ---------------- inner loop: multi-power steps (Algorithm 8, MPM branch)
     ARB_CUDA(ctx, cudaEventRecord(S.ev0, ctx->stream));
     double rc = std::numeric_limits<double>::infinity();
@@ -596,7 +597,7 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
       fprintf(stderr,
               "[arb] %s outer %d: filters %d (total %d) rc %.3e rank %d maxres %.3e b %.9g tol_t %.1e locked %d "
               "t_filter %.3fs t_arr %.3fs\n",
-              sizeof(T) == 4 ? "fp32" : "fp64", j, S.o.inner_fixed > 0 ? S.o.inner_fixed : -1, S.info.n_filters, rc,
+              sizeof(T) == 4 ? "fp32" : "fp64", j, S.info.n_filters - nf0, S.info.n_filters, rc,
               m, maxres, S.b, S.tol_t, S.nl, S.info.t_filter, S.info.t_arr);
     S.info.maxres = maxres;
     if (maxres < S.best) {
