@@ -74,7 +74,9 @@ typedef struct {
   int32_t inner_fixed;  /* > 0: exactly this many filters per outer iteration, no rcond rule */
   int32_t filter;       /* arb_filter_kind */
   int32_t precision;    /* arb_precision: ARB_FP64, or ARB_MIXED (FP32 phase, then FP64 refinement) */
-  int32_t reserved0;
+  int32_t b_update;     /* when the filter interval end b = mu_{k+q} is refreshed:
+                           0 = at continuation steps only (Algorithm 8, the default);
+                           1 = after every ARR projection (Section 5's estimation paragraph) */
   double tol1;          /* first continuation tolerance; 0: max(1e-6, tol) if tol <= 1e-8 else tol */
   double shift_sigma;   /* sigma of sigma I - A for ARB_SMALLEST; NaN: Gershgorin upper bound of A */
   double tol_switch;    /* ARB_MIXED: relative residual at which the FP32 phase hands over to

@@ -357,11 +357,14 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
                 maxit1: int = 10, maxit2: int = 5, tol1: float | None = None,
                 filter_kind: str = "chebinterp", sigma: float | None = None,
                 inner_fixed: int = 0, pad_pool: np.ndarray | None = None,
-                poly_eval: str = "clenshaw") -> OracleResult:
+                poly_eval: str = "clenshaw", b_update: str = "continuation") -> OracleResult:
     """ARRABIT with the multi-power inner solver, Algorithm 8, for the k largest (or, via
     B = sigma I - A, smallest) eigenpairs of symmetric A.  The block width is
     p = X0.shape[1] = k + guard vectors.  ``inner_fixed`` > 0 replaces the inner stop rule
     by exactly that many filter applications per outer iteration (for lock-step tests).
+    ``b_update`` = "continuation" refreshes b = mu_{k+q} only at a continuation step, as
+    Algorithm 8 does; "every_arr" refreshes it after every ARR projection, as the
+    estimation paragraph of Section 5 describes.
     """
     A = sp.csr_matrix(A, dtype=np.float64)
     n, p = X0.shape
@@ -473,6 +476,8 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
         # continuation (eq. contin)
         if maxres <= tol_t:
             tol_t = max(1e-2 * tol_t, tol)
+            b = float(mu[p - 1])
+        elif b_update == "every_arr":
             b = float(mu[p - 1])
         # deflation (eq. defl)
         thr = max(1e-14, tol_t ** 2)

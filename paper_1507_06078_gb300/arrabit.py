@@ -39,7 +39,7 @@ class ArbError(RuntimeError):
 class arb_options(C.Structure):
     _fields_ = [("p", C.c_int32), ("q", C.c_int32), ("degree", C.c_int32), ("maxit", C.c_int32),
                 ("maxit1", C.c_int32), ("maxit2", C.c_int32), ("inner_fixed", C.c_int32),
-                ("filter", C.c_int32), ("precision", C.c_int32), ("reserved0", C.c_int32),
+                ("filter", C.c_int32), ("precision", C.c_int32), ("b_update", C.c_int32),
                 ("tol1", C.c_double), ("shift_sigma", C.c_double), ("tol_switch", C.c_double),
                 ("seed", C.c_uint64)]
 

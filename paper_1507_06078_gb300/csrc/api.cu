@@ -624,8 +624,10 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     if (maxres <= S.tol_t) {  // continuation, eq. contin
       S.tol_t = std::max(1e-2 * S.tol_t, S.tol);
       S.b = S.h_mu[p - 1];
-      if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+    } else if (S.o.b_update == 1) {  // Section 5: a better estimate of lambda_{k+q} after each ARR
+      S.b = S.h_mu[p - 1];
     }
+    if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
     const double thr = std::max(1e-14, S.tol_t * S.tol_t);  // eq. defl
     std::vector<int32_t> lock_idx, free_idx;
     S.h_sigc.clear();
@@ -674,6 +676,7 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     return set_error(ctx, ARB_INVALID_ARG, "solve: need 0 < k <= p, (q+1) p < n, 1 <= degree <= 60, tol > 0");
   if (o.precision != ARB_FP64 && o.precision != ARB_MIXED)
     return set_error(ctx, ARB_INVALID_ARG, "solve: unknown precision");
+  if (o.b_update != 0 && o.b_update != 1) return set_error(ctx, ARB_INVALID_ARG, "solve: b_update must be 0 or 1");
   if (which != ARB_LARGEST && which != ARB_SMALLEST) return set_error(ctx, ARB_INVALID_ARG, "solve: bad which");
   if (evecs && ldq < n) return set_error(ctx, ARB_INVALID_ARG, "solve: ldq < n");
   S.smallest = (which == ARB_SMALLEST);

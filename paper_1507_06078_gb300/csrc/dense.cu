@@ -424,37 +424,65 @@ inline int blocks_for(int64_t count, int threads) {
 
 }  // namespace
 
+// Split-K plan of a Gram product: tile size and the number of row splits, limited so the
+// partial sums fit in `max_part` doubles (0: no limit).
+struct GramPlan {
+  int R = 4, TT = 64, gi = 1, gj = 1, symmetric = 0;
+  int64_t nsplit = 1, rows = 0;
+};
+
 template <typename T>
-arb_status gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t na, const T* Y, int64_t ldy,
-                int32_t nb, double* C, int64_t ldc) {
-  if (na <= 0 || nb <= 0) return ARB_OK;
-  const int symmetric = (X == Y && ldx == ldy && na == nb) ? 1 : 0;
+static GramPlan gram_plan(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t na, const T* Y, int64_t ldy,
+                          int32_t nb, size_t max_part) {
+  GramPlan g;
+  g.symmetric = (X == Y && ldx == ldy && na == nb) ? 1 : 0;
   const int mx = std::max(na, nb);
-  const int R = mx <= 16 ? 1 : (mx <= 32 ? 2 : 4);
-  const int TT = 16 * R;
-  const int gi = (na + TT - 1) / TT, gj = (nb + TT - 1) / TT;
-  const int tiles = symmetric ? gi * (gi + 1) / 2 : gi * gj;
+  g.R = mx <= 16 ? 1 : (mx <= 32 ? 2 : 4);
+  g.TT = 16 * g.R;
+  g.gi = (na + g.TT - 1) / g.TT;
+  g.gj = (nb + g.TT - 1) / g.TT;
+  const int tiles = g.symmetric ? g.gi * (g.gi + 1) / 2 : g.gi * g.gj;
   const int64_t target = static_cast<int64_t>(ctx->num_sms) * 3;
   int64_t nsplit = std::max<int64_t>(1, (target + tiles - 1) / tiles);
   nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, n / (4 * KSTEP)));
   nsplit = std::min<int64_t>(nsplit, 4096);
+  if (max_part > 0) {
+    const int64_t per = static_cast<int64_t>(na) * nb;
+    nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, static_cast<int64_t>(max_part) / per));
+  }
   int64_t rows = (n + nsplit - 1) / nsplit;
   rows = ((rows + KSTEP - 1) / KSTEP) * KSTEP;
-  nsplit = std::max<int64_t>(1, (n + rows - 1) / rows);
-  double* part;
-  ARB_TRY(ws<double>(ctx, WS_GRAM_PART, static_cast<size_t>(nsplit) * na * nb, &part));
-  dim3 grid(gi, gj, static_cast<unsigned>(nsplit));
-  if (R == 1)
-    gram_kernel<T, 1><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
-  else if (R == 2)
-    gram_kernel<T, 2><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+  g.rows = rows;
+  g.nsplit = std::max<int64_t>(1, (n + rows - 1) / rows);
+  return g;
+}
+
+// The two launches of a Gram product given a partial-sum buffer of g.nsplit * na * nb.
+template <typename T>
+static arb_status gram_launch(arb_ctx ctx, const GramPlan& g, int64_t n, const T* X, int64_t ldx, int32_t na,
+                              const T* Y, int64_t ldy, int32_t nb, double* part, double* C, int64_t ldc) {
+  dim3 grid(g.gi, g.gj, static_cast<unsigned>(g.nsplit));
+  if (g.R == 1)
+    gram_kernel<T, 1><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, g.rows, g.symmetric, part);
+  else if (g.R == 2)
+    gram_kernel<T, 2><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, g.rows, g.symmetric, part);
   else
-    gram_kernel<T, 4><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, rows, symmetric, part);
+    gram_kernel<T, 4><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, g.rows, g.symmetric, part);
   ARB_LAUNCHED(ctx);
   gram_reduce_kernel<<<blocks_for(static_cast<int64_t>(na) * nb, 256), 256, 0, ctx->stream>>>(
-      part, static_cast<int>(nsplit), na, nb, symmetric, TT, C, ldc);
+      part, static_cast<int>(g.nsplit), na, nb, g.symmetric, g.TT, C, ldc);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
+}
+
+template <typename T>
+arb_status gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t na, const T* Y, int64_t ldy,
+                int32_t nb, double* C, int64_t ldc) {
+  if (na <= 0 || nb <= 0) return ARB_OK;
+  const GramPlan g = gram_plan<T>(ctx, n, X, ldx, na, Y, ldy, nb, 0);
+  double* part;
+  ARB_TRY(ws<double>(ctx, WS_GRAM_PART, static_cast<size_t>(g.nsplit) * na * nb, &part));
+  return gram_launch<T>(ctx, g, n, X, ldx, na, Y, ldy, nb, part, C, ldc);
 }
 
 template <typename T>

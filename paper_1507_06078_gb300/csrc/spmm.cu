@@ -120,7 +120,14 @@ struct VecIO<float, 4> {
 
 // T is the storage and arithmetic type of the blocks and of A's values (FP64 path or
 // the FP32 filter of the mixed path); column reductions always accumulate in FP64.
-template <typename T, int VEC>
+//
+// A warp owns one row at a time and covers its columns in NC chunks of 32*VEC (all chunks
+// of a chunk group in flight together): for every nonzero a_ij it issues NC independent
+// vector loads of row j of Yin, and the rows of X and Z that the epilogue needs are
+// requested before the gather loop, so each warp keeps 7*NC + 2*NC loads in flight on a
+// 7-point stencil.  The grid is sized to the CTAs that are resident at once (a single
+// wave), rows are dealt out in a fixed grid-stride order.
+template <typename T, int VEC, int NC>
 __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) {
   extern __shared__ double s_red[];  // [SPMM_WARPS][ncols]
   const int warp = threadIdx.x >> 5;
@@ -136,12 +143,26 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) 
   for (int64_t row = first; row < P.n; row += stride) {
     const int beg = __ldg(P.rowptr + row);
     const int end = __ldg(P.rowptr + row + 1);
-    for (int c0 = 0; c0 < ncols; c0 += CH) {
-      const int c = c0 + lane * VEC;
-      const bool act = c < ncols;
-      T acc[VEC];
+    for (int g0 = 0; g0 < ncols; g0 += NC * CH) {
+      int cc[NC];
+      bool act[NC];
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) acc[u] = T(0);
+      for (int h = 0; h < NC; ++h) {
+        cc[h] = g0 + h * CH + lane * VEC;
+        act[h] = cc[h] < ncols;
+      }
+      // epilogue operands first: their latency overlaps the gathers
+      T xv[NC][VEC], zv[NC][VEC];
+#pragma unroll
+      for (int h = 0; h < NC; ++h) {
+        if (P.X && act[h]) VecIO<T, VEC>::lds(P.X + row * P.ldx + cc[h], xv[h]);
+        if (P.Z && act[h]) VecIO<T, VEC>::lds(P.Z + row * P.ldz + cc[h], zv[h]);
+      }
+      T acc[NC][VEC];
+#pragma unroll
+      for (int h = 0; h < NC; ++h)
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[h][u] = T(0);
       for (int base = beg; base < end; base += 32) {
         const int e = base + lane;
         int jc = 0;
@@ -151,19 +172,27 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) 
           av = __ldg(P.val + e);
         }
         const int cnt = min(32, end - base);
-#pragma unroll 4
+#pragma unroll 2
         for (int t = 0; t < cnt; ++t) {
           const int j = __shfl_sync(0xffffffffu, jc, t);
           const T v = __shfl_sync(0xffffffffu, av, t);
-          if (act) {
-            T y[VEC];
-            VecIO<T, VEC>::ld(P.Yin + static_cast<int64_t>(j) * P.ldy + c, y);
+          const T* yrow = P.Yin + static_cast<int64_t>(j) * P.ldy;
+          T y[NC][VEC];
 #pragma unroll
-            for (int u = 0; u < VEC; ++u) acc[u] = fma(v, y[u], acc[u]);
-          }
+          for (int h = 0; h < NC; ++h)
+            if (act[h]) VecIO<T, VEC>::ld(yrow + cc[h], y[h]);
+#pragma unroll
+          for (int h = 0; h < NC; ++h)
+            if (act[h]) {
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) acc[h][u] = fma(v, y[h][u], acc[h][u]);
+            }
         }
       }
-      if (act) {
+#pragma unroll
+      for (int h = 0; h < NC; ++h) {
+        if (!act[h]) continue;
+        const int c = cc[h];
         T yi[VEC], o[VEC];
         if (P.beta != T(0) || P.dot_with_yin) {
           VecIO<T, VEC>::ld(P.Yin + row * P.ldy + c, yi);
@@ -173,20 +202,16 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) 
         }
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-          const T s = fma(P.alpha, acc[u], P.beta * yi[u]);
+          const T s = fma(P.alpha, acc[h][u], P.beta * yi[u]);
           o[u] = P.sy ? static_cast<T>(P.sy[c + u]) * s : s;
         }
         if (P.X) {
-          T x[VEC];
-          VecIO<T, VEC>::lds(P.X + row * P.ldx + c, x);
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sx[c + u]), x[u], o[u]);
+          for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sx[c + u]), xv[h][u], o[u]);
         }
         if (P.Z) {
-          T z[VEC];
-          VecIO<T, VEC>::lds(P.Z + row * P.ldz + c, z);
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sz[c + u]), z[u], o[u]);
+          for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sz[c + u]), zv[h][u], o[u]);
         }
         if (P.out) VecIO<T, VEC>::sts(P.out + row * P.ldo + c, o);
         if (P.red_part) {
@@ -290,13 +315,37 @@ __global__ void col_sumsq_kernel(int64_t n, const double* __restrict__ X, int64_
   }
 }
 
-template <typename T, int VEC>
-arb_status launch_spmm(arb_ctx ctx, const KParams<T>& P, int grid, size_t smem) {
-  ARB_CUDA(ctx, cudaFuncSetAttribute(spmm_fused_kernel<T, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     200 * 1024));
-  spmm_fused_kernel<T, VEC><<<grid, SPMM_THREADS, smem, ctx->stream>>>(P);
+// One wave: as many CTAs as are resident at once (at most the rows need), so no second,
+// partly empty wave of CTAs runs at the end.  With want_red, the per-CTA partial column
+// sums go to a workspace of grid x ncols doubles (returned with the grid).
+template <typename T, int VEC, int NC>
+arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, int* grid_out,
+                       double** part_out) {
+  auto kern = spmm_fused_kernel<T, VEC, NC>;
+  ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  int per_sm = 0;
+  ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPMM_THREADS, smem));
+  const int64_t want = (P.n + SPMM_WARPS - 1) / SPMM_WARPS;
+  int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(ctx->num_sms) * std::max(per_sm, 1)));
+  grid = std::max(grid, 1);
+  P.red_part = nullptr;
+  if (want_red) ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * P.ncols, &P.red_part));
+  kern<<<grid, SPMM_THREADS, smem, ctx->stream>>>(P);
   ARB_LAUNCHED(ctx);
+  *grid_out = grid;
+  *part_out = P.red_part;
   return ARB_OK;
+}
+
+template <typename T, int VEC>
+arb_status launch_spmm_nc(arb_ctx ctx, const KParams<T>& P, size_t smem, bool want_red, int* grid,
+                          double** part) {
+  constexpr int CH = 32 * VEC;
+  const int chunks = (P.ncols + CH - 1) / CH;
+  if (chunks <= 1) return launch_spmm<T, VEC, 1>(ctx, P, smem, want_red, grid, part);
+  if (chunks <= 2) return launch_spmm<T, VEC, 2>(ctx, P, smem, want_red, grid, part);
+  if (chunks <= 4) return launch_spmm<T, VEC, 4>(ctx, P, smem, want_red, grid, part);
+  return launch_spmm<T, VEC, 8>(ctx, P, smem, want_red, grid, part);
 }
 
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -352,15 +401,11 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   P.ldo = a.ldo;
   P.dot_with_yin = a.dot_with_yin ? 1 : 0;
   P.red_part = nullptr;
-  // rows spread over a fixed grid so the per-block partial sums are deterministic
-  const int64_t want = (A->n + SPMM_WARPS - 1) / SPMM_WARPS;
-  int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(ctx->num_sms) * 8));
-  grid = std::max(grid, 1);
   size_t smem = 0;
-  if (a.colred) {
+  const bool want_red = a.colred != nullptr;
+  if (want_red) {
     smem = static_cast<size_t>(SPMM_WARPS) * a.ncols * sizeof(double);
     if (smem > 200 * 1024) return set_error(ctx, ARB_INVALID_ARG, "spmm: too many columns for reduction");
-    ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * a.ncols, &P.red_part));
   }
   // widest vector access that the column count, leading dimensions and bases allow
   auto fits = [&](int v) {
@@ -371,23 +416,25 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
     if (a.out) ok = ok && (a.ldo % v == 0) && aligned(a.out, bytes);
     return ok && a.ncols > 32 * (v / 2);
   };
+  int grid = 0;
+  double* part = nullptr;
   if constexpr (sizeof(T) == 4) {
     if (fits(4)) {
-      ARB_TRY((launch_spmm<T, 4>(ctx, P, grid, smem)));
+      ARB_TRY((launch_spmm_nc<T, 4>(ctx, P, smem, want_red, &grid, &part)));
     } else if (fits(2)) {
-      ARB_TRY((launch_spmm<T, 2>(ctx, P, grid, smem)));
+      ARB_TRY((launch_spmm_nc<T, 2>(ctx, P, smem, want_red, &grid, &part)));
     } else {
-      ARB_TRY((launch_spmm<T, 1>(ctx, P, grid, smem)));
+      ARB_TRY((launch_spmm_nc<T, 1>(ctx, P, smem, want_red, &grid, &part)));
     }
   } else {
     if (fits(2)) {
-      ARB_TRY((launch_spmm<T, 2>(ctx, P, grid, smem)));
+      ARB_TRY((launch_spmm_nc<T, 2>(ctx, P, smem, want_red, &grid, &part)));
     } else {
-      ARB_TRY((launch_spmm<T, 1>(ctx, P, grid, smem)));
+      ARB_TRY((launch_spmm_nc<T, 1>(ctx, P, smem, want_red, &grid, &part)));
     }
   }
-  if (a.colred) {
-    reduce_partials_kernel<<<a.ncols, 256, 0, ctx->stream>>>(P.red_part, grid, a.ncols, a.colred);
+  if (want_red) {
+    reduce_partials_kernel<<<a.ncols, 256, 0, ctx->stream>>>(part, grid, a.ncols, a.colred);
     ARB_LAUNCHED(ctx);
   }
   return ARB_OK;

@@ -136,3 +136,17 @@ def test_golden_fixture_matches_closed_form_and_oracle():
     c = json.load(open(os.path.join(here, "interpolant_coeffs.json")))["coeffs"]
     for d, a in c.items():
         np.testing.assert_allclose(a, O.interpolant_cheb_coeffs(int(d)), atol=1e-15)
+
+
+def test_oracle_b_every_arr_reading():
+    # Section 5's reading (b refreshed after every ARR) reaches the same pairs as
+    # Algorithm 8's literal continuation-only update
+    A = I.laplacian_3d(12)
+    X0 = I.gaussian_block(A.n, 24, 12)
+    r_lit = O.arrabit_mpm(_scipy(A), 20, X0, which="smallest", tol=1e-8, q=2, degree=10)
+    r_arr = O.arrabit_mpm(_scipy(A), 20, X0, which="smallest", tol=1e-8, q=2, degree=10, b_update="every_arr")
+    assert r_lit.converged and r_arr.converged
+    lam = laplacian_3d_eigs(12)[:20]
+    np.testing.assert_allclose(r_arr.evals, lam, atol=1e-9)
+    np.testing.assert_allclose(r_lit.evals, lam, atol=1e-9)
+    assert r_arr.history[-1].b > r_arr.history[0].b  # b moved towards lambda_{k+q} of B
