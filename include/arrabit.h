@@ -191,6 +191,23 @@ arb_status arb_spmm(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift,
 arb_status arb_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
                     const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
 
+/* arb_gram for callers that cannot allocate device memory (for example code running
+ * while a stream is captured into a CUDA graph, or applications whose device memory is
+ * owned by their own pool): the same product C = X^T Y, but its split-K partial sums live
+ * in a static device array of 1,048,576 doubles (8 MiB) that the library holds on every
+ * device it is loaded on, so the call allocates nothing.  The paper has no counterpart;
+ * this is an interface variant only.
+ *  - Limit: na * nb <= 1048576, else ARB_INVALID_ARG (nothing is launched).  Larger
+ *    shapes go through arb_gram.  The row split shrinks so the partial sums fit.
+ *  - The first call on a device looks up the array's device address (with that device
+ *    current) and caches it; make that first call before any stream capture.
+ *  - Every call shares the one array: calls whose kernels overlap on the GPU (different
+ *    streams, or two contexts on one device) race on it and must be serialised by the
+ *    caller.  Each call overwrites every partial sum it reads, so no clearing is needed.
+ *  - Results equal arb_gram's up to the order of the split sums. */
+arb_status arb_gram_noalloc(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
+                            const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
+
 /* Eigen-decomposition H = V diag(w) V^T of a symmetric m x m matrix (row-major, ldh) by
  * parallel cyclic Jacobi on the device (Alg. 1 step 3, reading H = V Sigma V^T).
  * w: float64[m] descending; V: m x m row-major (ldv), column j the eigenvector of w[j].

@@ -78,6 +78,7 @@ _PROTOS = {
     "arb_filter_coefficients": (_i32, [_i32, _i32, _vp]),
     "arb_spmm": (_i32, [_vp, _vp, _dbl, _dbl, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
+    "arb_gram_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
     "arb_syevj": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _i64, C.POINTER(_i32)]),
     "arb_rcond_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, C.POINTER(_dbl)]),
     "arb_orth": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, C.POINTER(_i32)]),
@@ -322,6 +323,17 @@ def arb_gram(ctx: Context, X, Y, C_out=None):
     ldc = _dev2d(C_out, "C")
     _check(ctx, load().arb_gram(ctx.handle, X.shape[0], _vp(_ptr(X)), ldx, X.shape[1], _vp(_ptr(Y)), ldy,
                                 Y.shape[1], _vp(_ptr(C_out)), ldc), "arb_gram")
+    return C_out
+
+
+def arb_gram_noalloc(ctx: Context, X, Y, C_out):
+    """C = X^T Y without any device allocation by the library (partial sums in its static
+    scratch); C_out must be given."""
+    ldx = _dev2d(X, "X")
+    ldy = _dev2d(Y, "Y")
+    ldc = _dev2d(C_out, "C")
+    _check(ctx, load().arb_gram_noalloc(ctx.handle, X.shape[0], _vp(_ptr(X)), ldx, X.shape[1], _vp(_ptr(Y)), ldy,
+                                        Y.shape[1], _vp(_ptr(C_out)), ldc), "arb_gram_noalloc")
     return C_out
 
 

@@ -163,6 +163,10 @@ arb_status col_sumsq(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32
 template <typename T>
 arb_status gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t na, const T* Y, int64_t ldy,
                 int32_t nb, double* C, int64_t ldc);
+// The FP64 Gram product with caller-provided partial-sum storage (part_capacity doubles,
+// at least na * nb); no workspace is requested.  The row split shrinks to fit.
+arb_status gram_into(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na, const double* Y,
+                     int64_t ldy, int32_t nb, double* C, int64_t ldc, double* part, size_t part_capacity);
 // Out (n x nb) = alpha * In (n x na) * W (na x nb, FP64, ldw) + beta * Out, accumulated in T.
 // Out must not alias In.
 template <typename T>

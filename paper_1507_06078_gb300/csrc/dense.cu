@@ -485,6 +485,15 @@ arb_status gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t na, con
   return gram_launch<T>(ctx, g, n, X, ldx, na, Y, ldy, nb, part, C, ldc);
 }
 
+arb_status gram_into(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na, const double* Y,
+                     int64_t ldy, int32_t nb, double* C, int64_t ldc, double* part, size_t part_capacity) {
+  if (na <= 0 || nb <= 0) return ARB_OK;
+  if (static_cast<size_t>(na) * static_cast<size_t>(nb) > part_capacity)
+    return set_error(ctx, ARB_INVALID_ARG, "gram: na * nb exceeds the partial-sum capacity");
+  const GramPlan g = gram_plan<double>(ctx, n, X, ldx, na, Y, ldy, nb, part_capacity);
+  return gram_launch<double>(ctx, g, n, X, ldx, na, Y, ldy, nb, part, C, ldc);
+}
+
 template <typename T>
 arb_status gemm_tall(arb_ctx ctx, int64_t n, const T* In, int64_t ldi, int32_t na, const double* W,
                      int64_t ldw, int32_t nb, double alpha, double beta, T* Out, int64_t ldo) {
