@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=128, help="3D grid side (128 = the benchmark workload)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--b-update", default="continuation", choices=["continuation", "every_arr"],
+                    help="when b = mu_{k+q} is refreshed: at continuation steps (Algorithm 8) or after "
+                         "every ARR (Section 5)")
     ap.add_argument("--compare-fp64", action="store_true",
                     help="also time one plain FP64 solve of the same workload")
     ap.add_argument("--no-e2e", action="store_true")
@@ -225,6 +228,7 @@ def run_ours(args):
     opts = arb.arb_options_default(W.k)
     opts.p, opts.q, opts.degree = W.p, W.q, W.degree
     opts.precision = arb.ARB_MIXED if args.precision == "mixed" else arb.ARB_FP64
+    opts.b_update = 1 if args.b_update == "every_arr" else 0
 
     def step():
         return arb.arb_solve(ctx, mat, W.k, arb.ARB_SMALLEST, W.tol, opts, x0=X0, evecs="device")
@@ -298,6 +302,7 @@ def run_ours(args):
     if args.compare_fp64 and args.precision == "mixed":
         o64 = arb.arb_options_default(W.k)
         o64.p, o64.q, o64.degree, o64.precision = W.p, W.q, W.degree, arb.ARB_FP64
+        o64.b_update = opts.b_update
         barrier()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -351,6 +356,7 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": W.name, "n": W.A.n, "nnz": W.A.nnz, "k": W.k, "p": W.p, "q": W.q,
                            "degree": W.degree, "tol": W.tol, "precision": args.precision,
+                           "b_update": args.b_update,
                            "l2": "inputs larger than L2 (A 175 MB, X0 4 GB, work blocks ~50 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
