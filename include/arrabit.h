@@ -80,7 +80,9 @@ typedef struct {
   double tol1;          /* first continuation tolerance; 0: max(1e-6, tol) if tol <= 1e-8 else tol */
   double shift_sigma;   /* sigma of sigma I - A for ARB_SMALLEST; NaN: Gershgorin upper bound of A */
   double tol_switch;    /* ARB_MIXED: relative residual at which the FP32 phase hands over to
-                           FP64 (one continuation step is taken there); 0: 1e-5 */
+                           FP64 (never below 32 u32 ||A||, the FP32 floor); 0: 1e-5.  The FP32
+                           phase also ends when an outer iteration fails to halve maxres.  The
+                           FP64 phase starts from the FP32 Ritz block with b = mu_{k+q}. */
   uint64_t seed;        /* stream for padding columns (Philox4x32-10 + Box-Muller) */
 } arb_options;
 

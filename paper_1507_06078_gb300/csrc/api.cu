@@ -493,7 +493,7 @@ arb_status alloc_blocks(arb_ctx ctx, const SolveState& S, BlockSet<T>& B) {
 // tol_t updated as in eq. contin) before returning.
 template <typename T>
 arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, double tol_phase, double rc_floor,
-                     bool lock, bool continue_on_phase_tol) {
+                     bool lock, bool continue_on_phase_tol, bool stop_on_stagnation = false) {
   const int64_t n = S.n;
   const int32_t p = S.p, k = S.k;
   S.best = std::numeric_limits<double>::infinity();
@@ -501,6 +501,7 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
   S.outer = 0;
   S.stop = ARB_STOP_MAXIT;
   float ms = 0.f;
+  double prev_maxres = std::numeric_limits<double>::infinity();
   for (int j = 1; j <= S.o.maxit; ++j) {
     S.outer = j;
     S.info.outer_iters++;
@@ -607,12 +608,20 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     if (maxres <= tol_phase) {
       S.stop = ARB_STOP_CONVERGED;
       if (continue_on_phase_tol && tol_phase > S.tol) {
-        S.tol_t = std::max(1e-2 * S.tol_t, S.tol);
         S.b = S.h_mu[p - 1];
         if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
       }
       return ARB_OK;
     }
+    // mixed path: the FP32 iterate has reached its accuracy floor when an outer iteration
+    // no longer halves maxres; hand over to FP64 with the best interval estimate
+    if (stop_on_stagnation && j >= 2 && maxres > 0.5 * prev_maxres) {
+      S.stop = ARB_STOP_STALLED;
+      S.b = S.h_mu[p - 1];
+      if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+      return ARB_OK;
+    }
+    prev_maxres = maxres;
     if (maxres < (1.0 + 9.0 * h / k) * tol_phase) {
       S.stop = ARB_STOP_NEAR_TOL;
       return ARB_OK;
@@ -779,12 +788,18 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     // Phase 1: FP32 blocks until the continuation tolerance of the FP32 phase is met
     // (reading c7: inner-stop threshold >= 100 u32; precision switches when continuation
     // tightens tol_t below what FP32 resolves).
-    const double sw = o.tol_switch > 0.0 ? o.tol_switch : 1e-5;
+    // FP32 residual floor ~ 32 u32 ||B|| (||B|| bounded by Gershgorin): the FP32 phase ends
+    // there, at tol_switch, or as soon as an outer iteration stops halving maxres.
+    const double normB = std::max(std::fabs(S.sigma - glo), std::fabs(S.sigma - ghi));
+    const double floor32 = 32.0 * 5.96e-8 * (S.smallest ? normB : std::max(std::fabs(glo), std::fabs(ghi)));
+    const double sw = std::max(o.tol_switch > 0.0 ? o.tol_switch : 1e-5, floor32);
     const double tol_phase = std::max(sw, tol);
+    const double tol_t64 = S.tol_t;  // the FP64 phase starts the paper's continuation at tol_1
     S.tol_t = std::max(S.tol_t, tol_phase);
     ARB_TRY((copy_block<double, float>(ctx, n, D.X, D.ld, p, F.X, F.ld)));
-    ARB_TRY(run_outer<float>(ctx, mat, S, F, tol_phase, 100.0 * 5.96e-8, false, true));
+    ARB_TRY(run_outer<float>(ctx, mat, S, F, tol_phase, 100.0 * 5.96e-8, false, true, true));
     S.info.outer_iters_fp32 = S.info.outer_iters;
+    S.tol_t = tol_t64;
     const bool done32 = (S.stop == ARB_STOP_CONVERGED || S.stop == ARB_STOP_NEAR_TOL) && tol_phase <= tol;
     // Phase 2: FP64 refinement from the FP32 Ritz block (Algorithm 8 continued in FP64)
     ARB_TRY((copy_block<float, double>(ctx, n, F.Xall, F.ld, p, D.Xall, D.ld)));

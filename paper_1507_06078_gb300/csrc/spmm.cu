@@ -126,31 +126,50 @@ struct VecIO<float, 4> {
 // vector loads of row j of Yin, and the rows of X and Z that the epilogue needs are
 // requested before the gather loop, so each warp keeps 7*NC + 2*NC loads in flight on a
 // 7-point stencil.  The grid is sized to the CTAs that are resident at once (a single
-// wave), rows are dealt out in a fixed grid-stride order.
-template <typename T, int VEC, int NC>
+// wave); rows are dealt out in a fixed grid-stride order.
+//
+// The per-column multipliers depend only on the lane's columns: the FP32 kernel converts
+// them once per chunk group into registers (an FP64->FP32 conversion per row would run on
+// GB300's narrow FP64 pipe).  RED selects the column reduction (sum of out^2 or out*Yin),
+// kept in FP64 registers per lane and reduced across the CTA at the end.
+template <typename T, int VEC, int NC, bool RED>
 __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) {
-  extern __shared__ double s_red[];  // [SPMM_WARPS][ncols]
+  extern __shared__ double s_red[];  // [SPMM_WARPS][ncols] when RED
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int ncols = P.ncols;
-  double* my_red = s_red + static_cast<size_t>(warp) * ncols;
-  if (P.red_part)
-    for (int c = lane; c < ncols; c += 32) my_red[c] = 0.0;
-  __syncwarp();
   constexpr int CH = 32 * VEC;
+  constexpr bool HOIST = sizeof(T) == 4;
   const int64_t first = static_cast<int64_t>(blockIdx.x) * SPMM_WARPS + warp;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * SPMM_WARPS;
-  for (int64_t row = first; row < P.n; row += stride) {
-    const int beg = __ldg(P.rowptr + row);
-    const int end = __ldg(P.rowptr + row + 1);
-    for (int g0 = 0; g0 < ncols; g0 += NC * CH) {
-      int cc[NC];
-      bool act[NC];
+  for (int g0 = 0; g0 < ncols; g0 += NC * CH) {
+    int cc[NC];
+    bool act[NC];
 #pragma unroll
-      for (int h = 0; h < NC; ++h) {
-        cc[h] = g0 + h * CH + lane * VEC;
-        act[h] = cc[h] < ncols;
-      }
+    for (int h = 0; h < NC; ++h) {
+      cc[h] = g0 + h * CH + lane * VEC;
+      act[h] = cc[h] < ncols;
+    }
+    T csy[HOIST ? NC : 1][VEC], csx[HOIST ? NC : 1][VEC], csz[HOIST ? NC : 1][VEC];
+    if constexpr (HOIST) {
+#pragma unroll
+      for (int h = 0; h < NC; ++h)
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          const int c = act[h] ? cc[h] + u : 0;
+          csy[h][u] = P.sy ? static_cast<T>(P.sy[c]) : T(1);
+          csx[h][u] = P.X ? static_cast<T>(P.sx[c]) : T(0);
+          csz[h][u] = P.Z ? static_cast<T>(P.sz[c]) : T(0);
+        }
+    }
+    double red[RED ? NC : 1][VEC];
+#pragma unroll
+    for (int h = 0; h < (RED ? NC : 1); ++h)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) red[h][u] = 0.0;
+    for (int64_t row = first; row < P.n; row += stride) {
+      const int beg = __ldg(P.rowptr + row);
+      const int end = __ldg(P.rowptr + row + 1);
       // epilogue operands first: their latency overlaps the gathers
       T xv[NC][VEC], zv[NC][VEC];
 #pragma unroll
@@ -194,7 +213,7 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) 
         if (!act[h]) continue;
         const int c = cc[h];
         T yi[VEC], o[VEC];
-        if (P.beta != T(0) || P.dot_with_yin) {
+        if (P.beta != T(0) || (RED && P.dot_with_yin)) {
           VecIO<T, VEC>::ld(P.Yin + row * P.ldy + c, yi);
         } else {
 #pragma unroll
@@ -202,29 +221,43 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) 
         }
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-          const T s = fma(P.alpha, acc[h][u], P.beta * yi[u]);
-          o[u] = P.sy ? static_cast<T>(P.sy[c + u]) * s : s;
+          const T sy = HOIST ? csy[HOIST ? h : 0][u] : (P.sy ? static_cast<T>(P.sy[c + u]) : T(1));
+          o[u] = sy * fma(P.alpha, acc[h][u], P.beta * yi[u]);
         }
         if (P.X) {
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sx[c + u]), xv[h][u], o[u]);
+          for (int u = 0; u < VEC; ++u) {
+            const T sx = HOIST ? csx[HOIST ? h : 0][u] : static_cast<T>(P.sx[c + u]);
+            o[u] = fma(sx, xv[h][u], o[u]);
+          }
         }
         if (P.Z) {
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) o[u] = fma(static_cast<T>(P.sz[c + u]), zv[h][u], o[u]);
+          for (int u = 0; u < VEC; ++u) {
+            const T sz = HOIST ? csz[HOIST ? h : 0][u] : static_cast<T>(P.sz[c + u]);
+            o[u] = fma(sz, zv[h][u], o[u]);
+          }
         }
         if (P.out) VecIO<T, VEC>::sts(P.out + row * P.ldo + c, o);
-        if (P.red_part) {
+        if constexpr (RED) {
 #pragma unroll
           for (int u = 0; u < VEC; ++u) {
             const double od = static_cast<double>(o[u]);
-            my_red[c + u] += P.dot_with_yin ? od * static_cast<double>(yi[u]) : od * od;
+            red[h][u] += P.dot_with_yin ? od * static_cast<double>(yi[u]) : od * od;
           }
         }
       }
     }
+    if constexpr (RED) {
+      double* my_red = s_red + static_cast<size_t>(warp) * ncols;
+#pragma unroll
+      for (int h = 0; h < NC; ++h)
+        if (act[h])
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) my_red[cc[h] + u] = red[h][u];
+    }
   }
-  if (P.red_part) {
+  if constexpr (RED) {
     __syncthreads();
     for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
       double s = 0.0;
@@ -321,7 +354,7 @@ __global__ void col_sumsq_kernel(int64_t n, const double* __restrict__ X, int64_
 template <typename T, int VEC, int NC>
 arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, int* grid_out,
                        double** part_out) {
-  auto kern = spmm_fused_kernel<T, VEC, NC>;
+  void (*kern)(KParams<T>) = want_red ? spmm_fused_kernel<T, VEC, NC, true> : spmm_fused_kernel<T, VEC, NC, false>;
   ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPMM_THREADS, smem));
@@ -342,10 +375,10 @@ arb_status launch_spmm_nc(arb_ctx ctx, const KParams<T>& P, size_t smem, bool wa
                           double** part) {
   constexpr int CH = 32 * VEC;
   const int chunks = (P.ncols + CH - 1) / CH;
+  // wider blocks loop over groups of (at most) 4 chunks: more would spill registers
   if (chunks <= 1) return launch_spmm<T, VEC, 1>(ctx, P, smem, want_red, grid, part);
   if (chunks <= 2) return launch_spmm<T, VEC, 2>(ctx, P, smem, want_red, grid, part);
-  if (chunks <= 4) return launch_spmm<T, VEC, 4>(ctx, P, smem, want_red, grid, part);
-  return launch_spmm<T, VEC, 8>(ctx, P, smem, want_red, grid, part);
+  return launch_spmm<T, VEC, 4>(ctx, P, smem, want_red, grid, part);
 }
 
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }

@@ -210,3 +210,73 @@ def workload_3d(m: int, k: int, p: int, degree: int = 20, q: int = 2, tol: float
     """Scaled-down member of the 3D Laplacian family (same stencil, smaller grid)."""
     return Workload(f"laplace3d_{m}^3_k{k}_p{p}_d{degree}_q{q}", laplacian_3d(m), k,
                     "smallest", p, q, degree, tol, seed)
+
+
+# ---------------------------------------------------------------------------------
+# Normalised graph Laplacian of a Chung-Lu random graph
+# ---------------------------------------------------------------------------------
+def chung_lu_weights(n: int, beta: float = 2.5, mean: float = 16.0, wmax: float = 5000.0) -> np.ndarray:
+    """Expected degrees w_i = c (i + i0)^(-1/(beta-1)), i = 0..n-1, with c and i0 chosen so
+    that the mean is `mean` and the largest (w_0) is `wmax` (bisection on i0)."""
+    g = 1.0 / (beta - 1.0)
+    i = np.arange(n, dtype=np.float64)
+
+    def mean_for(i0):
+        w = (i + i0) ** (-g)
+        return wmax * w.mean() / i0 ** (-g)
+
+    lo, hi = 1e-6, 1e12
+    for _ in range(200):
+        mid = np.sqrt(lo * hi)
+        if mean_for(mid) > mean:  # the mean grows with i0
+            hi = mid
+        else:
+            lo = mid
+    i0 = np.sqrt(lo * hi)
+    return wmax * ((i + i0) / i0) ** (-g)
+
+
+def chung_lu_laplacian(n: int, seed: int = 1507, beta: float = 2.5, mean: float = 16.0,
+                       wmax: float = 5000.0) -> tuple[CSR, np.ndarray]:
+    """L = I - D^{-1/2} W D^{-1/2} of the largest connected component of a Chung-Lu graph.
+
+    Edges: about sum(w)/2 endpoint pairs drawn independently with probability proportional
+    to w (a pair u != v is then present with probability 1 - exp(-w_u w_v / sum w), the
+    expected-degree model); duplicates and self-loops are dropped, the graph is symmetric
+    and unweighted.  Values -1/sqrt(d_u d_v) are computed in FP64 with the operands in a
+    fixed order and rounded to FP32 once (stored widened to float64).  Returns the CSR
+    matrix and the original vertex ids of the component.
+    """
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    w = chung_lu_weights(n, beta, mean, wmax)
+    S = w.sum()
+    rng = np.random.Generator(np.random.Philox(seed))
+    m = rng.poisson(S / 2.0)
+    cdf = np.cumsum(w / S)
+    cdf[-1] = 1.0
+    u = np.searchsorted(cdf, rng.random(m), side="right")
+    v = np.searchsorted(cdf, rng.random(m), side="right")
+    keep = u != v
+    u, v = u[keep], v[keep]
+    a, b = np.minimum(u, v), np.maximum(u, v)
+    key = np.unique(a.astype(np.int64) * n + b)
+    a, b = (key // n).astype(np.int64), (key % n).astype(np.int64)
+    W = sp.coo_matrix((np.ones(a.size), (a, b)), shape=(n, n)).tocsr()
+    W = (W + W.T).tocsr()
+    ncomp, lab = connected_components(W, directed=False)
+    big = np.argmax(np.bincount(lab))
+    ids = np.nonzero(lab == big)[0]
+    W = W[ids][:, ids].tocsr()
+    W.sort_indices()
+    deg = np.asarray(W.sum(axis=1)).ravel()
+    rows = np.repeat(np.arange(W.shape[0]), np.diff(W.indptr))
+    cols = W.indices
+    du, dv = deg[np.minimum(rows, cols)], deg[np.maximum(rows, cols)]
+    off = (-1.0 / np.sqrt(du * dv)).astype(np.float32).astype(np.float64)
+    nn = W.shape[0]
+    L = sp.csr_matrix((off, cols, W.indptr), shape=(nn, nn)) + sp.identity(nn, format="csr")
+    L = L.tocsr()
+    L.sort_indices()
+    return CSR(nn, L.indptr.astype(np.int32), L.indices.astype(np.int32), L.data.astype(np.float64)), ids
