@@ -18,6 +18,13 @@ namespace {
 
 constexpr int SPMM_THREADS = 256;
 constexpr int SPMM_WARPS = SPMM_THREADS / 32;
+// Tuning defaults: widest FP32 vector access per lane and gathers issued per batch.
+#ifndef ARB_SPMM_F32_MAX_VEC
+#define ARB_SPMM_F32_MAX_VEC 4
+#endif
+#ifndef ARB_SPMM_UNROLL
+#define ARB_SPMM_UNROLL 8
+#endif
 
 template <typename T>
 struct KParams {
@@ -121,67 +128,57 @@ struct VecIO<float, 4> {
 // T is the storage and arithmetic type of the blocks and of A's values (FP64 path or
 // the FP32 filter of the mixed path); column reductions always accumulate in FP64.
 //
-// A warp owns one row at a time and covers its columns in NC chunks of 32*VEC (all chunks
-// of a chunk group in flight together): for every nonzero a_ij it issues NC independent
-// vector loads of row j of Yin, and the rows of X and Z that the epilogue needs are
-// requested before the gather loop, so each warp keeps 7*NC + 2*NC loads in flight on a
-// 7-point stencil.  The grid is sized to the CTAs that are resident at once (a single
-// wave); rows are dealt out in a fixed grid-stride order.
-//
-// The per-column multipliers depend only on the lane's columns: the FP32 kernel converts
-// them once per chunk group into registers (an FP64->FP32 conversion per row would run on
-// GB300's narrow FP64 pipe).  RED selects the column reduction (sum of out^2 or out*Yin),
-// kept in FP64 registers per lane and reduced across the CTA at the end.
-template <typename T, int VEC, int NC, bool RED>
+// Work split: a row's columns are cut into nch chunks of 32*VEC; every warp owns one
+// fixed chunk (warp id mod nch) and walks the rows dealt to it in a fixed grid-stride
+// order, so its lanes always touch the same columns and the per-column multipliers are
+// loaded (and, for FP32, converted) once into registers instead of once per row.  For
+// every row the warp first requests the epilogue rows of X and Z, then gathers the rows
+// of Yin named by the row's nonzeros in batches of UNR loads issued back to back before
+// any of them is used: on a 7-point stencil all 7 gathers and both epilogue rows are in
+// flight together.  The grid is the number of CTAs resident at once (one wave).
+// RED adds the column reduction (sum of out^2 or out*Yin) in FP64 registers, combined per
+// CTA through shared memory.
+template <typename T, int VEC, bool RED>
 __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) {
   extern __shared__ double s_red[];  // [SPMM_WARPS][ncols] when RED
+  constexpr int CH = 32 * VEC;
+  constexpr int UNR = ARB_SPMM_UNROLL;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int ncols = P.ncols;
-  constexpr int CH = 32 * VEC;
-  constexpr bool HOIST = sizeof(T) == 4;
-  const int64_t first = static_cast<int64_t>(blockIdx.x) * SPMM_WARPS + warp;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * SPMM_WARPS;
-  for (int g0 = 0; g0 < ncols; g0 += NC * CH) {
-    int cc[NC];
-    bool act[NC];
+  const int nch = (ncols + CH - 1) / CH;
+  if constexpr (RED) {
+    for (int c = lane; c < ncols; c += 32) s_red[static_cast<size_t>(warp) * ncols + c] = 0.0;
+    __syncwarp();
+  }
+  const int64_t gw = static_cast<int64_t>(blockIdx.x) * SPMM_WARPS + warp;
+  const int64_t nwarps = static_cast<int64_t>(gridDim.x) * SPMM_WARPS;
+  const int64_t rstride = nwarps / nch;  // warps per chunk
+  const int chunk = static_cast<int>(gw % nch);
+  const int64_t r_first = gw / nch;
+  const int c = chunk * CH + lane * VEC;
+  const bool act = (r_first < rstride) && (c < ncols);
+  T csy[VEC], csx[VEC], csz[VEC];
 #pragma unroll
-    for (int h = 0; h < NC; ++h) {
-      cc[h] = g0 + h * CH + lane * VEC;
-      act[h] = cc[h] < ncols;
-    }
-    T csy[HOIST ? NC : 1][VEC], csx[HOIST ? NC : 1][VEC], csz[HOIST ? NC : 1][VEC];
-    if constexpr (HOIST) {
+  for (int u = 0; u < VEC; ++u) {
+    const int cu = act ? c + u : 0;
+    csy[u] = P.sy ? static_cast<T>(P.sy[cu]) : T(1);
+    csx[u] = P.X ? static_cast<T>(P.sx[cu]) : T(0);
+    csz[u] = P.Z ? static_cast<T>(P.sz[cu]) : T(0);
+  }
+  double red[VEC];
 #pragma unroll
-      for (int h = 0; h < NC; ++h)
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) {
-          const int c = act[h] ? cc[h] + u : 0;
-          csy[h][u] = P.sy ? static_cast<T>(P.sy[c]) : T(1);
-          csx[h][u] = P.X ? static_cast<T>(P.sx[c]) : T(0);
-          csz[h][u] = P.Z ? static_cast<T>(P.sz[c]) : T(0);
-        }
-    }
-    double red[RED ? NC : 1][VEC];
-#pragma unroll
-    for (int h = 0; h < (RED ? NC : 1); ++h)
-#pragma unroll
-      for (int u = 0; u < VEC; ++u) red[h][u] = 0.0;
-    for (int64_t row = first; row < P.n; row += stride) {
+  for (int u = 0; u < VEC; ++u) red[u] = 0.0;
+  if (r_first < rstride) {
+    for (int64_t row = r_first; row < P.n; row += rstride) {
       const int beg = __ldg(P.rowptr + row);
       const int end = __ldg(P.rowptr + row + 1);
-      // epilogue operands first: their latency overlaps the gathers
-      T xv[NC][VEC], zv[NC][VEC];
+      T xv[VEC], zv[VEC];
+      if (P.X && act) VecIO<T, VEC>::lds(P.X + row * P.ldx + c, xv);
+      if (P.Z && act) VecIO<T, VEC>::lds(P.Z + row * P.ldz + c, zv);
+      T acc[VEC];
 #pragma unroll
-      for (int h = 0; h < NC; ++h) {
-        if (P.X && act[h]) VecIO<T, VEC>::lds(P.X + row * P.ldx + cc[h], xv[h]);
-        if (P.Z && act[h]) VecIO<T, VEC>::lds(P.Z + row * P.ldz + cc[h], zv[h]);
-      }
-      T acc[NC][VEC];
-#pragma unroll
-      for (int h = 0; h < NC; ++h)
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) acc[h][u] = T(0);
+      for (int u = 0; u < VEC; ++u) acc[u] = T(0);
       for (int base = beg; base < end; base += 32) {
         const int e = base + lane;
         int jc = 0;
@@ -191,78 +188,62 @@ __global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) 
           av = __ldg(P.val + e);
         }
         const int cnt = min(32, end - base);
-#pragma unroll 2
-        for (int t = 0; t < cnt; ++t) {
-          const int j = __shfl_sync(0xffffffffu, jc, t);
-          const T v = __shfl_sync(0xffffffffu, av, t);
-          const T* yrow = P.Yin + static_cast<int64_t>(j) * P.ldy;
-          T y[NC][VEC];
+        for (int t0 = 0; t0 < cnt; t0 += UNR) {
+          int jj[UNR];
+          T vv[UNR];
 #pragma unroll
-          for (int h = 0; h < NC; ++h)
-            if (act[h]) VecIO<T, VEC>::ld(yrow + cc[h], y[h]);
+          for (int t = 0; t < UNR; ++t) {
+            jj[t] = __shfl_sync(0xffffffffu, jc, t0 + t < 32 ? t0 + t : 31);
+            vv[t] = __shfl_sync(0xffffffffu, av, t0 + t < 32 ? t0 + t : 31);
+          }
+          T y[UNR][VEC];
 #pragma unroll
-          for (int h = 0; h < NC; ++h)
-            if (act[h]) {
+          for (int t = 0; t < UNR; ++t)
+            if (act && t0 + t < cnt) VecIO<T, VEC>::ld(P.Yin + static_cast<int64_t>(jj[t]) * P.ldy + c, y[t]);
 #pragma unroll
-              for (int u = 0; u < VEC; ++u) acc[h][u] = fma(v, y[h][u], acc[h][u]);
-            }
+          for (int t = 0; t < UNR; ++t)
+            if (act && t0 + t < cnt)
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) acc[u] = fma(vv[t], y[t][u], acc[u]);
         }
       }
+      if (!act) continue;
+      T yi[VEC], o[VEC];
+      if (P.beta != T(0) || (RED && P.dot_with_yin)) {
+        VecIO<T, VEC>::ld(P.Yin + row * P.ldy + c, yi);
+      } else {
 #pragma unroll
-      for (int h = 0; h < NC; ++h) {
-        if (!act[h]) continue;
-        const int c = cc[h];
-        T yi[VEC], o[VEC];
-        if (P.beta != T(0) || (RED && P.dot_with_yin)) {
-          VecIO<T, VEC>::ld(P.Yin + row * P.ldy + c, yi);
-        } else {
+        for (int u = 0; u < VEC; ++u) yi[u] = T(0);
+      }
 #pragma unroll
-          for (int u = 0; u < VEC; ++u) yi[u] = T(0);
-        }
+      for (int u = 0; u < VEC; ++u) o[u] = csy[u] * fma(P.alpha, acc[u], P.beta * yi[u]);
+      if (P.X) {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) o[u] = fma(csx[u], xv[u], o[u]);
+      }
+      if (P.Z) {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) o[u] = fma(csz[u], zv[u], o[u]);
+      }
+      if (P.out) VecIO<T, VEC>::sts(P.out + row * P.ldo + c, o);
+      if constexpr (RED) {
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-          const T sy = HOIST ? csy[HOIST ? h : 0][u] : (P.sy ? static_cast<T>(P.sy[c + u]) : T(1));
-          o[u] = sy * fma(P.alpha, acc[h][u], P.beta * yi[u]);
-        }
-        if (P.X) {
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) {
-            const T sx = HOIST ? csx[HOIST ? h : 0][u] : static_cast<T>(P.sx[c + u]);
-            o[u] = fma(sx, xv[h][u], o[u]);
-          }
-        }
-        if (P.Z) {
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) {
-            const T sz = HOIST ? csz[HOIST ? h : 0][u] : static_cast<T>(P.sz[c + u]);
-            o[u] = fma(sz, zv[h][u], o[u]);
-          }
-        }
-        if (P.out) VecIO<T, VEC>::sts(P.out + row * P.ldo + c, o);
-        if constexpr (RED) {
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) {
-            const double od = static_cast<double>(o[u]);
-            red[h][u] += P.dot_with_yin ? od * static_cast<double>(yi[u]) : od * od;
-          }
+          const double od = static_cast<double>(o[u]);
+          red[u] += P.dot_with_yin ? od * static_cast<double>(yi[u]) : od * od;
         }
       }
-    }
-    if constexpr (RED) {
-      double* my_red = s_red + static_cast<size_t>(warp) * ncols;
-#pragma unroll
-      for (int h = 0; h < NC; ++h)
-        if (act[h])
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) my_red[cc[h] + u] = red[h][u];
     }
   }
   if constexpr (RED) {
+    if (act)
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) s_red[static_cast<size_t>(warp) * ncols + c + u] = red[u];
     __syncthreads();
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
-      double s = 0.0;
-      for (int w = 0; w < SPMM_WARPS; ++w) s += s_red[static_cast<size_t>(w) * ncols + c];
-      P.red_part[static_cast<size_t>(blockIdx.x) * ncols + c] = s;
+    for (int cc = threadIdx.x; cc < ncols; cc += blockDim.x) {
+      double sum = 0.0;
+      for (int w = 0; w < SPMM_WARPS; ++w) sum += s_red[static_cast<size_t>(w) * ncols + cc];
+      P.red_part[static_cast<size_t>(blockIdx.x) * ncols + cc] = sum;
     }
   }
 }
@@ -348,19 +329,21 @@ __global__ void col_sumsq_kernel(int64_t n, const double* __restrict__ X, int64_
   }
 }
 
-// One wave: as many CTAs as are resident at once (at most the rows need), so no second,
-// partly empty wave of CTAs runs at the end.  With want_red, the per-CTA partial column
-// sums go to a workspace of grid x ncols doubles (returned with the grid).
-template <typename T, int VEC, int NC>
+// One wave: as many CTAs as are resident at once (at most what the rows need), so no
+// second, partly empty wave of CTAs runs at the end.  With want_red, the per-CTA partial
+// column sums go to a workspace of grid x ncols doubles (returned with the grid).
+template <typename T, int VEC>
 arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, int* grid_out,
                        double** part_out) {
-  void (*kern)(KParams<T>) = want_red ? spmm_fused_kernel<T, VEC, NC, true> : spmm_fused_kernel<T, VEC, NC, false>;
+  void (*kern)(KParams<T>) = want_red ? spmm_fused_kernel<T, VEC, true> : spmm_fused_kernel<T, VEC, false>;
   ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPMM_THREADS, smem));
-  const int64_t want = (P.n + SPMM_WARPS - 1) / SPMM_WARPS;
+  const int nch = (P.ncols + 32 * VEC - 1) / (32 * VEC);
+  const int64_t want = (P.n * nch + SPMM_WARPS - 1) / SPMM_WARPS;
   int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(ctx->num_sms) * std::max(per_sm, 1)));
-  grid = std::max(grid, 1);
+  // every chunk needs at least one warp
+  grid = std::max(grid, (nch + SPMM_WARPS - 1) / SPMM_WARPS);
   P.red_part = nullptr;
   if (want_red) ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * P.ncols, &P.red_part));
   kern<<<grid, SPMM_THREADS, smem, ctx->stream>>>(P);
@@ -368,17 +351,6 @@ arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, in
   *grid_out = grid;
   *part_out = P.red_part;
   return ARB_OK;
-}
-
-template <typename T, int VEC>
-arb_status launch_spmm_nc(arb_ctx ctx, const KParams<T>& P, size_t smem, bool want_red, int* grid,
-                          double** part) {
-  constexpr int CH = 32 * VEC;
-  const int chunks = (P.ncols + CH - 1) / CH;
-  // wider blocks loop over groups of (at most) 4 chunks: more would spill registers
-  if (chunks <= 1) return launch_spmm<T, VEC, 1>(ctx, P, smem, want_red, grid, part);
-  if (chunks <= 2) return launch_spmm<T, VEC, 2>(ctx, P, smem, want_red, grid, part);
-  return launch_spmm<T, VEC, 4>(ctx, P, smem, want_red, grid, part);
 }
 
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -452,18 +424,18 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   int grid = 0;
   double* part = nullptr;
   if constexpr (sizeof(T) == 4) {
-    if (fits(4)) {
-      ARB_TRY((launch_spmm_nc<T, 4>(ctx, P, smem, want_red, &grid, &part)));
+    if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
+      ARB_TRY((launch_spmm<T, 4>(ctx, P, smem, want_red, &grid, &part)));
     } else if (fits(2)) {
-      ARB_TRY((launch_spmm_nc<T, 2>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, &grid, &part)));
     } else {
-      ARB_TRY((launch_spmm_nc<T, 1>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, &grid, &part)));
     }
   } else {
     if (fits(2)) {
-      ARB_TRY((launch_spmm_nc<T, 2>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, &grid, &part)));
     } else {
-      ARB_TRY((launch_spmm_nc<T, 1>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, &grid, &part)));
     }
   }
   if (want_red) {
