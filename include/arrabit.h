@@ -242,6 +242,36 @@ arb_status arb_arr(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, i
                    const double* X, int64_t ldx, int32_t ncols, int32_t q, int32_t npairs,
                    double* Y, int64_t ldy, double* w, int32_t* rank);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of eigen-solves on one GPU (a request loop over arb_solve).
+ * Requests are admitted in arrival order as soon as one of `max_slots` worker slots is free
+ * and the request's HBM footprint (arb_server_footprint) fits in what the admitted
+ * requests leave of `hbm_budget_bytes`; admitted solves run concurrently, each slot on
+ * its own CUDA stream and context.  A request whose footprint exceeds the whole budget
+ * is refused at submission with ARB_REJECTED.  Results are the same as a standalone
+ * arb_solve with the same inputs (the kernels are deterministic).  The server is
+ * thread-safe for arb_submit / arb_wait; destroy it only after every wait has returned. */
+typedef struct arb_server_s* arb_server;
+typedef int64_t arb_ticket;
+
+/* Bytes of device workspace a solve of an n x p block with q augmentation blocks takes
+ * (precision: arb_precision); -1 on bad arguments. */
+int64_t arb_server_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, int32_t precision);
+arb_status arb_server_create(int device, size_t hbm_budget_bytes, int32_t max_slots, arb_server* out);
+/* Queue a solve of `mat` (which must live on the server's device and stay alive until
+ * the request is waited for).  x0: host n x p start block (copied) or NULL; want_evecs:
+ * keep the eigenvectors for arb_wait. */
+arb_status arb_submit(arb_server srv, arb_mat mat, int32_t k, arb_which which, double tol,
+                      const arb_options* opts, const double* x0, int want_evecs, arb_ticket* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a request; ARB_TIMEOUT if it is not done yet
+ * (the ticket stays valid).  On completion the outputs are filled as by arb_solve (evecs
+ * host, column-major, ldq), latency_s (may be NULL) is submit-to-completion wall time,
+ * the ticket is retired, and the solve's own status is returned. */
+arb_status arb_wait(arb_server srv, arb_ticket ticket, int32_t timeout_ms, double* evals, double* evecs,
+                    int64_t ldq, arb_info* info, double* latency_s);
+/* Stop the server: queued requests are dropped, running ones finish, threads join. */
+arb_status arb_server_destroy(arb_server srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,11 @@ _PROTOS = {
     "arb_spmm": (_i32, [_vp, _vp, _dbl, _dbl, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
+    "arb_server_footprint": (_i64, [_i64, _i64, _i32, _i32, _i32]),
+    "arb_server_create": (_i32, [C.c_int, C.c_size_t, _i32, C.POINTER(_vp)]),
+    "arb_submit": (_i32, [_vp, _vp, _i32, _i32, _dbl, C.POINTER(arb_options), _vp, C.c_int, C.POINTER(_i64)]),
+    "arb_wait": (_i32, [_vp, _i64, _i32, _vp, _vp, _i64, C.POINTER(arb_info), C.POINTER(_dbl)]),
+    "arb_server_destroy": (_i32, [_vp]),
     "arb_syevj": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _i64, C.POINTER(_i32)]),
     "arb_rcond_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, C.POINTER(_dbl)]),
     "arb_orth": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, C.POINTER(_i32)]),
@@ -390,3 +395,62 @@ def arb_arr(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, X, q: i
                                X.shape[1], q, npairs, _vp(_ptr(Y)), Y.stride(0), _vp(_ptr(w)), C.byref(r)),
            "arb_arr")
     return Y, w, r.value
+
+
+def arb_server_footprint(n: int, nnz: int, p: int, q: int, precision: int = ARB_FP64) -> int:
+    return int(load().arb_server_footprint(n, nnz, p, q, precision))
+
+
+class Server:
+    """Continuous-batching solve server (arb_server_*): submit() returns a ticket,
+    wait() the result.  Matrices must outlive their requests."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 8 << 30, max_slots: int = 4):
+        h = _vp()
+        st = load().arb_server_create(device, hbm_budget_bytes, max_slots, C.byref(h))
+        if st != ARB_OK:
+            raise ArbError(st, "arb_server_create failed")
+        self.handle = h
+        self._meta = {}
+
+    def submit(self, mat: Matrix, k: int, which: int, tol: float, opts: arb_options | None = None, x0=None,
+               want_evecs: bool = True) -> int:
+        if opts is None:
+            opts = arb_options_default(k)
+        ptr = 0
+        if x0 is not None:
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            ptr = x0.ctypes.data
+        t = _i64()
+        st = load().arb_submit(self.handle, mat.handle, k, which, tol, C.byref(opts), _vp(ptr), int(want_evecs),
+                               C.byref(t))
+        if st != ARB_OK:
+            raise ArbError(st, "arb_submit: " + load().arb_status_string(st).decode())
+        self._meta[t.value] = (mat.n, k, want_evecs)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        n, k, want = self._meta[ticket]
+        ev = np.zeros(k)
+        vecs = np.zeros((k, n)) if want else None
+        info = arb_info()
+        lat = _dbl()
+        st = load().arb_wait(self.handle, ticket, timeout_ms, ev.ctypes.data, _vp(vecs.ctypes.data if want else 0), n,
+                             C.byref(info), C.byref(lat))
+        if st == ARB_TIMEOUT:
+            return None
+        del self._meta[ticket]
+        if st not in (ARB_OK, ARB_NOT_CONVERGED):
+            raise ArbError(st, "arb_wait: " + load().arb_status_string(st).decode())
+        return SolveResult(st, ev, vecs.T if want else None, dict(info.as_dict(), latency_s=lat.value))
+
+    def close(self):
+        if self.handle:
+            load().arb_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

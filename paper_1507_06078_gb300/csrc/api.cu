@@ -29,17 +29,40 @@ arb_status ws_get(arb_ctx ctx, int slot, size_t bytes, void** out) {
   if (slot < 0 || slot >= WS_NUM_SLOTS) return set_error(ctx, ARB_INVALID_ARG, "bad workspace slot");
   if (ctx->ws_bytes[slot] < bytes) {
     if (ctx->ws[slot]) {
-      ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-      ARB_CUDA(ctx, cudaFree(ctx->ws[slot]));
+      if (ctx->stream_ordered) {
+        ARB_CUDA(ctx, cudaFreeAsync(ctx->ws[slot], ctx->stream));
+      } else {
+        ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ARB_CUDA(ctx, cudaFree(ctx->ws[slot]));
+      }
       ctx->ws[slot] = nullptr;
       ctx->ws_bytes[slot] = 0;
     }
     void* p = nullptr;
-    ARB_CUDA(ctx, cudaMalloc(&p, bytes));
+    if (ctx->stream_ordered) {
+      ARB_CUDA(ctx, cudaMallocAsync(&p, bytes, ctx->stream));
+    } else {
+      ARB_CUDA(ctx, cudaMalloc(&p, bytes));
+    }
     ctx->ws[slot] = p;
     ctx->ws_bytes[slot] = bytes;
   }
   *out = ctx->ws[slot];
+  return ARB_OK;
+}
+
+arb_status ws_release_all(arb_ctx ctx) {
+  for (int i = 0; i < WS_NUM_SLOTS; ++i) {
+    if (!ctx->ws[i]) continue;
+    if (ctx->stream_ordered) {
+      ARB_CUDA(ctx, cudaFreeAsync(ctx->ws[i], ctx->stream));
+    } else {
+      ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      ARB_CUDA(ctx, cudaFree(ctx->ws[i]));
+    }
+    ctx->ws[i] = nullptr;
+    ctx->ws_bytes[i] = 0;
+  }
   return ARB_OK;
 }
 
@@ -133,7 +156,11 @@ extern "C" arb_status arb_ctx_destroy(arb_ctx ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (int i = 0; i < WS_NUM_SLOTS; ++i)
-    if (ctx->ws[i]) cudaFree(ctx->ws[i]);
+    if (ctx->ws[i]) {
+      if (ctx->stream_ordered) cudaFreeAsync(ctx->ws[i], ctx->stream);
+      else cudaFree(ctx->ws[i]);
+    }
+  cudaStreamSynchronize(ctx->stream);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -865,10 +892,31 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
 
 }  // namespace
 
+size_t arb::solve_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, bool mixed) {
+  const int64_t ld = p + (p & 1), ldm = static_cast<int64_t>(q + 1) * p + (((q + 1) * p) & 1);
+  const int64_t mcap = static_cast<int64_t>(q + 1) * p;
+  size_t b = static_cast<size_t>(n) * (7 * ld + 2 * ldm) * sizeof(double);
+  if (mixed) {
+    const int64_t l4 = (p + 3) / 4 * 4, m4 = (mcap + 3) / 4 * 4;
+    b += static_cast<size_t>(n) * (6 * l4 + 2 * m4) * sizeof(float) + static_cast<size_t>(nnz) * sizeof(float);
+  }
+  // small dense state (H, eigenvectors, Gram matrices, Jacobi copies), split-K and column
+  // reduction partial sums: bounded by a few m x m matrices plus one slab of partials
+  b += static_cast<size_t>(8 * mcap * mcap + 2048 * mcap) * sizeof(double) + (64u << 20);
+  return b;
+}
+
 extern "C" arb_status arb_solve(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol,
                                 const arb_options* opts, const double* x0, int x0_on_device, double* evals,
                                 double* evecs, int64_t ldq, int evecs_on_device, arb_info* info) {
-  if (!ctx || !mat || mat->ctx != ctx) return set_error(ctx, ARB_INVALID_ARG, "solve: bad context or matrix");
+  return arb::solve_on(ctx, mat, k, which, tol, opts, x0, x0_on_device, evals, evecs, ldq, evecs_on_device, info);
+}
+
+arb_status arb::solve_on(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol, const arb_options* opts,
+                         const double* x0, int x0_on_device, double* evals, double* evecs, int64_t ldq,
+                         int evecs_on_device, arb_info* info) {
+  if (!ctx || !mat || mat->device != ctx->device)
+    return set_error(ctx, ARB_INVALID_ARG, "solve: bad context or matrix (matrix on another device)");
   ARB_CUDA(ctx, cudaSetDevice(ctx->device));
   arb_options o;
   if (opts) {

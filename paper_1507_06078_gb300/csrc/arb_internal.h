@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -69,6 +70,7 @@ struct arb_ctx_s {
   void* host_pinned = nullptr;  // small staging area for read-backs
   size_t host_pinned_bytes = 0;
   int jacobi_max_blocks = 0;    // co-resident blocks for the cooperative Jacobi kernel
+  bool stream_ordered = false;  // workspaces from cudaMallocAsync/cudaFreeAsync on `stream`
 };
 
 struct arb_mat_s {
@@ -81,6 +83,7 @@ struct arb_mat_s {
   float* val32 = nullptr;  // FP32 copy of val for the mixed-precision filter (made on demand)
   bool gersh_valid = false;
   double gersh_lo = 0.0, gersh_hi = 0.0;
+  std::mutex mu;  // guards the lazily made val32 and Gershgorin cache (shared by server workers)
 };
 
 namespace arb {
@@ -115,6 +118,15 @@ template <typename T>
 inline arb_status ws(arb_ctx ctx, int slot, size_t count, T** out) {
   return ws_get(ctx, slot, count * sizeof(T) + 256, reinterpret_cast<void**>(out));
 }
+// Release every workspace slot of the context.
+arb_status ws_release_all(arb_ctx ctx);
+// Device bytes the solver's workspaces take for an n x p block, q augmentation blocks and
+// a matrix with nnz entries (FP32 copies included for the mixed path).
+size_t solve_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, bool mixed);
+// The whole method on ctx (used by arb_solve and by the server's workers).
+arb_status solve_on(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol, const arb_options* opts,
+                    const double* x0, int x0_on_device, double* evals, double* evecs, int64_t ldq,
+                    int evecs_on_device, arb_info* info);
 // Pinned host staging of at least `bytes`.
 arb_status host_stage(arb_ctx ctx, size_t bytes, void** out);
 // Copy `bytes` from device to a host pointer through the stream and wait.

@@ -23,7 +23,10 @@ constexpr int SPMM_WARPS = SPMM_THREADS / 32;
 #define ARB_SPMM_F32_MAX_VEC 4
 #endif
 #ifndef ARB_SPMM_UNROLL
-#define ARB_SPMM_UNROLL 8
+#define ARB_SPMM_UNROLL 4
+#endif
+#ifndef ARB_SPMM_MIN_BLOCKS
+#define ARB_SPMM_MIN_BLOCKS 1
 #endif
 
 template <typename T>
@@ -139,7 +142,7 @@ struct VecIO<float, 4> {
 // RED adds the column reduction (sum of out^2 or out*Yin) in FP64 registers, combined per
 // CTA through shared memory.
 template <typename T, int VEC, bool RED>
-__global__ void __launch_bounds__(SPMM_THREADS) spmm_fused_kernel(KParams<T> P) {
+__global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_kernel(KParams<T> P) {
   extern __shared__ double s_red[];  // [SPMM_WARPS][ncols] when RED
   constexpr int CH = 32 * VEC;
   constexpr int UNR = ARB_SPMM_UNROLL;
@@ -369,13 +372,17 @@ const float* values_of<float>(const arb_mat_s* A) {
 }  // namespace
 
 arb_status ensure_val32(arb_ctx ctx, arb_mat mat) {
+  std::lock_guard<std::mutex> lock(mat->mu);
   if (mat->val32) return ARB_OK;
-  ARB_CUDA(ctx, cudaMalloc(&mat->val32, std::max<int64_t>(mat->nnz, 1) * sizeof(float)));
+  float* v = nullptr;
+  ARB_CUDA(ctx, cudaMalloc(&v, std::max<int64_t>(mat->nnz, 1) * sizeof(float)));
   if (mat->nnz > 0) {
-    to_float_kernel<<<static_cast<int>((mat->nnz + 255) / 256), 256, 0, ctx->stream>>>(mat->nnz, mat->val,
-                                                                                     mat->val32);
+    to_float_kernel<<<static_cast<int>((mat->nnz + 255) / 256), 256, 0, ctx->stream>>>(mat->nnz, mat->val, v);
     ARB_LAUNCHED(ctx);
   }
+  // other contexts (other streams) may use the copy next: make it complete first
+  ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  mat->val32 = v;
   return ARB_OK;
 }
 
@@ -449,6 +456,7 @@ template arb_status spmm_fused<double>(arb_ctx, const SpmmArgs<double>&);
 template arb_status spmm_fused<float>(arb_ctx, const SpmmArgs<float>&);
 
 arb_status gershgorin(arb_ctx ctx, arb_mat mat, double* lo, double* hi) {
+  std::lock_guard<std::mutex> lock(mat->mu);
   if (mat->gersh_valid) {
     *lo = mat->gersh_lo;
     *hi = mat->gersh_hi;

@@ -280,3 +280,47 @@ def chung_lu_laplacian(n: int, seed: int = 1507, beta: float = 2.5, mean: float 
     L = L.tocsr()
     L.sort_indices()
     return CSR(nn, L.indptr.astype(np.int32), L.indices.astype(np.int32), L.data.astype(np.float64)), ids
+
+
+def diffusion_2d(side: int, seed: int) -> CSR:
+    """5-point variable-coefficient diffusion on a side x side grid with Dirichlet ghost
+    nodes: every grid edge (interior and boundary) gets a conductance exp(N(0,1))
+    (lognormal, mu = 0, sigma = 1); A_ii = sum of the 4 conductances at node i,
+    A_ij = -kappa_ij for the interior edge ij.  Symmetric positive definite."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    kx = np.exp(rng.standard_normal((side + 1, side)))  # edges between x-1 and x, per row y
+    ky = np.exp(rng.standard_normal((side, side + 1)))  # edges between y-1 and y, per column x
+    n = side * side
+    idx = np.arange(n).reshape(side, side)  # [y, x]
+    diag = kx[:-1, :].T + kx[1:, :].T + ky[:, :-1].T + ky[:, 1:].T  # [y, x]
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [diag.ravel()]
+    # x-neighbours: (y, x) - (y, x+1) through kx[x+1, y]
+    rows += [idx[:, :-1].ravel(), idx[:, 1:].ravel()]
+    cols += [idx[:, 1:].ravel(), idx[:, :-1].ravel()]
+    kxi = -kx[1:-1, :].T.ravel()
+    vals += [kxi, kxi]
+    # y-neighbours: (y, x) - (y+1, x) through ky[x, y+1]
+    rows += [idx[:-1, :].ravel(), idx[1:, :].ravel()]
+    cols += [idx[1:, :].ravel(), idx[:-1, :].ravel()]
+    kyi = -ky[:, 1:-1].T.ravel()
+    vals += [kyi, kyi]
+    import scipy.sparse as sp
+    M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    M.sort_indices()
+    return CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+def batched_diffusion_instances(count: int = 256, base_seed: int = 30000, side_range=(32, 512),
+                                k_range=(8, 64)) -> list[Workload]:
+    """Instance i: side ~ U{side_range}, k ~ U{k_range}, p = round(1.5 k), smallest
+    eigenpairs to relative residual 1e-8; the grid and the coefficients come from seed
+    base_seed + i."""
+    out = []
+    for i in range(count):
+        rng = np.random.Generator(np.random.Philox(base_seed + i))
+        side = int(rng.integers(side_range[0], side_range[1] + 1))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        p = int(round(1.5 * k))
+        A = diffusion_2d(side, base_seed + i)
+        out.append(Workload(f"diffusion2d_{side}x{side}_k{k}", A, k, "smallest", p, 1, 10, 1e-8, base_seed + i))
+    return out

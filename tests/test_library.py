@@ -50,3 +50,13 @@ def test_bad_coefficient_requests_rejected(lib):
     assert lib.arb_filter_coefficients(0, 0, buf.ctypes.data) == arb.ARB_INVALID_ARG
     assert lib.arb_filter_coefficients(0, 61, buf.ctypes.data) == arb.ARB_INVALID_ARG
     assert lib.arb_filter_coefficients(7, 3, buf.ctypes.data) == arb.ARB_INVALID_ARG
+
+
+def test_server_footprint_formula(lib):
+    # 7 FP64 n x p blocks + 2 FP64 n x (q+1)p blocks + small state; mixed adds FP32 copies
+    f = arb.arb_server_footprint(1000, 5000, 30, 1, arb.ARB_FP64)
+    base = 1000 * (7 * 30 + 2 * 60) * 8
+    assert base < f < base + (80 << 20)
+    fm = arb.arb_server_footprint(1000, 5000, 30, 1, arb.ARB_MIXED)
+    assert fm > f
+    assert arb.arb_server_footprint(0, 0, 30, 1, 0) == -1
