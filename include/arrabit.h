@@ -179,6 +179,30 @@ arb_status arb_filter_f32(arb_ctx ctx, arb_mat mat, double op_scale, double op_s
                           int64_t ldx, int32_t ncols, const double* xscale, float* Y,
                           int64_t ldy, double* colss);
 
+/* One instance of a batched filter (arb_filter_batched): the same arguments as arb_filter
+ * / arb_filter_f32, X and Y FP32 when fp32 != 0, else FP64. */
+typedef struct {
+  arb_mat mat;
+  double op_scale, op_shift, a, b;
+  int32_t degree;
+  int32_t fp32;
+  const double* coef;    /* HOST, degree+1 Chebyshev coefficients */
+  const void* X;         /* device, n x ncols, row-major */
+  int64_t ldx;
+  int32_t ncols;
+  int32_t reserved0;
+  const double* xscale;  /* device float64[ncols] or NULL */
+  void* Y;               /* device, n x ncols; must not overlap X */
+  int64_t ldy;
+  double* colss;         /* device float64[ncols] or NULL: column sums of squares of Y */
+} arb_filter_job;
+
+/* Filter many instances (different matrices, widths, degrees, precisions) in ONE
+ * persistent cooperative launch: all d_max passes of all instances, a grid-wide barrier
+ * between passes.  Results equal per-instance arb_filter / arb_filter_f32 up to the order
+ * of the FP operations within a row (none: the arithmetic is the same). */
+arb_status arb_filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs);
+
 /* Host-side coefficients c_0..c_d (float64[degree+1]) of the degree-d Chebyshev
  * interpolant of max(0,t)^(10 d) at t_j = -cos(j pi/d) (Section 5, eq. chebfun-f), or of
  * T_d for ARB_FILTER_CHEBYSHEV. */
@@ -271,6 +295,17 @@ arb_status arb_wait(arb_server srv, arb_ticket ticket, int32_t timeout_ms, doubl
                     int64_t ldq, arb_info* info, double* latency_s);
 /* Stop the server: queued requests are dropped, running ones finish, threads join. */
 arb_status arb_server_destroy(arb_server srv);
+
+/* Solve nb independent problems (uneven sizes) as one batch: up to max_concurrent solves
+ * run at once, each on its own stream, largest first; HBM admission as for the server
+ * with a budget of 90% of the device's free memory.  Per-instance arguments as for
+ * arb_solve (x0[i] host or NULL; evecs[i] host column-major or NULL; ldq may be NULL for
+ * ldq[i] = n_i; opts and info may be NULL).  Returns ARB_OK when every instance converged,
+ * else the first failing status (or ARB_NOT_CONVERGED). */
+arb_status arb_solve_batched(arb_ctx ctx, int32_t nb, const arb_mat* mats, const int32_t* k,
+                             const arb_which* which, const double* tol, const arb_options* opts,
+                             const double* const* x0, double* const* evals, double* const* evecs,
+                             const int64_t* ldq, arb_info* info, int32_t max_concurrent);
 
 #ifdef __cplusplus
 }

@@ -44,6 +44,13 @@ class arb_options(C.Structure):
                 ("seed", C.c_uint64)]
 
 
+class arb_filter_job(C.Structure):
+    _fields_ = [("mat", C.c_void_p), ("op_scale", C.c_double), ("op_shift", C.c_double), ("a", C.c_double),
+                ("b", C.c_double), ("degree", C.c_int32), ("fp32", C.c_int32), ("coef", C.c_void_p),
+                ("X", C.c_void_p), ("ldx", C.c_int64), ("ncols", C.c_int32), ("reserved0", C.c_int32),
+                ("xscale", C.c_void_p), ("Y", C.c_void_p), ("ldy", C.c_int64), ("colss", C.c_void_p)]
+
+
 class arb_info(C.Structure):
     _fields_ = [("maxres", C.c_double), ("a", C.c_double), ("b0", C.c_double), ("b_final", C.c_double),
                 ("sigma", C.c_double), ("t_total", C.c_double), ("t_filter", C.c_double),
@@ -76,6 +83,7 @@ _PROTOS = {
     "arb_filter_f32": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _dbl, _i32, _vp, _vp, _i64, _i32, _vp, _vp, _i64,
                               _vp]),
     "arb_filter_coefficients": (_i32, [_i32, _i32, _vp]),
+    "arb_filter_batched": (_i32, [_vp, _i32, _vp]),
     "arb_spmm": (_i32, [_vp, _vp, _dbl, _dbl, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
@@ -84,6 +92,7 @@ _PROTOS = {
     "arb_submit": (_i32, [_vp, _vp, _i32, _i32, _dbl, C.POINTER(arb_options), _vp, C.c_int, C.POINTER(_i64)]),
     "arb_wait": (_i32, [_vp, _i64, _i32, _vp, _vp, _i64, C.POINTER(arb_info), C.POINTER(_dbl)]),
     "arb_server_destroy": (_i32, [_vp]),
+    "arb_solve_batched": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32]),
     "arb_syevj": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _i64, C.POINTER(_i32)]),
     "arb_rcond_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, C.POINTER(_dbl)]),
     "arb_orth": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, C.POINTER(_i32)]),
@@ -454,3 +463,54 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def arb_filter_batched(ctx: Context, jobs: list[dict]):
+    """Filter several instances in one launch.  Each job: dict(mat, op_scale, op_shift, a, b,
+    coef (numpy), X (torch CUDA float32/float64, row-major), xscale=None, colss=None);
+    returns the list of outputs Y."""
+    import torch
+    arr = (arb_filter_job * len(jobs))()
+    keep, outs = [], []
+    for i, j in enumerate(jobs):
+        X = j["X"]
+        if not (X.is_cuda and X.dim() == 2 and X.stride(1) == 1 and X.dtype in (torch.float32, torch.float64)):
+            raise ValueError("X: row-major 2D float32/float64 CUDA tensor expected")
+        coef = np.ascontiguousarray(j["coef"], dtype=np.float64)
+        Y = torch.empty_like(X)
+        keep += [coef, X, Y]
+        outs.append(Y)
+        arr[i] = arb_filter_job(j["mat"].handle, j["op_scale"], j["op_shift"], j["a"], j["b"], len(coef) - 1,
+                                1 if X.dtype == torch.float32 else 0, coef.ctypes.data, X.data_ptr(), X.stride(0),
+                                X.shape[1], 0, _ptr(j.get("xscale")), Y.data_ptr(), Y.stride(0), _ptr(j.get("colss")))
+    _check(ctx, load().arb_filter_batched(ctx.handle, len(jobs), C.cast(arr, _vp)), "arb_filter_batched")
+    return outs
+
+
+def arb_solve_batched(ctx: Context, problems: list[dict], max_concurrent: int = 8, evecs: bool = True):
+    """problems: dicts with mat, k, which, tol, opts (arb_options) and optional x0 (numpy).
+    Returns (status, [SolveResult])."""
+    nb = len(problems)
+    mats = (_vp * nb)(*[p["mat"].handle.value for p in problems])
+    ks = (_i32 * nb)(*[p["k"] for p in problems])
+    wh = (_i32 * nb)(*[p["which"] for p in problems])
+    tl = (_dbl * nb)(*[p["tol"] for p in problems])
+    opts = (arb_options * nb)(*[p.get("opts") or arb_options_default(p["k"]) for p in problems])
+    keep = []
+    x0s = (_vp * nb)()
+    for i, p in enumerate(problems):
+        if p.get("x0") is not None:
+            x = np.ascontiguousarray(p["x0"], dtype=np.float64)
+            keep.append(x)
+            x0s[i] = x.ctypes.data
+    evs = [np.zeros(p["k"]) for p in problems]
+    vecs = [np.zeros((p["k"], p["mat"].n)) for p in problems] if evecs else None
+    evp = (_vp * nb)(*[e.ctypes.data for e in evs])
+    vcp = (_vp * nb)(*[v.ctypes.data for v in vecs]) if evecs else None
+    infos = (arb_info * nb)()
+    st = load().arb_solve_batched(ctx.handle, nb, C.cast(mats, _vp), C.cast(ks, _vp), C.cast(wh, _vp),
+                                  C.cast(tl, _vp), C.cast(opts, _vp), C.cast(x0s, _vp), C.cast(evp, _vp),
+                                  C.cast(vcp, _vp) if evecs else None, None, C.cast(infos, _vp), max_concurrent)
+    if st not in (ARB_OK, ARB_NOT_CONVERGED):
+        raise ArbError(st, "arb_solve_batched")
+    return st, [SolveResult(ARB_OK, evs[i], vecs[i].T if evecs else None, infos[i].as_dict()) for i in range(nb)]

@@ -213,7 +213,10 @@ extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz,
   if (n > INT32_MAX || nnz > INT32_MAX)
     return set_error(ctx, ARB_INVALID_ARG, "matrix_create_csr: int32 index range exceeded");
   *out = nullptr;
+  int32_t max_row = -1;
   if (!ptr_on_device) {
+    max_row = 0;
+    for (int64_t i = 0; i < n; ++i) max_row = std::max<int32_t>(max_row, rowptr[i + 1] - rowptr[i]);
     if (rowptr[0] != 0 || rowptr[n] != nnz)
       return set_error(ctx, ARB_INVALID_ARG, "matrix_create_csr: rowptr must start at 0 and end at nnz");
     for (int64_t i = 0; i < n; ++i)
@@ -225,6 +228,7 @@ extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz,
   arb_mat m = new arb_mat_s();
   m->ctx = ctx;
   m->device = ctx->device;
+  m->max_row_nnz = max_row;
   m->n = n;
   m->nnz = nnz;
   const cudaMemcpyKind kind = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

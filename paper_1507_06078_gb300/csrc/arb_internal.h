@@ -53,6 +53,9 @@ enum WsSlot : int {
   WS_F32_AU,
   WS_F32_T,
   WS_F32_T2,
+  WS_BATCH_WORK,      // batched filter: per-instance work blocks, tables, descriptors
+  WS_BATCH_TABLE,
+  WS_BATCH_DESC,
   WS_NUM_SLOTS
 };
 
@@ -81,6 +84,7 @@ struct arb_mat_s {
   int32_t* col = nullptr;
   double* val = nullptr;
   float* val32 = nullptr;  // FP32 copy of val for the mixed-precision filter (made on demand)
+  int32_t max_row_nnz = -1;  // longest row (-1: unknown)
   bool gersh_valid = false;
   double gersh_lo = 0.0, gersh_hi = 0.0;
   std::mutex mu;  // guards the lazily made val32 and Gershgorin cache (shared by server workers)
@@ -229,6 +233,9 @@ arb_status select_top(arb_ctx ctx, const double* vlock, int32_t nl, const double
 // i*ncols + j), same numbering as the input generators.
 arb_status gaussian_fill(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, double* X,
                          int64_t ldx);
+
+// ---------------------------------------------------------------- batched filter (batched.cu)
+arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs);
 
 // ---------------------------------------------------------------- Jacobi (jacobi.cu)
 // w (descending), V (row-major, column j = eigenvector) of symmetric H (not modified).

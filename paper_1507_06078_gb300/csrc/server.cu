@@ -231,3 +231,48 @@ extern "C" arb_status arb_server_destroy(arb_server srv) {
   delete srv;
   return ARB_OK;
 }
+
+extern "C" arb_status arb_solve_batched(arb_ctx ctx, int32_t nb, const arb_mat* mats, const int32_t* k,
+                                        const arb_which* which, const double* tol, const arb_options* opts,
+                                        const double* const* x0, double* const* evals, double* const* evecs,
+                                        const int64_t* ldq, arb_info* info, int32_t max_concurrent) {
+  if (!ctx || nb < 0 || (nb > 0 && (!mats || !k || !which || !tol || !evals)) || max_concurrent < 1)
+    return ARB_INVALID_ARG;
+  if (nb == 0) return ARB_OK;
+  size_t free_b = 0, total_b = 0;
+  if (cudaSetDevice(ctx->device) != cudaSuccess || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess)
+    return ARB_CUDA_ERROR;
+  arb_server srv = nullptr;
+  arb_status st = arb_server_create(ctx->device, static_cast<size_t>(0.9 * free_b), std::min(max_concurrent, nb), &srv);
+  if (st != ARB_OK) return st;
+  // largest footprints first, so the long solves start early
+  std::vector<int32_t> order(nb);
+  std::vector<size_t> fp(nb);
+  for (int32_t i = 0; i < nb; ++i) {
+    order[i] = i;
+    arb_options o;
+    if (opts) o = opts[i];
+    else arb_options_default(&o, k[i]);
+    const int32_t p = o.p > 0 ? o.p : k[i] + static_cast<int32_t>(std::lround(0.1 * k[i]));
+    fp[i] = arb::solve_footprint(mats[i]->n, mats[i]->nnz, p, o.q, o.precision == ARB_MIXED);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return fp[a] > fp[b]; });
+  std::vector<arb_ticket> tickets(nb, 0);
+  arb_status worst = ARB_OK;
+  for (int32_t idx : order) {
+    st = arb_submit(srv, mats[idx], k[idx], which[idx], tol[idx], opts ? &opts[idx] : nullptr, x0 ? x0[idx] : nullptr,
+                    evecs && evecs[idx] ? 1 : 0, &tickets[idx]);
+    if (st != ARB_OK) {
+      worst = st;
+      tickets[idx] = 0;
+    }
+  }
+  for (int32_t i = 0; i < nb; ++i) {
+    if (!tickets[i]) continue;
+    st = arb_wait(srv, tickets[i], -1, evals[i], evecs ? evecs[i] : nullptr, ldq ? ldq[i] : mats[i]->n,
+                  info ? &info[i] : nullptr, nullptr);
+    if (st != ARB_OK && (worst == ARB_OK || (worst == ARB_NOT_CONVERGED && st < 0))) worst = st;
+  }
+  arb_server_destroy(srv);
+  return worst;
+}

@@ -98,7 +98,7 @@ def test_filter_matches_oracle(arb, ctx, d, kind):
         np.testing.assert_allclose(Y, ref7, rtol=0, atol=1e-9 * scale)
 
 
-@pytest.mark.parametrize("d,ncols", [(1, 7), (3, 30), (10, 64), (20, 130)])
+@pytest.mark.parametrize("d,ncols", [(1, 7), (3, 30), (10, 64), (20, 130), (5, 128), (20, 240)])
 def test_filter_f32_against_oracle(arb, ctx, d, ncols):
     # FP32 filter of the mixed path vs the FP64 oracle.  Each Clenshaw pass adds a few
     # u32 of relative rounding, growing roughly linearly in d: an FP32 emulation of the same
@@ -394,3 +394,36 @@ def test_solve_b_every_arr_against_oracle(arb, ctx, precision):
     assert r.status == arb.ARB_OK, r.info
     np.testing.assert_allclose(r.evals, ref.evals, atol=1e-9)
     np.testing.assert_allclose(r.evals, laplacian_3d_eigs(12)[:20], atol=1e-9)
+
+
+def test_filter_batched_matches_single_instance_filters(arb, ctx):
+    # uneven instances (sizes, widths, degrees, both precisions) in one persistent launch,
+    # each compared with its own single-instance filter and with the oracle
+    specs = [(I.diffusion_2d(40, 1), 12, 10, True), (I.laplacian_3d(14), 30, 20, True),
+             (I.laplacian_2d(33), 7, 3, False), (I.diffusion_2d(25, 2), 65, 8, False),
+             (I.laplacian_2d(20), 130, 1, True), (I.diffusion_2d(60, 3), 96, 15, True)]
+    jobs, refs = [], []
+    for i, (A, ncols, d, f32) in enumerate(specs):
+        mat = arb.Matrix.from_csr(ctx, A)
+        B = O.csr_to_scipy(A.n, A.rowptr, A.col, A.val)
+        sigma = O.gershgorin_bounds(B)[1]
+        X = I.gaussian_block(A.n, ncols, 40 + i)
+        xs = np.linspace(0.5, 1.5, ncols)
+        coef = O.interpolant_cheb_coeffs(d)
+        Xd = dev(X).float() if f32 else dev(X)
+        colss = torch.zeros(ncols, dtype=torch.float64, device="cuda")
+        jobs.append(dict(mat=mat, op_scale=-1.0, op_shift=sigma, a=0.0, b=0.6 * sigma, coef=coef, X=Xd,
+                         xscale=dev(xs), colss=colss))
+        single = (arb.arb_filter_f32 if f32 else arb.arb_filter)(ctx, mat, -1.0, sigma, 0.0, 0.6 * sigma, coef, Xd,
+                                                                 xscale=dev(xs))
+        Bs = sigma * sp.identity(A.n, format="csr") - B
+        Xin = (X.astype(np.float32).astype(np.float64) if f32 else X) * xs[None, :]
+        ref = O.poly_clenshaw(Bs, Xin, 0.0, 0.6 * sigma, coef)
+        refs.append((host(single), ref, f32))
+    outs = arb.arb_filter_batched(ctx, jobs)
+    for (single, ref, f32), Y, job in zip(refs, outs, jobs):
+        Yh = host(Y)
+        np.testing.assert_array_equal(Yh, single)  # same arithmetic as the single-instance kernel
+        scale = np.abs(ref).max()
+        np.testing.assert_allclose(Yh, ref, rtol=0, atol=(1e-5 if f32 else 1e-12) * scale)
+        np.testing.assert_allclose(host(job["colss"]), np.sum(Yh.astype(np.float64) ** 2, axis=0), rtol=1e-10)

@@ -112,3 +112,22 @@ def test_server_queue_timeout_and_memory_bound_admission(arb, ctx):
     np.testing.assert_allclose(r1.evals, laplacian_3d_eigs(32)[:40], atol=1e-9)
     np.testing.assert_allclose(r2.evals, laplacian_2d_eigs(24)[:10], atol=1e-10)
     assert r2.info["latency_s"] >= r1.info["latency_s"] * 0.5
+
+
+def test_solve_batched_matches_standalone(arb, ctx):
+    # uneven diffusion instances (the batched workload's family) plus Laplacians
+    probs = []
+    for i, A in enumerate([I.diffusion_2d(20, 1), I.diffusion_2d(36, 2), I.laplacian_2d(28), I.diffusion_2d(48, 3),
+                           I.laplacian_3d(10)]):
+        k = 6 + 2 * i
+        p = int(round(1.5 * k))
+        o = _opts(arb, k, p, 1, 10, precision=i % 2)
+        probs.append(dict(mat=arb.Matrix.from_csr(ctx, A), k=k, which=1, tol=1e-8, opts=o,
+                          x0=I.gaussian_block(A.n, p, 900 + i), A=A))
+    st, res = arb.arb_solve_batched(ctx, probs, max_concurrent=3)
+    assert st == arb.ARB_OK
+    for pr, r in zip(probs, res):
+        alone = arb.arb_solve(ctx, pr["mat"], pr["k"], 1, 1e-8, pr["opts"], x0=pr["x0"])
+        np.testing.assert_allclose(r.evals, alone.evals, rtol=0, atol=1e-12)
+        wref = np.linalg.eigvalsh(pr["A"].to_dense())[:pr["k"]]
+        np.testing.assert_allclose(r.evals, wref, atol=1e-8 * max(1.0, np.abs(wref).max()))
