@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=128, help="3D grid side (128 = the benchmark workload)")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df", "fp64"])
     ap.add_argument("--b-update", default="every_arr", choices=["continuation", "every_arr"],
                     help="when b = mu_{k+q} is refreshed: at continuation steps (Algorithm 8) or after "
                          "every ARR (Section 5)")
@@ -227,7 +227,7 @@ def run_ours(args):
     X0 = torch.from_numpy(X0h).cuda(local)
     opts = arb.arb_options_default(W.k)
     opts.p, opts.q, opts.degree = W.p, W.q, W.degree
-    opts.precision = arb.ARB_MIXED if args.precision == "mixed" else arb.ARB_FP64
+    opts.precision = {"mixed": arb.ARB_MIXED, "mixed_df": arb.ARB_MIXED_DF, "fp64": arb.ARB_FP64}[args.precision]
     opts.b_update = 1 if args.b_update == "every_arr" else 0
 
     def step():
@@ -268,7 +268,7 @@ def run_ours(args):
     # dominant kernel: the fused filter SpMM (one filter = W.degree launches), timed live
     # with CUDA events on the context's stream, on the full n x p block of the workload
     coef = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, W.degree)
-    if args.precision == "mixed":
+    if args.precision in ("mixed", "mixed_df"):
         Xf = X0.float()
         run_filter = lambda Y: arb.arb_filter_f32(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, Xf, Y=Y)  # noqa: E731
         s_bytes, z_bytes, kname = 4, 4, "spmm_fused_kernel<float,4> (Clenshaw filter pass, FP32)"
@@ -299,7 +299,7 @@ def run_ours(args):
             "peak_source": peak_src + " hbm_gbs (STREAM-style copy)"}
 
     fp64_cmp = None
-    if args.compare_fp64 and args.precision == "mixed":
+    if args.compare_fp64 and args.precision != "fp64":
         o64 = arb.arb_options_default(W.k)
         o64.p, o64.q, o64.degree, o64.precision = W.p, W.q, W.degree, arb.ARB_FP64
         o64.b_update = opts.b_update
@@ -352,7 +352,7 @@ def run_ours(args):
         info = infos[-1]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+                "vs_baseline": None, "dtype": {"mixed": "f32+f64", "mixed_df": "f32+f32x2+f64", "fp64": "f64"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": W.name, "n": W.A.n, "nnz": W.A.nnz, "k": W.k, "p": W.p, "q": W.q,
                            "degree": W.degree, "tol": W.tol, "precision": args.precision,
@@ -389,6 +389,9 @@ def run_filter_only(args):
         X = X.float()
         f = arb.arb_filter_f32
         s = 4
+    elif args.precision == "mixed_df":  # double-float passes (plus one conversion each way per filter)
+        f = arb.arb_filter_df
+        s = 8
     else:
         f = arb.arb_filter
         s = 8

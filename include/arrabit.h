@@ -48,7 +48,13 @@ typedef enum {
 } arb_status;
 
 typedef enum { ARB_LARGEST = 0, ARB_SMALLEST = 1 } arb_which;
-typedef enum { ARB_FP64 = 0, ARB_MIXED = 1 } arb_precision;
+/* ARB_FP64: every step in FP64.  ARB_MIXED: an FP32 phase (FP32 blocks, filter and Gram
+ * runs), then FP64 refinement.  ARB_MIXED_DF: as ARB_MIXED, but the refinement's filter
+ * (Algorithm 8's multi-power steps) runs in double-float arithmetic (hi + lo FP32 pairs,
+ * about 44 significant bits) on the FP32 pipe; its Rayleigh-Ritz steps stay in FP64.  The
+ * paper runs one precision throughout; the FP32 and double-float variants are this
+ * library's. */
+typedef enum { ARB_FP64 = 0, ARB_MIXED = 1, ARB_MIXED_DF = 2 } arb_precision;
 /* Section 5: Chebyshev interpolant of max(0,t)^(10d) (the paper's choice) or the
  * classic Chebyshev polynomial T_d (eq. cheby-poly, the paper's comparison filter). */
 typedef enum { ARB_FILTER_CHEBINTERP = 0, ARB_FILTER_CHEBYSHEV = 1 } arb_filter_kind;
@@ -178,6 +184,17 @@ arb_status arb_filter_f32(arb_ctx ctx, arb_mat mat, double op_scale, double op_s
                           double b, int32_t degree, const double* coef, const float* X,
                           int64_t ldx, int32_t ncols, const double* xscale, float* Y,
                           int64_t ldy, double* colss);
+
+/* The same filter in double-float arithmetic (the ARB_MIXED_DF refinement's filter).  X and
+ * Y are FP64 n x ncols row-major (device); X is rounded to hi + lo FP32 pairs, the d
+ * Clenshaw passes run on those pairs (sums by two-sum, products by the FMA-exact product;
+ * about 2^-44 relative error per operation) and the result is returned as hi + lo in FP64.
+ * colss (device float64[ncols] or NULL) gets the FP64 column sums of squares of Y.  A's
+ * double-float values are made once and kept with the matrix.  Errors: as arb_filter. */
+arb_status arb_filter_df(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, double a,
+                         double b, int32_t degree, const double* coef, const double* X,
+                         int64_t ldx, int32_t ncols, const double* xscale, double* Y, int64_t ldy,
+                         double* colss);
 
 /* One instance of a batched filter (arb_filter_batched): the same arguments as arb_filter
  * / arb_filter_f32, X and Y FP32 when fp32 != 0, else FP64. */

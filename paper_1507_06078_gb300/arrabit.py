@@ -25,7 +25,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "arrabit.h")
 ARB_OK, ARB_NOT_CONVERGED, ARB_INVALID_ARG, ARB_OUT_OF_MEMORY = 0, 1, -1, -2
 ARB_NOT_SYMMETRIC, ARB_BREAKDOWN, ARB_CUDA_ERROR, ARB_TIMEOUT, ARB_REJECTED = -3, -4, -5, -6, -7
 ARB_LARGEST, ARB_SMALLEST = 0, 1
-ARB_FP64, ARB_MIXED = 0, 1
+ARB_FP64, ARB_MIXED, ARB_MIXED_DF = 0, 1, 2
 ARB_FILTER_CHEBINTERP, ARB_FILTER_CHEBYSHEV = 0, 1
 STOP_REASONS = {0: "converged", 1: "near_tol", 2: "stalled", 3: "maxit", 4: "all_locked"}
 
@@ -82,6 +82,7 @@ _PROTOS = {
     "arb_filter": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _dbl, _i32, _vp, _vp, _i64, _i32, _vp, _vp, _i64, _vp]),
     "arb_filter_f32": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _dbl, _i32, _vp, _vp, _i64, _i32, _vp, _vp, _i64,
                               _vp]),
+    "arb_filter_df": (_i32, [_vp, _vp, _dbl, _dbl, _dbl, _dbl, _i32, _vp, _vp, _i64, _i32, _vp, _vp, _i64, _vp]),
     "arb_filter_coefficients": (_i32, [_i32, _i32, _vp]),
     "arb_filter_batched": (_i32, [_vp, _i32, _vp]),
     "arb_spmm": (_i32, [_vp, _vp, _dbl, _dbl, _vp, _i64, _i32, _vp, _i64]),
@@ -298,6 +299,22 @@ def arb_filter(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, a: f
                            _vp(_ptr(X)), ldx, X.shape[1], _vp(_ptr(xscale)), _vp(_ptr(Y)), ldy,
                            _vp(_ptr(colss)))
     _check(ctx, st, "arb_filter")
+    return Y
+
+
+def arb_filter_df(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, a: float, b: float,
+                  coef: np.ndarray, X, xscale=None, Y=None, colss=None):
+    """arb_filter computed in double-float arithmetic (X, Y: FP64 CUDA tensors)."""
+    import torch
+    ldx = _dev2d(X, "X")
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    if Y is None:
+        Y = torch.empty_like(X)
+    ldy = _dev2d(Y, "Y")
+    st = load().arb_filter_df(ctx.handle, mat.handle, op_scale, op_shift, a, b, len(coef) - 1, coef.ctypes.data,
+                              _vp(_ptr(X)), ldx, X.shape[1], _vp(_ptr(xscale)), _vp(_ptr(Y)), ldy,
+                              _vp(_ptr(colss)))
+    _check(ctx, st, "arb_filter_df")
     return Y
 
 

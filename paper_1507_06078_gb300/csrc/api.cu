@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <type_traits>
 #include <vector>
 
 #include "arb_internal.h"
@@ -259,6 +260,7 @@ extern "C" arb_status arb_matrix_destroy(arb_mat m) {
   cudaFree(m->col);
   cudaFree(m->val);
   if (m->val32) cudaFree(m->val32);
+  if (m->valdf) cudaFree(m->valdf);
   delete m;
   return ARB_OK;
 }
@@ -324,6 +326,26 @@ extern "C" arb_status arb_filter_f32(arb_ctx ctx, arb_mat mat, double op_scale, 
   ARB_TRY(ws<float>(ctx, WS_F32_W2, static_cast<size_t>(n) * ldw, &W2));
   FilterPlan plan = make_filter_plan(op_scale, op_shift, a, b, degree, coef);
   return filter_apply<float>(ctx, mat, plan, X, ldx, ncols, xscale, W1, W2, ldw, Y, ldy, colss, nullptr);
+}
+
+extern "C" arb_status arb_filter_df(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, double a,
+                                    double b, int32_t degree, const double* coef, const double* X, int64_t ldx,
+                                    int32_t ncols, const double* xscale, double* Y, int64_t ldy, double* colss) {
+  if (!ctx || !mat || !coef || !X || !Y || ncols < 0 || ldx < ncols || ldy < ncols || !(b > a))
+    return set_error(ctx, ARB_INVALID_ARG, "filter_df: bad arguments");
+  if (degree < 1 || degree > 60) return set_error(ctx, ARB_INVALID_ARG, "filter_df: degree must be in [1, 60]");
+  ARB_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (ncols == 0) return ARB_OK;
+  const int64_t n = mat->n;
+  const int64_t ldw = ncols + (ncols & 1);  // double-float rows padded to 16 bytes
+  df2 *W1, *W2, *Xd, *R = nullptr;
+  ARB_TRY(ws<df2>(ctx, WS_FILT_W1, static_cast<size_t>(n) * ldw, &W1));
+  ARB_TRY(ws<df2>(ctx, WS_FILT_W2, static_cast<size_t>(n) * ldw, &W2));
+  ARB_TRY(ws<df2>(ctx, WS_TALL0, static_cast<size_t>(n) * ldw, &Xd));
+  ARB_TRY(to_df(ctx, n, X, ldx, ncols, Xd, ldw));
+  FilterPlan plan = make_filter_plan(op_scale, op_shift, a, b, degree, coef);
+  ARB_TRY(filter_apply<df2>(ctx, mat, plan, Xd, ldw, ncols, xscale, W1, W2, ldw, nullptr, 0, colss, &R));
+  return from_df(ctx, n, R, ldw, ncols, Y, ldy);
 }
 
 extern "C" arb_status arb_spmm(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, const double* X,
@@ -485,6 +507,7 @@ struct SolveState {
   arb_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool trace = false;  // ARB_TRACE set in the environment: one line per outer iteration on stderr
+  bool df_filter = false;  // FP64 phase filters in double-float arithmetic (ARB_MIXED_DF)
 };
 
 template <typename T>
@@ -547,9 +570,25 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
       for (int i2 = 0; i2 < n_steps; ++i2) {
         const FilterPlan plan = make_filter_plan(S.op_scale, S.op_shift, S.a, S.b, S.d, S.coef);
         T* result = nullptr;
-        ARB_TRY(filter_apply<T>(ctx, mat, plan, B.X, B.ld, S.w, S.xs, B.W1, B.W2, B.ld, nullptr, 0, S.ss, &result));
-        if (result == B.W1) std::swap(B.X, B.W1);
-        else std::swap(B.X, B.W2);
+        bool filtered = false;
+        if constexpr (std::is_same<T, double>::value) {
+          if (S.df_filter) {
+            // double-float filter: X rounded into T1 (free during the inner loop), the passes
+            // run in W1 / W2 (same bytes per element as FP64), the result read back into X
+            df2* Xd = reinterpret_cast<df2*>(B.wk.T1);
+            df2* R = nullptr;
+            ARB_TRY(to_df(ctx, n, B.X, B.ld, S.w, Xd, B.ld));
+            ARB_TRY(filter_apply<df2>(ctx, mat, plan, Xd, B.ld, S.w, S.xs, reinterpret_cast<df2*>(B.W1),
+                                      reinterpret_cast<df2*>(B.W2), B.ld, nullptr, 0, S.ss, &R));
+            ARB_TRY(from_df(ctx, n, R, B.ld, S.w, B.X, B.ld));
+            filtered = true;
+          }
+        }
+        if (!filtered) {
+          ARB_TRY(filter_apply<T>(ctx, mat, plan, B.X, B.ld, S.w, S.xs, B.W1, B.W2, B.ld, nullptr, 0, S.ss, &result));
+          if (result == B.W1) std::swap(B.X, B.W1);
+          else std::swap(B.X, B.W2);
+        }
         ARB_TRY(inv_sqrt(ctx, S.w, S.ss, S.xs));  // column normalisation, applied lazily
         if (S.nl > 0) ARB_TRY(project_out<T>(ctx, n, B.Qc, B.ld, S.nl, B.X, B.ld, S.w));
         S.info.n_filters++;
@@ -714,13 +753,14 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
   if (k <= 0 || k > p || S.q < 0 || S.d < 1 || S.d > 60 || o.maxit < 1 || o.maxit1 < 1 || o.maxit2 < 1 ||
       static_cast<int64_t>(S.q + 1) * p >= n || !(tol > 0.0))
     return set_error(ctx, ARB_INVALID_ARG, "solve: need 0 < k <= p, (q+1) p < n, 1 <= degree <= 60, tol > 0");
-  if (o.precision != ARB_FP64 && o.precision != ARB_MIXED)
+  if (o.precision != ARB_FP64 && o.precision != ARB_MIXED && o.precision != ARB_MIXED_DF)
     return set_error(ctx, ARB_INVALID_ARG, "solve: unknown precision");
   if (o.b_update != 0 && o.b_update != 1) return set_error(ctx, ARB_INVALID_ARG, "solve: b_update must be 0 or 1");
   if (which != ARB_LARGEST && which != ARB_SMALLEST) return set_error(ctx, ARB_INVALID_ARG, "solve: bad which");
   if (evecs && ldq < n) return set_error(ctx, ARB_INVALID_ARG, "solve: ldq < n");
   S.smallest = (which == ARB_SMALLEST);
-  const bool mixed = (o.precision == ARB_MIXED);
+  const bool mixed = (o.precision == ARB_MIXED || o.precision == ARB_MIXED_DF);
+  S.df_filter = (o.precision == ARB_MIXED_DF);
   S.trace = getenv("ARB_TRACE") != nullptr;
 
   // operator B = op_scale A + op_shift I whose largest eigenpairs are wanted
@@ -743,6 +783,7 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
   if (mixed) {
     ARB_TRY(alloc_blocks<float>(ctx, S, F));
     ARB_TRY(ensure_val32(ctx, mat));
+    if (S.df_filter) ARB_TRY(ensure_valdf(ctx, mat));
   }
   ARB_TRY(ws<double>(ctx, WS_S_V, static_cast<size_t>(S.mcap) * S.mcap, &S.V));
   ARB_TRY(ws<double>(ctx, WS_S_VSEL, static_cast<size_t>(S.mcap) * p, &S.Vsel));
@@ -896,7 +937,8 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
 
 }  // namespace
 
-size_t arb::solve_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, bool mixed) {
+size_t arb::solve_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, int32_t precision) {
+  const bool mixed = (precision == ARB_MIXED || precision == ARB_MIXED_DF);
   const int64_t ld = p + (p & 1), ldm = static_cast<int64_t>(q + 1) * p + (((q + 1) * p) & 1);
   const int64_t mcap = static_cast<int64_t>(q + 1) * p;
   size_t b = static_cast<size_t>(n) * (7 * ld + 2 * ldm) * sizeof(double);
@@ -904,6 +946,7 @@ size_t arb::solve_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, bool m
     const int64_t l4 = (p + 3) / 4 * 4, m4 = (mcap + 3) / 4 * 4;
     b += static_cast<size_t>(n) * (6 * l4 + 2 * m4) * sizeof(float) + static_cast<size_t>(nnz) * sizeof(float);
   }
+  if (precision == ARB_MIXED_DF) b += static_cast<size_t>(nnz) * 2 * sizeof(float);  // double-float values of A
   // small dense state (H, eigenvectors, Gram matrices, Jacobi copies), split-K and column
   // reduction partial sums: bounded by a few m x m matrices plus one slab of partials
   b += static_cast<size_t>(8 * mcap * mcap + 2048 * mcap) * sizeof(double) + (64u << 20);

@@ -12,6 +12,12 @@
 
 namespace arb {
 
+// A double-float value hi + lo (two FP32 numbers, |lo| <= ulp(hi)/2): blocks of the
+// double-float refinement filter (df.cu).
+struct __align__(8) df2 {
+  float hi, lo;
+};
+
 // Workspace slots owned by a context.  Each slot is one device allocation that grows on
 // demand; contents are not preserved across calls that request a larger size.
 enum WsSlot : int {
@@ -84,10 +90,11 @@ struct arb_mat_s {
   int32_t* col = nullptr;
   double* val = nullptr;
   float* val32 = nullptr;  // FP32 copy of val for the mixed-precision filter (made on demand)
+  arb::df2* valdf = nullptr;  // double-float copy of val for the double-float filter (made on demand)
   int32_t max_row_nnz = -1;  // longest row (-1: unknown)
   bool gersh_valid = false;
   double gersh_lo = 0.0, gersh_hi = 0.0;
-  std::mutex mu;  // guards the lazily made val32 and Gershgorin cache (shared by server workers)
+  std::mutex mu;  // guards the lazily made val32 / valdf and the Gershgorin cache (shared by server workers)
 };
 
 namespace arb {
@@ -125,8 +132,8 @@ inline arb_status ws(arb_ctx ctx, int slot, size_t count, T** out) {
 // Release every workspace slot of the context.
 arb_status ws_release_all(arb_ctx ctx);
 // Device bytes the solver's workspaces take for an n x p block, q augmentation blocks and
-// a matrix with nnz entries (FP32 copies included for the mixed path).
-size_t solve_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, bool mixed);
+// a matrix with nnz entries (FP32 / double-float copies included for the mixed paths).
+size_t solve_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, int32_t precision);
 // The whole method on ctx (used by arb_solve and by the server's workers).
 arb_status solve_on(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol, const arb_options* opts,
                     const double* x0, int x0_on_device, double* evals, double* evecs, int64_t ldq,
@@ -162,8 +169,19 @@ struct SpmmArgs {
 };
 template <typename T>
 arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a);
+// double-float blocks (df.cu): leading dimensions even, 16-byte aligned bases
+template <>
+arb_status spmm_fused<df2>(arb_ctx ctx, const SpmmArgs<df2>& a);
 // FP32 copy of A's values (kept with the matrix).
 arb_status ensure_val32(arb_ctx ctx, arb_mat mat);
+
+// ---------------------------------------------------------------- double-float (df.cu)
+// Double-float copy of A's values (kept with the matrix).
+arb_status ensure_valdf(arb_ctx ctx, arb_mat mat);
+// dst (n x ncols, df) = src (FP64), rounded to nearest double-float
+arb_status to_df(arb_ctx ctx, int64_t n, const double* src, int64_t lds, int32_t ncols, df2* dst, int64_t ldd);
+// dst (FP64) = hi + lo of src
+arb_status from_df(arb_ctx ctx, int64_t n, const df2* src, int64_t lds, int32_t ncols, double* dst, int64_t ldd);
 
 // Gershgorin lower/upper bound of A into host doubles.
 arb_status gershgorin(arb_ctx ctx, arb_mat mat, double* lo, double* hi);

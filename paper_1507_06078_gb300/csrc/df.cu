@@ -1,0 +1,313 @@
+// Double-float ("df") blocks for the refinement filter of the mixed path.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so an FP64 filter pass is bound by
+// the FP64 pipe (about 5x its HBM time).  A df element stores a value as an unevaluated
+// sum hi + lo of two FP32 numbers (8 bytes, the same traffic as FP64) and the arithmetic
+// uses only the FP32 pipe: products by the FMA-based exact product (Dekker / Kahan:
+// p = a*b, e = fma(a, b, -p)), sums by Knuth's two-sum followed by a fast renormalising
+// two-sum.  That carries about 2^-44 relative accuracy per operation, far below the
+// 1e-8 residuals and 1e-10 eigenvalue errors the solver is run to; the Rayleigh-Ritz
+// steps, residuals and reported eigenvalues stay in true FP64.
+#include <algorithm>
+
+#include "arb_internal.h"
+
+namespace arb {
+namespace {
+
+constexpr int DF_THREADS = 256;
+constexpr int DF_WARPS = DF_THREADS / 32;
+
+__device__ __forceinline__ df2 df_from(double x) {
+  const float h = __double2float_rn(x);
+  return df2{h, __double2float_rn(x - static_cast<double>(h))};
+}
+__device__ __forceinline__ double df_to(df2 a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
+// The transforms below are exact only as written: __fadd_rn / __fsub_rn / __fmul_rn are
+// never contracted into an FMA, so the compiler cannot fuse a product into a later sum.
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ df2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// s + e = a + b exactly when |a| >= |b|
+__device__ __forceinline__ df2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
+  df2 s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
+// p + e = a.hi * b.hi exactly (e from one FMA), then the cross terms a.hi b.lo + a.lo b.hi
+__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+struct DfParams {
+  int64_t n;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const df2* val;
+  int32_t ncols;
+  const df2* Yin;
+  int64_t ldy;
+  double alpha, beta;
+  const double* sy;
+  const df2* X;
+  int64_t ldx;
+  const double* sx;
+  const df2* Z;
+  int64_t ldz;
+  const double* sz;
+  df2* out;
+  int64_t ldo;
+  double* red_part;
+  int dot_with_yin;
+};
+
+// two df elements per lane (16-byte accesses); a warp owns a fixed 64-column chunk and
+// walks its rows, gathers issued four at a time (the same work split as the FP32/FP64
+// fused kernel).  Leading dimensions are even and bases 16-byte aligned; for odd ncols
+// the pad column (ld >= ncols + 1) is read and written but never reduced.
+__device__ __forceinline__ void ld2(const df2* p, df2 (&r)[2]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  r[0] = df2{t.x, t.y};
+  r[1] = df2{t.z, t.w};
+}
+__device__ __forceinline__ void ld2s(const df2* p, df2 (&r)[2]) {
+  const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+  r[0] = df2{t.x, t.y};
+  r[1] = df2{t.z, t.w};
+}
+
+template <bool RED>
+__global__ void __launch_bounds__(DF_THREADS, 2) spmm_df_kernel(DfParams P) {
+  extern __shared__ double s_red[];
+  constexpr int CH = 64;
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int ncols = P.ncols;
+  const int nch = (ncols + CH - 1) / CH;
+  if constexpr (RED) {
+    for (int c = lane; c < ncols; c += 32) s_red[static_cast<size_t>(warp) * ncols + c] = 0.0;
+    __syncwarp();
+  }
+  const int64_t gw = static_cast<int64_t>(blockIdx.x) * DF_WARPS + warp;
+  const int64_t nwarps = static_cast<int64_t>(gridDim.x) * DF_WARPS;
+  const int64_t rstride = nwarps / nch;
+  const int chunk = static_cast<int>(gw % nch);
+  const int64_t r_first = gw / nch;
+  const int c = chunk * CH + lane * 2;
+  const bool act = (r_first < rstride) && (c < ncols);
+  const bool act1 = act && (c + 1 < ncols);  // odd ncols: the pad column is carried, not reduced
+  df2 csy[2], csx[2], csz[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int cu = (act && c + u < ncols) ? c + u : 0;
+    csy[u] = df_from(P.sy ? P.sy[cu] : 1.0);
+    csx[u] = df_from(P.X ? P.sx[cu] : 0.0);
+    csz[u] = df_from(P.Z ? P.sz[cu] : 0.0);
+  }
+  const df2 alpha = df_from(P.alpha), beta = df_from(P.beta);
+  double red[2] = {0.0, 0.0};
+  if (r_first < rstride) {
+    for (int64_t row = r_first; row < P.n; row += rstride) {
+      df2 xv[2], zv[2];
+      if (P.X && act) ld2s(P.X + row * P.ldx + c, xv);
+      if (P.Z && act) ld2s(P.Z + row * P.ldz + c, zv);
+      df2 acc[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}};
+      const int beg = __ldg(P.rowptr + row), end = __ldg(P.rowptr + row + 1);
+      for (int base = beg; base < end; base += 32) {
+        const int e = base + lane;
+        int jc = 0;
+        float ah = 0.f, al = 0.f;
+        if (e < end) {
+          jc = __ldg(P.col + e);
+          const float2 v = __ldg(reinterpret_cast<const float2*>(P.val) + e);
+          ah = v.x;
+          al = v.y;
+        }
+        const int cnt = min(32, end - base);
+        for (int t0 = 0; t0 < cnt; t0 += 4) {
+          int jj[4];
+          df2 aa[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int src = t0 + t < 32 ? t0 + t : 31;
+            jj[t] = __shfl_sync(0xffffffffu, jc, src);
+            aa[t] = df2{__shfl_sync(0xffffffffu, ah, src), __shfl_sync(0xffffffffu, al, src)};
+          }
+          df2 y[4][2];
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (act && t0 + t < cnt) ld2(P.Yin + static_cast<int64_t>(jj[t]) * P.ldy + c, y[t]);
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (act && t0 + t < cnt) {
+              acc[0] = df_add(acc[0], df_mul(aa[t], y[t][0]));
+              acc[1] = df_add(acc[1], df_mul(aa[t], y[t][1]));
+            }
+        }
+      }
+      if (!act) continue;
+      df2 yi[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}};
+      if (P.beta != 0.0 || (RED && P.dot_with_yin)) ld2(P.Yin + row * P.ldy + c, yi);
+      df2 o[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        o[u] = df_mul(csy[u], df_add(df_mul(alpha, acc[u]), df_mul(beta, yi[u])));
+        if (P.X) o[u] = df_add(o[u], df_mul(csx[u], xv[u]));
+        if (P.Z) o[u] = df_add(o[u], df_mul(csz[u], zv[u]));
+      }
+      if (P.out)
+        __stcs(reinterpret_cast<float4*>(P.out + row * P.ldo + c), make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo));
+      if constexpr (RED) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const double od = df_to(o[u]);
+          if (u == 0 || act1) red[u] += P.dot_with_yin ? od * df_to(yi[u]) : od * od;
+        }
+      }
+    }
+  }
+  if constexpr (RED) {
+    if (act) s_red[static_cast<size_t>(warp) * ncols + c] = red[0];
+    if (act1) s_red[static_cast<size_t>(warp) * ncols + c + 1] = red[1];
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < ncols; cc += blockDim.x) {
+      double sum = 0.0;
+      for (int w = 0; w < DF_WARPS; ++w) sum += s_red[static_cast<size_t>(w) * ncols + cc];
+      P.red_part[static_cast<size_t>(blockIdx.x) * ncols + cc] = sum;
+    }
+  }
+}
+
+__global__ void reduce_cols_kernel(const double* __restrict__ part, int nb, int ncols, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[static_cast<size_t>(b) * ncols + c];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+__global__ void to_df_kernel(int64_t n, const double* __restrict__ src, int64_t lds, int ncols, df2* __restrict__ dst,
+                             int64_t ldd) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * ncols) return;
+  const int64_t r = t / ncols;
+  const int c = static_cast<int>(t % ncols);
+  dst[r * ldd + c] = df_from(src[r * lds + c]);
+}
+
+__global__ void from_df_kernel(int64_t n, const df2* __restrict__ src, int64_t lds, int ncols, double* __restrict__ dst,
+                               int64_t ldd) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= n * ncols) return;
+  const int64_t r = t / ncols;
+  const int c = static_cast<int>(t % ncols);
+  dst[r * ldd + c] = df_to(src[r * lds + c]);
+}
+
+__global__ void val_df_kernel(int64_t nnz, const double* __restrict__ v, df2* __restrict__ out) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t < nnz) out[t] = df_from(v[t]);
+}
+
+inline int blocks_of(int64_t count, int threads) {
+  return static_cast<int>(std::max<int64_t>(1, (count + threads - 1) / threads));
+}
+
+}  // namespace
+
+arb_status ensure_valdf(arb_ctx ctx, arb_mat mat) {
+  std::lock_guard<std::mutex> lock(mat->mu);
+  if (mat->valdf) return ARB_OK;
+  df2* v = nullptr;
+  ARB_CUDA(ctx, cudaMalloc(&v, std::max<int64_t>(mat->nnz, 1) * sizeof(df2)));
+  if (mat->nnz > 0) {
+    val_df_kernel<<<blocks_of(mat->nnz, 256), 256, 0, ctx->stream>>>(mat->nnz, mat->val, v);
+    ARB_LAUNCHED(ctx);
+  }
+  ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  mat->valdf = v;
+  return ARB_OK;
+}
+
+arb_status to_df(arb_ctx ctx, int64_t n, const double* src, int64_t lds, int32_t ncols, df2* dst, int64_t ldd) {
+  if (n <= 0 || ncols <= 0) return ARB_OK;
+  to_df_kernel<<<blocks_of(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status from_df(arb_ctx ctx, int64_t n, const df2* src, int64_t lds, int32_t ncols, double* dst, int64_t ldd) {
+  if (n <= 0 || ncols <= 0) return ARB_OK;
+  from_df_kernel<<<blocks_of(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+template <>
+arb_status spmm_fused<df2>(arb_ctx ctx, const SpmmArgs<df2>& a) {
+  const arb_mat_s* A = a.A;
+  if (a.ncols <= 0 || A->n <= 0) return ARB_OK;
+  if (!A->valdf) return set_error(ctx, ARB_INVALID_ARG, "spmm(df): matrix has no double-float values");
+  const bool even = (a.ldy % 2 == 0) && (!a.X || a.ldx % 2 == 0) && (!a.Z || a.ldz % 2 == 0) &&
+                    (!a.out || a.ldo % 2 == 0);
+  if (!even) return set_error(ctx, ARB_INVALID_ARG, "spmm(df): leading dimensions must be even");
+  DfParams P;
+  P.n = A->n;
+  P.rowptr = A->rowptr;
+  P.col = A->col;
+  P.val = A->valdf;
+  P.ncols = a.ncols;
+  P.Yin = a.Yin;
+  P.ldy = a.ldy;
+  P.alpha = a.alpha;
+  P.beta = a.beta;
+  P.sy = a.sy;
+  P.X = a.X;
+  P.ldx = a.ldx;
+  P.sx = a.sx;
+  P.Z = a.Z;
+  P.ldz = a.ldz;
+  P.sz = a.sz;
+  P.out = a.out;
+  P.ldo = a.ldo;
+  P.dot_with_yin = a.dot_with_yin ? 1 : 0;
+  P.red_part = nullptr;
+  const bool want_red = a.colred != nullptr;
+  const size_t smem = want_red ? static_cast<size_t>(DF_WARPS) * a.ncols * sizeof(double) : 0;
+  if (smem > 200 * 1024) return set_error(ctx, ARB_INVALID_ARG, "spmm(df): too many columns for reduction");
+  void (*kern)(DfParams) = want_red ? spmm_df_kernel<true> : spmm_df_kernel<false>;
+  ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  int per_sm = 0;
+  ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DF_THREADS, smem));
+  const int nch = (a.ncols + 63) / 64;
+  const int64_t want = (P.n * nch + DF_WARPS - 1) / DF_WARPS;
+  int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(ctx->num_sms) * std::max(per_sm, 1)));
+  grid = std::max(grid, (nch + DF_WARPS - 1) / DF_WARPS);
+  if (want_red) ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * a.ncols, &P.red_part));
+  kern<<<grid, DF_THREADS, smem, ctx->stream>>>(P);
+  ARB_LAUNCHED(ctx);
+  if (want_red) {
+    reduce_cols_kernel<<<a.ncols, 256, 0, ctx->stream>>>(P.red_part, grid, a.ncols, a.colred);
+    ARB_LAUNCHED(ctx);
+  }
+  return ARB_OK;
+}
+
+}  // namespace arb

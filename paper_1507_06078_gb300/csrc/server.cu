@@ -113,7 +113,8 @@ void worker_loop(arb_server srv, int slot) {
 
 extern "C" int64_t arb_server_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, int32_t precision) {
   if (n <= 0 || p <= 0 || q < 0) return -1;
-  return static_cast<int64_t>(arb::solve_footprint(n, nnz, p, q, precision == ARB_MIXED));
+  if (precision != ARB_FP64 && precision != ARB_MIXED && precision != ARB_MIXED_DF) return -1;
+  return static_cast<int64_t>(arb::solve_footprint(n, nnz, p, q, precision));
 }
 
 extern "C" arb_status arb_server_create(int device, size_t hbm_budget_bytes, int32_t max_slots, arb_server* out) {
@@ -166,7 +167,7 @@ extern "C" arb_status arb_submit(arb_server srv, arb_mat mat, int32_t k, arb_whi
   const int32_t p = req->opts.p > 0 ? req->opts.p : k + static_cast<int32_t>(std::lround(0.1 * k));
   if (x0) req->x0.assign(x0, x0 + static_cast<size_t>(mat->n) * p);
   req->want_vecs = want_evecs != 0;
-  req->footprint = arb::solve_footprint(mat->n, mat->nnz, p, req->opts.q, req->opts.precision == ARB_MIXED);
+  req->footprint = arb::solve_footprint(mat->n, mat->nnz, p, req->opts.q, req->opts.precision);
   std::lock_guard<std::mutex> lock(srv->mu);
   if (srv->stop) return ARB_REJECTED;
   if (req->footprint > srv->budget) {
@@ -254,7 +255,7 @@ extern "C" arb_status arb_solve_batched(arb_ctx ctx, int32_t nb, const arb_mat* 
     if (opts) o = opts[i];
     else arb_options_default(&o, k[i]);
     const int32_t p = o.p > 0 ? o.p : k[i] + static_cast<int32_t>(std::lround(0.1 * k[i]));
-    fp[i] = arb::solve_footprint(mats[i]->n, mats[i]->nnz, p, o.q, o.precision == ARB_MIXED);
+    fp[i] = arb::solve_footprint(mats[i]->n, mats[i]->nnz, p, o.q, o.precision);
   }
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return fp[a] > fp[b]; });
   std::vector<arb_ticket> tickets(nb, 0);

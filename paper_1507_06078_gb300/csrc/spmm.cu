@@ -29,9 +29,6 @@ constexpr int SPMM_WARPS = SPMM_THREADS / 32;
 #ifndef ARB_SPMM_MIN_BLOCKS
 #define ARB_SPMM_MIN_BLOCKS 3
 #endif
-#ifndef ARB_SPMM_PIPE
-#define ARB_SPMM_PIPE 1
-#endif
 
 template <typename T>
 struct KParams {
@@ -255,155 +252,6 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
   }
 }
 
-// Pipelined variant for short rows (at most PIPE_MAXNZ nonzeros, e.g. stencils), 16-byte
-// lanes: the same work split and arithmetic as spmm_fused_kernel, but every operand a row
-// needs - the gathered segments of Yin, the rows of X and Z and the row's own segment of
-// Yin - is fetched by cp.async into a per-warp ring of PIPE_STAGES stages in shared
-// memory.  A warp issues the copies of the row PIPE_STAGES-1 rows ahead, waits for the
-// oldest stage, and computes from shared memory, so several rows' loads are in flight
-// per warp without holding registers for them.
-constexpr int PIPE_STAGES = 4;
-constexpr int PIPE_MAXNZ = 8;
-constexpr int PIPE_SEGS = PIPE_MAXNZ + 3;
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-template <typename T, int VEC, bool RED>
-__global__ void __launch_bounds__(SPMM_THREADS, 1) spmm_pipe_kernel(KParams<T> P) {
-  static_assert(VEC * sizeof(T) == 16, "16-byte lanes");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int CH = 32 * VEC;
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int ncols = P.ncols;
-  const int nch = (ncols + CH - 1) / CH;
-  T* ring = reinterpret_cast<T*>(smem_raw) + static_cast<size_t>(warp) * PIPE_STAGES * PIPE_SEGS * CH;
-  double* s_red = reinterpret_cast<double*>(smem_raw + static_cast<size_t>(SPMM_WARPS) * PIPE_STAGES * PIPE_SEGS * CH *
-                                                           sizeof(T));
-  auto slot = [&](int st, int seg) { return ring + (static_cast<size_t>(st) * PIPE_SEGS + seg) * CH + lane * VEC; };
-  if constexpr (RED) {
-    for (int c = lane; c < ncols; c += 32) s_red[static_cast<size_t>(warp) * ncols + c] = 0.0;
-    __syncwarp();
-  }
-  const int64_t gw = static_cast<int64_t>(blockIdx.x) * SPMM_WARPS + warp;
-  const int64_t nwarps = static_cast<int64_t>(gridDim.x) * SPMM_WARPS;
-  const int64_t rstride = nwarps / nch;
-  const int chunk = static_cast<int>(gw % nch);
-  const int64_t r_first = gw / nch;
-  const bool warp_on = r_first < rstride;  // warp-uniform
-  const int c = chunk * CH + lane * VEC;
-  const bool act = warp_on && c < ncols;
-  T csy[VEC], csx[VEC], csz[VEC];
-#pragma unroll
-  for (int u = 0; u < VEC; ++u) {
-    const int cu = act ? c + u : 0;
-    csy[u] = P.sy ? static_cast<T>(P.sy[cu]) : T(1);
-    csx[u] = P.X ? static_cast<T>(P.sx[cu]) : T(0);
-    csz[u] = P.Z ? static_cast<T>(P.sz[cu]) : T(0);
-  }
-  const bool need_yi = P.beta != T(0) || (RED && P.dot_with_yin);
-  // copies of row r into stage st (one commit group per call, possibly empty)
-  auto issue = [&](int64_t r, int st) {
-    if (warp_on && r < P.n) {
-      const int beg = __ldg(P.rowptr + r);
-      const int cnt = __ldg(P.rowptr + r + 1) - beg;
-      const int jc = lane < cnt ? __ldg(P.col + beg + lane) : 0;
-#pragma unroll
-      for (int t = 0; t < PIPE_MAXNZ; ++t) {
-        const int j = __shfl_sync(0xffffffffu, jc, t);
-        if (t < cnt && act) cp_async16(slot(st, t), P.Yin + static_cast<int64_t>(j) * P.ldy + c);
-      }
-      if (act) {
-        if (P.X) cp_async16(slot(st, PIPE_MAXNZ), P.X + r * P.ldx + c);
-        if (P.Z) cp_async16(slot(st, PIPE_MAXNZ + 1), P.Z + r * P.ldz + c);
-        if (need_yi) cp_async16(slot(st, PIPE_MAXNZ + 2), P.Yin + r * P.ldy + c);
-      }
-    }
-    cp_async_commit();
-  };
-  double red[VEC];
-#pragma unroll
-  for (int u = 0; u < VEC; ++u) red[u] = 0.0;
-#pragma unroll
-  for (int s0 = 0; s0 < PIPE_STAGES - 1; ++s0) issue(r_first + s0 * rstride, s0);
-  for (int64_t k = 0;; ++k) {
-    const int64_t row = r_first + k * rstride;
-    if (!warp_on || row >= P.n) break;
-    issue(r_first + (k + PIPE_STAGES - 1) * rstride, static_cast<int>((k + PIPE_STAGES - 1) % PIPE_STAGES));
-    cp_async_wait<PIPE_STAGES - 1>();
-    __syncwarp();
-    const int st = static_cast<int>(k % PIPE_STAGES);
-    const int beg = __ldg(P.rowptr + row);
-    const int cnt = __ldg(P.rowptr + row + 1) - beg;
-    const T av = lane < cnt ? __ldg(P.val + beg + lane) : T(0);
-    T acc[VEC];
-#pragma unroll
-    for (int u = 0; u < VEC; ++u) acc[u] = T(0);
-#pragma unroll
-    for (int t = 0; t < PIPE_MAXNZ; ++t) {
-      const T v = __shfl_sync(0xffffffffu, av, t);
-      if (t < cnt && act) {
-        T y[VEC];
-        VecIO<T, VEC>::ld(slot(st, t), y);
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) acc[u] = fma(v, y[u], acc[u]);
-      }
-    }
-    if (act) {
-      T yi[VEC], o[VEC];
-      if (need_yi) {
-        VecIO<T, VEC>::ld(slot(st, PIPE_MAXNZ + 2), yi);
-      } else {
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) yi[u] = T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < VEC; ++u) o[u] = csy[u] * fma(P.alpha, acc[u], P.beta * yi[u]);
-      if (P.X) {
-        T xv[VEC];
-        VecIO<T, VEC>::ld(slot(st, PIPE_MAXNZ), xv);
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) o[u] = fma(csx[u], xv[u], o[u]);
-      }
-      if (P.Z) {
-        T zv[VEC];
-        VecIO<T, VEC>::ld(slot(st, PIPE_MAXNZ + 1), zv);
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) o[u] = fma(csz[u], zv[u], o[u]);
-      }
-      if (P.out) VecIO<T, VEC>::sts(P.out + row * P.ldo + c, o);
-      if constexpr (RED) {
-#pragma unroll
-        for (int u = 0; u < VEC; ++u) {
-          const double od = static_cast<double>(o[u]);
-          red[u] += P.dot_with_yin ? od * static_cast<double>(yi[u]) : od * od;
-        }
-      }
-    }
-    __syncwarp();  // the stage is refilled by the next iteration's copies
-  }
-  cp_async_wait<0>();
-  if constexpr (RED) {
-    if (act)
-#pragma unroll
-      for (int u = 0; u < VEC; ++u) s_red[static_cast<size_t>(warp) * ncols + c + u] = red[u];
-    __syncthreads();
-    for (int cc = threadIdx.x; cc < ncols; cc += blockDim.x) {
-      double sum = 0.0;
-      for (int w = 0; w < SPMM_WARPS; ++w) sum += s_red[static_cast<size_t>(w) * ncols + cc];
-      P.red_part[static_cast<size_t>(blockIdx.x) * ncols + cc] = sum;
-    }
-  }
-}
-
 __global__ void to_float_kernel(int64_t n, const double* __restrict__ src, float* __restrict__ dst) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t < n) dst[t] = static_cast<float>(src[t]);
@@ -488,27 +336,6 @@ __global__ void col_sumsq_kernel(int64_t n, const double* __restrict__ X, int64_
 // One wave: as many CTAs as are resident at once (at most what the rows need), so no
 // second, partly empty wave of CTAs runs at the end.  With want_red, the per-CTA partial
 // column sums go to a workspace of grid x ncols doubles (returned with the grid).
-template <typename T, int VEC>
-arb_status launch_spmm_pipe(arb_ctx ctx, KParams<T> P, bool want_red, int* grid_out, double** part_out) {
-  void (*kern)(KParams<T>) = want_red ? spmm_pipe_kernel<T, VEC, true> : spmm_pipe_kernel<T, VEC, false>;
-  const size_t smem = static_cast<size_t>(SPMM_WARPS) * PIPE_STAGES * PIPE_SEGS * 32 * VEC * sizeof(T) +
-                      (want_red ? static_cast<size_t>(SPMM_WARPS) * P.ncols * sizeof(double) : 0);
-  ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-  int per_sm = 0;
-  ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPMM_THREADS, smem));
-  const int nch = (P.ncols + 32 * VEC - 1) / (32 * VEC);
-  const int64_t want = (P.n * nch + SPMM_WARPS - 1) / SPMM_WARPS;
-  int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(ctx->num_sms) * std::max(per_sm, 1)));
-  grid = std::max(grid, (nch + SPMM_WARPS - 1) / SPMM_WARPS);
-  P.red_part = nullptr;
-  if (want_red) ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(grid) * P.ncols, &P.red_part));
-  kern<<<grid, SPMM_THREADS, smem, ctx->stream>>>(P);
-  ARB_LAUNCHED(ctx);
-  *grid_out = grid;
-  *part_out = P.red_part;
-  return ARB_OK;
-}
-
 template <typename T, int VEC>
 arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, int* grid_out,
                        double** part_out) {
@@ -604,15 +431,8 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   };
   int grid = 0;
   double* part = nullptr;
-  // short rows and 16-byte lanes: the cp.async pipeline (FP32 blocks)
-  const size_t pipe_smem = static_cast<size_t>(SPMM_WARPS) * PIPE_STAGES * PIPE_SEGS * 512 +
-                           (want_red ? static_cast<size_t>(SPMM_WARPS) * a.ncols * sizeof(double) : 0);
-  const bool pipe = sizeof(T) == 4 && A->max_row_nnz >= 0 && A->max_row_nnz <= PIPE_MAXNZ && fits(4) &&
-                    pipe_smem <= 220 * 1024 && ARB_SPMM_PIPE;
   if constexpr (sizeof(T) == 4) {
-    if (pipe) {
-      ARB_TRY((launch_spmm_pipe<T, 4>(ctx, P, want_red, &grid, &part)));
-    } else if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
+    if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
       ARB_TRY((launch_spmm<T, 4>(ctx, P, smem, want_red, &grid, &part)));
     } else if (fits(2)) {
       ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, &grid, &part)));

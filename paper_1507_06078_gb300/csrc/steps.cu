@@ -2,6 +2,7 @@
 // built from the kernels of spmm.cu, dense.cu and jacobi.cu.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "arb_internal.h"
@@ -90,7 +91,8 @@ arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const 
   auto sx_of = [&](int t) { return table + (3 * static_cast<int64_t>(t) + 1) * ncols; };
   auto sz_of = [&](int t) { return table + (3 * static_cast<int64_t>(t) + 2) * ncols; };
 
-  if (sizeof(T) == 4) ARB_TRY(ensure_val32(ctx, mat));
+  if constexpr (std::is_same<T, float>::value) ARB_TRY(ensure_val32(ctx, mat));
+  if constexpr (std::is_same<T, df2>::value) ARB_TRY(ensure_valdf(ctx, mat));
   SpmmArgs<T> a;
   a.A = mat;
   a.ncols = ncols;
@@ -309,6 +311,8 @@ template arb_status filter_apply<double>(arb_ctx, arb_mat, const FilterPlan&, co
                                          double**);
 template arb_status filter_apply<float>(arb_ctx, arb_mat, const FilterPlan&, const float*, int64_t, int32_t,
                                         const double*, float*, float*, int64_t, float*, int64_t, double*, float**);
+template arb_status filter_apply<df2>(arb_ctx, arb_mat, const FilterPlan&, const df2*, int64_t, int32_t, const double*,
+                                      df2*, df2*, int64_t, df2*, int64_t, double*, df2**);
 template arb_status orth<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, double*, int64_t, double*,
                                  int64_t, int32_t*);
 template arb_status orth<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, float*, int64_t, float*,

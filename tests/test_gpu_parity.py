@@ -120,6 +120,35 @@ def test_filter_f32_against_oracle(arb, ctx, d, ncols):
     np.testing.assert_allclose(host(colss), np.sum(ref * ref, axis=0), rtol=1e-4)
 
 
+@pytest.mark.parametrize("d,ncols,diffusion", [(1, 7, False), (3, 30, False), (10, 64, True), (20, 131, False),
+                                                (20, 240, False), (15, 33, True)])
+def test_filter_df_against_oracle(arb, ctx, d, ncols, diffusion):
+    # double-float filter vs the FP64 oracle.  Each double-float product or sum is good to
+    # about 2^-46 of its operands; the FP32 filter's error grows to ~22 u32 of max|Y| at
+    # d = 20 on these inputs, the same growth at 2^-46 is ~3e-13, so 1e-11 of max|Y| is the
+    # bar (odd widths exercise the pad column; the diffusion matrix has non-integer values
+    # that do not fit one FP32 number).
+    A = I.diffusion_2d(40, 3) if diffusion else I.laplacian_2d(40)
+    mat = arb.Matrix.from_csr(ctx, A)
+    B = scipy_of(A)
+    sigma = O.gershgorin_bounds(B)[1]
+    Bs = sigma * sp.identity(A.n, format="csr") - B
+    X = I.gaussian_block(A.n, ncols, 5)
+    xs = np.linspace(0.5, 2.0, ncols)
+    a, b = 0.0, 0.45 * sigma
+    coef = O.interpolant_cheb_coeffs(d)
+    colss = torch.zeros(ncols, dtype=torch.float64, device="cuda")
+    Y = host(arb.arb_filter_df(ctx, mat, -1.0, sigma, a, b, coef, dev(X), xscale=dev(xs), colss=colss))
+    ref = O.poly_clenshaw(Bs, X * xs[None, :], 0.0, b, coef)
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(Y, ref, rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(host(colss), np.sum(ref * ref, axis=0), rtol=1e-10)
+    # and far below the FP32 filter's error on the same inputs
+    Y32 = host(arb.arb_filter_f32(ctx, mat, -1.0, sigma, a, b, coef, dev(X).float(), xscale=dev(xs)))
+    ref32 = O.poly_clenshaw(Bs, X.astype(np.float32).astype(np.float64) * xs[None, :], 0.0, b, coef)
+    assert np.abs(Y - ref).max() * 1e3 < max(np.abs(Y32 - ref32).max(), 1e-300)
+
+
 def test_filter_on_closed_form_eigenvectors(arb, ctx):
     # spectral mapping (eq. poly-A): rho(A) v = rho(lambda) v for the sin-product eigenvectors
     m = 20
@@ -369,11 +398,27 @@ def test_solve_mixed_2d64_against_oracle(arb, ctx):
     assert r.info["outer_iters_fp32"] >= 1
 
 
-def test_solve_mixed_3d_scaled(arb, ctx):
+def test_solve_mixed_df_2d64_against_oracle(arb, ctx):
+    # FP32 phase + refinement with the double-float filter: the same bar as the FP64 path
+    W = I.workload_2d64()
+    X0 = I.gaussian_block(W.A.n, W.p, W.seed)
+    r = _solve(arb, ctx, W.A, W.k, W.p, W.q, W.degree, W.tol, X0, precision=arb.ARB_MIXED_DF)
+    assert r.status == arb.ARB_OK, r.info
+    lam = np.array(json_golden()["evals"])
+    assert np.max(np.abs(r.evals - lam) / np.maximum(1.0, np.abs(lam))) <= 1e-10
+    Q = r.evecs
+    R = scipy_of(W.A) @ Q - Q * r.evals[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= W.tol * 8.0
+    np.testing.assert_allclose(Q.T @ Q, np.eye(W.k), atol=1e-12)
+    assert r.info["maxres"] <= W.tol
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_solve_mixed_3d_scaled(arb, ctx, precision):
     m, k, p = 24, 30, 36
     A = I.laplacian_3d(m)
     X0 = I.gaussian_block(A.n, p, 99)
-    r = _solve(arb, ctx, A, k, p, 2, 12, 1e-8, X0, precision=arb.ARB_MIXED)
+    r = _solve(arb, ctx, A, k, p, 2, 12, 1e-8, X0, precision=precision)
     assert r.status == arb.ARB_OK, r.info
     np.testing.assert_allclose(r.evals, laplacian_3d_eigs(m)[:k], atol=1e-9)
 
@@ -385,7 +430,7 @@ def json_golden():
     return json.load(open(here))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_solve_b_every_arr_against_oracle(arb, ctx, precision):
     A = I.laplacian_3d(12)
     X0 = I.gaussian_block(A.n, 24, 12)

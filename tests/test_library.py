@@ -59,4 +59,7 @@ def test_server_footprint_formula(lib):
     assert base < f < base + (80 << 20)
     fm = arb.arb_server_footprint(1000, 5000, 30, 1, arb.ARB_MIXED)
     assert fm > f
+    fdf = arb.arb_server_footprint(1000, 5000, 30, 1, arb.ARB_MIXED_DF)
+    assert fdf == fm + 5000 * 8  # plus the double-float copy of A's values
+    assert arb.arb_server_footprint(1000, 5000, 30, 1, 7) == -1
     assert arb.arb_server_footprint(0, 0, 30, 1, 0) == -1
