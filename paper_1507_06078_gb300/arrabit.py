@@ -528,6 +528,5 @@ def arb_solve_batched(ctx: Context, problems: list[dict], max_concurrent: int = 
     st = load().arb_solve_batched(ctx.handle, nb, C.cast(mats, _vp), C.cast(ks, _vp), C.cast(wh, _vp),
                                   C.cast(tl, _vp), C.cast(opts, _vp), C.cast(x0s, _vp), C.cast(evp, _vp),
                                   C.cast(vcp, _vp) if evecs else None, None, C.cast(infos, _vp), max_concurrent)
-    if st not in (ARB_OK, ARB_NOT_CONVERGED):
-        raise ArbError(st, "arb_solve_batched")
+    _check(ctx, st, "arb_solve_batched")
     return st, [SolveResult(ARB_OK, evs[i], vecs[i].T if evecs else None, infos[i].as_dict()) for i in range(nb)]

@@ -80,6 +80,10 @@ struct arb_ctx_s {
   size_t host_pinned_bytes = 0;
   int jacobi_max_blocks = 0;    // co-resident blocks for the cooperative Jacobi kernel
   bool stream_ordered = false;  // workspaces from cudaMallocAsync/cudaFreeAsync on `stream`
+  // Cooperative (grid-synchronising) launches use at most 1/coop_share of the device's
+  // co-resident CTAs, so that the grids of coop_share contexts running concurrently (the
+  // server's slots) always fit on the device together and none waits on another's CTAs.
+  int coop_share = 1;
 };
 
 struct arb_mat_s {

@@ -361,7 +361,7 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
   const int64_t* doff = reinterpret_cast<const int64_t*>(desc + bj + bp);
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_filter_kernel, BT_THREADS, 0));
-  const int grid = std::max(1, per_sm) * ctx->num_sms;
+  const int grid = std::max(1, std::max(1, per_sm) * ctx->num_sms / std::max(1, ctx->coop_share));
   int nj = njobs;
   void* args[] = {&dj, &dp, &doff, &nj, &dmax};
   ARB_CUDA(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(batched_filter_kernel), dim3(grid),

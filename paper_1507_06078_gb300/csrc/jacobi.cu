@@ -2,20 +2,23 @@
 // (Algorithm 1, step 3) and for the small Gram matrices of orth(Z) and of the inner stop
 // rule: parallel two-sided cyclic Jacobi in FP64.
 //
-// Ordering: the round-robin ("circle") tournament on M = m rounded up to even indices.
-// Each of the M-1 rounds of a sweep pairs every index exactly once, so the M/2 plane
-// rotations of a round commute and are applied together: every 2x2 block A[P, Q] (P, Q
-// pairs of the round) becomes J_P^T A[P, Q] J_Q, and every pair of columns of V is
-// rotated.  Blocks are disjoint, so each is updated in place by one thread, which also
-// writes the mirror block so that A stays exactly symmetric.  With an odd
-// m, index m is a dummy whose rotations are the identity.
+// Every rotation of the (i, j) plane with a_ij != 0 uses theta = (a_jj - a_ii)/(2 a_ij),
+// t = sign(theta)/(|theta| + sqrt(theta^2+1)), c = 1/sqrt(1+t^2), s = t c, which zeroes
+// a_ij of J^T A J.  Rotations are scheduled by the round-robin ("circle") tournament: each
+// of the N-1 rounds pairs every one of N indices exactly once, so the rotations of a round
+// commute and are applied together.  Sweeps stop when off(A) <= 1e-15 ||H||_F or after 60.
 //
-// One cooperative launch runs all sweeps; grid-wide barriers separate the rotation and
-// update phases.  The off-diagonal norm is reduced deterministically (per-block partials
-// summed in block order by every thread), so all threads take the same stop decision:
-// stop when off(A) <= 1e-15 ||H||_F or after 60 sweeps.  The rotation of a pair (i, j)
-// with a_ij != 0 uses theta = (a_jj - a_ii)/(2 a_ij), t = sign(theta)/(|theta| +
-// sqrt(theta^2+1)), c = 1/sqrt(1+t^2), s = t c, which zeroes a_ij of J^T A J.
+// m <= 96: one CTA holds A and V in shared memory and rotates single indices.
+// m > 96: block Jacobi.  The indices are cut into NB blocks of 16 (NB even; padding
+// indices have zero rows and columns, so no rotation ever couples them to real ones).  A
+// round of the tournament on the NB blocks pairs blocks (I, J); for each pair the 32 x 32
+// subproblem A[I+J, I+J] gets one cyclic Jacobi sweep in shared memory, accumulating the
+// orthogonal Q_p (phase 1).  Then (phase 2) every block of A is transformed,
+// A[P, P'] <- Q_p^T A[P, P'] Q_p', and V[:, P] <- V[:, P] Q_p.  Both phases are split over
+// the CTAs of one cooperative launch with two grid barriers per round, 2 (NB - 1) per
+// sweep instead of 2 (m - 1) for index-by-index rounds.  The off-diagonal norm is reduced
+// deterministically (per-CTA partials summed in CTA order by every thread), so all
+// threads take the same stop decision.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -37,13 +40,13 @@ struct JacParams {
   int64_t ldh;
   double* A;     // M x M work copy
   double* V;     // M x M
-  double2* rot;  // M/2 rotations (c, s) of the current round
   double* red;   // 2 * gridDim.x partials
   int32_t* perm; // m: sorted position of index i
   double* w_out;
   double* V_out;
   int64_t ldv;
   int32_t* sweeps_out;
+  double* Q;     // block kernel: NB/2 orthogonal 32 x 32 factors of the current round
 };
 
 __device__ __forceinline__ void round_pair(int M, int r, int k, int& i, int& j) {
@@ -75,10 +78,108 @@ __device__ double block_sum(double v, double* sh) {
   return r;
 }
 
-__global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacParams P) {
+__device__ __forceinline__ double2 jacobi_rotation(double aii, double ajj, double aij) {
+  if (aij == 0.0) return make_double2(1.0, 0.0);
+  const double theta = (ajj - aii) / (2.0 * aij);
+  const double sg = theta >= 0.0 ? 1.0 : -1.0;
+  const double t = sg / (fabs(theta) + sqrt(theta * theta + 1.0));
+  const double c = 1.0 / sqrt(t * t + 1.0);
+  return make_double2(c, t * c);
+}
+
+constexpr int BJ_B = 16;          // index block
+constexpr int BJ_S = 2 * BJ_B;    // subproblem order
+constexpr int BJ_LD = BJ_S + 1;   // shared-memory row pitch (bank spread)
+
+// global index of local index x (< 32) of block pair (I, J)
+__device__ __forceinline__ int bj_index(int I, int J, int x) {
+  return x < BJ_B ? I * BJ_B + x : J * BJ_B + (x - BJ_B);
+}
+
+struct BJShared {
+  double S[BJ_S * BJ_LD];   // subproblem / block of A or V
+  double Qa[BJ_S * BJ_LD];
+  double Qb[BJ_S * BJ_LD];
+  double X[BJ_S * BJ_LD];
+  double2 rot[BJ_B];
+  double red[JAC_THREADS];
+};
+
+// One cyclic sweep (31 rounds of 16 rotations) on the 32 x 32 matrix in sh.S, accumulating
+// the rotations into sh.Qa (initially I).
+__device__ void bj_inner_sweep(BJShared& sh) {
+  const int tid = threadIdx.x;
+  for (int r = 0; r < BJ_S - 1; ++r) {
+    if (tid < BJ_B) {
+      int i, j;
+      round_pair(BJ_S, r, tid, i, j);
+      sh.rot[tid] = jacobi_rotation(sh.S[i * BJ_LD + i], sh.S[j * BJ_LD + j], sh.S[i * BJ_LD + j]);
+    }
+    __syncthreads();
+    constexpr int nblk = BJ_B * BJ_B;
+    for (int it = tid; it < nblk + BJ_S * BJ_B; it += blockDim.x) {
+      if (it < nblk) {
+        const int kp = it / BJ_B, kq = it % BJ_B;
+        if (kp > kq) continue;  // the (kq, kp) thread's mirror
+        int i1, j1, i2, j2;
+        round_pair(BJ_S, r, kp, i1, j1);
+        round_pair(BJ_S, r, kq, i2, j2);
+        const double2 r1 = sh.rot[kp], r2 = sh.rot[kq];
+        const double a = sh.S[i1 * BJ_LD + i2], b = sh.S[i1 * BJ_LD + j2];
+        const double cc = sh.S[j1 * BJ_LD + i2], d = sh.S[j1 * BJ_LD + j2];
+        const double ra0 = r1.x * a - r1.y * cc, ra1 = r1.x * b - r1.y * d;
+        const double rb0 = r1.y * a + r1.x * cc, rb1 = r1.y * b + r1.x * d;
+        double na = r2.x * ra0 - r2.y * ra1, nb = r2.y * ra0 + r2.x * ra1;
+        double nc = r2.x * rb0 - r2.y * rb1, nd = r2.y * rb0 + r2.x * rb1;
+        if (kp == kq && r1.y != 0.0) {
+          nb = 0.0;
+          nc = 0.0;
+        }
+        sh.S[i1 * BJ_LD + i2] = na;
+        sh.S[i1 * BJ_LD + j2] = nb;
+        sh.S[j1 * BJ_LD + i2] = nc;
+        sh.S[j1 * BJ_LD + j2] = nd;
+        if (kp != kq) {
+          sh.S[i2 * BJ_LD + i1] = na;
+          sh.S[j2 * BJ_LD + i1] = nb;
+          sh.S[i2 * BJ_LD + j1] = nc;
+          sh.S[j2 * BJ_LD + j1] = nd;
+        }
+      } else {
+        const int it2 = it - nblk;
+        const int row = it2 / BJ_B, kp = it2 % BJ_B;
+        int i, j;
+        round_pair(BJ_S, r, kp, i, j);
+        const double2 rr = sh.rot[kp];
+        if (rr.y != 0.0) {
+          const double x = sh.Qa[row * BJ_LD + i], y = sh.Qa[row * BJ_LD + j];
+          sh.Qa[row * BJ_LD + i] = rr.x * x - rr.y * y;
+          sh.Qa[row * BJ_LD + j] = rr.y * x + rr.x * y;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// out (32 x 32, pitch BJ_LD) = L^T R (transL) or L R; 256 threads, 4 outputs each
+__device__ __forceinline__ void bj_matmul(const double* L, const double* R, double* out, bool transL) {
+  const int z = threadIdx.x / 8, y0 = (threadIdx.x % 8) * 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+  for (int x = 0; x < BJ_S; ++x) {
+    const double l = transL ? L[x * BJ_LD + z] : L[z * BJ_LD + x];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = fma(l, R[x * BJ_LD + y0 + u], acc[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) out[z * BJ_LD + y0 + u] = acc[u];
+}
+
+__global__ void __launch_bounds__(JAC_THREADS) jacobi_block_kernel(JacParams P) {
   cg::grid_group g = cg::this_grid();
-  __shared__ double sh[JAC_THREADS];
-  const int m = P.m, M = P.M, half = M / 2;
+  __shared__ BJShared sh;
+  const int m = P.m, M = P.M, NB = M / BJ_B, npairs = NB / 2;
   const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t nth = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t MM = static_cast<int64_t>(M) * M;
@@ -93,7 +194,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacParams P) {
     fro += v * v;
   }
   {
-    const double b = block_sum(fro, sh);
+    const double b = block_sum(fro, sh.red);
     if (threadIdx.x == 0) P.red[blockIdx.x] = b;
   }
   g.sync();
@@ -102,6 +203,8 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacParams P) {
   const double normF = sqrt(normF2);
   g.sync();
 
+  const int nA = npairs * (npairs + 1) / 2;        // blocks (p <= p') of A
+  const int nV = (M / BJ_S) * npairs;              // 32-row chunks of V x pairs
   int sweep = 0;
   for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
     double off = 0.0;
@@ -110,77 +213,89 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_kernel(JacParams P) {
       if (i != j) off += P.A[t] * P.A[t];
     }
     {
-      const double b = block_sum(off, sh);
+      const double b = block_sum(off, sh.red);
       if (threadIdx.x == 0) P.red[gridDim.x + blockIdx.x] = b;
     }
     g.sync();
     double off2 = 0.0;
     for (int b = 0; b < static_cast<int>(gridDim.x); ++b) off2 += P.red[gridDim.x + b];
     if (sqrt(off2) <= JAC_TOL * normF || normF == 0.0) break;
-    for (int r = 0; r < M - 1; ++r) {
-      for (int64_t k = tid; k < half; k += nth) {
-        int i, j;
-        round_pair(M, r, static_cast<int>(k), i, j);
-        double c = 1.0, s = 0.0;
-        const double aij = P.A[static_cast<int64_t>(i) * M + j];
-        if (j < m && aij != 0.0) {
-          const double theta = (P.A[static_cast<int64_t>(j) * M + j] - P.A[static_cast<int64_t>(i) * M + i]) / (2.0 * aij);
-          const double sg = theta >= 0.0 ? 1.0 : -1.0;
-          const double t = sg / (fabs(theta) + sqrt(theta * theta + 1.0));
-          c = 1.0 / sqrt(t * t + 1.0);
-          s = t * c;
+    for (int r = 0; r < NB - 1; ++r) {
+      // phase 1: one Jacobi sweep per block-pair subproblem -> Q_p
+      for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+        int I, J;
+        round_pair(NB, r, p, I, J);
+        for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+          const int x = t / BJ_S, y = t % BJ_S;
+          sh.S[x * BJ_LD + y] = P.A[static_cast<int64_t>(bj_index(I, J, x)) * M + bj_index(I, J, y)];
+          sh.Qa[x * BJ_LD + y] = (x == y) ? 1.0 : 0.0;
         }
-        P.rot[k] = make_double2(c, s);
+        __syncthreads();
+        bj_inner_sweep(sh);
+        double* Qp = P.Q + static_cast<size_t>(p) * BJ_S * BJ_S;
+        for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x)
+          Qp[t] = sh.Qa[(t / BJ_S) * BJ_LD + (t % BJ_S)];
+        __syncthreads();
       }
       g.sync();
-      const int64_t nblk = static_cast<int64_t>(half) * half;
-      const int64_t total = nblk + static_cast<int64_t>(M) * half;
-      for (int64_t it = tid; it < total; it += nth) {
-        if (it < nblk) {
-          const int kp = static_cast<int>(it / half), kq = static_cast<int>(it % half);
-          if (kp > kq) continue;  // the mirror block is written by the (kq, kp) thread
-          int i1, j1, i2, j2;
-          round_pair(M, r, kp, i1, j1);
-          round_pair(M, r, kq, i2, j2);
-          const double2 r1 = P.rot[kp], r2 = P.rot[kq];
-          double* p_a = P.A + static_cast<int64_t>(i1) * M + i2;
-          double* p_b = P.A + static_cast<int64_t>(i1) * M + j2;
-          double* p_c = P.A + static_cast<int64_t>(j1) * M + i2;
-          double* p_d = P.A + static_cast<int64_t>(j1) * M + j2;
-          const double a = *p_a, b = *p_b, cc = *p_c, d = *p_d;
-          // rows: J_P^T
-          const double ra0 = r1.x * a - r1.y * cc, ra1 = r1.x * b - r1.y * d;
-          const double rb0 = r1.y * a + r1.x * cc, rb1 = r1.y * b + r1.x * d;
-          // columns: J_Q
-          double na = r2.x * ra0 - r2.y * ra1, nb = r2.y * ra0 + r2.x * ra1;
-          double nc = r2.x * rb0 - r2.y * rb1, nd = r2.y * rb0 + r2.x * rb1;
-          if (kp == kq && r1.y != 0.0) {
-            nb = 0.0;  // the rotation annihilates the pivot entry
-            nc = 0.0;
+      // phase 2: A[P, P'] <- Q_p^T A[P, P'] Q_p' (p <= p', mirrored) and V[:, P] <- V[:, P] Q_p
+      for (int task = blockIdx.x; task < nA + nV; task += gridDim.x) {
+        if (task < nA) {
+          int p = 0, rem = task;
+          while (rem >= npairs - p) {
+            rem -= npairs - p;
+            ++p;
           }
-          *p_a = na;
-          *p_b = nb;
-          *p_c = nc;
-          *p_d = nd;
-          if (kp != kq) {  // keep A exactly symmetric
-            P.A[static_cast<int64_t>(i2) * M + i1] = na;
-            P.A[static_cast<int64_t>(j2) * M + i1] = nb;
-            P.A[static_cast<int64_t>(i2) * M + j1] = nc;
-            P.A[static_cast<int64_t>(j2) * M + j1] = nd;
+          const int pp = p + rem;
+          int I1, J1, I2, J2;
+          round_pair(NB, r, p, I1, J1);
+          round_pair(NB, r, pp, I2, J2);
+          const double* Q1 = P.Q + static_cast<size_t>(p) * BJ_S * BJ_S;
+          const double* Q2 = P.Q + static_cast<size_t>(pp) * BJ_S * BJ_S;
+          for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+            const int x = t / BJ_S, y = t % BJ_S;
+            sh.S[x * BJ_LD + y] = P.A[static_cast<int64_t>(bj_index(I1, J1, x)) * M + bj_index(I2, J2, y)];
+            sh.Qa[x * BJ_LD + y] = Q1[t];
+            sh.Qb[x * BJ_LD + y] = Q2[t];
           }
+          __syncthreads();
+          bj_matmul(sh.Qa, sh.S, sh.X, true);   // X = Q_p^T A[P, P']
+          __syncthreads();
+          bj_matmul(sh.X, sh.Qb, sh.S, false);  // S = X Q_p'
+          __syncthreads();
+          for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+            const int z = t / BJ_S, w = t % BJ_S;
+            const int64_t gz = bj_index(I1, J1, z), gw = bj_index(I2, J2, w);
+            if (p != pp) {
+              const double v = sh.S[z * BJ_LD + w];
+              P.A[gz * M + gw] = v;
+              P.A[gw * M + gz] = v;
+            } else if (z <= w) {  // diagonal block: the upper triangle, mirrored (exact symmetry)
+              const double v = sh.S[z * BJ_LD + w];
+              P.A[gz * M + gw] = v;
+              P.A[gw * M + gz] = v;
+            }
+          }
+          __syncthreads();
         } else {
-          const int64_t it2 = it - nblk;
-          const int row = static_cast<int>(it2 / half), kp = static_cast<int>(it2 % half);
-          int i, j;
-          round_pair(M, r, kp, i, j);
-          const double2 rr = P.rot[kp];
-          if (rr.y != 0.0) {
-            double* vi = P.V + static_cast<int64_t>(row) * M + i;
-            double* vj = P.V + static_cast<int64_t>(row) * M + j;
-            const double x = *vi, y = *vj;
-            *vi = rr.x * x - rr.y * y;
-            *vj = rr.y * x + rr.x * y;
+          const int t2 = task - nA;
+          const int chunk = t2 / npairs, p = t2 % npairs;
+          int I, J;
+          round_pair(NB, r, p, I, J);
+          const double* Qp = P.Q + static_cast<size_t>(p) * BJ_S * BJ_S;
+          for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+            const int x = t / BJ_S, y = t % BJ_S;
+            sh.S[x * BJ_LD + y] = P.V[static_cast<int64_t>(chunk * BJ_S + x) * M + bj_index(I, J, y)];
+            sh.Qa[x * BJ_LD + y] = Qp[t];
           }
+          __syncthreads();
+          bj_matmul(sh.S, sh.Qa, sh.X, false);  // X = V[rows, P] Q_p
+          __syncthreads();
+          for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+            const int x = t / BJ_S, y = t % BJ_S;
+            P.V[static_cast<int64_t>(chunk * BJ_S + x) * M + bj_index(I, J, y)] = sh.X[x * BJ_LD + y];
+          }
+          __syncthreads();
         }
       }
       g.sync();
@@ -329,8 +444,13 @@ arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w
     const size_t smem = (2 * static_cast<size_t>(M) * M + 2 * half + JAC_SMALL_THREADS) * sizeof(double);
     int32_t* sw;
     ARB_TRY(ws<int32_t>(ctx, WS_JACOBI, 4, &sw));
+    // the limit is a property of the kernel shared by all host threads: always set it to
+    // the largest size any call uses, so concurrent solves of different orders cannot
+    // lower it between another thread's set and launch
+    constexpr size_t smem_max =
+        (2 * static_cast<size_t>(JAC_SMALL_M) * JAC_SMALL_M + JAC_SMALL_M + JAC_SMALL_THREADS) * sizeof(double);
     ARB_CUDA(ctx, cudaFuncSetAttribute(jacobi_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(smem)));
+                                       static_cast<int>(smem_max)));
     JacParams P = {};
     P.m = m;
     P.M = M;
@@ -347,33 +467,35 @@ arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w
   }
   if (ctx->jacobi_max_blocks == 0) {
     int per_sm = 0;
-    ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JAC_THREADS, 0));
+    ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel, JAC_THREADS, 0));
     ctx->jacobi_max_blocks = std::max(1, per_sm) * ctx->num_sms;
   }
-  const int64_t work = static_cast<int64_t>(half) * half + static_cast<int64_t>(M) * half;
-  int grid = static_cast<int>(std::min<int64_t>((work + JAC_THREADS * 4 - 1) / (JAC_THREADS * 4),
-                                                static_cast<int64_t>(ctx->num_sms) * 2));
-  grid = std::max(1, std::min(grid, ctx->jacobi_max_blocks));
-  // scratch: A, V (M x M), rotations, reductions, permutation, sweep count
-  const size_t mm = static_cast<size_t>(M) * M;
+  const int NB = ((m + BJ_B - 1) / BJ_B + 1) / 2 * 2;  // index blocks, even
+  const int MB = NB * BJ_B;
+  const int npairs = NB / 2;
+  const int tasks = npairs * (npairs + 1) / 2 + (MB / BJ_S) * npairs;
+  int grid = std::max(1, std::min(tasks, ctx->jacobi_max_blocks / std::max(1, ctx->coop_share)));
+  // scratch: A, V (MB x MB), Q factors, reductions, permutation, sweep count
+  const size_t mm = static_cast<size_t>(MB) * MB;
+  const size_t qsz = static_cast<size_t>(npairs) * BJ_S * BJ_S;
   double* base;
-  ARB_TRY(ws<double>(ctx, WS_JACOBI, 2 * mm + 2 * half + 2 * static_cast<size_t>(grid) + m + 8, &base));
-  JacParams P;
+  ARB_TRY(ws<double>(ctx, WS_JACOBI, 2 * mm + qsz + 2 * static_cast<size_t>(grid) + m + 8, &base));
+  JacParams P = {};
   P.m = m;
-  P.M = M;
+  P.M = MB;
   P.H = H;
   P.ldh = ldh;
   P.A = base;
   P.V = base + mm;
-  P.rot = reinterpret_cast<double2*>(base + 2 * mm);
-  P.red = base + 2 * mm + 2 * half;
+  P.Q = base + 2 * mm;
+  P.red = base + 2 * mm + qsz;
   P.perm = reinterpret_cast<int32_t*>(P.red + 2 * grid);
   P.w_out = w;
   P.V_out = V;
   P.ldv = ldv;
   P.sweeps_out = reinterpret_cast<int32_t*>(P.red + 2 * grid + m + 2);
   void* args[] = {&P};
-  ARB_CUDA(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(jacobi_kernel), dim3(grid),
+  ARB_CUDA(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(jacobi_block_kernel), dim3(grid),
                                             dim3(JAC_THREADS), args, 0, ctx->stream));
   ARB_LAUNCHED(ctx);
   if (sweeps) ARB_TRY(d2h_sync(ctx, sweeps, P.sweeps_out, sizeof(int32_t)));

@@ -142,6 +142,7 @@ extern "C" arb_status arb_server_create(int device, size_t hbm_budget_bytes, int
       return ARB_CUDA_ERROR;
     }
     ctx->stream_ordered = true;
+    ctx->coop_share = max_slots;
     srv->ctxs.push_back(ctx);
     srv->streams.push_back(s);
   }
@@ -197,6 +198,7 @@ extern "C" arb_status arb_wait(arb_server srv, arb_ticket ticket, int32_t timeou
     return ARB_TIMEOUT;
   }
   srv->requests.erase(it);
+  if (req->status != ARB_OK && req->status != ARB_NOT_CONVERGED) srv->last_error = req->error;
   lock.unlock();
   const int64_t n = req->mat->n;
   if (evecs && !req->want_vecs) return ARB_INVALID_ARG;
@@ -273,6 +275,10 @@ extern "C" arb_status arb_solve_batched(arb_ctx ctx, int32_t nb, const arb_mat* 
     st = arb_wait(srv, tickets[i], -1, evals[i], evecs ? evecs[i] : nullptr, ldq ? ldq[i] : mats[i]->n,
                   info ? &info[i] : nullptr, nullptr);
     if (st != ARB_OK && (worst == ARB_OK || (worst == ARB_NOT_CONVERGED && st < 0))) worst = st;
+  }
+  if (worst != ARB_OK && worst != ARB_NOT_CONVERGED) {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    ctx->last_error = "solve_batched: " + srv->last_error;
   }
   arb_server_destroy(srv);
   return worst;

@@ -188,7 +188,7 @@ def test_gram_matches_numpy(arb, ctx, n, na, nb):
     assert np.array_equal(G, G.T)
 
 
-@pytest.mark.parametrize("m", [1, 2, 3, 10, 31, 64, 65, 200])
+@pytest.mark.parametrize("m", [1, 2, 3, 10, 31, 64, 65, 96, 97, 200, 256, 720])
 def test_syevj_matches_oracle_jacobi(arb, ctx, m):
     rng = np.random.default_rng(m)
     H = rng.standard_normal((m, m))

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
+from conftest import laplacian_3d_eigs
 from paper_1507_06078_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -131,3 +132,25 @@ def test_solve_batched_matches_standalone(arb, ctx):
         np.testing.assert_allclose(r.evals, alone.evals, rtol=0, atol=1e-12)
         wref = np.linalg.eigvalsh(pr["A"].to_dense())[:pr["k"]]
         np.testing.assert_allclose(r.evals, wref, atol=1e-8 * max(1.0, np.abs(wref).max()))
+
+
+def test_server_concurrent_block_jacobi(arb, ctx):
+    # Rayleigh-Ritz orders above 96 run the cooperative block-Jacobi kernel; three slots run
+    # it concurrently, each on its share of the device, and every result matches the
+    # standalone solve
+    mix = []
+    for i, m in enumerate([14, 15, 16]):
+        A = I.laplacian_3d(m)
+        k, p = 50, 64
+        mix.append((arb.Matrix.from_csr(ctx, A), k, _opts(arb, k, p, 1, 10), I.gaussian_block(A.n, p, 800 + i), m))
+    alone = [arb.arb_solve(ctx, mat, k, 1, 1e-8, o, x0=x0) for (mat, k, o, x0, m) in mix]
+    srv = arb.Server(0, hbm_budget_bytes=8 << 30, max_slots=3)
+    try:
+        tickets = [srv.submit(mat, k, 1, 1e-8, o, x0=x0) for (mat, k, o, x0, m) in mix]
+        got = [srv.wait(t) for t in tickets]
+    finally:
+        srv.close()
+    for a, g, (mat, k, o, x0, m) in zip(alone, got, mix):
+        assert g.status == arb.ARB_OK
+        np.testing.assert_allclose(g.evals, a.evals, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(g.evals, laplacian_3d_eigs(m)[:k], atol=1e-8)
