@@ -87,7 +87,28 @@ __device__ __forceinline__ void ld2s(const df2* p, df2 (&r)[2]) {
   r[1] = df2{t.z, t.w};
 }
 
-template <bool RED>
+// Compensated accumulation (Ogita, Rump & Oishi's Dot2): S collects the rounded sums of
+// the leading products, E the exact rounding errors of those sums and of the products, so
+// S + E carries the dot product as if computed with twice the working precision.  12 FP32
+// operations per term, against 18 for a double-float product followed by a double-float
+// sum.
+__device__ __forceinline__ void dot2_acc(float& S, float& E, df2 c, df2 v) {
+  const float p = __fmul_rn(c.hi, v.hi);
+  float e = fmaf(c.hi, v.hi, -p);
+  e = fmaf(c.hi, v.lo, e);
+  e = fmaf(c.lo, v.hi, e);
+  const float s = __fadd_rn(S, p);
+  const float bb = __fsub_rn(s, S);
+  const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  S = s;
+  E = __fadd_rn(E, __fadd_rn(t, e));
+}
+
+constexpr int DF_BATCH = 8;  // gathers in flight per lane (a 7-point stencil row in one batch)
+
+// SHORT (rows of at most 32 nonzeros): row pointers loaded two rows ahead and column
+// indices / values one row ahead, as in the FP32/FP64 kernel.
+template <bool RED, bool SHORT>
 __global__ void __launch_bounds__(DF_THREADS, 2) spmm_df_kernel(DfParams P) {
   extern __shared__ double s_red[];
   constexpr int CH = 64;
@@ -107,64 +128,124 @@ __global__ void __launch_bounds__(DF_THREADS, 2) spmm_df_kernel(DfParams P) {
   const int c = chunk * CH + lane * 2;
   const bool act = (r_first < rstride) && (c < ncols);
   const bool act1 = act && (c + 1 < ncols);  // odd ncols: the pad column is carried, not reduced
-  df2 csy[2], csx[2], csz[2];
+  // out = ka (A Yin) + kb Yin + kx X + kz Z with ka = sy alpha, kb = sy beta, kx = sx, kz = sz
+  df2 ka[2], kb[2], kx[2], kz[2];
+  {
+    const df2 alpha = df_from(P.alpha), beta = df_from(P.beta);
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int cu = (act && c + u < ncols) ? c + u : 0;
-    csy[u] = df_from(P.sy ? P.sy[cu] : 1.0);
-    csx[u] = df_from(P.X ? P.sx[cu] : 0.0);
-    csz[u] = df_from(P.Z ? P.sz[cu] : 0.0);
+    for (int u = 0; u < 2; ++u) {
+      const int cu = (act && c + u < ncols) ? c + u : 0;
+      const df2 sy = df_from(P.sy ? P.sy[cu] : 1.0);
+      ka[u] = df_mul(sy, alpha);
+      kb[u] = df_mul(sy, beta);
+      kx[u] = df_from(P.X ? P.sx[cu] : 0.0);
+      kz[u] = df_from(P.Z ? P.sz[cu] : 0.0);
+    }
   }
-  const df2 alpha = df_from(P.alpha), beta = df_from(P.beta);
+  const bool need_yi = P.beta != 0.0 || (RED && P.dot_with_yin);
   double red[2] = {0.0, 0.0};
+  int n_jc = 0, n_cnt = 0, p_beg = 0, p_end = 0;
+  float n_ah = 0.f, n_al = 0.f;
+  if (SHORT && r_first < rstride && r_first < P.n) {
+    const int b0 = __ldg(P.rowptr + r_first), e0 = __ldg(P.rowptr + r_first + 1);
+    n_cnt = e0 - b0;
+    if (lane < n_cnt) {
+      n_jc = __ldg(P.col + b0 + lane);
+      const float2 v = __ldg(reinterpret_cast<const float2*>(P.val) + b0 + lane);
+      n_ah = v.x;
+      n_al = v.y;
+    }
+    if (r_first + rstride < P.n) {
+      p_beg = __ldg(P.rowptr + r_first + rstride);
+      p_end = __ldg(P.rowptr + r_first + rstride + 1);
+    }
+  }
   if (r_first < rstride) {
     for (int64_t row = r_first; row < P.n; row += rstride) {
-      df2 xv[2], zv[2];
+      int beg = 0, end = 0, s_jc = 0;
+      float s_ah = 0.f, s_al = 0.f;
+      if constexpr (SHORT) {
+        s_jc = n_jc;
+        s_ah = n_ah;
+        s_al = n_al;
+        end = n_cnt;
+        const int64_t r1 = row + rstride, r2 = row + 2 * rstride;
+        n_cnt = 0;
+        n_jc = 0;
+        n_ah = n_al = 0.f;
+        if (r1 < P.n) {
+          n_cnt = p_end - p_beg;
+          if (lane < n_cnt) {
+            n_jc = __ldg(P.col + p_beg + lane);
+            const float2 v = __ldg(reinterpret_cast<const float2*>(P.val) + p_beg + lane);
+            n_ah = v.x;
+            n_al = v.y;
+          }
+        }
+        if (r2 < P.n) {
+          p_beg = __ldg(P.rowptr + r2);
+          p_end = __ldg(P.rowptr + r2 + 1);
+        }
+      } else {
+        beg = __ldg(P.rowptr + row);
+        end = __ldg(P.rowptr + row + 1);
+      }
+      // the row's own streams first, so their latency overlaps the gathers
+      df2 xv[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}}, zv[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}};
+      df2 yi[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}};
       if (P.X && act) ld2s(P.X + row * P.ldx + c, xv);
       if (P.Z && act) ld2s(P.Z + row * P.ldz + c, zv);
-      df2 acc[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}};
-      const int beg = __ldg(P.rowptr + row), end = __ldg(P.rowptr + row + 1);
+      if (need_yi && act) ld2(P.Yin + row * P.ldy + c, yi);
+      float S[2] = {0.f, 0.f}, E[2] = {0.f, 0.f};
       for (int base = beg; base < end; base += 32) {
-        const int e = base + lane;
         int jc = 0;
         float ah = 0.f, al = 0.f;
-        if (e < end) {
-          jc = __ldg(P.col + e);
-          const float2 v = __ldg(reinterpret_cast<const float2*>(P.val) + e);
-          ah = v.x;
-          al = v.y;
+        if constexpr (SHORT) {
+          jc = s_jc;
+          ah = s_ah;
+          al = s_al;
+        } else {
+          const int e = base + lane;
+          if (e < end) {
+            jc = __ldg(P.col + e);
+            const float2 v = __ldg(reinterpret_cast<const float2*>(P.val) + e);
+            ah = v.x;
+            al = v.y;
+          }
         }
         const int cnt = min(32, end - base);
-        for (int t0 = 0; t0 < cnt; t0 += 4) {
-          int jj[4];
-          df2 aa[4];
+        for (int t0 = 0; t0 < cnt; t0 += DF_BATCH) {
+          int jj[DF_BATCH];
+          df2 aa[DF_BATCH];
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
+          for (int t = 0; t < DF_BATCH; ++t) {
             const int src = t0 + t < 32 ? t0 + t : 31;
             jj[t] = __shfl_sync(0xffffffffu, jc, src);
             aa[t] = df2{__shfl_sync(0xffffffffu, ah, src), __shfl_sync(0xffffffffu, al, src)};
           }
-          df2 y[4][2];
+          df2 y[DF_BATCH][2];
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < DF_BATCH; ++t)
             if (act && t0 + t < cnt) ld2(P.Yin + static_cast<int64_t>(jj[t]) * P.ldy + c, y[t]);
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
+          for (int t = 0; t < DF_BATCH; ++t)
             if (act && t0 + t < cnt) {
-              acc[0] = df_add(acc[0], df_mul(aa[t], y[t][0]));
-              acc[1] = df_add(acc[1], df_mul(aa[t], y[t][1]));
+              dot2_acc(S[0], E[0], aa[t], y[t][0]);
+              dot2_acc(S[1], E[1], aa[t], y[t][1]);
             }
         }
       }
       if (!act) continue;
-      df2 yi[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}};
-      if (P.beta != 0.0 || (RED && P.dot_with_yin)) ld2(P.Yin + row * P.ldy + c, yi);
       df2 o[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        o[u] = df_mul(csy[u], df_add(df_mul(alpha, acc[u]), df_mul(beta, yi[u])));
-        if (P.X) o[u] = df_add(o[u], df_mul(csx[u], xv[u]));
-        if (P.Z) o[u] = df_add(o[u], df_mul(csz[u], zv[u]));
+        const df2 acc = fast_two_sum(S[u], E[u]);
+        float So = 0.f, Eo = 0.f;
+        dot2_acc(So, Eo, ka[u], acc);
+        if (P.beta != 0.0) dot2_acc(So, Eo, kb[u], yi[u]);
+        if (P.X) dot2_acc(So, Eo, kx[u], xv[u]);
+        if (P.Z) dot2_acc(So, Eo, kz[u], zv[u]);
+        o[u] = fast_two_sum(So, Eo);
       }
       if (P.out)
         __stcs(reinterpret_cast<float4*>(P.out + row * P.ldo + c), make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo));
@@ -292,7 +373,9 @@ arb_status spmm_fused<df2>(arb_ctx ctx, const SpmmArgs<df2>& a) {
   const bool want_red = a.colred != nullptr;
   const size_t smem = want_red ? static_cast<size_t>(DF_WARPS) * a.ncols * sizeof(double) : 0;
   if (smem > 200 * 1024) return set_error(ctx, ARB_INVALID_ARG, "spmm(df): too many columns for reduction");
-  void (*kern)(DfParams) = want_red ? spmm_df_kernel<true> : spmm_df_kernel<false>;
+  const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32;
+  void (*kern)(DfParams) = short_rows ? (want_red ? spmm_df_kernel<true, true> : spmm_df_kernel<false, true>)
+                                      : (want_red ? spmm_df_kernel<true, false> : spmm_df_kernel<false, false>);
   ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DF_THREADS, smem));

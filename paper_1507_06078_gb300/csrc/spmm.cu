@@ -142,7 +142,12 @@ struct VecIO<float, 4> {
 // flight together.  The grid is the number of CTAs resident at once (one wave).
 // RED adds the column reduction (sum of out^2 or out*Yin) in FP64 registers, combined per
 // CTA through shared memory.
-template <typename T, int VEC, bool RED>
+//
+// SHORT (every row has at most 32 nonzeros, e.g. stencils): the index loads of a row are
+// software-pipelined across the warp's rows - the row pointers two rows ahead, the column
+// indices and values one row ahead - so a row waits only on its gathers, not on the chain
+// rowptr -> col -> Yin of three dependent loads.
+template <typename T, int VEC, bool RED, bool SHORT>
 __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_kernel(KParams<T> P) {
   extern __shared__ double s_red[];  // [SPMM_WARPS][ncols] when RED
   constexpr int CH = 32 * VEC;
@@ -173,10 +178,48 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
   double red[VEC];
 #pragma unroll
   for (int u = 0; u < VEC; ++u) red[u] = 0.0;
+  // SHORT pipeline state: indices of the next row, row pointers of the one after
+  int n_jc = 0, n_cnt = 0, p_beg = 0, p_end = 0;
+  T n_av = T(0);
+  if (SHORT && r_first < rstride && r_first < P.n) {
+    const int b0 = __ldg(P.rowptr + r_first), e0 = __ldg(P.rowptr + r_first + 1);
+    n_cnt = e0 - b0;
+    if (lane < n_cnt) {
+      n_jc = __ldg(P.col + b0 + lane);
+      n_av = __ldg(P.val + b0 + lane);
+    }
+    if (r_first + rstride < P.n) {
+      p_beg = __ldg(P.rowptr + r_first + rstride);
+      p_end = __ldg(P.rowptr + r_first + rstride + 1);
+    }
+  }
   if (r_first < rstride) {
     for (int64_t row = r_first; row < P.n; row += rstride) {
-      const int beg = __ldg(P.rowptr + row);
-      const int end = __ldg(P.rowptr + row + 1);
+      int beg = 0, end = 0, s_jc = 0;
+      T s_av = T(0);
+      if constexpr (SHORT) {
+        s_jc = n_jc;
+        s_av = n_av;
+        end = n_cnt;  // the row's nonzeros are lanes 0..n_cnt-1 of (s_jc, s_av)
+        const int64_t r1 = row + rstride, r2 = row + 2 * rstride;
+        n_cnt = 0;
+        n_jc = 0;
+        n_av = T(0);
+        if (r1 < P.n) {
+          n_cnt = p_end - p_beg;
+          if (lane < n_cnt) {
+            n_jc = __ldg(P.col + p_beg + lane);
+            n_av = __ldg(P.val + p_beg + lane);
+          }
+        }
+        if (r2 < P.n) {
+          p_beg = __ldg(P.rowptr + r2);
+          p_end = __ldg(P.rowptr + r2 + 1);
+        }
+      } else {
+        beg = __ldg(P.rowptr + row);
+        end = __ldg(P.rowptr + row + 1);
+      }
       T xv[VEC], zv[VEC];
       if (P.X && act) VecIO<T, VEC>::lds(P.X + row * P.ldx + c, xv);
       if (P.Z && act) VecIO<T, VEC>::lds(P.Z + row * P.ldz + c, zv);
@@ -184,12 +227,17 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
 #pragma unroll
       for (int u = 0; u < VEC; ++u) acc[u] = T(0);
       for (int base = beg; base < end; base += 32) {
-        const int e = base + lane;
         int jc = 0;
         T av = T(0);
-        if (e < end) {
-          jc = __ldg(P.col + e);
-          av = __ldg(P.val + e);
+        if constexpr (SHORT) {
+          jc = s_jc;
+          av = s_av;
+        } else {
+          const int e = base + lane;
+          if (e < end) {
+            jc = __ldg(P.col + e);
+            av = __ldg(P.val + e);
+          }
         }
         const int cnt = min(32, end - base);
         for (int t0 = 0; t0 < cnt; t0 += UNR) {
@@ -337,9 +385,11 @@ __global__ void col_sumsq_kernel(int64_t n, const double* __restrict__ X, int64_
 // second, partly empty wave of CTAs runs at the end.  With want_red, the per-CTA partial
 // column sums go to a workspace of grid x ncols doubles (returned with the grid).
 template <typename T, int VEC>
-arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, int* grid_out,
+arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, bool short_rows, int* grid_out,
                        double** part_out) {
-  void (*kern)(KParams<T>) = want_red ? spmm_fused_kernel<T, VEC, true> : spmm_fused_kernel<T, VEC, false>;
+  void (*kern)(KParams<T>) =
+      short_rows ? (want_red ? spmm_fused_kernel<T, VEC, true, true> : spmm_fused_kernel<T, VEC, false, true>)
+                 : (want_red ? spmm_fused_kernel<T, VEC, true, false> : spmm_fused_kernel<T, VEC, false, false>);
   ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPMM_THREADS, smem));
@@ -431,19 +481,20 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   };
   int grid = 0;
   double* part = nullptr;
+  const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32;
   if constexpr (sizeof(T) == 4) {
     if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
-      ARB_TRY((launch_spmm<T, 4>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 4>(ctx, P, smem, want_red, short_rows, &grid, &part)));
     } else if (fits(2)) {
-      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, short_rows, &grid, &part)));
     } else {
-      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, short_rows, &grid, &part)));
     }
   } else {
     if (fits(2)) {
-      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, short_rows, &grid, &part)));
     } else {
-      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, short_rows, &grid, &part)));
     }
   }
   if (want_red) {
