@@ -29,6 +29,9 @@ constexpr int SPMM_WARPS = SPMM_THREADS / 32;
 #ifndef ARB_SPMM_MIN_BLOCKS
 #define ARB_SPMM_MIN_BLOCKS 3
 #endif
+#ifndef ARB_SPMM_SHORT_UNROLL
+#define ARB_SPMM_SHORT_UNROLL 4
+#endif
 
 template <typename T>
 struct KParams {
@@ -143,15 +146,16 @@ struct VecIO<float, 4> {
 // RED adds the column reduction (sum of out^2 or out*Yin) in FP64 registers, combined per
 // CTA through shared memory.
 //
-// SHORT (every row has at most 32 nonzeros, e.g. stencils): the index loads of a row are
-// software-pipelined across the warp's rows - the row pointers two rows ahead, the column
-// indices and values one row ahead - so a row waits only on its gathers, not on the chain
-// rowptr -> col -> Yin of three dependent loads.
+// SHORT (every row has at most 32 nonzeros, e.g. stencils, and every block has fewer than
+// 2^31 elements): the index loads of a row are software-pipelined across the warp's rows -
+// the row pointers two rows ahead, the column indices and values one row ahead - so a row
+// waits only on its gathers, not on the chain rowptr -> col -> Yin of three dependent
+// loads; element offsets are 32-bit products.
 template <typename T, int VEC, bool RED, bool SHORT>
 __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_kernel(KParams<T> P) {
   extern __shared__ double s_red[];  // [SPMM_WARPS][ncols] when RED
   constexpr int CH = 32 * VEC;
-  constexpr int UNR = ARB_SPMM_UNROLL;
+  constexpr int UNR = SHORT ? ARB_SPMM_SHORT_UNROLL : ARB_SPMM_UNROLL;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int ncols = P.ncols;
@@ -220,9 +224,14 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
         beg = __ldg(P.rowptr + row);
         end = __ldg(P.rowptr + row + 1);
       }
+      // element offset of (r, c) in a block of leading dimension ld
+      auto off = [&](int64_t r, int64_t ld) -> int64_t {
+        if constexpr (SHORT) return static_cast<int64_t>(static_cast<uint32_t>(r) * static_cast<uint32_t>(ld));
+        else return r * ld;
+      };
       T xv[VEC], zv[VEC];
-      if (P.X && act) VecIO<T, VEC>::lds(P.X + row * P.ldx + c, xv);
-      if (P.Z && act) VecIO<T, VEC>::lds(P.Z + row * P.ldz + c, zv);
+      if (P.X && act) VecIO<T, VEC>::lds(P.X + off(row, P.ldx) + c, xv);
+      if (P.Z && act) VecIO<T, VEC>::lds(P.Z + off(row, P.ldz) + c, zv);
       T acc[VEC];
 #pragma unroll
       for (int u = 0; u < VEC; ++u) acc[u] = T(0);
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
           T y[UNR][VEC];
 #pragma unroll
           for (int t = 0; t < UNR; ++t)
-            if (act && t0 + t < cnt) VecIO<T, VEC>::ld(P.Yin + static_cast<int64_t>(jj[t]) * P.ldy + c, y[t]);
+            if (act && t0 + t < cnt) VecIO<T, VEC>::ld(P.Yin + off(jj[t], P.ldy) + c, y[t]);
 #pragma unroll
           for (int t = 0; t < UNR; ++t)
             if (act && t0 + t < cnt)
@@ -262,7 +271,7 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
       if (!act) continue;
       T yi[VEC], o[VEC];
       if (P.beta != T(0) || (RED && P.dot_with_yin)) {
-        VecIO<T, VEC>::ld(P.Yin + row * P.ldy + c, yi);
+        VecIO<T, VEC>::ld(P.Yin + off(row, P.ldy) + c, yi);
       } else {
 #pragma unroll
         for (int u = 0; u < VEC; ++u) yi[u] = T(0);
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
 #pragma unroll
         for (int u = 0; u < VEC; ++u) o[u] = fma(csz[u], zv[u], o[u]);
       }
-      if (P.out) VecIO<T, VEC>::sts(P.out + row * P.ldo + c, o);
+      if (P.out) VecIO<T, VEC>::sts(P.out + off(row, P.ldo) + c, o);
       if constexpr (RED) {
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
@@ -481,7 +490,11 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   };
   int grid = 0;
   double* part = nullptr;
-  const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32;
+  int64_t ld_max = a.ldy;
+  if (a.X) ld_max = std::max(ld_max, a.ldx);
+  if (a.Z) ld_max = std::max(ld_max, a.ldz);
+  if (a.out) ld_max = std::max(ld_max, a.ldo);
+  const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32 && A->n * ld_max < (int64_t(1) << 31);
   if constexpr (sizeof(T) == 4) {
     if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
       ARB_TRY((launch_spmm<T, 4>(ctx, P, smem, want_red, short_rows, &grid, &part)));
