@@ -8,6 +8,12 @@
 // two-sum.  That carries about 2^-44 relative accuracy per operation, far below the
 // 1e-8 residuals and 1e-10 eigenvalue errors the solver is run to; the Rayleigh-Ritz
 // steps, residuals and reported eigenvalues stay in true FP64.
+//
+// Block layout ("paired planar"): row-major with an even leading dimension ld (in df
+// elements); the columns 2j and 2j+1 of a row are the four floats
+// [hi(2j), hi(2j+1), lo(2j), lo(2j+1)], so one 16-byte load gives a lane the hi parts and
+// the lo parts of its two columns as float2 pairs, the operands of the packed FP32x2
+// instructions (FFMA2 / FADD2 / FMUL2) that do the arithmetic of both columns at once.
 #include <algorithm>
 
 #include "arb_internal.h"
@@ -22,24 +28,12 @@ __device__ __forceinline__ df2 df_from(double x) {
   const float h = __double2float_rn(x);
   return df2{h, __double2float_rn(x - static_cast<double>(h))};
 }
-__device__ __forceinline__ double df_to(df2 a) { return static_cast<double>(a.hi) + static_cast<double>(a.lo); }
 // The transforms below are exact only as written: __fadd_rn / __fsub_rn / __fmul_rn are
 // never contracted into an FMA, so the compiler cannot fuse a product into a later sum.
-// s + e = a + b exactly (Knuth)
-__device__ __forceinline__ df2 two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return df2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
 // s + e = a + b exactly when |a| >= |b|
 __device__ __forceinline__ df2 fast_two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
   return df2{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
-  df2 s = two_sum(a.hi, b.hi);
-  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
-  return fast_two_sum(s.hi, s.lo);
 }
 // p + e = a.hi * b.hi exactly (e from one FMA), then the cross terms a.hi b.lo + a.lo b.hi
 __device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
@@ -72,44 +66,60 @@ struct DfParams {
   int dot_with_yin;
 };
 
-// two df elements per lane (16-byte accesses); a warp owns a fixed 64-column chunk and
-// walks its rows, gathers issued four at a time (the same work split as the FP32/FP64
-// fused kernel).  Leading dimensions are even and bases 16-byte aligned; for odd ncols
-// the pad column (ld >= ncols + 1) is read and written but never reduced.
-__device__ __forceinline__ void ld2(const df2* p, df2 (&r)[2]) {
+// two double-float values (a lane's two columns): hi parts and lo parts as pairs
+struct dfp {
+  float2 hi, lo;
+};
+__device__ __forceinline__ dfp ldp(const df2* p) {
   const float4 t = *reinterpret_cast<const float4*>(p);
-  r[0] = df2{t.x, t.y};
-  r[1] = df2{t.z, t.w};
+  return dfp{make_float2(t.x, t.y), make_float2(t.z, t.w)};
 }
-__device__ __forceinline__ void ld2s(const df2* p, df2 (&r)[2]) {
+__device__ __forceinline__ dfp ldps(const df2* p) {
   const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
-  r[0] = df2{t.x, t.y};
-  r[1] = df2{t.z, t.w};
+  return dfp{make_float2(t.x, t.y), make_float2(t.z, t.w)};
+}
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ dfp dfp_of(df2 a, df2 b) { return dfp{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+__device__ __forceinline__ dfp fast_two_sum2(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  return dfp{s, __fadd2_rn(b, neg2(__fadd2_rn(s, neg2(a))))};
 }
 
-// Compensated accumulation (Ogita, Rump & Oishi's Dot2): S collects the rounded sums of
-// the leading products, E the exact rounding errors of those sums and of the products, so
-// S + E carries the dot product as if computed with twice the working precision.  12 FP32
-// operations per term, against 18 for a double-float product followed by a double-float
-// sum.
-__device__ __forceinline__ void dot2_acc(float& S, float& E, df2 c, df2 v) {
-  const float p = __fmul_rn(c.hi, v.hi);
-  float e = fmaf(c.hi, v.hi, -p);
-  e = fmaf(c.hi, v.lo, e);
-  e = fmaf(c.lo, v.hi, e);
-  const float s = __fadd_rn(S, p);
-  const float bb = __fsub_rn(s, S);
-  const float t = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+// Compensated accumulation (Ogita, Rump & Oishi's Dot2) of c * v into (S, E), for both
+// columns at once: S collects the rounded sums of the leading products, E the exact
+// rounding errors of those sums (Knuth's two-sum) and of the products (one FMA each) plus
+// the cross terms, so S + E carries the dot product as if computed with twice the working
+// precision.  12 packed instructions per term for two columns.
+__device__ __forceinline__ void dot2p(float2& S, float2& E, const dfp& c, const dfp& v) {
+  const float2 p = __fmul2_rn(c.hi, v.hi);
+  float2 e = __ffma2_rn(c.hi, v.hi, neg2(p));
+  e = __ffma2_rn(c.hi, v.lo, e);
+  e = __ffma2_rn(c.lo, v.hi, e);
+  const float2 s = __fadd2_rn(S, p);
+  const float2 bb = __fadd2_rn(s, neg2(S));
+  const float2 t = __fadd2_rn(__fadd2_rn(S, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
   S = s;
-  E = __fadd_rn(E, __fadd_rn(t, e));
+  E = __fadd2_rn(E, __fadd2_rn(t, e));
 }
 
-constexpr int DF_BATCH = 8;  // gathers in flight per lane (a 7-point stencil row in one batch)
+// Tuning defaults (measured on the 128^3 x 240 filter): gathers in flight per lane and the
+// CTAs per SM the register budget must allow.
+#ifndef ARB_DF_BATCH
+#define ARB_DF_BATCH 8
+#endif
+#ifndef ARB_DF_MIN_BLOCKS
+#define ARB_DF_MIN_BLOCKS 2
+#endif
+constexpr int DF_BATCH = ARB_DF_BATCH;
 
-// SHORT (rows of at most 32 nonzeros): row pointers loaded two rows ahead and column
-// indices / values one row ahead, as in the FP32/FP64 kernel.
+// A warp owns a fixed 64-column chunk (two columns per lane, 16-byte accesses) and walks
+// its rows, gathers issued DF_BATCH at a time, as in the FP32/FP64 fused kernel.  Leading
+// dimensions are even and bases 16-byte aligned; for odd ncols the pad column (ld >=
+// ncols + 1) is read and written but never reduced.
+// SHORT (rows of at most 32 nonzeros, blocks below 2^31 elements): row pointers loaded two
+// rows ahead, column indices and values one row ahead, 32-bit element offsets.
 template <bool RED, bool SHORT>
-__global__ void __launch_bounds__(DF_THREADS, 2) spmm_df_kernel(DfParams P) {
+__global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(DfParams P) {
   extern __shared__ double s_red[];
   constexpr int CH = 64;
   const int warp = threadIdx.x >> 5;
@@ -129,20 +139,31 @@ __global__ void __launch_bounds__(DF_THREADS, 2) spmm_df_kernel(DfParams P) {
   const bool act = (r_first < rstride) && (c < ncols);
   const bool act1 = act && (c + 1 < ncols);  // odd ncols: the pad column is carried, not reduced
   // out = ka (A Yin) + kb Yin + kx X + kz Z with ka = sy alpha, kb = sy beta, kx = sx, kz = sz
-  df2 ka[2], kb[2], kx[2], kz[2];
+  dfp ka, kb, kx, kz;
   {
     const df2 alpha = df_from(P.alpha), beta = df_from(P.beta);
+    df2 a[2], b[2], x[2], z[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int cu = (act && c + u < ncols) ? c + u : 0;
       const df2 sy = df_from(P.sy ? P.sy[cu] : 1.0);
-      ka[u] = df_mul(sy, alpha);
-      kb[u] = df_mul(sy, beta);
-      kx[u] = df_from(P.X ? P.sx[cu] : 0.0);
-      kz[u] = df_from(P.Z ? P.sz[cu] : 0.0);
+      a[u] = df_mul(sy, alpha);
+      b[u] = df_mul(sy, beta);
+      x[u] = df_from(P.X ? P.sx[cu] : 0.0);
+      z[u] = df_from(P.Z ? P.sz[cu] : 0.0);
     }
+    ka = dfp_of(a[0], a[1]);
+    kb = dfp_of(b[0], b[1]);
+    kx = dfp_of(x[0], x[1]);
+    kz = dfp_of(z[0], z[1]);
   }
-  const bool need_yi = P.beta != 0.0 || (RED && P.dot_with_yin);
+  auto off = [&](int64_t r, int64_t ld) -> int64_t {
+    if constexpr (SHORT) return static_cast<int64_t>(static_cast<uint32_t>(r) * static_cast<uint32_t>(ld));
+    else return r * ld;
+  };
+  const bool has_beta = P.beta != 0.0;  // one FP64 compare per thread, not one per row
+  const bool need_yi = has_beta || (RED && P.dot_with_yin);
+  const dfp zero{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   double red[2] = {0.0, 0.0};
   int n_jc = 0, n_cnt = 0, p_beg = 0, p_end = 0;
   float n_ah = 0.f, n_al = 0.f;
@@ -191,12 +212,11 @@ __global__ void __launch_bounds__(DF_THREADS, 2) spmm_df_kernel(DfParams P) {
         end = __ldg(P.rowptr + row + 1);
       }
       // the row's own streams first, so their latency overlaps the gathers
-      df2 xv[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}}, zv[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}};
-      df2 yi[2] = {df2{0.f, 0.f}, df2{0.f, 0.f}};
-      if (P.X && act) ld2s(P.X + row * P.ldx + c, xv);
-      if (P.Z && act) ld2s(P.Z + row * P.ldz + c, zv);
-      if (need_yi && act) ld2(P.Yin + row * P.ldy + c, yi);
-      float S[2] = {0.f, 0.f}, E[2] = {0.f, 0.f};
+      dfp xv = zero, zv = zero, yi = zero;
+      if (P.X && act) xv = ldps(P.X + off(row, P.ldx) + c);
+      if (P.Z && act) zv = ldps(P.Z + off(row, P.ldz) + c);
+      if (need_yi && act) yi = ldp(P.Yin + off(row, P.ldy) + c);
+      float2 S = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
       for (int base = beg; base < end; base += 32) {
         int jc = 0;
         float ah = 0.f, al = 0.f;
@@ -216,44 +236,43 @@ __global__ void __launch_bounds__(DF_THREADS, 2) spmm_df_kernel(DfParams P) {
         const int cnt = min(32, end - base);
         for (int t0 = 0; t0 < cnt; t0 += DF_BATCH) {
           int jj[DF_BATCH];
-          df2 aa[DF_BATCH];
+          float aah[DF_BATCH], aal[DF_BATCH];
 #pragma unroll
           for (int t = 0; t < DF_BATCH; ++t) {
             const int src = t0 + t < 32 ? t0 + t : 31;
             jj[t] = __shfl_sync(0xffffffffu, jc, src);
-            aa[t] = df2{__shfl_sync(0xffffffffu, ah, src), __shfl_sync(0xffffffffu, al, src)};
+            aah[t] = __shfl_sync(0xffffffffu, ah, src);
+            aal[t] = __shfl_sync(0xffffffffu, al, src);
           }
-          df2 y[DF_BATCH][2];
+          dfp y[DF_BATCH];
 #pragma unroll
           for (int t = 0; t < DF_BATCH; ++t)
-            if (act && t0 + t < cnt) ld2(P.Yin + static_cast<int64_t>(jj[t]) * P.ldy + c, y[t]);
+            if (act && t0 + t < cnt) y[t] = ldp(P.Yin + off(jj[t], P.ldy) + c);
 #pragma unroll
           for (int t = 0; t < DF_BATCH; ++t)
-            if (act && t0 + t < cnt) {
-              dot2_acc(S[0], E[0], aa[t], y[t][0]);
-              dot2_acc(S[1], E[1], aa[t], y[t][1]);
-            }
+            if (act && t0 + t < cnt)
+              dot2p(S, E, dfp{make_float2(aah[t], aah[t]), make_float2(aal[t], aal[t])}, y[t]);
         }
       }
       if (!act) continue;
-      df2 o[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const df2 acc = fast_two_sum(S[u], E[u]);
-        float So = 0.f, Eo = 0.f;
-        dot2_acc(So, Eo, ka[u], acc);
-        if (P.beta != 0.0) dot2_acc(So, Eo, kb[u], yi[u]);
-        if (P.X) dot2_acc(So, Eo, kx[u], xv[u]);
-        if (P.Z) dot2_acc(So, Eo, kz[u], zv[u]);
-        o[u] = fast_two_sum(So, Eo);
-      }
+      const dfp acc = fast_two_sum2(S, E);
+      float2 So = make_float2(0.f, 0.f), Eo = make_float2(0.f, 0.f);
+      dot2p(So, Eo, ka, acc);
+      if (has_beta) dot2p(So, Eo, kb, yi);
+      if (P.X) dot2p(So, Eo, kx, xv);
+      if (P.Z) dot2p(So, Eo, kz, zv);
+      const dfp o = fast_two_sum2(So, Eo);
       if (P.out)
-        __stcs(reinterpret_cast<float4*>(P.out + row * P.ldo + c), make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo));
+        __stcs(reinterpret_cast<float4*>(P.out + off(row, P.ldo) + c), make_float4(o.hi.x, o.hi.y, o.lo.x, o.lo.y));
       if constexpr (RED) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const double od = df_to(o[u]);
-          if (u == 0 || act1) red[u] += P.dot_with_yin ? od * df_to(yi[u]) : od * od;
+        const double o0 = static_cast<double>(o.hi.x) + static_cast<double>(o.lo.x);
+        const double o1 = static_cast<double>(o.hi.y) + static_cast<double>(o.lo.y);
+        if (P.dot_with_yin) {
+          red[0] += o0 * (static_cast<double>(yi.hi.x) + static_cast<double>(yi.lo.x));
+          if (act1) red[1] += o1 * (static_cast<double>(yi.hi.y) + static_cast<double>(yi.lo.y));
+        } else {
+          red[0] += o0 * o0;
+          if (act1) red[1] += o1 * o1;
         }
       }
     }
@@ -284,22 +303,29 @@ __global__ void reduce_cols_kernel(const double* __restrict__ part, int nb, int 
   if (threadIdx.x == 0) out[c] = sh[0];
 }
 
+// one thread per (row, column pair): FP64 -> paired planar double-float
 __global__ void to_df_kernel(int64_t n, const double* __restrict__ src, int64_t lds, int ncols, df2* __restrict__ dst,
                              int64_t ldd) {
+  const int npair = (ncols + 1) / 2;
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (t >= n * ncols) return;
-  const int64_t r = t / ncols;
-  const int c = static_cast<int>(t % ncols);
-  dst[r * ldd + c] = df_from(src[r * lds + c]);
+  if (t >= n * npair) return;
+  const int64_t r = t / npair;
+  const int c = 2 * static_cast<int>(t % npair);
+  const df2 a = df_from(src[r * lds + c]);
+  const df2 b = df_from(c + 1 < ncols ? src[r * lds + c + 1] : 0.0);
+  *reinterpret_cast<float4*>(dst + r * ldd + c) = make_float4(a.hi, b.hi, a.lo, b.lo);
 }
 
 __global__ void from_df_kernel(int64_t n, const df2* __restrict__ src, int64_t lds, int ncols, double* __restrict__ dst,
                                int64_t ldd) {
+  const int npair = (ncols + 1) / 2;
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (t >= n * ncols) return;
-  const int64_t r = t / ncols;
-  const int c = static_cast<int>(t % ncols);
-  dst[r * ldd + c] = df_to(src[r * lds + c]);
+  if (t >= n * npair) return;
+  const int64_t r = t / npair;
+  const int c = 2 * static_cast<int>(t % npair);
+  const float4 v = *reinterpret_cast<const float4*>(src + r * lds + c);
+  dst[r * ldd + c] = static_cast<double>(v.x) + static_cast<double>(v.z);
+  if (c + 1 < ncols) dst[r * ldd + c + 1] = static_cast<double>(v.y) + static_cast<double>(v.w);
 }
 
 __global__ void val_df_kernel(int64_t nnz, const double* __restrict__ v, df2* __restrict__ out) {
@@ -329,14 +355,16 @@ arb_status ensure_valdf(arb_ctx ctx, arb_mat mat) {
 
 arb_status to_df(arb_ctx ctx, int64_t n, const double* src, int64_t lds, int32_t ncols, df2* dst, int64_t ldd) {
   if (n <= 0 || ncols <= 0) return ARB_OK;
-  to_df_kernel<<<blocks_of(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
+  if (ldd % 2) return set_error(ctx, ARB_INVALID_ARG, "to_df: leading dimension must be even");
+  to_df_kernel<<<blocks_of(n * ((ncols + 1) / 2), 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
 
 arb_status from_df(arb_ctx ctx, int64_t n, const df2* src, int64_t lds, int32_t ncols, double* dst, int64_t ldd) {
   if (n <= 0 || ncols <= 0) return ARB_OK;
-  from_df_kernel<<<blocks_of(n * ncols, 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
+  if (lds % 2) return set_error(ctx, ARB_INVALID_ARG, "from_df: leading dimension must be even");
+  from_df_kernel<<<blocks_of(n * ((ncols + 1) / 2), 256), 256, 0, ctx->stream>>>(n, src, lds, ncols, dst, ldd);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
@@ -373,7 +401,11 @@ arb_status spmm_fused<df2>(arb_ctx ctx, const SpmmArgs<df2>& a) {
   const bool want_red = a.colred != nullptr;
   const size_t smem = want_red ? static_cast<size_t>(DF_WARPS) * a.ncols * sizeof(double) : 0;
   if (smem > 200 * 1024) return set_error(ctx, ARB_INVALID_ARG, "spmm(df): too many columns for reduction");
-  const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32;
+  int64_t ld_max = a.ldy;
+  if (a.X) ld_max = std::max(ld_max, a.ldx);
+  if (a.Z) ld_max = std::max(ld_max, a.ldz);
+  if (a.out) ld_max = std::max(ld_max, a.ldo);
+  const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32 && A->n * ld_max < (int64_t(1) << 31);
   void (*kern)(DfParams) = short_rows ? (want_red ? spmm_df_kernel<true, true> : spmm_df_kernel<false, true>)
                                       : (want_red ? spmm_df_kernel<true, false> : spmm_df_kernel<false, false>);
   ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));

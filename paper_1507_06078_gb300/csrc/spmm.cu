@@ -10,6 +10,7 @@
 // coalesced 256/512-byte transaction.  Column indices and values of a row are loaded
 // once per 32 nonzeros (one per lane) and broadcast with shuffles.
 #include <algorithm>
+#include <type_traits>
 
 #include "arb_internal.h"
 
@@ -263,9 +264,21 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
             if (act && t0 + t < cnt) VecIO<T, VEC>::ld(P.Yin + off(jj[t], P.ldy) + c, y[t]);
 #pragma unroll
           for (int t = 0; t < UNR; ++t)
-            if (act && t0 + t < cnt)
+            if (act && t0 + t < cnt) {
+              if constexpr (std::is_same<T, float>::value && VEC % 2 == 0) {
+                // packed FP32 (two lanes of one FFMA2 instruction): half the issue slots
+                const float2 v2 = make_float2(vv[t], vv[t]);
 #pragma unroll
-              for (int u = 0; u < VEC; ++u) acc[u] = fma(vv[t], y[t][u], acc[u]);
+                for (int u = 0; u < VEC; u += 2) {
+                  const float2 r = __ffma2_rn(v2, make_float2(y[t][u], y[t][u + 1]), make_float2(acc[u], acc[u + 1]));
+                  acc[u] = r.x;
+                  acc[u + 1] = r.y;
+                }
+              } else {
+#pragma unroll
+                for (int u = 0; u < VEC; ++u) acc[u] = fma(vv[t], y[t][u], acc[u]);
+              }
+            }
         }
       }
       if (!act) continue;
@@ -276,15 +289,30 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
 #pragma unroll
         for (int u = 0; u < VEC; ++u) yi[u] = T(0);
       }
+      if constexpr (std::is_same<T, float>::value && VEC % 2 == 0) {
+        // the same operations, two columns per packed instruction
+        const float2 al2 = make_float2(P.alpha, P.alpha), be2 = make_float2(P.beta, P.beta);
 #pragma unroll
-      for (int u = 0; u < VEC; ++u) o[u] = csy[u] * fma(P.alpha, acc[u], P.beta * yi[u]);
-      if (P.X) {
+        for (int u = 0; u < VEC; u += 2) {
+          float2 r = __fmul2_rn(be2, make_float2(yi[u], yi[u + 1]));
+          r = __ffma2_rn(al2, make_float2(acc[u], acc[u + 1]), r);
+          r = __fmul2_rn(make_float2(csy[u], csy[u + 1]), r);
+          if (P.X) r = __ffma2_rn(make_float2(csx[u], csx[u + 1]), make_float2(xv[u], xv[u + 1]), r);
+          if (P.Z) r = __ffma2_rn(make_float2(csz[u], csz[u + 1]), make_float2(zv[u], zv[u + 1]), r);
+          o[u] = r.x;
+          o[u + 1] = r.y;
+        }
+      } else {
 #pragma unroll
-        for (int u = 0; u < VEC; ++u) o[u] = fma(csx[u], xv[u], o[u]);
-      }
-      if (P.Z) {
+        for (int u = 0; u < VEC; ++u) o[u] = csy[u] * fma(P.alpha, acc[u], P.beta * yi[u]);
+        if (P.X) {
 #pragma unroll
-        for (int u = 0; u < VEC; ++u) o[u] = fma(csz[u], zv[u], o[u]);
+          for (int u = 0; u < VEC; ++u) o[u] = fma(csx[u], xv[u], o[u]);
+        }
+        if (P.Z) {
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) o[u] = fma(csz[u], zv[u], o[u]);
+        }
       }
       if (P.out) VecIO<T, VEC>::sts(P.out + off(row, P.ldo) + c, o);
       if constexpr (RED) {
