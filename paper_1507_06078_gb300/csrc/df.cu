@@ -138,6 +138,9 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
   const int c = chunk * CH + lane * 2;
   const bool act = (r_first < rstride) && (c < ncols);
   const bool act1 = act && (c + 1 < ncols);  // odd ncols: the pad column is carried, not reduced
+  // lanes past the last column load columns 0-1 of the same rows (always in bounds) and
+  // discard the result, so the gathers need no per-lane predicate
+  const int cl = act ? c : 0;
   // out = ka (A Yin) + kb Yin + kx X + kz Z with ka = sy alpha, kb = sy beta, kx = sx, kz = sz
   dfp ka, kb, kx, kz;
   {
@@ -213,9 +216,9 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
       }
       // the row's own streams first, so their latency overlaps the gathers
       dfp xv = zero, zv = zero, yi = zero;
-      if (P.X && act) xv = ldps(P.X + off(row, P.ldx) + c);
-      if (P.Z && act) zv = ldps(P.Z + off(row, P.ldz) + c);
-      if (need_yi && act) yi = ldp(P.Yin + off(row, P.ldy) + c);
+      if (P.X) xv = ldps(P.X + off(row, P.ldx) + cl);
+      if (P.Z) zv = ldps(P.Z + off(row, P.ldz) + cl);
+      if (need_yi) yi = ldp(P.Yin + off(row, P.ldy) + cl);
       float2 S = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
       for (int base = beg; base < end; base += 32) {
         int jc = 0;
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
             al = v.y;
           }
         }
-        const int cnt = min(32, end - base);
+        const int cnt = __shfl_sync(0xffffffffu, min(32, end - base), 0);  // warp-uniform
         for (int t0 = 0; t0 < cnt; t0 += DF_BATCH) {
           int jj[DF_BATCH];
           float aah[DF_BATCH], aal[DF_BATCH];
@@ -247,10 +250,10 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
           dfp y[DF_BATCH];
 #pragma unroll
           for (int t = 0; t < DF_BATCH; ++t)
-            if (act && t0 + t < cnt) y[t] = ldp(P.Yin + off(jj[t], P.ldy) + c);
+            if (t0 + t < cnt) y[t] = ldp(P.Yin + off(jj[t], P.ldy) + cl);
 #pragma unroll
           for (int t = 0; t < DF_BATCH; ++t)
-            if (act && t0 + t < cnt)
+            if (t0 + t < cnt)
               dot2p(S, E, dfp{make_float2(aah[t], aah[t]), make_float2(aal[t], aal[t])}, y[t]);
         }
       }

@@ -172,6 +172,9 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
   const int64_t r_first = gw / nch;
   const int c = chunk * CH + lane * VEC;
   const bool act = (r_first < rstride) && (c < ncols);
+  // lanes past the last column load column 0 of the same rows (always in bounds) and
+  // discard the result, so the gathers need no per-lane predicate
+  const int cl = act ? c : 0;
   T csy[VEC], csx[VEC], csz[VEC];
 #pragma unroll
   for (int u = 0; u < VEC; ++u) {
@@ -231,8 +234,8 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
         else return r * ld;
       };
       T xv[VEC], zv[VEC];
-      if (P.X && act) VecIO<T, VEC>::lds(P.X + off(row, P.ldx) + c, xv);
-      if (P.Z && act) VecIO<T, VEC>::lds(P.Z + off(row, P.ldz) + c, zv);
+      if (P.X) VecIO<T, VEC>::lds(P.X + off(row, P.ldx) + cl, xv);
+      if (P.Z) VecIO<T, VEC>::lds(P.Z + off(row, P.ldz) + cl, zv);
       T acc[VEC];
 #pragma unroll
       for (int u = 0; u < VEC; ++u) acc[u] = T(0);
@@ -249,7 +252,7 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
             av = __ldg(P.val + e);
           }
         }
-        const int cnt = min(32, end - base);
+        const int cnt = __shfl_sync(0xffffffffu, min(32, end - base), 0);  // warp-uniform
         for (int t0 = 0; t0 < cnt; t0 += UNR) {
           int jj[UNR];
           T vv[UNR];
@@ -261,10 +264,10 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
           T y[UNR][VEC];
 #pragma unroll
           for (int t = 0; t < UNR; ++t)
-            if (act && t0 + t < cnt) VecIO<T, VEC>::ld(P.Yin + off(jj[t], P.ldy) + c, y[t]);
+            if (t0 + t < cnt) VecIO<T, VEC>::ld(P.Yin + off(jj[t], P.ldy) + cl, y[t]);
 #pragma unroll
           for (int t = 0; t < UNR; ++t)
-            if (act && t0 + t < cnt) {
+            if (t0 + t < cnt) {
               if constexpr (std::is_same<T, float>::value && VEC % 2 == 0) {
                 // packed FP32 (two lanes of one FFMA2 instruction): half the issue slots
                 const float2 v2 = make_float2(vv[t], vv[t]);
