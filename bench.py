@@ -3,8 +3,10 @@
 Workload (default): 3D 7-point Dirichlet Laplacian on a 128^3 grid (n = 2,097,152,
 nnz = 14,581,760), k = 200 smallest eigenpairs (largest of 12 I - A), block p = 240,
 Chebyshev-interpolant degree d = 20, q = 2 augmentation blocks, relative residual 1e-8.
-Default precision: the mixed path (FP32 filter and FP32 block-Krylov Rayleigh-Ritz, then
-an FP64 refinement phase to the same tolerance); --precision fp64 runs the plain FP64 path.
+Default precision: mixed_df (FP32 filter and FP32 block-Krylov Rayleigh-Ritz, then a
+refinement phase to the same tolerance whose filter runs in double-float arithmetic and
+whose Rayleigh-Ritz runs in FP64); --precision mixed refines with an FP64 filter,
+--precision fp64 runs the plain FP64 path.
 One step = one whole solve (every step of the hot path) with A and the Gaussian start block
 already resident in HBM.
 
@@ -45,7 +47,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=128, help="3D grid side (128 = the benchmark workload)")
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df", "fp64"])
+    ap.add_argument("--precision", default="mixed_df", choices=["mixed", "mixed_df", "fp64"])
     ap.add_argument("--b-update", default="every_arr", choices=["continuation", "every_arr"],
                     help="when b = mu_{k+q} is refreshed: at continuation steps (Algorithm 8) or after "
                          "every ARR (Section 5)")
@@ -58,6 +60,8 @@ def parse():
     ap.add_argument("--degree", type=int, default=0)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tol-switch", type=float, default=0.0,
+                    help="mixed paths: residual at which the FP32 phase hands over (0: library default)")
     return ap.parse_args()
 
 
@@ -229,6 +233,7 @@ def run_ours(args):
     opts.p, opts.q, opts.degree = W.p, W.q, W.degree
     opts.precision = {"mixed": arb.ARB_MIXED, "mixed_df": arb.ARB_MIXED_DF, "fp64": arb.ARB_FP64}[args.precision]
     opts.b_update = 1 if args.b_update == "every_arr" else 0
+    opts.tol_switch = args.tol_switch
 
     def step():
         return arb.arb_solve(ctx, mat, W.k, arb.ARB_SMALLEST, W.tol, opts, x0=X0, evecs="device")

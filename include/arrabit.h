@@ -112,6 +112,16 @@ typedef struct {
  * context's device work runs on; NULL means the legacy default stream. */
 arb_status arb_ctx_create(arb_ctx* out, int device, void* cuda_stream);
 arb_status arb_ctx_destroy(arb_ctx ctx);
+
+/* Dense arithmetic of a context: with enable != 0, its FP64 Gram products and tall-skinny
+ * products (arb_gram, arb_orth, arb_rcond_gram, arb_rayleigh_ritz, arb_arr and the same
+ * steps inside arb_solve) take FP64 operands, split them into hi + lo FP32 pairs and
+ * multiply-add in double-float arithmetic on the FP32 pipe (compensated Dot2 sums, about
+ * 2^-44 relative per term), returning FP64.  Off by default (plain FP64).  ARB_MIXED_DF
+ * solves switch it on for their refinement phase and restore the setting afterwards.  The
+ * paper computes in FP64 throughout; this mode is the library's.  Errors:
+ * ARB_INVALID_ARG for a NULL context. */
+arb_status arb_ctx_set_dense_df(arb_ctx ctx, int enable);
 /* Description of the last error seen by this context (static storage, never NULL). */
 const char* arb_last_error(arb_ctx ctx);
 const char* arb_status_string(arb_status s);

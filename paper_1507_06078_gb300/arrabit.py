@@ -67,6 +67,7 @@ class arb_info(C.Structure):
 _lib = None
 _vp, _i32, _i64, _dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
 _PROTOS = {
+    "arb_ctx_set_dense_df": (_i32, [_vp, C.c_int]),
     "arb_ctx_create": (_i32, [C.POINTER(_vp), C.c_int, _vp]),
     "arb_ctx_destroy": (_i32, [_vp]),
     "arb_last_error": (C.c_char_p, [_vp]),
@@ -171,6 +172,10 @@ class Context:
 
     def launches(self) -> int:
         return int(load().arb_kernel_launches(self.handle))
+
+    def set_dense_df(self, enable: bool):
+        """FP64 Gram / tall-skinny products of this context in double-float arithmetic."""
+        _check(self, load().arb_ctx_set_dense_df(self.handle, 1 if enable else 0), "arb_ctx_set_dense_df")
 
     def __del__(self):
         try:

@@ -152,6 +152,12 @@ extern "C" arb_status arb_ctx_create(arb_ctx* out, int device, void* cuda_stream
   return ARB_OK;
 }
 
+extern "C" arb_status arb_ctx_set_dense_df(arb_ctx ctx, int enable) {
+  if (!ctx) return ARB_INVALID_ARG;
+  ctx->dense_df = enable != 0;
+  return ARB_OK;
+}
+
 extern "C" arb_status arb_ctx_destroy(arb_ctx ctx) {
   if (!ctx) return ARB_INVALID_ARG;
   cudaSetDevice(ctx->device);
@@ -508,6 +514,10 @@ struct SolveState {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool trace = false;  // ARB_TRACE set in the environment: one line per outer iteration on stderr
   bool df_filter = false;  // FP64 phase filters in double-float arithmetic (ARB_MIXED_DF)
+  // mixed paths: an idle FP32 n x ld32 block the FP64 phase uses for FP32 Gram products of
+  // its inner stop rule (rcond thresholds >= 1e-6 are far above what FP32 Grams resolve)
+  float* x32 = nullptr;
+  int64_t ld32 = 0;
 };
 
 template <typename T>
@@ -596,7 +606,15 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
       }
       if (S.o.inner_fixed > 0) break;
       const double rcp = rc;
-      ARB_TRY(rcond_gram<T>(ctx, n, B.X, B.ld, S.w, S.xs, &rc));
+      bool done_rc = false;
+      if constexpr (std::is_same<T, double>::value) {
+        if (S.x32 && rc_thr >= 1e-6) {
+          ARB_TRY((copy_block<double, float>(ctx, n, B.X, B.ld, S.w, S.x32, S.ld32)));
+          ARB_TRY(rcond_gram<float>(ctx, n, S.x32, S.ld32, S.w, S.xs, &rc));
+          done_rc = true;
+        }
+      }
+      if (!done_rc) ARB_TRY(rcond_gram<T>(ctx, n, B.X, B.ld, S.w, S.xs, &rc));
       if (rc <= rc_thr || rc / rcp > 0.99) break;  // eq. inn-stop
     }
     ARB_CUDA(ctx, cudaEventRecord(S.ev1, ctx->stream));
@@ -811,28 +829,39 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     ARB_TRY(gaussian_fill(ctx, n, p, o.seed, D.X, D.ld));
   }
 
-  // b: smallest Ritz value of orth(X0) (Section 5, "Estimation of lambda_n and lambda_{k+q}")
-  {
+  // b: smallest Ritz value of orth(X0) (Section 5, "Estimation of lambda_n and lambda_{k+q}");
+  // an estimate, so the mixed paths take it from FP32 blocks
+  auto initial_b = [&](auto& Bk) -> arb_status {
+    using E = typename std::remove_reference<decltype(*Bk.X)>::type;
     int32_t r = 0;
-    ARB_TRY(orth<double>(ctx, n, D.X, D.ld, p, D.wk.U, D.ldm, D.wk.T1, D.ld, &r));
+    ARB_TRY(orth<E>(ctx, n, Bk.X, Bk.ld, p, Bk.wk.U, Bk.ldm, Bk.wk.T1, Bk.ld, &r));
     if (r == 0) return set_error(ctx, ARB_BREAKDOWN, "solve: start block has no numerical rank");
-    SpmmArgs<double> sa;
+    SpmmArgs<E> sa;
     sa.A = mat;
     sa.ncols = r;
-    sa.Yin = D.wk.U;
-    sa.ldy = D.ldm;
+    sa.Yin = Bk.wk.U;
+    sa.ldy = Bk.ldm;
     sa.alpha = S.op_scale;
     sa.beta = S.op_shift;
-    sa.out = D.wk.AU;
-    sa.ldo = D.ldm;
-    ARB_TRY(spmm_fused<double>(ctx, sa));
+    sa.out = Bk.wk.AU;
+    sa.ldo = Bk.ldm;
+    ARB_TRY(spmm_fused<E>(ctx, sa));
     double* H;
     ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(r) * r, &H));
-    ARB_TRY(gram<double>(ctx, n, D.wk.U, D.ldm, r, D.wk.AU, D.ldm, r, H, r));
+    ARB_TRY(gram<E>(ctx, n, Bk.wk.U, Bk.ldm, r, Bk.wk.AU, Bk.ldm, r, H, r));
     ARB_TRY(symmetrize(ctx, r, H, r));
     ARB_TRY(syevj(ctx, r, H, r, S.theta, S.V, r, nullptr));
     ARB_TRY(d2h_sync(ctx, &S.b, S.theta + (r - 1), sizeof(double)));
     S.info.spmm_cols += r;
+    return ARB_OK;
+  };
+  if (mixed) {
+    ARB_TRY((copy_block<double, float>(ctx, n, D.X, D.ld, p, F.X, F.ld)));
+    ARB_TRY(initial_b(F));
+    S.x32 = F.wk.T2;
+    S.ld32 = F.ld;
+  } else {
+    ARB_TRY(initial_b(D));
   }
   S.info.a = S.a;
   S.info.b0 = S.b;
@@ -868,7 +897,6 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     const double tol_phase = std::max(sw, tol);
     const double tol_t64 = S.tol_t;  // the FP64 phase starts the paper's continuation at tol_1
     S.tol_t = std::max(S.tol_t, tol_phase);
-    ARB_TRY((copy_block<double, float>(ctx, n, D.X, D.ld, p, F.X, F.ld)));
     ARB_TRY(run_outer<float>(ctx, mat, S, F, tol_phase, 100.0 * 5.96e-8, false, true, true));
     S.info.outer_iters_fp32 = S.info.outer_iters;
     S.tol_t = tol_t64;
@@ -880,6 +908,13 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
       S.w = p;
       S.nl = 0;
       ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
+      // ARB_MIXED_DF: the refinement's dense products in double-float arithmetic too
+      struct DenseGuard {
+        arb_ctx c;
+        bool saved;
+        ~DenseGuard() { c->dense_df = saved; }
+      } dg{ctx, ctx->dense_df};
+      if (S.df_filter) ctx->dense_df = true;
       ARB_TRY(run_outer<double>(ctx, mat, S, D, tol, 0.0, true, false));
     }
   } else {

@@ -84,6 +84,9 @@ struct arb_ctx_s {
   // co-resident CTAs, so that the grids of coop_share contexts running concurrently (the
   // server's slots) always fit on the device together and none waits on another's CTAs.
   int coop_share = 1;
+  // FP64 Gram and tall-skinny products in double-float arithmetic on the FP32 pipe
+  // (arb_ctx_set_dense_df; ARB_MIXED_DF solves set it for their refinement phase)
+  bool dense_df = false;
 };
 
 struct arb_mat_s {

@@ -8,8 +8,10 @@
 // staged in shared memory) so that the pipe, not memory, is the limit.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "arb_internal.h"
+#include "df_arith.cuh"
 
 namespace arb {
 namespace {
@@ -96,7 +98,10 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nsplit, 
   if (idx >= static_cast<int64_t>(na) * nb) return;
   int i = static_cast<int>(idx / nb), j = static_cast<int>(idx % nb);
   int si = i, sj = j;
-  if (symmetric && (j / tile) < (i / tile)) {
+  // symmetric products: every entry below the diagonal takes its mirror's partial sums
+  // (computed: the tiles with tj >= ti hold every i <= j), so C is exactly symmetric even
+  // when the two orders of a product round differently
+  if (symmetric && j < i) {
     si = j;
     sj = i;
   }
@@ -155,6 +160,171 @@ gemm_tall_kernel(int64_t n, const T* __restrict__ In, int64_t ldi, int na, const
       T* o = Out + r * ldo + c;
       const T val = alpha * acc[u][v];
       *o = (beta == T(0)) ? val : fma(beta, *o, val);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- double-float products
+// The FP64 Gram and tall-skinny products of a context in double-float mode: operands are
+// split into (hi, lo) FP32 pairs as they are staged in shared memory (split_f64, integer
+// operations only), products and sums run on the FP32 pipe by Dot2 (dot2p, two outputs per
+// packed instruction), and every 64 terms the compensated pair is folded into a running
+// double-float sum.  Results are written in FP64.  GB300 executes FP64 at about 1/64 of
+// its FP32 rate; these kernels trade ~12 FP32 operations per multiply-add for that.
+constexpr int DF_FOLD = 4;  // k-steps of 16 terms per fold into the running sum
+
+// running double-float sum (Ah, Al) += (S + E), two outputs at once; S = E = 0 after
+__device__ __forceinline__ void df_fold(float2& Ah, float2& Al, float2& S, float2& E) {
+  const dfp t = fast_two_sum2(S, E);
+  const float2 s = __fadd2_rn(Ah, t.hi);
+  const float2 bb = __fadd2_rn(s, neg2(Ah));
+  const float2 err = __fadd2_rn(__fadd2_rn(Ah, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(t.hi, neg2(bb)));
+  const dfp r = fast_two_sum2(s, __fadd2_rn(err, __fadd2_rn(Al, t.lo)));
+  Ah = r.hi;
+  Al = r.lo;
+  S = make_float2(0.f, 0.f);
+  E = make_float2(0.f, 0.f);
+}
+
+// part[s][i][j] = sum over the rows of split s of X[r][i] * Y[r][j] (the tiling of
+// gram_kernel; R >= 2 so that a thread's outputs pair up along j).
+template <int R>
+__global__ void __launch_bounds__(256)
+gram_df_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int na, const double* __restrict__ Y,
+               int64_t ldy, int nb, int64_t rows_per_split, int symmetric, double* __restrict__ part) {
+  constexpr int TT = 16 * R, H = R / 2;
+  const int ti = blockIdx.x, tj = blockIdx.y, s = blockIdx.z;
+  if (symmetric && tj < ti) return;
+  __shared__ float Xh[KSTEP][TT + 1], Xl[KSTEP][TT + 1], Yh[KSTEP][TT + 1], Yl[KSTEP][TT + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = ti * TT, j0 = tj * TT;
+  const int64_t r0 = s * rows_per_split;
+  const int64_t r1 = min(n, r0 + rows_per_split);
+  float2 S[R][H], E[R][H], Ah[R][H], Al[R][H];
+#pragma unroll
+  for (int u = 0; u < R; ++u)
+#pragma unroll
+    for (int v = 0; v < H; ++v) S[u][v] = E[u][v] = Ah[u][v] = Al[u][v] = make_float2(0.f, 0.f);
+  int steps = 0;
+  for (int64_t rb = r0; rb < r1; rb += KSTEP) {
+    for (int t = threadIdx.x; t < KSTEP * TT; t += 256) {
+      const int rr = t / TT, cc = t % TT;
+      const int64_t r = rb + rr;
+      const bool rok = r < r1;
+      split_f64((rok && i0 + cc < na) ? X[r * ldx + i0 + cc] : 0.0, Xh[rr][cc], Xl[rr][cc]);
+      split_f64((rok && j0 + cc < nb) ? Y[r * ldy + j0 + cc] : 0.0, Yh[rr][cc], Yl[rr][cc]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < KSTEP; ++k) {
+      dfp b[H];
+#pragma unroll
+      for (int v = 0; v < H; ++v)
+        b[v] = dfp{make_float2(Yh[k][tx + 32 * v], Yh[k][tx + 32 * v + 16]),
+                   make_float2(Yl[k][tx + 32 * v], Yl[k][tx + 32 * v + 16])};
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const float ah = Xh[k][ty + 16 * u], al = Xl[k][ty + 16 * u];
+        const dfp a{make_float2(ah, ah), make_float2(al, al)};
+#pragma unroll
+        for (int v = 0; v < H; ++v) dot2p(S[u][v], E[u][v], a, b[v]);
+      }
+    }
+    __syncthreads();
+    if (++steps == DF_FOLD) {
+      steps = 0;
+#pragma unroll
+      for (int u = 0; u < R; ++u)
+#pragma unroll
+        for (int v = 0; v < H; ++v) df_fold(Ah[u][v], Al[u][v], S[u][v], E[u][v]);
+    }
+  }
+  double* P = part + static_cast<size_t>(s) * na * nb;
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int i = i0 + ty + 16 * u;
+    if (i >= na) continue;
+#pragma unroll
+    for (int v = 0; v < H; ++v) {
+      df_fold(Ah[u][v], Al[u][v], S[u][v], E[u][v]);
+      const int j = j0 + tx + 32 * v;
+      if (j < nb) P[static_cast<size_t>(i) * nb + j] = static_cast<double>(Ah[u][v].x) + static_cast<double>(Al[u][v].x);
+      if (j + 16 < nb)
+        P[static_cast<size_t>(i) * nb + j + 16] = static_cast<double>(Ah[u][v].y) + static_cast<double>(Al[u][v].y);
+    }
+  }
+}
+
+// Out[r][c] = alpha * sum_k In[r][k] W[k][c] + beta * Out[r][c] (the tiling of
+// gemm_tall_kernel, RN >= 2); the sum in double-float, the final update in FP64.
+template <int RN>
+__global__ void __launch_bounds__(256)
+gemm_df_kernel(int64_t n, const double* __restrict__ In, int64_t ldi, int na, const double* __restrict__ W,
+               int64_t ldw, int nb, double alpha, double beta, double* __restrict__ Out, int64_t ldo) {
+  constexpr int TR = 64, TC = 16 * RN, H = RN / 2;
+  __shared__ float Ih[KSTEP][TR + 1], Il[KSTEP][TR + 1], Wh[KSTEP][TC + 1], Wl[KSTEP][TC + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TR;
+  const int c0 = blockIdx.y * TC;
+  float2 S[4][H], E[4][H], Ah[4][H], Al[4][H];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < H; ++v) S[u][v] = E[u][v] = Ah[u][v] = Al[u][v] = make_float2(0.f, 0.f);
+  int steps = 0;
+  for (int k0 = 0; k0 < na; k0 += KSTEP) {
+    for (int t = threadIdx.x; t < KSTEP * TR; t += 256) {
+      const int kk = t % KSTEP, rr = t / KSTEP;
+      const int64_t r = r0 + rr;
+      split_f64((r < n && k0 + kk < na) ? In[r * ldi + k0 + kk] : 0.0, Ih[kk][rr], Il[kk][rr]);
+    }
+    for (int t = threadIdx.x; t < KSTEP * TC; t += 256) {
+      const int kw = t / TC, cw = t % TC;
+      split_f64((k0 + kw < na && c0 + cw < nb) ? W[static_cast<int64_t>(k0 + kw) * ldw + c0 + cw] : 0.0, Wh[kw][cw],
+                Wl[kw][cw]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < KSTEP; ++k) {
+      dfp b[H];
+#pragma unroll
+      for (int v = 0; v < H; ++v)
+        b[v] = dfp{make_float2(Wh[k][tx + 32 * v], Wh[k][tx + 32 * v + 16]),
+                   make_float2(Wl[k][tx + 32 * v], Wl[k][tx + 32 * v + 16])};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float ah = Ih[k][ty + 16 * u], al = Il[k][ty + 16 * u];
+        const dfp a{make_float2(ah, ah), make_float2(al, al)};
+#pragma unroll
+        for (int v = 0; v < H; ++v) dot2p(S[u][v], E[u][v], a, b[v]);
+      }
+    }
+    __syncthreads();
+    if (++steps == DF_FOLD) {
+      steps = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < H; ++v) df_fold(Ah[u][v], Al[u][v], S[u][v], E[u][v]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t r = r0 + ty + 16 * u;
+    if (r >= n) continue;
+#pragma unroll
+    for (int v = 0; v < H; ++v) {
+      df_fold(Ah[u][v], Al[u][v], S[u][v], E[u][v]);
+      const double val[2] = {static_cast<double>(Ah[u][v].x) + static_cast<double>(Al[u][v].x),
+                             static_cast<double>(Ah[u][v].y) + static_cast<double>(Al[u][v].y)};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = c0 + tx + 32 * v + 16 * h;
+        if (c >= nb) continue;
+        double* o = Out + r * ldo + c;
+        const double x = alpha * val[h];
+        *o = (beta == 0.0) ? x : fma(beta, *o, x);
+      }
     }
   }
 }
@@ -438,6 +608,7 @@ static GramPlan gram_plan(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32
   g.symmetric = (X == Y && ldx == ldy && na == nb) ? 1 : 0;
   const int mx = std::max(na, nb);
   g.R = mx <= 16 ? 1 : (mx <= 32 ? 2 : 4);
+  if (std::is_same<T, double>::value && ctx->dense_df) g.R = std::max(g.R, 2);  // outputs in pairs
   g.TT = 16 * g.R;
   g.gi = (na + g.TT - 1) / g.TT;
   g.gj = (nb + g.TT - 1) / g.TT;
@@ -462,6 +633,19 @@ template <typename T>
 static arb_status gram_launch(arb_ctx ctx, const GramPlan& g, int64_t n, const T* X, int64_t ldx, int32_t na,
                               const T* Y, int64_t ldy, int32_t nb, double* part, double* C, int64_t ldc) {
   dim3 grid(g.gi, g.gj, static_cast<unsigned>(g.nsplit));
+  if constexpr (std::is_same<T, double>::value) {
+    if (ctx->dense_df) {
+      if (g.R == 2)
+        gram_df_kernel<2><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, g.rows, g.symmetric, part);
+      else
+        gram_df_kernel<4><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, g.rows, g.symmetric, part);
+      ARB_LAUNCHED(ctx);
+      gram_reduce_kernel<<<blocks_for(static_cast<int64_t>(na) * nb, 256), 256, 0, ctx->stream>>>(
+          part, static_cast<int>(g.nsplit), na, nb, g.symmetric, g.TT, C, ldc);
+      ARB_LAUNCHED(ctx);
+      return ARB_OK;
+    }
+  }
   if (g.R == 1)
     gram_kernel<T, 1><<<grid, 256, 0, ctx->stream>>>(n, X, ldx, na, Y, ldy, nb, g.rows, g.symmetric, part);
   else if (g.R == 2)
@@ -501,6 +685,19 @@ arb_status gemm_tall(arb_ctx ctx, int64_t n, const T* In, int64_t ldi, int32_t n
   if (na <= 0) {
     if (beta == 1.0) return ARB_OK;
     return set_error(ctx, ARB_INVALID_ARG, "gemm_tall: empty inner dimension with beta != 1");
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    if (ctx->dense_df) {
+      const int RN = nb <= 32 ? 2 : 4;
+      const int TC = 16 * RN;
+      dim3 grid(static_cast<unsigned>((n + 63) / 64), static_cast<unsigned>((nb + TC - 1) / TC));
+      if (RN == 2)
+        gemm_df_kernel<2><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
+      else
+        gemm_df_kernel<4><<<grid, 256, 0, ctx->stream>>>(n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
+      ARB_LAUNCHED(ctx);
+      return ARB_OK;
+    }
   }
   const int RN = nb <= 16 ? 1 : (nb <= 32 ? 2 : 4);
   const int TC = 16 * RN;

@@ -17,32 +17,13 @@
 #include <algorithm>
 
 #include "arb_internal.h"
+#include "df_arith.cuh"
 
 namespace arb {
 namespace {
 
 constexpr int DF_THREADS = 256;
 constexpr int DF_WARPS = DF_THREADS / 32;
-
-__device__ __forceinline__ df2 df_from(double x) {
-  const float h = __double2float_rn(x);
-  return df2{h, __double2float_rn(x - static_cast<double>(h))};
-}
-// The transforms below are exact only as written: __fadd_rn / __fsub_rn / __fmul_rn are
-// never contracted into an FMA, so the compiler cannot fuse a product into a later sum.
-// s + e = a + b exactly when |a| >= |b|
-__device__ __forceinline__ df2 fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return df2{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-// p + e = a.hi * b.hi exactly (e from one FMA), then the cross terms a.hi b.lo + a.lo b.hi
-__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
-}
 
 struct DfParams {
   int64_t n;
@@ -66,10 +47,7 @@ struct DfParams {
   int dot_with_yin;
 };
 
-// two double-float values (a lane's two columns): hi parts and lo parts as pairs
-struct dfp {
-  float2 hi, lo;
-};
+// one 16-byte load of a column pair of a paired planar block
 __device__ __forceinline__ dfp ldp(const df2* p) {
   const float4 t = *reinterpret_cast<const float4*>(p);
   return dfp{make_float2(t.x, t.y), make_float2(t.z, t.w)};
@@ -77,29 +55,6 @@ __device__ __forceinline__ dfp ldp(const df2* p) {
 __device__ __forceinline__ dfp ldps(const df2* p) {
   const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
   return dfp{make_float2(t.x, t.y), make_float2(t.z, t.w)};
-}
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ dfp dfp_of(df2 a, df2 b) { return dfp{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
-__device__ __forceinline__ dfp fast_two_sum2(float2 a, float2 b) {
-  const float2 s = __fadd2_rn(a, b);
-  return dfp{s, __fadd2_rn(b, neg2(__fadd2_rn(s, neg2(a))))};
-}
-
-// Compensated accumulation (Ogita, Rump & Oishi's Dot2) of c * v into (S, E), for both
-// columns at once: S collects the rounded sums of the leading products, E the exact
-// rounding errors of those sums (Knuth's two-sum) and of the products (one FMA each) plus
-// the cross terms, so S + E carries the dot product as if computed with twice the working
-// precision.  12 packed instructions per term for two columns.
-__device__ __forceinline__ void dot2p(float2& S, float2& E, const dfp& c, const dfp& v) {
-  const float2 p = __fmul2_rn(c.hi, v.hi);
-  float2 e = __ffma2_rn(c.hi, v.hi, neg2(p));
-  e = __ffma2_rn(c.hi, v.lo, e);
-  e = __ffma2_rn(c.lo, v.hi, e);
-  const float2 s = __fadd2_rn(S, p);
-  const float2 bb = __fadd2_rn(s, neg2(S));
-  const float2 t = __fadd2_rn(__fadd2_rn(S, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
-  S = s;
-  E = __fadd2_rn(E, __fadd2_rn(t, e));
 }
 
 // Tuning defaults (measured on the 128^3 x 240 filter): gathers in flight per lane and the

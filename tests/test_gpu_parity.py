@@ -273,6 +273,83 @@ def test_arr_matches_oracle(arb, ctx, q):
     np.testing.assert_allclose(res, reso, atol=1e-9)
 
 
+# ------------------------------------------------------------------ double-float dense products
+@pytest.fixture(scope="module")
+def ctx_df(arb):
+    c = arb.Context(0)
+    c.set_dense_df(True)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,na,nb", [(1, 1, 1), (17, 3, 5), (1000, 30, 30), (4099, 65, 130), (20000, 64, 64),
+                                     (100003, 240, 240)])
+def test_gram_df_matches_numpy(arb, ctx_df, n, na, nb):
+    # operands split into hi + lo FP32 (2^-48 relative), Dot2 sums folded every 64 terms
+    # into a double-float running sum: the FP64 kernel's per-entry bound holds
+    X = I.gaussian_block(n, na, 1)
+    Y = I.gaussian_block(n, nb, 2)
+    C = host(arb.arb_gram(ctx_df, dev(X), dev(Y)))
+    bound = 1e-13 * np.outer(np.linalg.norm(X, axis=0), np.linalg.norm(Y, axis=0))
+    assert np.all(np.abs(C - X.T @ Y) <= bound)
+    Xd = dev(X)
+    G = host(arb.arb_gram(ctx_df, Xd, Xd))  # one operand: the symmetric path, exactly symmetric
+    bx = 1e-13 * np.outer(np.linalg.norm(X, axis=0), np.linalg.norm(X, axis=0))
+    assert np.all(np.abs(G - X.T @ X) <= bx)
+    assert np.array_equal(G, G.T)
+
+
+def test_gram_df_extreme_magnitudes(arb, ctx_df):
+    # columns scaled over 1e-15 .. 1e15 (within the double-float split's range): relative
+    # accuracy per entry is unchanged
+    X = I.gaussian_block(5000, 8, 7) * np.logspace(-15, 15, 8)[None, :]
+    G = host(arb.arb_gram(ctx_df, dev(X), dev(X)))
+    nrm = np.linalg.norm(X, axis=0)
+    assert np.all(np.abs(G - X.T @ X) <= 1e-13 * np.outer(nrm, nrm))
+
+
+def test_orth_rr_arr_in_double_float_mode(arb, ctx_df):
+    rng = np.random.default_rng(4)
+    Z = rng.standard_normal((5000, 20))
+    Z[:, 15:] = Z[:, :5] @ rng.standard_normal((5, 5))  # rank 15
+    U = host(arb.arb_orth(ctx_df, dev(Z)))
+    assert U.shape[1] == 15
+    np.testing.assert_allclose(U.T @ U, np.eye(15), atol=1e-12)
+    Uo = O.orth(Z)
+    np.testing.assert_allclose(U @ (U.T @ Uo), Uo, atol=1e-11)
+    A = I.laplacian_2d(32)
+    mat = arb.Matrix.from_csr(ctx_df, A)
+    B = 8.0 * sp.identity(A.n, format="csr") - scipy_of(A)
+    Z = I.gaussian_block(A.n, 24, 3)
+    Y, w = arb.arb_rayleigh_ritz(ctx_df, mat, -1.0, 8.0, dev(Z))
+    Yo, wo = O.rayleigh_ritz(B, Z)
+    np.testing.assert_allclose(host(w), wo, atol=1e-12 * 8)
+    np.testing.assert_allclose(host(Y).T @ host(Y), np.eye(24), atol=1e-12)
+    X = I.gaussian_block(A.n, 16, 8)
+    coef = O.interpolant_cheb_coeffs(6)
+    for _ in range(3):
+        X = O.normalize_columns(O.poly_clenshaw(B, X, 0.0, 4.0, coef))
+    Y, w, rank = arb.arb_arr(ctx_df, mat, -1.0, 8.0, dev(X), 2)
+    Yo, wo = O.arr(B, X, 2)
+    assert rank == 48
+    np.testing.assert_allclose(host(w), wo, atol=1e-11 * 8)
+    np.testing.assert_allclose(O.residual_norms(B, host(Y), host(w), host(w)), O.residual_norms(B, Yo, wo, wo),
+                               atol=1e-9)
+
+
+def test_solve_fp64_with_double_float_dense_products(arb, ctx_df):
+    # the whole FP64 method with every Gram / tall-skinny product in double-float
+    W = I.workload_2d64()
+    X0 = I.gaussian_block(W.A.n, W.p, W.seed)
+    r = _solve(arb, ctx_df, W.A, W.k, W.p, W.q, W.degree, W.tol, X0)
+    assert r.status == arb.ARB_OK, r.info
+    lam = np.array(json_golden()["evals"])
+    assert np.max(np.abs(r.evals - lam) / np.maximum(1.0, np.abs(lam))) <= 1e-10
+    Q = r.evecs
+    np.testing.assert_allclose(Q.T @ Q, np.eye(W.k), atol=1e-12)
+    assert np.linalg.norm(scipy_of(W.A) @ Q - Q * r.evals[None, :], axis=0).max() <= W.tol * 8.0
+
+
 # ------------------------------------------------------------------ whole method
 def _solve(arb, ctx, A, k, p, q, d, tol, X0, which=1, **kw):
     mat = arb.Matrix.from_csr(ctx, A)
