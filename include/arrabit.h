@@ -244,6 +244,16 @@ arb_status arb_spmm(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift,
 arb_status arb_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
                     const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
 
+/* C = X^T Y for FP32 blocks X (n x na), Y (n x nb), result FP64 (the mixed path's FP32
+ * Gram products).  Runs on the tensor cores when both blocks have leading dimensions that
+ * are multiples of 4 and 16-byte aligned bases: every product as hi*hi + hi*lo + lo*hi of
+ * TF32 parts (tcgen05.mma kind::tf32), FP32 sums over runs of 256 rows added in
+ * double-float, about 1e-8 relative to ||x_i|| ||y_j|| per entry; otherwise on CUDA cores
+ * (FP32 over 64-row runs, FP64 across runs).  Deterministic.  Errors: ARB_INVALID_ARG,
+ * ARB_CUDA_ERROR (also if a tensor-core pipeline wait timed out). */
+arb_status arb_gram_f32(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, int32_t na,
+                        const float* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
+
 /* arb_gram for callers that cannot allocate device memory (for example code running
  * while a stream is captured into a CUDA graph, or applications whose device memory is
  * owned by their own pool): the same product C = X^T Y, but its split-K partial sums live

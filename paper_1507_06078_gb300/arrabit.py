@@ -88,6 +88,7 @@ _PROTOS = {
     "arb_filter_batched": (_i32, [_vp, _i32, _vp]),
     "arb_spmm": (_i32, [_vp, _vp, _dbl, _dbl, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
+    "arb_gram_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
     "arb_server_footprint": (_i64, [_i64, _i64, _i32, _i32, _i32]),
     "arb_server_create": (_i32, [C.c_int, C.c_size_t, _i32, C.POINTER(_vp)]),
@@ -359,6 +360,20 @@ def arb_gram(ctx: Context, X, Y, C_out=None):
     ldc = _dev2d(C_out, "C")
     _check(ctx, load().arb_gram(ctx.handle, X.shape[0], _vp(_ptr(X)), ldx, X.shape[1], _vp(_ptr(Y)), ldy,
                                 Y.shape[1], _vp(_ptr(C_out)), ldc), "arb_gram")
+    return C_out
+
+
+def arb_gram_f32(ctx: Context, X, Y, C_out=None):
+    """C = X^T Y for FP32 CUDA tensors (row-major 2D), FP64 result."""
+    import torch
+    for name, T in (("X", X), ("Y", Y)):
+        if not (T.is_cuda and T.dtype == torch.float32 and T.dim() == 2 and T.stride(1) == 1):
+            raise ValueError(f"{name}: expected a row-major 2D float32 CUDA tensor")
+    if C_out is None:
+        C_out = torch.empty((X.shape[1], Y.shape[1]), dtype=torch.float64, device=X.device)
+    ldc = _dev2d(C_out, "C")
+    _check(ctx, load().arb_gram_f32(ctx.handle, X.shape[0], _vp(_ptr(X)), X.stride(0), X.shape[1], _vp(_ptr(Y)),
+                                    Y.stride(0), Y.shape[1], _vp(_ptr(C_out)), ldc), "arb_gram_f32")
     return C_out
 
 

@@ -383,6 +383,18 @@ extern "C" arb_status arb_gram(arb_ctx ctx, int64_t n, const double* X, int64_t 
   return gram<double>(ctx, n, X, ldx, na, Y, ldy, nb, C, ldc);
 }
 
+extern "C" arb_status arb_gram_f32(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, int32_t na,
+                                   const float* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc) {
+  if (!ctx || n < 0 || na < 0 || nb < 0 || !C || ldc < nb || (n > 0 && (!X || !Y || ldx < na || ldy < nb)))
+    return set_error(ctx, ARB_INVALID_ARG, "gram_f32: bad arguments");
+  ARB_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (n == 0) {
+    for (int32_t i = 0; i < na; ++i) ARB_TRY(fill(ctx, C + static_cast<int64_t>(i) * ldc, nb, 0.0));
+    return ARB_OK;
+  }
+  return gram<float>(ctx, n, X, ldx, na, Y, ldy, nb, C, ldc);
+}
+
 extern "C" arb_status arb_syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
                                 int64_t ldv, int32_t* sweeps) {
   if (!ctx || m < 0 || (m > 0 && (!H || !w || !V || ldh < m || ldv < m)))

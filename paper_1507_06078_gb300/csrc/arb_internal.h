@@ -62,6 +62,7 @@ enum WsSlot : int {
   WS_BATCH_WORK,      // batched filter: per-instance work blocks, tables, descriptors
   WS_BATCH_TABLE,
   WS_BATCH_DESC,
+  WS_TC_ERR,          // tensor-core kernels: error word
   WS_NUM_SLOTS
 };
 
@@ -258,6 +259,17 @@ arb_status select_top(arb_ctx ctx, const double* vlock, int32_t nl, const double
 // i*ncols + j), same numbering as the input generators.
 arb_status gaussian_fill(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, double* X,
                          int64_t ldx);
+
+// ---------------------------------------------------------------- tensor-core Gram (tc.cu)
+// part[s] (na x nb, FP64) = X^T Y over rows [s*rows, (s+1)*rows) of FP32 blocks by
+// split-TF32 tcgen05 products; *err_dev set nonzero if an mbarrier wait gave up.
+bool gram_tc_supported(int64_t n, int64_t ldx, int64_t ldy, const void* X, const void* Y);
+int gram_tc_rows_align();
+int gram_tc_tile_m();
+int gram_tc_tile_n();
+arb_status gram_tc_launch(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, int32_t na, const float* Y,
+                          int64_t ldy, int32_t nb, int symmetric, double* part, int64_t nsplit, int64_t rows,
+                          int* err_dev);
 
 // ---------------------------------------------------------------- batched filter (batched.cu)
 arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs);

@@ -659,10 +659,40 @@ static arb_status gram_launch(arb_ctx ctx, const GramPlan& g, int64_t n, const T
   return ARB_OK;
 }
 
+// FP32 Gram products on the tensor cores (tc.cu): split-K over row ranges that are whole
+// multiples of the kernel's 256-row fold, about two CTAs per SM.
+static arb_status gram_f32_tc(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, int32_t na, const float* Y,
+                              int64_t ldy, int32_t nb, double* C, int64_t ldc) {
+  const int symmetric = (X == Y && ldx == ldy && na == nb) ? 1 : 0;
+  const int tm = gram_tc_tile_m(), tn = gram_tc_tile_n(), al = gram_tc_rows_align();
+  const int64_t tiles = static_cast<int64_t>((na + tm - 1) / tm) * ((nb + tn - 1) / tn);
+  int64_t nsplit = std::max<int64_t>(1, (2 * static_cast<int64_t>(ctx->num_sms) + tiles - 1) / tiles);
+  nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, n / al));
+  int64_t rows = (n + nsplit - 1) / nsplit;
+  rows = ((rows + al - 1) / al) * al;
+  nsplit = (n + rows - 1) / rows;
+  double* part;
+  int* err;
+  ARB_TRY(ws<double>(ctx, WS_GRAM_PART, static_cast<size_t>(nsplit) * na * nb, &part));
+  ARB_TRY(ws<int>(ctx, WS_TC_ERR, 1, &err));
+  ARB_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  ARB_TRY(gram_tc_launch(ctx, n, X, ldx, na, Y, ldy, nb, symmetric, part, nsplit, rows, err));
+  gram_reduce_kernel<<<blocks_for(static_cast<int64_t>(na) * nb, 256), 256, 0, ctx->stream>>>(
+      part, static_cast<int>(nsplit), na, nb, symmetric, 0, C, ldc);
+  ARB_LAUNCHED(ctx);
+  int herr = 0;
+  ARB_TRY(d2h_sync(ctx, &herr, err, sizeof(int)));
+  if (herr) return set_error(ctx, ARB_CUDA_ERROR, "gram (tensor cores): a pipeline wait timed out");
+  return ARB_OK;
+}
+
 template <typename T>
 arb_status gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t na, const T* Y, int64_t ldy,
                 int32_t nb, double* C, int64_t ldc) {
   if (na <= 0 || nb <= 0) return ARB_OK;
+  if constexpr (std::is_same<T, float>::value) {
+    if (gram_tc_supported(n, ldx, ldy, X, Y)) return gram_f32_tc(ctx, n, X, ldx, na, Y, ldy, nb, C, ldc);
+  }
   const GramPlan g = gram_plan<T>(ctx, n, X, ldx, na, Y, ldy, nb, 0);
   double* part;
   ARB_TRY(ws<double>(ctx, WS_GRAM_PART, static_cast<size_t>(g.nsplit) * na * nb, &part));

@@ -188,6 +188,27 @@ def test_gram_matches_numpy(arb, ctx, n, na, nb):
     assert np.array_equal(G, G.T)
 
 
+# leading dimensions that are multiples of 4 take the tensor cores (ragged against the
+# 128 x 64 CTA tile and the 32-row steps); the others the CUDA-core kernel
+@pytest.mark.parametrize("n,na,nb", [(1, 1, 1), (33, 3, 5), (1000, 32, 36), (4099, 68, 132), (20000, 64, 64),
+                                     (100003, 240, 240), (50000, 720, 240), (7, 200, 132), (300, 4, 8)])
+def test_gram_f32_tensor_cores(arb, ctx, n, na, nb):
+    # split-TF32 tcgen05 products carry ~21 significand bits and are summed in FP32 over
+    # 256-row runs, the CUDA-core kernel sums FP32 products over 64-row runs: both within
+    # the FP32 bound of a few u32 * sqrt(run) relative to ||x_i|| ||y_j||
+    X = I.gaussian_block(n, na, 11).astype(np.float32)
+    Y = I.gaussian_block(n, nb, 12).astype(np.float32)
+    Xd, Yd = dev(X).float(), dev(Y).float()
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    C = host(arb.arb_gram_f32(ctx, Xd, Yd))
+    nx, ny = np.linalg.norm(X64, axis=0), np.linalg.norm(Y64, axis=0)
+    err = np.abs(C - X64.T @ Y64) / np.outer(nx, ny)
+    assert err.max() <= 1e-6, err.max()
+    G = host(arb.arb_gram_f32(ctx, Xd, Xd))  # symmetric path
+    assert np.array_equal(G, G.T)
+    assert (np.abs(G - X64.T @ X64) / np.outer(nx, nx)).max() <= 1e-6
+
+
 @pytest.mark.parametrize("m", [1, 2, 3, 10, 31, 64, 65, 96, 97, 200, 256, 720])
 def test_syevj_matches_oracle_jacobi(arb, ctx, m):
     rng = np.random.default_rng(m)
