@@ -6,18 +6,19 @@
 // TF32 number and lo = the remainder x - hi rounded to TF32 (x = hi + lo to 2^-23), and
 // x*y is formed as hi*hi + hi*lo + lo*hi by tcgen05.mma.kind::tf32 products.  The tensor
 // core's FP32 accumulation in tensor memory does not round to nearest, and accumulating
-// long runs there biases sums of squares by ~1e-6 relative (measured), so every 32-row
-// step gives each K slice of eight rows its own fresh accumulator for hi*hi (the cross
-// terms, 2^-11 smaller, share one): the step's partial sums are read back, added in
-// registers in FP32 (round to nearest), and folded every 256 rows into double-float sums.
+// long runs there biases sums of squares by ~1e-6 relative (measured), so within every
+// 32-row step each 16-row half gets its own fresh accumulator for hi*hi (two MMAs) and the
+// cross terms (2^-11 smaller) share a third: the step's partial sums are read back, added
+// in registers in FP32 (round to nearest) and folded every 256 rows into double-float sums.
 //
 // CTA tile: 128 columns of X (the MMA's M, tensor-memory lanes) x 64 columns of Y (N,
 // tensor-memory columns), rows of the split in steps of 32.  Operands are staged by all
 // 256 threads into shared memory in the canonical K-major layout without swizzling (core
 // matrices of 8 rows x 16 bytes; LBO = 128 bytes between the two core matrices of one MMA's
-// K = 8, SBO = 1024 bytes between 8-row groups); one elected thread issues the MMAs and
-// commits them to an mbarrier.  Every wait on the mbarrier is bounded; a wait that gives
-// up sets the error word and the CTA stops issuing work.
+// K = 8, SBO = 1024 bytes between 8-row groups).  Two shared-memory stages and two
+// tensor-memory buffers form a software pipeline; one elected thread issues the MMAs and
+// commits them to the buffer's mbarrier.  Every wait on an mbarrier is bounded; a wait that
+// gives up sets the error word and the CTA stops issuing work.
 #include <algorithm>
 
 #include "arb_internal.h"
@@ -30,11 +31,16 @@ constexpr int TC_M = 128;          // columns of X per CTA (MMA M)
 constexpr int TC_N = 64;           // columns of Y per CTA (MMA N)
 constexpr int TC_KS = 32;          // rows per pipeline step
 constexpr int TC_FOLD = 8;         // steps (256 rows) per fold of the FP32 run sums into double-float
-constexpr int TC_TMEM_COLS = 512;  // accumulators: 4 leading-product slices + 1 cross-product, 64 columns each
+constexpr int TC_TMEM_COLS = 512;  // two buffers of 3 accumulators (2 leading-product slices, 1 cross) x 64 columns
 constexpr int TC_A_BYTES = TC_M * TC_KS * 4;   // one operand copy (hi or lo) of the X tile
 constexpr int TC_B_BYTES = TC_N * TC_KS * 4;
 constexpr int TC_STAGE = 2 * TC_A_BYTES + 2 * TC_B_BYTES;  // hi, lo of both
-constexpr int TC_SMEM = TC_STAGE + 1024;                   // one stage + barrier
+constexpr int TC_NR = 4;                                   // raw (FP32) stages of rows in flight
+// raw rows padded by 32 bytes so that a warp reading 8 columns x 4 rows hits 32 banks
+constexpr int TC_RSA = TC_M + 8, TC_RSB = TC_N + 8;        // raw row strides (floats)
+constexpr int TC_RAW_A = TC_KS * TC_RSA * 4;
+constexpr int TC_RAW = TC_RAW_A + TC_KS * TC_RSB * 4;
+constexpr int TC_SMEM = TC_NR * TC_RAW + 2 * TC_STAGE + 1024;  // raw ring, operand stages, barriers
 constexpr long long TC_SPIN = 1ll << 26;                   // mbarrier polls before giving up
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -139,6 +145,90 @@ __device__ __forceinline__ void df_acc(float& h, float& l, float v) {
   l = __fsub_rn(t, __fsub_rn(h, s));
 }
 
+__device__ __forceinline__ void mbar_expect_tx(void* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bulk copy (TMA, untiled) of `bytes` (a multiple of 16) from 16-byte aligned global memory
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, void* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Warp 0: request step u's rows into raw stage `raw` (row k of the X tile at k * TC_RSA
+// floats, of the Y tile at TC_RAW_A + k * TC_RSB floats): one bulk copy per row and operand, issued by
+// lane k, the columns of the tile rounded up to whole 16-byte groups (within the leading
+// dimension).  Lane 0 posts the expected byte count first.
+__device__ __forceinline__ void request_step(unsigned char* raw, void* bar, const float* X, int64_t ldx, int na,
+                                             const float* Y, int64_t ldy, int nb, int64_t rb, int64_t r1, int i0,
+                                             int j0, int lane) {
+  const int ca = min(TC_M, na - i0), cb = min(TC_N, nb - j0);
+  const unsigned sa = static_cast<unsigned>((ca + 3) / 4 * 16), sb = static_cast<unsigned>((cb + 3) / 4 * 16);
+  const int rows = static_cast<int>(max(static_cast<int64_t>(0), min(static_cast<int64_t>(TC_KS), r1 - rb)));
+  if (lane == 0) mbar_expect_tx(bar, static_cast<unsigned>(rows) * (sa + sb));
+  __syncwarp();
+  if (lane < rows) {
+    bulk_g2s(raw + lane * (TC_RSA * 4), X + (rb + lane) * ldx + i0, sa, bar);
+    bulk_g2s(raw + TC_RAW_A + lane * (TC_RSB * 4), Y + (rb + lane) * ldy + j0, sb, bar);
+  }
+}
+
+// all threads: raw stage -> split-TF32 operand stage (K-major core-matrix layout); entries
+// outside the rows or columns of the product are zero.  A warp converts one core-matrix
+// group of 8 columns x 4 rows at a time, lane = 4 * column + row, so both its shared-memory
+// reads (padded raw rows) and its writes (128 contiguous bytes) are free of bank conflicts.
+__device__ __forceinline__ void split_step(const unsigned char* raw, unsigned char* stage, int rows, int ca, int cb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cl = lane >> 2, kl = lane & 3;
+  unsigned char* Ahi = stage;
+  unsigned char* Alo = Ahi + TC_A_BYTES;
+  unsigned char* Bhi = Alo + TC_A_BYTES;
+  unsigned char* Blo = Bhi + TC_B_BYTES;
+  const float* ra = reinterpret_cast<const float*>(raw);
+  const float* rbv = reinterpret_cast<const float*>(raw + TC_RAW_A);
+  constexpr int KG = TC_KS / 4;
+#pragma unroll 4
+  for (int blk = warp; blk < (TC_M / 8) * KG; blk += TC_THREADS / 32) {
+    const int c = (blk / KG) * 8 + cl, k = (blk % KG) * 4 + kl;
+    const float x = (k < rows && c < ca) ? ra[k * TC_RSA + c] : 0.f;
+    float h, l;
+    split_tf32(x, h, l);
+    const int o = kmajor_off(c, k);
+    *reinterpret_cast<float*>(Ahi + o) = h;
+    *reinterpret_cast<float*>(Alo + o) = l;
+  }
+#pragma unroll 4
+  for (int blk = warp; blk < (TC_N / 8) * KG; blk += TC_THREADS / 32) {
+    const int c = (blk / KG) * 8 + cl, k = (blk % KG) * 4 + kl;
+    const float x = (k < rows && c < cb) ? rbv[k * TC_RSB + c] : 0.f;
+    float h, l;
+    split_tf32(x, h, l);
+    const int o = kmajor_off(c, k);
+    *reinterpret_cast<float*>(Bhi + o) = h;
+    *reinterpret_cast<float*>(Blo + o) = l;
+  }
+}
+
+// the MMAs of one step into tensor-memory buffer `dbase`: leading products of K rows 0-15
+// into slice 0, of rows 16-31 into slice 1 (each slice two MMAs, fresh every step), all
+// cross products into slice 2.  d[0..3]: descriptors of the stage's A hi, A lo, B hi, B lo
+// at K = 0; the start-address field (bits 0-13, 16-byte units) advances by 16 per MMA K = 8.
+__device__ __forceinline__ void issue_step(const unsigned long long (&d)[4], unsigned dbase, unsigned idesc) {
+#pragma unroll
+  for (int kk = 0; kk < TC_KS / 8; ++kk) {
+    const unsigned long long o = 16ull * kk;
+    mma_tf32(dbase + (kk >> 1) * TC_N, d[0] + o, d[2] + o, idesc, (kk & 1) ? 1u : 0u);
+    mma_tf32(dbase + 2 * TC_N, d[0] + o, d[3] + o, idesc, kk > 0 ? 1u : 0u);
+    mma_tf32(dbase + 2 * TC_N, d[1] + o, d[2] + o, idesc, 1u);
+  }
+}
+
+// Pipeline over the 32-row steps, one CTA per SM: bulk copies keep TC_NR steps of raw rows
+// in flight; at step t the threads split step t into operand stage t%2, thread 0 issues
+// step t's MMAs into tensor-memory buffer t%2, warp 1 requests step t+TC_NR, and the
+// threads add up buffer (t-1)%2 while those MMAs run.
 __global__ void __launch_bounds__(TC_THREADS, 1)
 gram_tc_kernel(int64_t n, const float* __restrict__ X, int64_t ldx, int na, const float* __restrict__ Y,
                int64_t ldy, int nb, int64_t rows_per_split, int symmetric, double* __restrict__ part,
@@ -148,12 +238,12 @@ gram_tc_kernel(int64_t n, const float* __restrict__ X, int64_t ldx, int na, cons
   const int i0 = ti * TC_M, j0 = tj * TC_N;
   // symmetric products need every entry with i <= j: skip tiles entirely below the diagonal
   if (symmetric && j0 + TC_N - 1 < i0) return;
-  unsigned char* Ahi = smem;
-  unsigned char* Alo = Ahi + TC_A_BYTES;
-  unsigned char* Bhi = Alo + TC_A_BYTES;
-  unsigned char* Blo = Bhi + TC_B_BYTES;
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + TC_STAGE);  // MMAs of a step done
-  unsigned* tmem_slot = reinterpret_cast<unsigned*>(smem + TC_STAGE + 64);
+  unsigned char* raw = smem;                                   // TC_NR raw stages
+  unsigned char* opnd = smem + TC_NR * TC_RAW;                 // 2 operand stages
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(opnd + 2 * TC_STAGE);
+  unsigned long long* bar_raw = bars;                          // [TC_NR] rows landed
+  unsigned long long* bar_mma = bars + TC_NR;                  // [2] MMAs of a buffer done
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(bars + TC_NR + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -162,7 +252,7 @@ gram_tc_kernel(int64_t n, const float* __restrict__ X, int64_t ldx, int na, cons
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int q = 0; q < TC_NR + 2; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -170,114 +260,105 @@ gram_tc_kernel(int64_t n, const float* __restrict__ X, int64_t ldx, int na, cons
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = *tmem_slot;
   const unsigned idesc = make_idesc_tf32(TC_M, TC_N);
+  const unsigned dbuf[2] = {tmem, tmem + 3 * TC_N};
+  unsigned long long sd[2][4];  // operand descriptors of the two stages (K = 0)
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const unsigned base = smem_u32(opnd + b * TC_STAGE);
+    sd[b][0] = make_sdesc(base, 128, 1024);
+    sd[b][1] = make_sdesc(base + TC_A_BYTES, 128, 1024);
+    sd[b][2] = make_sdesc(base + 2 * TC_A_BYTES, 128, 1024);
+    sd[b][3] = make_sdesc(base + 2 * TC_A_BYTES + TC_B_BYTES, 128, 1024);
+  }
 
   const int64_t r0 = s * rows_per_split;
   const int64_t r1 = min(n, r0 + rows_per_split);
   const int nsteps = static_cast<int>((r1 - r0 + TC_KS - 1) / TC_KS);
+  const int ca = min(TC_M, na - i0), cb = min(TC_N, nb - j0);
   // this thread's slice of the accumulators: lane quarter (warp & 3), column half (warp >> 2)
   const int row_q = (warp & 3) * 32, col_h = (warp >> 2) * 32;
-  const unsigned tslice = tmem + (static_cast<unsigned>(row_q) << 16) + col_h;
+  const unsigned tlane = (static_cast<unsigned>(row_q) << 16) + col_h;
   float acc_h[32], acc_l[32], run[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) acc_h[c] = acc_l[c] = run[c] = 0.f;
-  unsigned phase = 0u;
+  unsigned ph_raw = 0u;   // bit q: parity to wait for on raw stage q
+  unsigned ph_mma = 0u;   // bit b: parity to wait for on buffer b
+  unsigned pend_raw = 0u, pend_mma = 0u;
   bool ok = true;
 
-  for (int t = 0; t < nsteps; ++t) {
-    const int64_t rb = r0 + static_cast<int64_t>(t) * TC_KS;
-    // X tile: 32 rows x 128 columns, one float4 per thread per pass
-    for (int q = tid; q < TC_KS * (TC_M / 4); q += TC_THREADS) {
-      const int k = q / (TC_M / 4), c4 = (q % (TC_M / 4)) * 4;
-      const int64_t r = rb + k;
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
-      if (r < r1) {
-        const float* src = X + r * ldx + i0 + c4;
-        if (i0 + c4 + 3 < na) {
-          const float4 f = *reinterpret_cast<const float4*>(src);
-          v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-        } else {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = (i0 + c4 + u < na) ? src[u] : 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float h, l;
-        split_tf32(v[u], h, l);
-        const int o = kmajor_off(c4 + u, k);
-        *reinterpret_cast<float*>(Ahi + o) = h;
-        *reinterpret_cast<float*>(Alo + o) = l;
-      }
-    }
-    // Y tile: 32 rows x 64 columns
-    for (int q = tid; q < TC_KS * (TC_N / 4); q += TC_THREADS) {
-      const int k = q / (TC_N / 4), c4 = (q % (TC_N / 4)) * 4;
-      const int64_t r = rb + k;
-      float v[4] = {0.f, 0.f, 0.f, 0.f};
-      if (r < r1) {
-        const float* src = Y + r * ldy + j0 + c4;
-        if (j0 + c4 + 3 < nb) {
-          const float4 f = *reinterpret_cast<const float4*>(src);
-          v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-        } else {
-#pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = (j0 + c4 + u < nb) ? src[u] : 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float h, l;
-        split_tf32(v[u], h, l);
-        const int o = kmajor_off(c4 + u, k);
-        *reinterpret_cast<float*>(Bhi + o) = h;
-        *reinterpret_cast<float*>(Blo + o) = l;
-      }
-    }
-    // generic-proxy writes -> visible to the tensor core
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const unsigned ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
-#pragma unroll
-      for (int kk = 0; kk < TC_KS / 8; ++kk) {
-        const unsigned off = kk * 256;  // two core matrices of 128 bytes per MMA K = 8
-        const unsigned long long dah = make_sdesc(ah + off, 128, 1024), dal = make_sdesc(al + off, 128, 1024);
-        const unsigned long long dbh = make_sdesc(bh + off, 128, 1024), dbl = make_sdesc(bl + off, 128, 1024);
-        // the leading products of each K slice into their own fresh accumulator, the two
-        // cross products of the whole step into one more
-        mma_tf32(tmem + kk * TC_N, dah, dbh, idesc, 0u);
-        mma_tf32(tmem + 4 * TC_N, dah, dbl, idesc, kk > 0 ? 1u : 0u);
-        mma_tf32(tmem + 4 * TC_N, dal, dbh, idesc, 1u);
-      }
-      mma_commit(bar);
-    }
-    ok = mbar_wait(bar, phase) && ok;
-    phase ^= 1u;
-    ok = __syncthreads_and(ok) != 0;
-    if (!ok) break;
+  if (warp == 0)
+    for (int u = 0; u < TC_NR && u < nsteps; ++u)
+      request_step(raw + u * TC_RAW, &bar_raw[u], X, ldx, na, Y, ldy, nb, r0 + static_cast<int64_t>(u) * TC_KS, r1,
+                   i0, j0, lane);
+  for (int u = 0; u < TC_NR && u < nsteps; ++u) pend_raw |= 1u << u;
+
+  // add up tensor-memory buffer b (a finished step) into the running sums
+  auto drain_buffer = [&](int b, bool fold) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float v[32], w[32];
-    tmem_ld32(tslice, v);
+    tmem_ld32(dbuf[b] + tlane, v);
 #pragma unroll
-    for (int a = 1; a <= 4; ++a) {
-      tmem_ld32(tslice + a * TC_N, w);
+    for (int a = 1; a <= 2; ++a) {
+      tmem_ld32(dbuf[b] + tlane + a * TC_N, w);
 #pragma unroll
       for (int c = 0; c < 32; ++c) v[c] = __fadd_rn(v[c], w[c]);
     }
 #pragma unroll
     for (int c = 0; c < 32; ++c) run[c] = __fadd_rn(run[c], v[c]);
-    if ((t % TC_FOLD) == TC_FOLD - 1 || t == nsteps - 1) {
+    if (fold) {
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         df_acc(acc_h[c], acc_l[c], run[c]);
         run[c] = 0.f;
       }
     }
-    // every thread has read tensor memory and shared memory before they are overwritten
+  };
+
+  for (int t = 0; t < nsteps; ++t) {
+    const int q = t % TC_NR, b = t & 1;
+    const int64_t rb = r0 + static_cast<int64_t>(t) * TC_KS;
+    const int rows = static_cast<int>(min(static_cast<int64_t>(TC_KS), r1 - rb));
+    // rows of step t landed; operand stage b was read by the MMAs of step t-2, done
+    ok = mbar_wait(&bar_raw[q], (ph_raw >> q) & 1u) && ok;
+    ph_raw ^= 1u << q;
+    pend_raw &= ~(1u << q);
+    split_step(raw + q * TC_RAW, opnd + b * TC_STAGE, rows, ca, cb);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue_step(sd[b], dbuf[b], idesc);
+      mma_commit(&bar_mma[b]);
+    }
+    if (warp == 1 && t + TC_NR < nsteps)
+      request_step(raw + q * TC_RAW, &bar_raw[q], X, ldx, na, Y, ldy, nb, r0 + static_cast<int64_t>(t + TC_NR) * TC_KS,
+                   r1, i0, j0, lane);
+    pend_mma |= 1u << b;
+    if (t + TC_NR < nsteps) pend_raw |= 1u << q;
+    if (t >= 1) {
+      const int pb = b ^ 1;
+      ok = mbar_wait(&bar_mma[pb], (ph_mma >> pb) & 1u) && ok;
+      ph_mma ^= 1u << pb;
+      pend_mma &= ~(1u << pb);
+      drain_buffer(pb, ((t - 1) % TC_FOLD) == TC_FOLD - 1);
+    }
   }
+  if (ok && nsteps > 0) {
+    const int lb = (nsteps - 1) & 1;
+    ok = mbar_wait(&bar_mma[lb], (ph_mma >> lb) & 1u);
+    ph_mma ^= 1u << lb;
+    pend_mma &= ~(1u << lb);
+    if (ok) drain_buffer(lb, true);
+  }
+  // after a failed wait: let whatever is still in flight finish before the memory goes
+  for (int b = 0; b < 2; ++b)
+    if ((pend_mma >> b) & 1u)
+      if (!mbar_wait(&bar_mma[b], (ph_mma >> b) & 1u)) ok = false;
+  for (int qq = 0; qq < TC_NR; ++qq)
+    if ((pend_raw >> qq) & 1u)
+      if (!mbar_wait(&bar_raw[qq], (ph_raw >> qq) & 1u)) ok = false;
   if (!ok && lane == 0) atomicExch(err, 1);
   if (ok) {
     const int i = i0 + row_q + lane;
