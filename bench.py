@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--filter-only", action="store_true",
                     help="only apply the filter (--reps times) to an n x --ncols block: for profiling")
+    ap.add_argument("--dense-only", action="store_true",
+                    help="only time the dense building blocks of one ARR at the workload's sizes: for profiling")
     ap.add_argument("--ncols", type=int, default=0)
     ap.add_argument("--degree", type=int, default=0)
     ap.add_argument("--reps", type=int, default=1)
@@ -376,6 +378,50 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_dense_only(args):
+    """Time (CUDA events, context stream, after one warm-up call) the dense products of the
+    Rayleigh-Ritz steps at the workload's sizes: FP32 Grams (tensor cores), FP64 and
+    double-float Grams, and the Jacobi eigensolver at m = p and m = (q+1) p."""
+    import torch
+
+    from paper_1507_06078_gb300 import arrabit as arb
+    from paper_1507_06078_gb300 import build
+    build.build()
+    W = workload(args.grid)
+    n, p, m = W.A.n, W.p, (W.q + 1) * W.p
+    ctx = arb.Context(0)
+    ctx_df = arb.Context(0)
+    ctx_df.set_dense_df(True)
+
+    def timed(f, reps=3):
+        f()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        for _ in range(reps):
+            f()
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"dense_only": True, "n": n, "p": p, "m": m}
+    X32 = torch.randn((n, p), dtype=torch.float32, device="cuda")
+    out["gram_f32_pxp_sym_ms"] = timed(lambda: arb.arb_gram_f32(ctx, X32, X32))
+    U32 = torch.randn((n, m), dtype=torch.float32, device="cuda")
+    AU32 = torch.randn((n, m), dtype=torch.float32, device="cuda")
+    out["gram_f32_mxm_ms"] = timed(lambda: arb.arb_gram_f32(ctx, U32, AU32), reps=1)
+    del U32, AU32
+    X64 = torch.randn((n, p), dtype=torch.float64, device="cuda")
+    out["gram_f64_pxp_sym_ms"] = timed(lambda: arb.arb_gram(ctx, X64, X64), reps=1)
+    out["gram_df_pxp_sym_ms"] = timed(lambda: arb.arb_gram(ctx_df, X64, X64), reps=2)
+    for mm in (p, m):
+        H = torch.randn((mm, mm), dtype=torch.float64, device="cuda")
+        H = 0.5 * (H + H.T)
+        out[f"syevj_{mm}_ms"] = timed(lambda: arb.arb_syevj(ctx, H), reps=2)
+    print(json.dumps(out))
+
+
 def run_filter_only(args):
     """Apply the Chebyshev-interpolant filter to a Gaussian block of the workload matrix and
     print the per-pass time (CUDA events on the context's stream)."""
@@ -421,6 +467,9 @@ def main():
     args = parse()
     if args.filter_only:
         run_filter_only(args)
+        return
+    if args.dense_only:
+        run_dense_only(args)
         return
     if args.impl == "reference":
         run_reference(args)

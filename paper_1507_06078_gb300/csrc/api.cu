@@ -862,7 +862,7 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(r) * r, &H));
     ARB_TRY(gram<E>(ctx, n, Bk.wk.U, Bk.ldm, r, Bk.wk.AU, Bk.ldm, r, H, r));
     ARB_TRY(symmetrize(ctx, r, H, r));
-    ARB_TRY(syevj(ctx, r, H, r, S.theta, S.V, r, nullptr));
+    ARB_TRY(syevj(ctx, r, H, r, S.theta, S.V, r, nullptr, sizeof(E) == 4 ? 1e-10 : 1e-15));
     ARB_TRY(d2h_sync(ctx, &S.b, S.theta + (r - 1), sizeof(double)));
     S.info.spmm_cols += r;
     return ARB_OK;

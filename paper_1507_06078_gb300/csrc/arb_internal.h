@@ -276,8 +276,10 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
 
 // ---------------------------------------------------------------- Jacobi (jacobi.cu)
 // w (descending), V (row-major, column j = eigenvector) of symmetric H (not modified).
+// Sweeps stop when off(A) <= tol ||H||_F: 1e-15 for FP64 data, 1e-10 where H is formed from
+// FP32 blocks and so carries FP32-level errors itself.
 arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
-                 int64_t ldv, int32_t* sweeps);
+                 int64_t ldv, int32_t* sweeps, double tol = 1e-15);
 
 // ---------------------------------------------------------------- composite steps (steps.cu)
 struct FilterPlan {

@@ -6,7 +6,8 @@
 // t = sign(theta)/(|theta| + sqrt(theta^2+1)), c = 1/sqrt(1+t^2), s = t c, which zeroes
 // a_ij of J^T A J.  Rotations are scheduled by the round-robin ("circle") tournament: each
 // of the N-1 rounds pairs every one of N indices exactly once, so the rotations of a round
-// commute and are applied together.  Sweeps stop when off(A) <= 1e-15 ||H||_F or after 60.
+// commute and are applied together.  Sweeps stop when off(A) <= tol ||H||_F (1e-15 for
+// FP64 data; callers whose matrices carry FP32-level errors pass 1e-10) or after 60.
 //
 // m <= 96: one CTA holds A and V in shared memory and rotates single indices.
 // m > 96: block Jacobi.  The indices are cut into NB blocks of 16 (NB even; padding
@@ -32,7 +33,6 @@ namespace {
 
 constexpr int JAC_THREADS = 256;
 constexpr int JAC_MAX_SWEEPS = 60;
-constexpr double JAC_TOL = 1e-15;
 
 struct JacParams {
   int m, M;
@@ -47,6 +47,7 @@ struct JacParams {
   int64_t ldv;
   int32_t* sweeps_out;
   double* Q;     // block kernel: NB/2 orthogonal 32 x 32 factors of the current round
+  double tol;    // stop when off(A) <= tol ||H||_F
 };
 
 __device__ __forceinline__ void round_pair(int M, int r, int k, int& i, int& j) {
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(JAC_THREADS) jacobi_block_kernel(JacParams P) 
     g.sync();
     double off2 = 0.0;
     for (int b = 0; b < static_cast<int>(gridDim.x); ++b) off2 += P.red[gridDim.x + b];
-    if (sqrt(off2) <= JAC_TOL * normF || normF == 0.0) break;
+    if (sqrt(off2) <= P.tol * normF || normF == 0.0) break;
     for (int r = 0; r < NB - 1; ++r) {
       // phase 1: one Jacobi sweep per block-pair subproblem -> Q_p
       for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(JAC_SMALL_THREADS) jacobi_small_kernel(JacPara
     for (int t = tid; t < M * M; t += nth)
       if (t / M != t % M) off += A[t] * A[t];
     const double off2 = block_sum(off, red);
-    if (sqrt(off2) <= JAC_TOL * normF || normF == 0.0) break;
+    if (sqrt(off2) <= P.tol * normF || normF == 0.0) break;
     for (int r = 0; r < M - 1; ++r) {
       for (int k = tid; k < half; k += nth) {
         int i, j;
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(JAC_SMALL_THREADS) jacobi_small_kernel(JacPara
 }  // namespace
 
 arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
-                 int64_t ldv, int32_t* sweeps) {
+                 int64_t ldv, int32_t* sweeps, double tol) {
   if (m <= 0) {
     if (sweeps) *sweeps = 0;
     return ARB_OK;
@@ -452,6 +453,7 @@ arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w
     ARB_CUDA(ctx, cudaFuncSetAttribute(jacobi_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(smem_max)));
     JacParams P = {};
+    P.tol = tol;
     P.m = m;
     P.M = M;
     P.H = H;
@@ -481,6 +483,7 @@ arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w
   double* base;
   ARB_TRY(ws<double>(ctx, WS_JACOBI, 2 * mm + qsz + 2 * static_cast<size_t>(grid) + m + 8, &base));
   JacParams P = {};
+  P.tol = tol;
   P.m = m;
   P.M = MB;
   P.H = H;
