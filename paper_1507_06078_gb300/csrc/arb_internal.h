@@ -238,6 +238,11 @@ arb_status write_colmajor(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, 
 arb_status fill(arb_ctx ctx, double* p, int64_t count, double v);
 // H <- (H + H^T)/2 for an m x m row-major matrix
 arb_status symmetrize(arb_ctx ctx, int32_t m, double* H, int64_t ldh);
+// H with its diagonal blocks (starts off[b], sizes rk[b]) computed in full and, off the
+// diagonal, only the upper blocks (the lower ones zero): averaged inside diagonal blocks,
+// the upper blocks mirrored below
+arb_status symmetrize_upper_blocks(arb_ctx ctx, int32_t m, double* H, int64_t ldh, const int32_t* off,
+                                  const int32_t* rk, int32_t nblk);
 // G <- diag(s) G diag(s)
 arb_status scale_sym(arb_ctx ctx, int32_t m, double* G, int64_t ldg, const double* s);
 // s[c] = 1/sqrt(ss[c]) (0 when ss[c] == 0)

@@ -428,6 +428,29 @@ __global__ void symmetrize_kernel(int m, double* H, int64_t ldh) {
   H[static_cast<int64_t>(j) * ldh + i] = v;
 }
 
+struct BlockOffsets {
+  int n;
+  int off[17];  // block starts, off[n] = m
+};
+
+// H (i < j): the average of H_ij and H_ji inside a diagonal block (both computed), their
+// sum across blocks (one of the two was left zero)
+__global__ void symmetrize_blocks_kernel(int m, double* H, int64_t ldh, BlockOffsets bo) {
+  const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (t >= static_cast<int64_t>(m) * m) return;
+  const int i = static_cast<int>(t / m), j = static_cast<int>(t % m);
+  if (j <= i) return;
+  int bi = 0, bj = 0;
+  for (int b = 1; b < bo.n; ++b) {
+    bi += (i >= bo.off[b]);
+    bj += (j >= bo.off[b]);
+  }
+  const double a = H[static_cast<int64_t>(i) * ldh + j], c = H[static_cast<int64_t>(j) * ldh + i];
+  const double v = (bi == bj) ? 0.5 * (a + c) : a + c;
+  H[static_cast<int64_t>(i) * ldh + j] = v;
+  H[static_cast<int64_t>(j) * ldh + i] = v;
+}
+
 __global__ void scale_sym_kernel(int m, double* G, int64_t ldg, const double* __restrict__ s) {
   const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (t >= static_cast<int64_t>(m) * m) return;
@@ -829,6 +852,19 @@ arb_status fill(arb_ctx ctx, double* p, int64_t count, double v) {
 arb_status symmetrize(arb_ctx ctx, int32_t m, double* H, int64_t ldh) {
   if (m <= 1) return ARB_OK;
   symmetrize_kernel<<<blocks_for(static_cast<int64_t>(m) * m, 256), 256, 0, ctx->stream>>>(m, H, ldh);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status symmetrize_upper_blocks(arb_ctx ctx, int32_t m, double* H, int64_t ldh, const int32_t* off,
+                                  const int32_t* rk, int32_t nblk) {
+  if (m <= 1) return ARB_OK;
+  if (nblk < 1 || nblk > 16) return set_error(ctx, ARB_INVALID_ARG, "symmetrize: 1..16 blocks");
+  BlockOffsets bo{};
+  bo.n = nblk;
+  for (int b = 0; b < nblk; ++b) bo.off[b] = off[b];
+  bo.off[nblk] = off[nblk - 1] + rk[nblk - 1];
+  symmetrize_blocks_kernel<<<blocks_for(static_cast<int64_t>(m) * m, 256), 256, 0, ctx->stream>>>(m, H, ldh, bo);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }

@@ -246,12 +246,13 @@ arb_status rcond_gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t n
 // U_i = orth(W).  In exact arithmetic span{U_0..U_q} = span{X, BX, ..., B^q X} of
 // Algorithm 5; building it block by block keeps the small residual directions that
 // columns of [X, BX, ...] carry at full relative accuracy.  Then AU_q = B U_q and
-// H = U^T (B U) (Algorithm 1) is diagonalised.
+// H = U^T (B U) (Algorithm 1) is formed from its block-tridiagonal part and diagonalised.
 template <typename T>
 arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double op_shift, int64_t n, T* X,
                              int64_t ldx, int32_t w, const T* Qc, int64_t ldqc, int32_t nl, int32_t q,
                              const ArrWork<T>& wk, int32_t* m_out, double* theta, double* V) {
   *m_out = 0;
+  if (q > 15) return set_error(ctx, ARB_INVALID_ARG, "ARR: at most 15 augmentation blocks");
   if (sizeof(T) == 4) ARB_TRY(ensure_val32(ctx, mat));
   if (nl > 0) ARB_TRY(project_out<T>(ctx, n, Qc, ldqc, nl, X, ldx, w));
   int32_t r0 = 0;
@@ -297,10 +298,21 @@ arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double o
     s.ldo = wk.ldau;
     ARB_TRY(spmm_fused(ctx, s));
   }
+  // H = U^T (B U) is block tridiagonal for this basis: B U_i lies in span{U_0..U_{i+1}}
+  // up to the directions orth truncated (below its threshold), so only the blocks
+  // H_ii and H_{i,i+1} are formed (H_{i+1,i} = H_{i,i+1}^T, the rest zero) - 3q+1 of the
+  // (q+1)^2 block products of the full U^T (BU)
   double* H;
   ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(m) * m, &H));
-  ARB_TRY(gram<T>(ctx, n, wk.U, wk.ldu, m, wk.AU, wk.ldau, m, H, m));
-  ARB_TRY(symmetrize(ctx, m, H, m));
+  ARB_TRY(fill(ctx, H, static_cast<int64_t>(m) * m, 0.0));
+  const int nblk = static_cast<int>(off.size());
+  for (int bi = 0; bi < nblk; ++bi) {
+    for (int bj = bi; bj < std::min(nblk, bi + 2); ++bj) {
+      double* Hij = H + static_cast<size_t>(off[bi]) * m + off[bj];
+      ARB_TRY(gram<T>(ctx, n, wk.U + off[bi], wk.ldu, rk[bi], wk.AU + off[bj], wk.ldau, rk[bj], Hij, m));
+    }
+  }
+  ARB_TRY(symmetrize_upper_blocks(ctx, m, H, m, off.data(), rk.data(), nblk));
   ARB_TRY(syevj(ctx, m, H, m, theta, V, m, nullptr, sizeof(T) == 4 ? 1e-10 : 1e-15));
   *m_out = m;
   return ARB_OK;
