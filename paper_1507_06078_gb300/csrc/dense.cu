@@ -177,8 +177,8 @@ constexpr int DF_FOLD = 4;  // k-steps of 16 terms per fold into the running sum
 __device__ __forceinline__ void df_fold(float2& Ah, float2& Al, float2& S, float2& E) {
   const dfp t = fast_two_sum2(S, E);
   const float2 s = __fadd2_rn(Ah, t.hi);
-  const float2 bb = __fadd2_rn(s, neg2(Ah));
-  const float2 err = __fadd2_rn(__fadd2_rn(Ah, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(t.hi, neg2(bb)));
+  const float2 bb = sub2(s, Ah);
+  const float2 err = __fadd2_rn(sub2(Ah, sub2(s, bb)), sub2(t.hi, bb));
   const dfp r = fast_two_sum2(s, __fadd2_rn(err, __fadd2_rn(Al, t.lo)));
   Ah = r.hi;
   Al = r.lo;
@@ -226,8 +226,9 @@ gram_df_kernel(int64_t n, const double* __restrict__ X, int64_t ldx, int na, con
       for (int u = 0; u < R; ++u) {
         const float ah = Xh[k][ty + 16 * u], al = Xl[k][ty + 16 * u];
         const dfp a{make_float2(ah, ah), make_float2(al, al)};
+        const dfp na{make_float2(-ah, -ah), make_float2(-al, -al)};
 #pragma unroll
-        for (int v = 0; v < H; ++v) dot2p(S[u][v], E[u][v], a, b[v]);
+        for (int v = 0; v < H; ++v) dot2p(S[u][v], E[u][v], a, na, b[v]);
       }
     }
     __syncthreads();
@@ -295,8 +296,9 @@ gemm_df_kernel(int64_t n, const double* __restrict__ In, int64_t ldi, int na, co
       for (int u = 0; u < 4; ++u) {
         const float ah = Ih[k][ty + 16 * u], al = Il[k][ty + 16 * u];
         const dfp a{make_float2(ah, ah), make_float2(al, al)};
+        const dfp na{make_float2(-ah, -ah), make_float2(-al, -al)};
 #pragma unroll
-        for (int v = 0; v < H; ++v) dot2p(S[u][v], E[u][v], a, b[v]);
+        for (int v = 0; v < H; ++v) dot2p(S[u][v], E[u][v], a, na, b[v]);
       }
     }
     __syncthreads();

@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
     kx = dfp_of(x[0], x[1]);
     kz = dfp_of(z[0], z[1]);
   }
+  const dfp nka = neg(ka), nkb = neg(kb), nkx = neg(kx), nkz = neg(kz);
   auto off = [&](int64_t r, int64_t ld) -> int64_t {
     if constexpr (SHORT) return static_cast<int64_t>(static_cast<uint32_t>(r) * static_cast<uint32_t>(ld));
     else return r * ld;
@@ -209,16 +210,17 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
 #pragma unroll
           for (int t = 0; t < DF_BATCH; ++t)
             if (t0 + t < cnt)
-              dot2p(S, E, dfp{make_float2(aah[t], aah[t]), make_float2(aal[t], aal[t])}, y[t]);
+              dot2p(S, E, dfp{make_float2(aah[t], aah[t]), make_float2(aal[t], aal[t])},
+                    dfp{make_float2(-aah[t], -aah[t]), make_float2(-aal[t], -aal[t])}, y[t]);
         }
       }
       if (!act) continue;
       const dfp acc = fast_two_sum2(S, E);
       float2 So = make_float2(0.f, 0.f), Eo = make_float2(0.f, 0.f);
-      dot2p(So, Eo, ka, acc);
-      if (has_beta) dot2p(So, Eo, kb, yi);
-      if (P.X) dot2p(So, Eo, kx, xv);
-      if (P.Z) dot2p(So, Eo, kz, zv);
+      dot2p(So, Eo, ka, nka, acc);
+      if (has_beta) dot2p(So, Eo, kb, nkb, yi);
+      if (P.X) dot2p(So, Eo, kx, nkx, xv);
+      if (P.Z) dot2p(So, Eo, kz, nkz, zv);
       const dfp o = fast_two_sum2(So, Eo);
       if (P.out)
         __stcs(reinterpret_cast<float4*>(P.out + off(row, P.ldo) + c), make_float4(o.hi.x, o.hi.y, o.lo.x, o.lo.y));

@@ -33,27 +33,31 @@ struct dfp {
   float2 hi, lo;
 };
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ dfp neg(const dfp& a) { return dfp{neg2(a.hi), neg2(a.lo)}; }
 __device__ __forceinline__ dfp dfp_of(df2 a, df2 b) { return dfp{make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+// b - a, exactly rounded, as one packed FMA with the constant -1 (no separate negation)
+__device__ __forceinline__ float2 sub2(float2 b, float2 a) { return __ffma2_rn(a, make_float2(-1.f, -1.f), b); }
 __device__ __forceinline__ dfp fast_two_sum2(float2 a, float2 b) {
   const float2 s = __fadd2_rn(a, b);
-  return dfp{s, __fadd2_rn(b, neg2(__fadd2_rn(s, neg2(a))))};
+  return dfp{s, sub2(b, sub2(s, a))};
 }
 
 // Compensated accumulation (Ogita, Rump & Oishi's Dot2) of c * v into (S, E), for both
 // columns at once: S collects the rounded sums of the leading products, E the exact
 // rounding errors of those sums (Knuth's two-sum) and of the products (one FMA each) plus
 // the cross terms, so S + E carries the dot product as if computed with twice the working
-// precision.  12 packed instructions per term for two columns.
-__device__ __forceinline__ void dot2p(float2& S, float2& E, const dfp& c, const dfp& v) {
+// precision.  nc = -c is passed in so that every subtraction is an FMA with -1 or with
+// the negated multiplier: 12 packed instructions per term for two columns.
+__device__ __forceinline__ void dot2p(float2& S, float2& E, const dfp& c, const dfp& nc, const dfp& v) {
   const float2 p = __fmul2_rn(c.hi, v.hi);
-  float2 e = __ffma2_rn(c.hi, v.hi, neg2(p));
-  e = __ffma2_rn(c.hi, v.lo, e);
-  e = __ffma2_rn(c.lo, v.hi, e);
+  float2 en = __ffma2_rn(nc.hi, v.hi, p);  // -(exact rounding error of p)
+  en = __ffma2_rn(nc.hi, v.lo, en);
+  en = __ffma2_rn(nc.lo, v.hi, en);
   const float2 s = __fadd2_rn(S, p);
-  const float2 bb = __fadd2_rn(s, neg2(S));
-  const float2 t = __fadd2_rn(__fadd2_rn(S, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(p, neg2(bb)));
+  const float2 bb = sub2(s, S);
+  const float2 t = __fadd2_rn(sub2(S, sub2(s, bb)), sub2(p, bb));
   S = s;
-  E = __fadd2_rn(E, __fadd2_rn(t, e));
+  E = __fadd2_rn(E, sub2(t, en));
 }
 
 // (hi, lo) of a double with hi + lo = x up to 2^-48 |x|, by integer operations on its bits
