@@ -30,8 +30,10 @@ design notes of the repository):
   pairs are candidates for locking.
 * Stall rule (ii): stop when the best maxres so far was reached 3 or more outer
   iterations ago.  Rule (iii): h counts wanted pairs with res_i < 0.1 tol.
-* For the smallest eigenpairs the method runs on B = sigma I - A with sigma the
-  Gershgorin upper bound of A; a = Gershgorin lower bound of B.  Residuals use the
+* For the smallest eigenpairs the method runs on B = sigma I - A with sigma an upper
+  bound of A's spectrum, the tighter of Gershgorin's and a 32-step Lanczos estimate with
+  residual margins (Section 5 estimates the spectrum's far end; the paper calls eigs);
+  a = sigma - that bound.  For the largest, a = the corresponding lower bound.  Residuals use the
   original eigenvalue estimate lambda_i = sigma - mu_i in the denominator, and the
   reported eigenvalues are the Rayleigh quotients x_i^T A x_i on the original A.
 * If orth(Z) leaves fewer than p directions, the Ritz set is padded with columns
@@ -352,12 +354,47 @@ class OracleResult:
     history: list = field(default_factory=list)
 
 
+def lanczos_bounds(A: sp.csr_matrix, steps: int, seed: int) -> tuple[float, float]:
+    """Estimates (lo, hi) of the extreme eigenvalues of A (Section 5 estimates the far end
+    of the spectrum; the paper calls eigs): ``steps`` steps of plain Lanczos from the
+    Gaussian column of stream ``seed``, the extreme eigenvalues theta of the tridiagonal
+    matrix widened by their residual bounds |beta_m y_m| and by 1e-3 max(1, |theta|)."""
+    from paper_1507_06078_gb300.inputs import gaussian_block
+    n = A.shape[0]
+    steps = min(steps, n)
+    v = gaussian_block(n, 1, seed)[:, 0]
+    v = v / np.sqrt(v @ v)
+    vp = np.zeros(n)
+    al, be, bprev = [], [], 0.0
+    for _ in range(steps):
+        w = A @ v
+        a = float(v @ w)
+        w = w - a * v - bprev * vp
+        b = math.sqrt(max(float(w @ w), 0.0))
+        al.append(a)
+        be.append(b)
+        if not b > 1e-12 * max(1.0, abs(a)):
+            break
+        vp, v, bprev = v, w / b, b
+    m = len(al)
+    T = np.diag(al) + np.diag(be[:m - 1], 1) + np.diag(be[:m - 1], -1)
+    th, Y = np.linalg.eigh(T)
+    hi = th[-1] + abs(be[-1] * Y[-1, -1]) + 1e-3 * max(1.0, abs(th[-1]))
+    lo = th[0] - abs(be[-1] * Y[-1, 0]) - 1e-3 * max(1.0, abs(th[0]))
+    return float(lo), float(hi)
+
+
+# the library draws the Lanczos start column from stream seed + 0x9E3779B97F4A7C15 (mod 2^64)
+BOUND_SEED_OFFSET = 0x9E3779B97F4A7C15
+
+
 def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest",
                 tol: float = 1e-10, q: int = 1, degree: int = 10, maxit: int = 30,
                 maxit1: int = 10, maxit2: int = 5, tol1: float | None = None,
                 filter_kind: str = "chebinterp", sigma: float | None = None,
                 inner_fixed: int = 0, pad_pool: np.ndarray | None = None,
-                poly_eval: str = "clenshaw", b_update: str = "continuation") -> OracleResult:
+                poly_eval: str = "clenshaw", b_update: str = "continuation",
+                seed: int = 20150722) -> OracleResult:
     """ARRABIT with the multi-power inner solver, Algorithm 8, for the k largest (or, via
     B = sigma I - A, smallest) eigenpairs of symmetric A.  The block width is
     p = X0.shape[1] = k + guard vectors.  ``inner_fixed`` > 0 replaces the inner stop rule
@@ -370,24 +407,30 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
     n, p = X0.shape
     if not (0 < k <= p and (q + 1) * p < n):
         raise ValueError("need 0 < k <= p and (q+1) p < n")
+    # the far end of the spectrum: the tighter of Gershgorin's bound and a Lanczos estimate
+    glo, ghi = gershgorin_bounds(A)
+    llo, lhi = lanczos_bounds(A, 32, (seed + BOUND_SEED_OFFSET) % (1 << 64))
+    lo_A, hi_A = max(glo, llo), min(ghi, lhi)
     if which == "smallest":
         if sigma is None:
-            sigma = gershgorin_bounds(A)[1]
+            sigma = hi_A
         B = (sp.identity(n, format="csr") * sigma - A).tocsr()
+        a = sigma - hi_A
 
         def to_orig(mu):
             return sigma - mu
     elif which == "largest":
         sigma = 0.0
         B = A
+        a = lo_A
 
         def to_orig(mu):
             return mu
     else:
         raise ValueError(which)
 
-    # interval [a, b] (Section 5): a = lower spectrum bound, b = smallest Ritz value of orth(X0)
-    a = gershgorin_bounds(B)[0]
+    # interval [a, b] (Section 5): a = lower bound of B's spectrum (above), b = smallest
+    # Ritz value of orth(X0)
     U0 = orth(X0)
     H0 = U0.T @ (B @ U0)
     b = float(jacobi_eigh(H0)[0][-1])
@@ -453,6 +496,7 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
         allw = np.concatenate([Sc, w])
         order = np.argsort(-allw, kind="stable")[:p]
         Xall, mu = allv[:, order], allw[order]
+        padded = Xall.shape[1] < p  # mu_{k+q} of a padding column is no estimate of b
         Xall, mu = pad_ritz(B, Xall, mu, p, pad_pool)
         lam = to_orig(mu)
         res = residual_norms(B, Xall, mu, lam)
@@ -476,9 +520,9 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
         # continuation (eq. contin)
         if maxres <= tol_t:
             tol_t = max(1e-2 * tol_t, tol)
-            b = float(mu[p - 1])
+            b = float(mu[p - 1]) if not padded else b
         elif b_update == "every_arr":
-            b = float(mu[p - 1])
+            b = float(mu[p - 1]) if not padded else b
         # deflation (eq. defl)
         thr = max(1e-14, tol_t ** 2)
         lock = np.zeros(p, dtype=bool)

@@ -561,6 +561,120 @@ arb_status alloc_blocks(arb_ctx ctx, const SolveState& S, BlockSet<T>& B) {
   return ARB_OK;
 }
 
+}  // namespace
+
+// Section 5 estimates the far end of the spectrum (the paper calls eigs); a loose bound
+// widens the filter's damping interval [a, b] and slows the method down, badly for graph
+// Laplacians whose Gershgorin discs reach far beyond the spectrum.  Plain Lanczos (no
+// reorthogonalisation: only the extreme Ritz values are used) on A, then the extreme
+// eigenvalues of the tridiagonal matrix widened by their residual bounds |beta_m y_m| and
+// by 1e-3 max(1, |theta|).
+arb_status arb::lanczos_bounds(arb_ctx ctx, arb_mat mat, int32_t steps, uint64_t seed, double* lo, double* hi) {
+  const int64_t n = mat->n;
+  steps = static_cast<int32_t>(std::min<int64_t>(steps, n));
+  double* base;
+  ARB_TRY(ws<double>(ctx, WS_TALL0, 3 * static_cast<size_t>(n), &base));
+  double *vp = base, *v = base + n, *w = base + 2 * n;
+  double* dot;
+  ARB_TRY(ws<double>(ctx, WS_VEC2, 2, &dot));
+  ARB_TRY(gaussian_fill<double>(ctx, n, 1, seed, v, 1));
+  ARB_TRY(fill(ctx, vp, n, 0.0));
+  double h = 0.0;
+  ARB_TRY(gram<double>(ctx, n, v, 1, 1, v, 1, 1, dot, 1));
+  ARB_TRY(d2h_sync(ctx, &h, dot, sizeof(double)));
+  ARB_TRY(scale_vec(ctx, n, v, v, 1.0 / std::sqrt(h)));
+  std::vector<double> al, be;
+  double bprev = 0.0;
+  for (int j = 0; j < steps; ++j) {
+    SpmmArgs<double> sa;
+    sa.A = mat;
+    sa.ncols = 1;
+    sa.Yin = v;
+    sa.ldy = 1;
+    sa.out = w;
+    sa.ldo = 1;
+    ARB_TRY(spmm_fused<double>(ctx, sa));
+    double aj = 0.0, bj2 = 0.0;
+    ARB_TRY(gram<double>(ctx, n, v, 1, 1, w, 1, 1, dot, 1));
+    ARB_TRY(d2h_sync(ctx, &aj, dot, sizeof(double)));
+    ARB_TRY(lin3(ctx, n, w, aj, v, bprev, vp));
+    ARB_TRY(gram<double>(ctx, n, w, 1, 1, w, 1, 1, dot, 1));
+    ARB_TRY(d2h_sync(ctx, &bj2, dot, sizeof(double)));
+    al.push_back(aj);
+    const double bj = std::sqrt(std::max(bj2, 0.0));
+    be.push_back(bj);
+    if (!(bj > 1e-12 * std::max(1.0, std::fabs(aj)))) break;  // invariant subspace found
+    ARB_TRY(scale_vec(ctx, n, vp, v, 1.0));
+    ARB_TRY(scale_vec(ctx, n, v, w, 1.0 / bj));
+    bprev = bj;
+  }
+  const int m = static_cast<int>(al.size());
+  std::vector<double> T(static_cast<size_t>(m) * m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    T[static_cast<size_t>(i) * m + i] = al[i];
+    if (i + 1 < m) T[static_cast<size_t>(i) * m + i + 1] = T[static_cast<size_t>(i + 1) * m + i] = be[i];
+  }
+  double *Td, *wd, *Vd;
+  ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(m) * m, &Td));
+  ARB_TRY(ws<double>(ctx, WS_SMALL2, static_cast<size_t>(m) * m, &Vd));
+  ARB_TRY(ws<double>(ctx, WS_VEC1, m, &wd));
+  ARB_TRY(h2d(ctx, Td, T.data(), T.size() * sizeof(double)));
+  ARB_TRY(syevj(ctx, m, Td, m, wd, Vd, m, nullptr));
+  std::vector<double> ev(m), V(static_cast<size_t>(m) * m);
+  ARB_TRY(d2h_sync(ctx, ev.data(), wd, m * sizeof(double)));
+  ARB_TRY(d2h_sync(ctx, V.data(), Vd, V.size() * sizeof(double)));
+  const double bm = be[m - 1];
+  const double rhi = std::fabs(bm * V[static_cast<size_t>(m - 1) * m + 0]);
+  const double rlo = std::fabs(bm * V[static_cast<size_t>(m - 1) * m + (m - 1)]);
+  *hi = ev[0] + rhi + 1e-3 * std::max(1.0, std::fabs(ev[0]));
+  *lo = ev[m - 1] - rlo - 1e-3 * std::max(1.0, std::fabs(ev[m - 1]));
+  return ARB_OK;
+}
+
+namespace {
+
+// The augmented subspace kept fewer than p directions (orth truncated a block that lost
+// numerical rank): complete the Ritz block with Gaussian columns (stream seed + outer
+// iteration) orthogonalised twice against the count Ritz vectors, orthonormalised and
+// orthogonalised again, with their Rayleigh quotients as Ritz values - the same completion
+// the oracle makes.
+template <typename T>
+arb_status pad_ritz_block(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, int32_t count, int outer) {
+  const int64_t n = S.n;
+  const int32_t need = S.p - count;
+  T* P = B.wk.T2;  // free after the Rayleigh-Ritz step
+  ARB_TRY(gaussian_fill<T>(ctx, n, need, S.o.seed + 1000003ull * static_cast<uint64_t>(S.info.outer_iters + outer),
+                           P, B.ld));
+  for (int pass = 0; pass < 2; ++pass) ARB_TRY(project_out<T>(ctx, n, B.Xall, B.ld, count, P, B.ld, need));
+  int32_t r = 0;
+  ARB_TRY(orth<T>(ctx, n, P, B.ld, need, B.wk.T1, B.ld, B.wk.U, B.ldm, &r));
+  if (r < need) return set_error(ctx, ARB_BREAKDOWN, "solve: padding columns lost rank");
+  for (int pass = 0; pass < 2; ++pass) ARB_TRY(project_out<T>(ctx, n, B.Xall, B.ld, count, B.wk.T1, B.ld, need));
+  ARB_TRY((copy_block<T, T>(ctx, n, B.wk.T1, B.ld, need, B.Xall + count, B.ld)));
+  // Rayleigh quotients x^T B x / x^T x of the padding columns
+  SpmmArgs<T> sa;
+  sa.A = mat;
+  sa.ncols = need;
+  sa.Yin = B.Xall + count;
+  sa.ldy = B.ld;
+  sa.alpha = S.op_scale;
+  sa.beta = S.op_shift;
+  sa.colred = S.ss;
+  sa.dot_with_yin = true;
+  ARB_TRY(spmm_fused<T>(ctx, sa));
+  std::vector<double> xbx(need), xx(need), mu(need);
+  ARB_TRY(d2h_sync(ctx, xbx.data(), S.ss, need * sizeof(double)));
+  sa.alpha = 0.0;  // out = x: the column sums of squares are x^T x
+  sa.beta = 1.0;
+  sa.dot_with_yin = false;
+  ARB_TRY(spmm_fused<T>(ctx, sa));
+  ARB_TRY(d2h_sync(ctx, xx.data(), S.ss, need * sizeof(double)));
+  for (int c = 0; c < need; ++c) mu[c] = xx[c] > 0.0 ? xbx[c] / xx[c] : 0.0;
+  ARB_TRY(h2d(ctx, S.mu + count, mu.data(), need * sizeof(double)));
+  S.info.spmm_cols += need;
+  return ARB_OK;
+}
+
 // Outer iterations of Algorithm 8 with blocks of type T until the outer stop rule holds for
 // `tol_phase` (or a stall / maxit / all-locked stop).  rc_floor bounds the inner-stop
 // threshold from below (reading c7: 100 u of the filter precision); lock = false disables
@@ -644,10 +758,14 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     // the p leading pairs of (Q_c, Sigma_c) and (U V, theta)
     ARB_TRY(select_top(ctx, S.sigc, S.nl, S.theta, m, p, S.imap, S.mu));
     ARB_TRY(d2h_sync(ctx, S.h_map.data(), S.imap, p * sizeof(int32_t)));
-    for (int s = 0; s < p; ++s)
-      if (S.h_map[s] < 0) return set_error(ctx, ARB_BREAKDOWN, "solve: fewer Ritz pairs than the block width");
-    std::vector<int32_t> newcols, src(p);
-    for (int s = 0; s < p; ++s) {
+    int32_t count = 0;  // Ritz pairs available (the rest of the block is padded below)
+    while (count < p && S.h_map[count] >= 0) ++count;
+    // mu_{k+q} is an estimate of lambda_{k+q} only when it is a Ritz value: after padding
+    // (a Rayleigh quotient of a random column) b keeps its previous value
+    const bool b_ok = (count == p);
+    if (count == 0) return set_error(ctx, ARB_BREAKDOWN, "solve: no Ritz pairs");
+    std::vector<int32_t> newcols, src(count);
+    for (int s = 0; s < count; ++s) {
       if (S.h_map[s] < S.nl) {
         src[s] = -S.h_map[s] - 1;  // locked column
       } else {
@@ -662,7 +780,8 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
       ARB_TRY(gemm_tall<T>(ctx, n, B.wk.U, B.ldm, m, S.Vsel, pn, pn, 1.0, 0.0, B.wk.T1, B.ld));
     }
     ARB_TRY(upload_ints(ctx, S.imap, src));
-    ARB_TRY(gather_cols2<T>(ctx, n, B.wk.T1, B.ld, B.Qc, B.ld, S.imap, p, B.Xall, B.ld));
+    ARB_TRY(gather_cols2<T>(ctx, n, B.wk.T1, B.ld, B.Qc, B.ld, S.imap, count, B.Xall, B.ld));
+    if (count < p) ARB_TRY(pad_ritz_block(ctx, mat, S, B, count, j));
     // residuals (eq. resi): ||B x - mu x|| with the sign folded (-B x + mu x)
     {
       SpmmArgs<T> sa;
@@ -708,7 +827,7 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     if (maxres <= tol_phase) {
       S.stop = ARB_STOP_CONVERGED;
       if (continue_on_phase_tol && tol_phase > S.tol) {
-        S.b = S.h_mu[p - 1];
+        if (b_ok) S.b = S.h_mu[p - 1];
         if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
       }
       return ARB_OK;
@@ -717,7 +836,7 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     // no longer halves maxres; hand over to FP64 with the best interval estimate
     if (stop_on_stagnation && j >= 2 && maxres > 0.5 * prev_maxres) {
       S.stop = ARB_STOP_STALLED;
-      S.b = S.h_mu[p - 1];
+      if (b_ok) S.b = S.h_mu[p - 1];
       if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
       return ARB_OK;
     }
@@ -732,9 +851,9 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     }
     if (maxres <= S.tol_t) {  // continuation, eq. contin
       S.tol_t = std::max(1e-2 * S.tol_t, S.tol);
-      S.b = S.h_mu[p - 1];
+      if (b_ok) S.b = S.h_mu[p - 1];
     } else if (S.o.b_update == 1) {  // Section 5: a better estimate of lambda_{k+q} after each ARR
-      S.b = S.h_mu[p - 1];
+      if (b_ok) S.b = S.h_mu[p - 1];
     }
     if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
     const double thr = std::max(1e-14, S.tol_t * S.tol_t);  // eq. defl
@@ -793,16 +912,19 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
   S.df_filter = (o.precision == ARB_MIXED_DF);
   S.trace = getenv("ARB_TRACE") != nullptr;
 
-  // operator B = op_scale A + op_shift I whose largest eigenpairs are wanted
-  double glo, ghi;
+  // operator B = op_scale A + op_shift I whose largest eigenpairs are wanted; the far end
+  // of A's spectrum from the tighter of Gershgorin's bound and a Lanczos estimate
+  double glo, ghi, llo, lhi;
   ARB_TRY(gershgorin(ctx, mat, &glo, &ghi));
+  ARB_TRY(lanczos_bounds(ctx, mat, 32, o.seed + 0x9E3779B97F4A7C15ull, &llo, &lhi));
+  const double hi_A = std::min(ghi, lhi), lo_A = std::max(glo, llo);
   if (S.smallest) {
-    S.sigma = std::isnan(o.shift_sigma) ? ghi : o.shift_sigma;
+    S.sigma = std::isnan(o.shift_sigma) ? hi_A : o.shift_sigma;
     S.op_scale = -1.0;
     S.op_shift = S.sigma;
-    S.a = S.sigma - ghi;  // Gershgorin lower bound of sigma I - A
+    S.a = S.sigma - hi_A;  // lower bound of sigma I - A
   } else {
-    S.a = glo;
+    S.a = lo_A;
   }
 
   // device buffers
@@ -903,8 +1025,8 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     // tightens tol_t below what FP32 resolves).
     // FP32 residual floor ~ 32 u32 ||B|| (||B|| bounded by Gershgorin): the FP32 phase ends
     // there, at tol_switch, or as soon as an outer iteration stops halving maxres.
-    const double normB = std::max(std::fabs(S.sigma - glo), std::fabs(S.sigma - ghi));
-    const double floor32 = 32.0 * 5.96e-8 * (S.smallest ? normB : std::max(std::fabs(glo), std::fabs(ghi)));
+    const double normB = std::max(std::fabs(S.sigma - lo_A), std::fabs(S.sigma - hi_A));
+    const double floor32 = 32.0 * 5.96e-8 * (S.smallest ? normB : std::max(std::fabs(lo_A), std::fabs(hi_A)));
     const double sw = std::max(o.tol_switch > 0.0 ? o.tol_switch : 1e-5, floor32);
     const double tol_phase = std::max(sw, tol);
     const double tol_t64 = S.tol_t;  // the FP64 phase starts the paper's continuation at tol_1
@@ -913,10 +1035,22 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     S.info.outer_iters_fp32 = S.info.outer_iters;
     S.tol_t = tol_t64;
     const bool done32 = (S.stop == ARB_STOP_CONVERGED || S.stop == ARB_STOP_NEAR_TOL) && tol_phase <= tol;
-    // Phase 2: FP64 refinement from the FP32 Ritz block (Algorithm 8 continued in FP64)
-    ARB_TRY((copy_block<float, double>(ctx, n, F.Xall, F.ld, p, D.Xall, D.ld)));
-    if (!done32) {
-      ARB_TRY((copy_block<double, double>(ctx, n, D.Xall, D.ld, p, D.X, D.ld)));
+    // Phase 2: FP64 refinement from the FP32 Ritz block (Algorithm 8 continued in FP64).
+    // If the FP32 phase made no usable progress - its block lost rank (the filter's dynamic
+    // range outran FP32 before the inner stop rule could see it, e.g. an isolated extreme
+    // eigenvalue and a crude first b) or maxres stayed above 1e-2 - the refinement starts
+    // over from X0 with the first interval estimate instead, as the FP64 method would.
+    const bool fp32_failed = !(S.info.maxres <= 1e-2) || S.info.last_rank < p;
+    if (fp32_failed) {
+      S.b = S.info.b0;
+      if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+      S.tol_t = tol_t64;
+    } else {
+      ARB_TRY((copy_block<float, double>(ctx, n, F.Xall, F.ld, p, D.Xall, D.ld)));
+    }
+    if (!done32 || fp32_failed) {
+      // D.X still holds X0 (the FP32 phase ran on its own blocks)
+      if (!fp32_failed) ARB_TRY((copy_block<double, double>(ctx, n, D.Xall, D.ld, p, D.X, D.ld)));
       S.w = p;
       S.nl = 0;
       ARB_TRY(fill(ctx, S.xs, S.w, 1.0));

@@ -243,6 +243,13 @@ arb_status symmetrize(arb_ctx ctx, int32_t m, double* H, int64_t ldh);
 // the upper blocks mirrored below
 arb_status symmetrize_upper_blocks(arb_ctx ctx, int32_t m, double* H, int64_t ldh, const int32_t* off,
                                   const int32_t* rk, int32_t nblk);
+// w <- w - a v - b u and dst <- s src (n-vectors)
+arb_status lin3(arb_ctx ctx, int64_t n, double* w, double a, const double* v, double b, const double* u);
+arb_status scale_vec(arb_ctx ctx, int64_t n, double* dst, const double* src, double s);
+// Lanczos estimates of the extreme eigenvalues of A with residual-based margins
+// (*lo <= lambda_min, *hi >= lambda_max up to the Lanczos residual bound), from `steps`
+// steps started at the Gaussian column of Philox stream `seed`.
+arb_status lanczos_bounds(arb_ctx ctx, arb_mat mat, int32_t steps, uint64_t seed, double* lo, double* hi);
 // G <- diag(s) G diag(s)
 arb_status scale_sym(arb_ctx ctx, int32_t m, double* G, int64_t ldg, const double* s);
 // s[c] = 1/sqrt(ss[c]) (0 when ss[c] == 0)
@@ -262,8 +269,8 @@ arb_status select_top(arb_ctx ctx, const double* vlock, int32_t nl, const double
                       int32_t nn, int32_t p, int32_t* map, double* val);
 // Gaussian fill from the Philox4x32-10 stream `seed` (row-major n x ncols, element
 // i*ncols + j), same numbering as the input generators.
-arb_status gaussian_fill(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, double* X,
-                         int64_t ldx);
+template <typename T>
+arb_status gaussian_fill(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, T* X, int64_t ldx);
 
 // ---------------------------------------------------------------- tensor-core Gram (tc.cu)
 // part[s] (na x nb, FP64) = X^T Y over rows [s*rows, (s+1)*rows) of FP32 blocks by

@@ -110,6 +110,18 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nsplit, 
   C[static_cast<int64_t>(i) * ldc + j] = s;
 }
 
+// w <- w - a v - b u (the three-term recurrence of Lanczos)
+__global__ void lin3_kernel(int64_t n, double* __restrict__ w, double a, const double* __restrict__ v, double b,
+                            const double* __restrict__ u) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i < n) w[i] = w[i] - a * v[i] - b * u[i];
+}
+
+__global__ void scale_vec_kernel(int64_t n, double* __restrict__ dst, const double* __restrict__ src, double s) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i < n) dst[i] = src[i] * s;
+}
+
 // Out[r][c] = alpha * sum_k In[r][k] W[k][c] + beta * Out[r][c]; a 64 x (16 RN) output tile
 // per CTA, each thread owning 4 x RN outputs; W (FP64) is rounded to T as it is staged.
 template <typename T, int RN>
@@ -595,7 +607,8 @@ __device__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t k0, uint32_t k1
   out[3] = c[3];
 }
 
-__global__ void gaussian_fill_kernel(int64_t n, int ncols, uint64_t seed, double* X, int64_t ldx) {
+template <typename T>
+__global__ void gaussian_fill_kernel(int64_t n, int ncols, uint64_t seed, T* X, int64_t ldx) {
   const int64_t pair = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t total = n * ncols;
   if (2 * pair >= total) return;
@@ -609,8 +622,8 @@ __global__ void gaussian_fill_kernel(int64_t n, int ncols, uint64_t seed, double
   double sn, cs;
   sincospi(2.0 * u2, &sn, &cs);
   const int64_t e0 = 2 * pair;
-  X[(e0 / ncols) * ldx + (e0 % ncols)] = r * cs;
-  if (e0 + 1 < total) X[((e0 + 1) / ncols) * ldx + ((e0 + 1) % ncols)] = r * sn;
+  X[(e0 / ncols) * ldx + (e0 % ncols)] = static_cast<T>(r * cs);
+  if (e0 + 1 < total) X[((e0 + 1) / ncols) * ldx + ((e0 + 1) % ncols)] = static_cast<T>(r * sn);
 }
 
 inline int blocks_for(int64_t count, int threads) {
@@ -871,6 +884,18 @@ arb_status symmetrize_upper_blocks(arb_ctx ctx, int32_t m, double* H, int64_t ld
   return ARB_OK;
 }
 
+arb_status lin3(arb_ctx ctx, int64_t n, double* w, double a, const double* v, double b, const double* u) {
+  lin3_kernel<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(n, w, a, v, b, u);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status scale_vec(arb_ctx ctx, int64_t n, double* dst, const double* src, double s) {
+  scale_vec_kernel<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(n, dst, src, s);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
 arb_status scale_sym(arb_ctx ctx, int32_t m, double* G, int64_t ldg, const double* s) {
   if (m <= 0) return ARB_OK;
   scale_sym_kernel<<<blocks_for(static_cast<int64_t>(m) * m, 256), 256, 0, ctx->stream>>>(m, G, ldg, s);
@@ -918,11 +943,14 @@ arb_status select_top(arb_ctx ctx, const double* vlock, int32_t nl, const double
   return ARB_OK;
 }
 
-arb_status gaussian_fill(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, double* X, int64_t ldx) {
+template <typename T>
+arb_status gaussian_fill(arb_ctx ctx, int64_t n, int32_t ncols, uint64_t seed, T* X, int64_t ldx) {
   const int64_t pairs = (n * ncols + 1) / 2;
-  gaussian_fill_kernel<<<blocks_for(pairs, 256), 256, 0, ctx->stream>>>(n, ncols, seed, X, ldx);
+  gaussian_fill_kernel<T><<<blocks_for(pairs, 256), 256, 0, ctx->stream>>>(n, ncols, seed, X, ldx);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }
+template arb_status gaussian_fill<double>(arb_ctx, int64_t, int32_t, uint64_t, double*, int64_t);
+template arb_status gaussian_fill<float>(arb_ctx, int64_t, int32_t, uint64_t, float*, int64_t);
 
 }  // namespace arb

@@ -421,6 +421,23 @@ def test_solve_bruteforce_random_sparse(arb, ctx, which):
     np.testing.assert_allclose(r.evals, want, atol=1e-9 * np.abs(wref).max())
 
 
+@pytest.mark.parametrize("precision", [0, 2])
+def test_solve_chung_lu_scaled(arb, ctx, precision):
+    # the power-law graph Laplacian family of the Chung-Lu workload, scaled down: rows from
+    # 2 to hundreds of nonzeros (the general, non-short-row SpMM), FP32-rounded values;
+    # k smallest against LAPACK
+    A, _ = I.chung_lu_laplacian(3000, seed=11)
+    k, p = 20, 30
+    X0 = I.gaussian_block(A.n, p, 5)
+    r = _solve(arb, ctx, A, k, p, 1, 15, 1e-8, X0, precision=precision)
+    assert r.status == arb.ARB_OK, r.info
+    lam = np.linalg.eigvalsh(A.to_dense())[:k]
+    np.testing.assert_allclose(r.evals, lam, atol=1e-9)
+    Q = r.evecs
+    R = scipy_of(A) @ Q - Q * r.evals[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= 1e-8 * 8.0
+
+
 def test_solve_lockstep_fixed_schedule(arb, ctx):
     A = I.laplacian_2d(16)
     X0 = I.gaussian_block(A.n, 12, 10)

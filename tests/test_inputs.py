@@ -67,3 +67,61 @@ def test_laplacian_3d_128_count_formula():
     # The 128^3 operator has 7*128^3 - 6*128^2 entries; checked through the formula
     # validated above at small m, without building the 2M-row matrix here.
     assert 7 * 128 ** 3 - 6 * 128 ** 2 == 14581760
+
+
+def test_chung_lu_weights_hit_mean_and_max():
+    # c and i0 are fixed by the two constraints (mean 16, largest 5000) and the power law
+    from paper_1507_06078_gb300.inputs import chung_lu_weights
+    w = chung_lu_weights(100000)
+    assert abs(w.mean() - 16.0) <= 1e-6 * 16.0
+    assert w[0] == 5000.0
+    assert np.all(np.diff(w) < 0)
+    # log-log slope of a power law with exponent -1/(beta-1) = -2/3 far from i0
+    i = np.array([20000, 80000])
+    r = np.log(w[i[1]] / w[i[0]])
+    assert -2.0 / 3.0 - 0.05 < r / np.log((i[1] + 1.0) / (i[0] + 1.0)) < -2.0 / 3.0 + 0.05
+
+
+def test_chung_lu_laplacian_invariants():
+    # normalized Laplacian I - D^-1/2 W D^-1/2 of a connected graph: symmetric, unit
+    # diagonal, off-diagonals -1/sqrt(d_u d_v), D^1/2 1 in its kernel (up to the FP32
+    # rounding of the values), spectrum in [0, 2], one connected component
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    from paper_1507_06078_gb300.inputs import chung_lu_laplacian
+    A, ids = chung_lu_laplacian(3000, seed=7)
+    L = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+    assert abs(L - L.T).max() == 0.0
+    assert np.all(L.diagonal() == 1.0)
+    W = -(L - sp.identity(A.n))
+    W.eliminate_zeros()
+    d = np.asarray((W != 0).sum(axis=1)).ravel().astype(np.float64)
+    r, c = W.nonzero()
+    np.testing.assert_allclose(np.asarray(W[r, c]).ravel(), 1.0 / np.sqrt(d[r] * d[c]), rtol=1e-7)
+    assert connected_components(W, directed=False)[0] == 1
+    z = np.sqrt(d)
+    assert np.abs(L @ z).max() <= 1e-6 * np.abs(z).max()
+    lam = np.linalg.eigvalsh(L.toarray())
+    assert lam[0] > -1e-6 and lam[-1] < 2.0 + 1e-6 and abs(lam[0]) < 1e-6
+    assert len(ids) == A.n and np.all(np.diff(ids) > 0)
+
+
+def test_diffusion_2d_invariants():
+    # conductance Laplacian with Dirichlet ghost nodes: symmetric, 5-point structure,
+    # interior rows sum to zero, boundary rows to their (positive) boundary conductances,
+    # positive definite; the same seed gives the same matrix
+    from paper_1507_06078_gb300.inputs import diffusion_2d
+    side = 12
+    A = diffusion_2d(side, 3)
+    M = A.to_dense()
+    assert np.array_equal(M, M.T)
+    assert A.rowptr[-1] == 5 * side * side - 4 * side
+    rs = M.sum(axis=1).reshape(side, side)
+    interior = rs[1:-1, 1:-1]
+    assert np.abs(interior).max() <= 1e-12 * np.abs(M).max()
+    boundary = np.concatenate([rs[0, :], rs[-1, :], rs[1:-1, 0], rs[1:-1, -1]])
+    assert np.all(boundary > 0)
+    assert np.linalg.eigvalsh(M)[0] > 0
+    assert np.array_equal(diffusion_2d(side, 3).val, A.val)
+    assert not np.array_equal(diffusion_2d(side, 4).val, A.val)

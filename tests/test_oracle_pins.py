@@ -288,3 +288,28 @@ def test_planted_interpolation_nodes_slip_is_caught():
     a_bad = np.linalg.solve(T, np.maximum(t1, 0) ** (10 * d))
     t = -np.cos(np.arange(d + 1) * np.pi / d)
     assert not np.allclose(npc.chebval(t, a_bad), np.maximum(t, 0) ** (10 * d), atol=1e-6)
+
+
+@pytest.mark.parametrize("which", ["laplace2d", "diag", "chung_lu"])
+def test_lanczos_bounds_enclose_the_spectrum(which):
+    # the estimates of the far ends of the spectrum contain the true extreme eigenvalues
+    # (residual margins) and are close to them (Kaniel-Paige: extreme Ritz values converge
+    # first)
+    import scipy.sparse as sp
+
+    from paper_1507_06078_gb300 import inputs as I
+    if which == "laplace2d":
+        A = sp.csr_matrix(I.laplacian_2d(20).to_dense())
+    elif which == "diag":
+        A = sp.diags(np.linspace(-3.0, 5.0, 500)).tocsr()
+    else:
+        C, _ = I.chung_lu_laplacian(1500, seed=3)
+        A = sp.csr_matrix((C.val, C.col, C.rowptr), shape=(C.n, C.n))
+    lam = np.linalg.eigvalsh(A.toarray())
+    lo, hi = O.lanczos_bounds(A, 32, 99)
+    assert lo <= lam[0] and hi >= lam[-1]
+    span = lam[-1] - lam[0]
+    assert hi - lam[-1] <= 0.05 * span and lam[0] - lo <= 0.05 * span
+    # far tighter than Gershgorin on the graph Laplacian
+    if which == "chung_lu":
+        assert hi < 0.5 * O.gershgorin_bounds(A)[1]
