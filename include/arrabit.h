@@ -140,6 +140,17 @@ void arb_options_default(arb_options* opts, int32_t k);
 arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz, const int32_t* rowptr,
                                  const int32_t* col, const double* val, int ptr_on_device,
                                  arb_mat* out);
+/* The same with FP32 values (val: float32[nnz], host or device as ptr_on_device): they are
+ * widened to FP64 on the device and also kept as the FP32 copy the mixed paths use. */
+arb_status arb_matrix_create_csr_f32(arb_ctx ctx, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                     const int32_t* col, const float* val, int ptr_on_device,
+                                     arb_mat* out);
+/* Host-side symmetry check of CSR arrays (host pointers): ARB_OK when every stored a_ij
+ * (duplicates summed) matches a_ji to rel_tol * max|a|, ARB_NOT_SYMMETRIC otherwise,
+ * ARB_INVALID_ARG for malformed arrays.  The method assumes symmetry (Section 1); the
+ * matrix-creation calls take it as the caller's promise, this checks it. */
+arb_status arb_csr_check_symmetric(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                                   const double* val, double rel_tol);
 arb_status arb_matrix_destroy(arb_mat mat);
 /* Gershgorin interval [lo, hi] of A (host outputs); stands in for the paper's eigs
  * estimate of lambda_n (Section 5, "Estimation of lambda_n and lambda_{k+q}"). */

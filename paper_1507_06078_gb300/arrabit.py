@@ -75,6 +75,8 @@ _PROTOS = {
     "arb_kernel_launches": (_i64, [_vp]),
     "arb_options_default": (None, [C.POINTER(arb_options), _i32]),
     "arb_matrix_create_csr": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, C.c_int, C.POINTER(_vp)]),
+    "arb_matrix_create_csr_f32": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, C.c_int, C.POINTER(_vp)]),
+    "arb_csr_check_symmetric": (_i32, [_i64, _i64, _vp, _vp, _vp, _dbl]),
     "arb_matrix_destroy": (_i32, [_vp]),
     "arb_matrix_gershgorin": (_i32, [_vp, _vp, C.POINTER(_dbl), C.POINTER(_dbl)]),
     "arb_solve": (_i32, [_vp, _vp, _i32, _i32, _dbl, C.POINTER(arb_options), _vp, C.c_int, _vp, _vp, _i64,
@@ -189,14 +191,16 @@ class Matrix:
     """A CSR matrix copied into library-owned device memory."""
 
     def __init__(self, ctx: Context, n: int, rowptr, col, val):
+        """val: float64 values, or float32 (arb_matrix_create_csr_f32)."""
         lib = load()
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
         col = np.ascontiguousarray(col, dtype=np.int32)
-        val = np.ascontiguousarray(val, dtype=np.float64)
+        f32 = np.asarray(val).dtype == np.float32
+        val = np.ascontiguousarray(val, dtype=np.float32 if f32 else np.float64)
         h = _vp()
-        st = lib.arb_matrix_create_csr(ctx.handle, n, col.shape[0], rowptr.ctypes.data, col.ctypes.data,
-                                       val.ctypes.data, 0, C.byref(h))
-        _check(ctx, st, "arb_matrix_create_csr")
+        fn = lib.arb_matrix_create_csr_f32 if f32 else lib.arb_matrix_create_csr
+        st = fn(ctx.handle, n, col.shape[0], rowptr.ctypes.data, col.ctypes.data, val.ctypes.data, 0, C.byref(h))
+        _check(ctx, st, "arb_matrix_create_csr_f32" if f32 else "arb_matrix_create_csr")
         self.ctx, self.handle, self.n, self.nnz = ctx, h, n, col.shape[0]
         ctx._mats.add(self)
 
@@ -279,6 +283,15 @@ def arb_solve(ctx: Context, mat: Matrix, k: int, which: int, tol: float, opts: a
     if out is not None:
         vecs = out.T
     return SolveResult(st, ev, vecs, info.as_dict())
+
+
+def arb_csr_check_symmetric(n: int, rowptr, col, val, rel_tol: float = 0.0) -> int:
+    """ARB_OK or ARB_NOT_SYMMETRIC (host arrays; no context, no device)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    return int(load().arb_csr_check_symmetric(n, col.shape[0], rowptr.ctypes.data, col.ctypes.data,
+                                              val.ctypes.data, rel_tol))
 
 
 def arb_gaussian_block(ctx: Context, n: int, ncols: int, seed: int, X=None):

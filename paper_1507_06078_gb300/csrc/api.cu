@@ -212,9 +212,10 @@ extern "C" void arb_options_default(arb_options* o, int32_t k) {
   o->seed = 20150722ull;
 }
 
-extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz, const int32_t* rowptr,
-                                            const int32_t* col, const double* val, int ptr_on_device,
-                                            arb_mat* out) {
+// idx_on_device: rowptr/col are device pointers; val_on_device: val is
+static arb_status create_csr(arb_ctx ctx, int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                             const double* val, int idx_on_device, int val_on_device, arb_mat* out) {
+  const int ptr_on_device = idx_on_device;
   if (!ctx || !out || n <= 0 || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val)))
     return set_error(ctx, ARB_INVALID_ARG, "matrix_create_csr: bad arguments");
   if (n > INT32_MAX || nnz > INT32_MAX)
@@ -232,6 +233,12 @@ extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz,
       if (col[e] < 0 || col[e] >= n) return set_error(ctx, ARB_INVALID_ARG, "matrix_create_csr: column out of range");
   }
   ARB_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (ptr_on_device) {  // the longest row selects the short-row SpMM: read the row pointers once
+    std::vector<int32_t> hrp(static_cast<size_t>(n) + 1);
+    ARB_CUDA(ctx, cudaMemcpy(hrp.data(), rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    max_row = 0;
+    for (int64_t i = 0; i < n; ++i) max_row = std::max<int32_t>(max_row, hrp[i + 1] - hrp[i]);
+  }
   arb_mat m = new arb_mat_s();
   m->ctx = ctx;
   m->device = ctx->device;
@@ -239,12 +246,13 @@ extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz,
   m->n = n;
   m->nnz = nnz;
   const cudaMemcpyKind kind = ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind vkind = val_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   cudaError_t e = cudaMalloc(&m->rowptr, (n + 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&m->col, std::max<int64_t>(nnz, 1) * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&m->val, std::max<int64_t>(nnz, 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->rowptr, rowptr, (n + 1) * sizeof(int32_t), kind, ctx->stream);
   if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(m->col, col, nnz * sizeof(int32_t), kind, ctx->stream);
-  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(m->val, val, nnz * sizeof(double), kind, ctx->stream);
+  if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(m->val, val, nnz * sizeof(double), vkind, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     cudaFree(m->rowptr);
@@ -254,6 +262,76 @@ extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz,
     return cuda_error(ctx, e, "matrix upload", __FILE__, __LINE__);
   }
   *out = m;
+  return ARB_OK;
+}
+
+extern "C" arb_status arb_matrix_create_csr(arb_ctx ctx, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                            const int32_t* col, const double* val, int ptr_on_device,
+                                            arb_mat* out) {
+  return create_csr(ctx, n, nnz, rowptr, col, val, ptr_on_device, ptr_on_device, out);
+}
+
+extern "C" arb_status arb_matrix_create_csr_f32(arb_ctx ctx, int64_t n, int64_t nnz, const int32_t* rowptr,
+                                                const int32_t* col, const float* val, int ptr_on_device,
+                                                arb_mat* out) {
+  if (!ctx || !out || (nnz > 0 && !val)) return set_error(ctx, ARB_INVALID_ARG, "matrix_create_csr_f32: bad arguments");
+  ARB_CUDA(ctx, cudaSetDevice(ctx->device));
+  // widen on the device: the values go up once as FP32 and are kept in both precisions
+  float* v32 = nullptr;
+  double* v64 = nullptr;
+  ARB_CUDA(ctx, cudaMalloc(&v32, std::max<int64_t>(nnz, 1) * sizeof(float)));
+  cudaError_t e = cudaMalloc(&v64, std::max<int64_t>(nnz, 1) * sizeof(double));
+  if (e == cudaSuccess && nnz > 0)
+    e = cudaMemcpyAsync(v32, val, nnz * sizeof(float), ptr_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(v32);
+    cudaFree(v64);
+    return cuda_error(ctx, e, "matrix_create_csr_f32 upload", __FILE__, __LINE__);
+  }
+  arb_status st = ARB_OK;
+  if (nnz > 0) st = copy_block<float, double>(ctx, nnz, v32, 1, 1, v64, 1);
+  if (st == ARB_OK) st = create_csr(ctx, n, nnz, rowptr, col, v64, ptr_on_device, 1, out);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(v64);
+  if (st != ARB_OK) {
+    cudaFree(v32);
+    return st;
+  }
+  (*out)->val32 = v32;
+  return ARB_OK;
+}
+
+extern "C" arb_status arb_csr_check_symmetric(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                                              const double* val, double rel_tol) {
+  if (n <= 0 || nnz < 0 || !rowptr || (nnz > 0 && (!col || !val)) || !(rel_tol >= 0.0)) return ARB_INVALID_ARG;
+  if (rowptr[0] != 0 || rowptr[n] != nnz) return ARB_INVALID_ARG;
+  // (row, col) -> value for every stored entry, duplicates summed; then a_ij vs a_ji
+  std::vector<std::pair<int64_t, double>> e(static_cast<size_t>(nnz));
+  double amax = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) return ARB_INVALID_ARG;
+    for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      if (col[k] < 0 || col[k] >= n) return ARB_INVALID_ARG;
+      e[k] = {i * n + col[k], val[k]};
+      amax = std::max(amax, std::fabs(val[k]));
+    }
+  }
+  std::sort(e.begin(), e.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  std::vector<std::pair<int64_t, double>> u;
+  for (const auto& x : e) {
+    if (!u.empty() && u.back().first == x.first) u.back().second += x.second;
+    else u.push_back(x);
+  }
+  const double tol = rel_tol * amax;
+  for (const auto& x : u) {
+    const int64_t i = x.first / n, j = x.first % n;
+    if (i == j) continue;
+    const auto it = std::lower_bound(u.begin(), u.end(), j * n + i,
+                                     [](const auto& a, int64_t key) { return a.first < key; });
+    const double mirror = (it != u.end() && it->first == j * n + i) ? it->second : 0.0;
+    if (std::fabs(x.second - mirror) > tol) return ARB_NOT_SYMMETRIC;
+  }
   return ARB_OK;
 }
 

@@ -438,6 +438,21 @@ def test_solve_chung_lu_scaled(arb, ctx, precision):
     assert np.linalg.norm(R, axis=0).max() <= 1e-8 * 8.0
 
 
+def test_matrix_from_fp32_values(arb, ctx):
+    # FP32 values widened on the device give the same matrix (and solve) as the FP64 upload
+    # of the same numbers; device-pointer uploads record the longest row too
+    A, _ = I.chung_lu_laplacian(1200, seed=2)  # values are FP32 numbers already
+    m64 = arb.Matrix.from_csr(ctx, A)
+    m32 = arb.Matrix(ctx, A.n, A.rowptr, A.col, A.val.astype(np.float32))
+    X = dev(I.gaussian_block(A.n, 8, 3))
+    np.testing.assert_array_equal(host(arb.arb_spmm(ctx, m32, 1.0, 0.0, X)), host(arb.arb_spmm(ctx, m64, 1.0, 0.0, X)))
+    o = arb.arb_options_default(6)
+    o.p, o.q, o.degree = 10, 1, 10
+    r32 = arb.arb_solve(ctx, m32, 6, 1, 1e-9, o, x0=I.gaussian_block(A.n, 10, 4))
+    r64 = arb.arb_solve(ctx, m64, 6, 1, 1e-9, o, x0=I.gaussian_block(A.n, 10, 4))
+    np.testing.assert_array_equal(r32.evals, r64.evals)
+
+
 def test_solve_lockstep_fixed_schedule(arb, ctx):
     A = I.laplacian_2d(16)
     X0 = I.gaussian_block(A.n, 12, 10)

@@ -7,6 +7,7 @@ import pytest
 
 from paper_1507_06078_gb300 import arrabit as arb
 from paper_1507_06078_gb300 import build as B
+from paper_1507_06078_gb300 import inputs as I
 
 
 @pytest.fixture(scope="module")
@@ -63,3 +64,26 @@ def test_server_footprint_formula(lib):
     assert fdf == fm + 5000 * 8  # plus the double-float copy of A's values
     assert arb.arb_server_footprint(1000, 5000, 30, 1, 7) == -1
     assert arb.arb_server_footprint(0, 0, 30, 1, 0) == -1
+
+
+def test_symmetry_check_host_only(lib):
+    # host-side check of CSR arrays (no device involved): stencil Laplacians and a
+    # symmetric random matrix pass, a one-sided perturbation or entry fails, malformed
+    # arrays are rejected
+    import scipy.sparse as sp
+    A = I.laplacian_3d(6)
+    assert arb.arb_csr_check_symmetric(A.n, A.rowptr, A.col, A.val) == arb.ARB_OK
+    rng = np.random.default_rng(1)
+    M = sp.random(300, 300, density=0.05, random_state=rng, format="csr")
+    M = (M + M.T).tocsr()
+    assert arb.arb_csr_check_symmetric(300, M.indptr, M.indices, M.data) == arb.ARB_OK
+    v = M.data.copy()
+    v[5] += 1e-6
+    assert arb.arb_csr_check_symmetric(300, M.indptr, M.indices, v) == arb.ARB_NOT_SYMMETRIC
+    assert arb.arb_csr_check_symmetric(300, M.indptr, M.indices, v, 1e-5) == arb.ARB_OK
+    U = sp.triu(M, k=1).tocsr()  # strictly upper part only
+    if U.nnz:
+        assert arb.arb_csr_check_symmetric(300, U.indptr, U.indices, U.data) == arb.ARB_NOT_SYMMETRIC
+    bad = A.rowptr.copy()
+    bad[-1] += 1
+    assert arb.arb_csr_check_symmetric(A.n, bad, A.col, A.val) == arb.ARB_INVALID_ARG
