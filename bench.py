@@ -397,15 +397,15 @@ def run_dense_only(args):
     ctx_df = arb.Context(0)
     ctx_df.set_dense_df(True)
 
-    def timed(f, reps=3):
+    def timed(f, reps=3, c=ctx):
         f()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(ctx.stream)
+        e0.record(c.stream)
         for _ in range(reps):
             f()
-        e1.record(ctx.stream)
+        e1.record(c.stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
@@ -418,11 +418,12 @@ def run_dense_only(args):
     del U32, AU32
     X64 = torch.randn((n, p), dtype=torch.float64, device="cuda")
     out["gram_f64_pxp_sym_ms"] = timed(lambda: arb.arb_gram(ctx, X64, X64), reps=1)
-    out["gram_df_pxp_sym_ms"] = timed(lambda: arb.arb_gram(ctx_df, X64, X64), reps=2)
+    out["gram_df_pxp_sym_ms"] = timed(lambda: arb.arb_gram(ctx_df, X64, X64), reps=2, c=ctx_df)
     for mm in (p, m):
         H = torch.randn((mm, mm), dtype=torch.float64, device="cuda")
         H = 0.5 * (H + H.T)
         out[f"syevj_{mm}_ms"] = timed(lambda: arb.arb_syevj(ctx, H), reps=2)
+        out[f"syevj_df_{mm}_ms"] = timed(lambda: arb.arb_syevj(ctx_df, H), reps=2, c=ctx_df)
     print(json.dumps(out))
 
 

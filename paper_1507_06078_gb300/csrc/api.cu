@@ -478,7 +478,7 @@ extern "C" arb_status arb_syevj(arb_ctx ctx, int32_t m, const double* H, int64_t
   if (!ctx || m < 0 || (m > 0 && (!H || !w || !V || ldh < m || ldv < m)))
     return set_error(ctx, ARB_INVALID_ARG, "syevj: bad arguments");
   ARB_CUDA(ctx, cudaSetDevice(ctx->device));
-  return syevj(ctx, m, H, ldh, w, V, ldv, sweeps);
+  return syevj(ctx, m, H, ldh, w, V, ldv, sweeps, jac_tol<double>(ctx), jac_df<double>(ctx));
 }
 
 extern "C" arb_status arb_rcond_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t ncols,
@@ -527,7 +527,7 @@ extern "C" arb_status arb_rayleigh_ritz(arb_ctx ctx, arb_mat mat, double op_scal
   ARB_TRY(ws<double>(ctx, WS_S_VSEL, static_cast<size_t>(r) * r, &V));
   ARB_TRY(gram<double>(ctx, n, U, m, r, AU, m, r, H, r));
   ARB_TRY(symmetrize(ctx, r, H, r));
-  ARB_TRY(syevj(ctx, r, H, r, w, V, r, nullptr));
+  ARB_TRY(syevj(ctx, r, H, r, w, V, r, nullptr, jac_tol<double>(ctx), jac_df<double>(ctx)));
   return gemm_tall<double>(ctx, n, U, m, r, V, r, r, 1.0, 0.0, Y, ldy);
 }
 
@@ -1062,7 +1062,7 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(r) * r, &H));
     ARB_TRY(gram<E>(ctx, n, Bk.wk.U, Bk.ldm, r, Bk.wk.AU, Bk.ldm, r, H, r));
     ARB_TRY(symmetrize(ctx, r, H, r));
-    ARB_TRY(syevj(ctx, r, H, r, S.theta, S.V, r, nullptr, sizeof(E) == 4 ? 1e-10 : 1e-15));
+    ARB_TRY(syevj(ctx, r, H, r, S.theta, S.V, r, nullptr, jac_tol<E>(ctx), jac_df<E>(ctx)));
     ARB_TRY(d2h_sync(ctx, &S.b, S.theta + (r - 1), sizeof(double)));
     S.info.spmm_cols += r;
     return ARB_OK;

@@ -80,6 +80,7 @@ struct arb_ctx_s {
   void* host_pinned = nullptr;  // small staging area for read-backs
   size_t host_pinned_bytes = 0;
   int jacobi_max_blocks = 0;    // co-resident blocks for the cooperative Jacobi kernel
+  int jacobi_max_blocks_df = 0;  // ... and for its double-float form
   bool stream_ordered = false;  // workspaces from cudaMallocAsync/cudaFreeAsync on `stream`
   // Cooperative (grid-synchronising) launches use at most 1/coop_share of the device's
   // co-resident CTAs, so that the grids of coop_share contexts running concurrently (the
@@ -290,8 +291,20 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
 // w (descending), V (row-major, column j = eigenvector) of symmetric H (not modified).
 // Sweeps stop when off(A) <= tol ||H||_F: 1e-15 for FP64 data, 1e-10 where H is formed from
 // FP32 blocks and so carries FP32-level errors itself.
+// df: orders above 96 in double-float arithmetic on the FP32 pipe (stops at <= 1e-13).
+// jac_df / jac_tol: the Jacobi arithmetic and tolerance for matrices formed from element
+// type T: FP32 bases (accurate to ~1e-7) and double-float dense products take the
+// double-float kernel; plain FP64 keeps FP64 throughout.
 arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
-                 int64_t ldv, int32_t* sweeps, double tol = 1e-15);
+                 int64_t ldv, int32_t* sweeps, double tol = 1e-15, bool df = false);
+template <typename T>
+inline bool jac_df(arb_ctx ctx) {
+  return sizeof(T) == 4 || ctx->dense_df;
+}
+template <typename T>
+inline double jac_tol(arb_ctx ctx) {
+  return sizeof(T) == 4 ? 1e-10 : (ctx->dense_df ? 1e-13 : 1e-15);
+}
 
 // ---------------------------------------------------------------- composite steps (steps.cu)
 struct FilterPlan {

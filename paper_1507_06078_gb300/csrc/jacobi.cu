@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "arb_internal.h"
+#include "df_arith.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -430,10 +431,320 @@ __global__ void __launch_bounds__(JAC_SMALL_THREADS) jacobi_small_kernel(JacPara
   if (tid == 0 && P.sweeps_out) *P.sweeps_out = sweep;
 }
 
+// ---------------------------------------------------------------- double-float block Jacobi
+// The block method above with its arithmetic on GB300's FP32 pipe: the pair subproblems and
+// their orthogonal factors are held in double-float (hi + lo FP32) in shared memory, every
+// rotation update and every block product is a compensated (Dot2) sum of double-float
+// products, and A and V stay FP64 in global memory (split on load, hi + lo on store).  The
+// rotation angles themselves are computed in FP64 from the current entries.  Each update
+// carries about 2^-44 relative error, so sweeps stop at off(A) <= max(tol, 1e-13) ||H||_F.
+struct DFShared {
+  float Sh[BJ_S * BJ_LD], Sl[BJ_S * BJ_LD];   // subproblem / block of A or V
+  float Ah[BJ_S * BJ_LD], Al[BJ_S * BJ_LD];   // Q_p (phase 1 accumulation / phase 2 left factor)
+  float Bh[BJ_S * BJ_LD], Bl[BJ_S * BJ_LD];   // Q_p' (phase 2 right factor)
+  float Xh[BJ_S * BJ_LD], Xl[BJ_S * BJ_LD];   // phase 2 intermediate
+  float rot[BJ_B][4];                          // c_hi, c_lo, s_hi, s_lo
+  double red[JAC_THREADS];
+};
+
+// (c1 x1 + c2 x2) for two lanes at once, compensated
+__device__ __forceinline__ dfp dot2_two(const dfp& c1, const dfp& x1, const dfp& c2, const dfp& x2) {
+  float2 S = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
+  dot2p(S, E, c1, neg(c1), x1);
+  dot2p(S, E, c2, neg(c2), x2);
+  return fast_two_sum2(S, E);
+}
+__device__ __forceinline__ dfp bcast(float h, float l) { return dfp{make_float2(h, h), make_float2(l, l)}; }
+__device__ __forceinline__ dfp pair_of(float h0, float l0, float h1, float l1) {
+  return dfp{make_float2(h0, h1), make_float2(l0, l1)};
+}
+
+// one cyclic sweep on the 32 x 32 double-float matrix (Sh, Sl), accumulating into (Ah, Al)
+__device__ __forceinline__ void dfj_inner_sweep(DFShared& sh) {
+  const int tid = threadIdx.x;
+  for (int r = 0; r < BJ_S - 1; ++r) {
+    if (tid < BJ_B) {
+      int i, j;
+      round_pair(BJ_S, r, tid, i, j);
+      const double aii = static_cast<double>(sh.Sh[i * BJ_LD + i]) + sh.Sl[i * BJ_LD + i];
+      const double ajj = static_cast<double>(sh.Sh[j * BJ_LD + j]) + sh.Sl[j * BJ_LD + j];
+      const double aij = static_cast<double>(sh.Sh[i * BJ_LD + j]) + sh.Sl[i * BJ_LD + j];
+      const double2 cs = jacobi_rotation(aii, ajj, aij);
+      split_f64(cs.x, sh.rot[tid][0], sh.rot[tid][1]);
+      split_f64(cs.y, sh.rot[tid][2], sh.rot[tid][3]);
+    }
+    __syncthreads();
+    constexpr int nblk = BJ_B * BJ_B;
+    for (int it = tid; it < nblk + BJ_S * BJ_B; it += blockDim.x) {
+      if (it < nblk) {
+        const int kp = it / BJ_B, kq = it % BJ_B;
+        if (kp > kq) continue;
+        int i1, j1, i2, j2;
+        round_pair(BJ_S, r, kp, i1, j1);
+        round_pair(BJ_S, r, kq, i2, j2);
+        const float* r1 = sh.rot[kp];
+        const float* r2 = sh.rot[kq];
+        const bool pivot = (kp == kq) && (r1[2] != 0.f || r1[3] != 0.f);
+        // rows: (a b; cc d) -> J_P^T (a b; cc d), both columns of the pair at once
+        const dfp ab = pair_of(sh.Sh[i1 * BJ_LD + i2], sh.Sl[i1 * BJ_LD + i2], sh.Sh[i1 * BJ_LD + j2],
+                               sh.Sl[i1 * BJ_LD + j2]);
+        const dfp cd = pair_of(sh.Sh[j1 * BJ_LD + i2], sh.Sl[j1 * BJ_LD + i2], sh.Sh[j1 * BJ_LD + j2],
+                               sh.Sl[j1 * BJ_LD + j2]);
+        const dfp c1 = bcast(r1[0], r1[1]), s1 = bcast(r1[2], r1[3]);
+        const dfp ra = dot2_two(c1, ab, neg(s1), cd);  // (ra0, ra1) = c1 (a, b) - s1 (cc, d)
+        const dfp rb = dot2_two(s1, ab, c1, cd);       // (rb0, rb1) = s1 (a, b) + c1 (cc, d)
+        // columns: (x0 x1) -> (c2 x0 - s2 x1, s2 x0 + c2 x1) for x = ra and x = rb
+        const dfp c2s2 = pair_of(r2[0], r2[1], r2[2], r2[3]);
+        const dfp ms2c2 = dfp{make_float2(-r2[2], r2[0]), make_float2(-r2[3], r2[1])};
+        const dfp ra0 = bcast(ra.hi.x, ra.lo.x), ra1 = bcast(ra.hi.y, ra.lo.y);
+        const dfp rb0 = bcast(rb.hi.x, rb.lo.x), rb1 = bcast(rb.hi.y, rb.lo.y);
+        const dfp nab = dot2_two(c2s2, ra0, ms2c2, ra1);  // (na, nb)
+        const dfp ncd = dot2_two(c2s2, rb0, ms2c2, rb1);  // (nc, nd)
+        float nbh = nab.hi.y, nbl = nab.lo.y, nch = ncd.hi.x, ncl = ncd.lo.x;
+        if (pivot) nbh = nbl = nch = ncl = 0.f;  // the rotation annihilates the pivot entry
+        sh.Sh[i1 * BJ_LD + i2] = nab.hi.x;
+        sh.Sl[i1 * BJ_LD + i2] = nab.lo.x;
+        sh.Sh[i1 * BJ_LD + j2] = nbh;
+        sh.Sl[i1 * BJ_LD + j2] = nbl;
+        sh.Sh[j1 * BJ_LD + i2] = nch;
+        sh.Sl[j1 * BJ_LD + i2] = ncl;
+        sh.Sh[j1 * BJ_LD + j2] = ncd.hi.y;
+        sh.Sl[j1 * BJ_LD + j2] = ncd.lo.y;
+        if (kp != kq) {
+          sh.Sh[i2 * BJ_LD + i1] = nab.hi.x;
+          sh.Sl[i2 * BJ_LD + i1] = nab.lo.x;
+          sh.Sh[j2 * BJ_LD + i1] = nbh;
+          sh.Sl[j2 * BJ_LD + i1] = nbl;
+          sh.Sh[i2 * BJ_LD + j1] = nch;
+          sh.Sl[i2 * BJ_LD + j1] = ncl;
+          sh.Sh[j2 * BJ_LD + j1] = ncd.hi.y;
+          sh.Sl[j2 * BJ_LD + j1] = ncd.lo.y;
+        }
+      } else {
+        const int it2 = it - nblk;
+        const int row = it2 / BJ_B, kp = it2 % BJ_B;
+        int i, j;
+        round_pair(BJ_S, r, kp, i, j);
+        const float* rr = sh.rot[kp];
+        if (rr[2] != 0.f || rr[3] != 0.f) {
+          // (q_i, q_j) -> (c q_i - s q_j, s q_i + c q_j)
+          const dfp qi = bcast(sh.Ah[row * BJ_LD + i], sh.Al[row * BJ_LD + i]);
+          const dfp qj = bcast(sh.Ah[row * BJ_LD + j], sh.Al[row * BJ_LD + j]);
+          const dfp cs = pair_of(rr[0], rr[1], rr[2], rr[3]);
+          const dfp msc = dfp{make_float2(-rr[2], rr[0]), make_float2(-rr[3], rr[1])};
+          const dfp q = dot2_two(cs, qi, msc, qj);
+          sh.Ah[row * BJ_LD + i] = q.hi.x;
+          sh.Al[row * BJ_LD + i] = q.lo.x;
+          sh.Ah[row * BJ_LD + j] = q.hi.y;
+          sh.Al[row * BJ_LD + j] = q.lo.y;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// out = L^T R (transL) or L R, 32 x 32 double-float, compensated sums; 256 threads x 4
+// outputs (two packed pairs)
+__device__ __forceinline__ void dfj_matmul(const float* Lh, const float* Ll, const float* Rh, const float* Rl,
+                                           float* Oh, float* Ol, bool transL) {
+  const int z = threadIdx.x / 8, y0 = (threadIdx.x % 8) * 4;
+  float2 S[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  float2 E[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll 4
+  for (int x = 0; x < BJ_S; ++x) {
+    const int li = transL ? x * BJ_LD + z : z * BJ_LD + x;
+    const dfp l = bcast(Lh[li], Ll[li]);
+    const dfp nl = neg(l);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int ri = x * BJ_LD + y0 + 2 * u;
+      dot2p(S[u], E[u], l, nl, pair_of(Rh[ri], Rl[ri], Rh[ri + 1], Rl[ri + 1]));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const dfp o = fast_two_sum2(S[u], E[u]);
+    Oh[z * BJ_LD + y0 + 2 * u] = o.hi.x;
+    Ol[z * BJ_LD + y0 + 2 * u] = o.lo.x;
+    Oh[z * BJ_LD + y0 + 2 * u + 1] = o.hi.y;
+    Ol[z * BJ_LD + y0 + 2 * u + 1] = o.lo.y;
+  }
+}
+
+__global__ void __launch_bounds__(JAC_THREADS, 3) jacobi_block_df_kernel(JacParams P) {
+  cg::grid_group g = cg::this_grid();
+  __shared__ DFShared sh;
+  const int m = P.m, M = P.M, NB = M / BJ_B, npairs = NB / 2;
+  const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t nth = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t MM = static_cast<int64_t>(M) * M;
+  float* Qh = reinterpret_cast<float*>(P.Q);
+  float* Ql = Qh + static_cast<size_t>(npairs) * BJ_S * BJ_S;
+  float* Dh = Ql + static_cast<size_t>(npairs) * BJ_S * BJ_S;  // the diagonalised pair blocks
+  float* Dl = Dh + static_cast<size_t>(npairs) * BJ_S * BJ_S;
+
+  double fro = 0.0;
+  for (int64_t t = tid; t < MM; t += nth) {
+    const int i = static_cast<int>(t / M), j = static_cast<int>(t % M);
+    const double v = (i < m && j < m) ? P.H[static_cast<int64_t>(i) * P.ldh + j] : 0.0;
+    P.A[t] = v;
+    P.V[t] = (i == j) ? 1.0 : 0.0;
+    fro += v * v;
+  }
+  {
+    const double b = block_sum(fro, sh.red);
+    if (threadIdx.x == 0) P.red[blockIdx.x] = b;
+  }
+  g.sync();
+  double normF2 = 0.0;
+  for (int b = 0; b < static_cast<int>(gridDim.x); ++b) normF2 += P.red[b];
+  // scale by 2^-e (exact) so that ||A||_F lies in [1/2, 1): every entry then stays inside
+  // FP32's range and the split keeps its low part down to 2^-75 ||A||_F
+  int e2 = 0;
+  const double normF = normF2 > 0.0 ? frexp(sqrt(normF2), &e2) : 0.0;
+  for (int64_t t = tid; t < MM; t += nth) P.A[t] = ldexp(P.A[t], -e2);  // this thread's own entries
+  g.sync();
+  const double tol = fmax(P.tol, 1e-13);
+
+  const int nA = npairs * (npairs + 1) / 2;
+  const int nV = (M / BJ_S) * npairs;
+  int sweep = 0;
+  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
+    double off = 0.0;
+    for (int64_t t = tid; t < MM; t += nth) {
+      const int i = static_cast<int>(t / M), j = static_cast<int>(t % M);
+      if (i != j) off += P.A[t] * P.A[t];
+    }
+    {
+      const double b = block_sum(off, sh.red);
+      if (threadIdx.x == 0) P.red[gridDim.x + blockIdx.x] = b;
+    }
+    g.sync();
+    double off2 = 0.0;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) off2 += P.red[gridDim.x + b];
+    if (sqrt(off2) <= tol * normF || normF == 0.0) break;
+    for (int r = 0; r < NB - 1; ++r) {
+      for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+        int I, J;
+        round_pair(NB, r, p, I, J);
+        for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+          const int x = t / BJ_S, y = t % BJ_S;
+          split_f64(P.A[static_cast<int64_t>(bj_index(I, J, x)) * M + bj_index(I, J, y)], sh.Sh[x * BJ_LD + y],
+                    sh.Sl[x * BJ_LD + y]);
+          sh.Ah[x * BJ_LD + y] = (x == y) ? 1.f : 0.f;
+          sh.Al[x * BJ_LD + y] = 0.f;
+        }
+        __syncthreads();
+        dfj_inner_sweep(sh);
+        for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+          const size_t o = static_cast<size_t>(p) * BJ_S * BJ_S + t;
+          const int si = (t / BJ_S) * BJ_LD + (t % BJ_S);
+          Qh[o] = sh.Ah[si];
+          Ql[o] = sh.Al[si];
+          Dh[o] = sh.Sh[si];
+          Dl[o] = sh.Sl[si];
+        }
+        __syncthreads();
+      }
+      g.sync();
+      for (int task = blockIdx.x; task < nA + nV; task += gridDim.x) {
+        if (task < nA) {
+          int p = 0, rem = task;
+          while (rem >= npairs - p) {
+            rem -= npairs - p;
+            ++p;
+          }
+          const int pp = p + rem;
+          int I1, J1, I2, J2;
+          round_pair(NB, r, p, I1, J1);
+          round_pair(NB, r, pp, I2, J2);
+          const size_t o1 = static_cast<size_t>(p) * BJ_S * BJ_S, o2 = static_cast<size_t>(pp) * BJ_S * BJ_S;
+          if (p == pp) {
+            // the pair's own block is the rotated subproblem itself: rotations act on entries
+            // near convergence with errors relative to those entries, where the product
+            // Q_p^T A Q_p would leave errors of 2^-48 |a_ii| in every off-diagonal entry
+            for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+              const int z = t / BJ_S, w = t % BJ_S;
+              if (z > w) continue;
+              const int64_t gz = bj_index(I1, J1, z), gw = bj_index(I1, J1, w);
+              const double v = static_cast<double>(Dh[o1 + t]) + Dl[o1 + t];
+              P.A[gz * M + gw] = v;
+              P.A[gw * M + gz] = v;
+            }
+            continue;
+          }
+          for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+            const int x = t / BJ_S, y = t % BJ_S;
+            split_f64(P.A[static_cast<int64_t>(bj_index(I1, J1, x)) * M + bj_index(I2, J2, y)],
+                      sh.Sh[x * BJ_LD + y], sh.Sl[x * BJ_LD + y]);
+            sh.Ah[x * BJ_LD + y] = Qh[o1 + t];
+            sh.Al[x * BJ_LD + y] = Ql[o1 + t];
+            sh.Bh[x * BJ_LD + y] = Qh[o2 + t];
+            sh.Bl[x * BJ_LD + y] = Ql[o2 + t];
+          }
+          __syncthreads();
+          dfj_matmul(sh.Ah, sh.Al, sh.Sh, sh.Sl, sh.Xh, sh.Xl, true);   // X = Q_p^T A[P, P']
+          __syncthreads();
+          dfj_matmul(sh.Xh, sh.Xl, sh.Bh, sh.Bl, sh.Sh, sh.Sl, false);  // S = X Q_p'
+          __syncthreads();
+          for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+            const int z = t / BJ_S, w = t % BJ_S;
+            const int64_t gz = bj_index(I1, J1, z), gw = bj_index(I2, J2, w);
+            const double v = static_cast<double>(sh.Sh[z * BJ_LD + w]) + sh.Sl[z * BJ_LD + w];
+            P.A[gz * M + gw] = v;
+            P.A[gw * M + gz] = v;
+          }
+          __syncthreads();
+        } else {
+          const int t2 = task - nA;
+          const int chunk = t2 / npairs, p = t2 % npairs;
+          int I, J;
+          round_pair(NB, r, p, I, J);
+          const size_t o1 = static_cast<size_t>(p) * BJ_S * BJ_S;
+          for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+            const int x = t / BJ_S, y = t % BJ_S;
+            split_f64(P.V[static_cast<int64_t>(chunk * BJ_S + x) * M + bj_index(I, J, y)], sh.Sh[x * BJ_LD + y],
+                      sh.Sl[x * BJ_LD + y]);
+            sh.Ah[x * BJ_LD + y] = Qh[o1 + t];
+            sh.Al[x * BJ_LD + y] = Ql[o1 + t];
+          }
+          __syncthreads();
+          dfj_matmul(sh.Sh, sh.Sl, sh.Ah, sh.Al, sh.Xh, sh.Xl, false);  // X = V[rows, P] Q_p
+          __syncthreads();
+          for (int t = threadIdx.x; t < BJ_S * BJ_S; t += blockDim.x) {
+            const int x = t / BJ_S, y = t % BJ_S;
+            P.V[static_cast<int64_t>(chunk * BJ_S + x) * M + bj_index(I, J, y)] =
+                static_cast<double>(sh.Xh[x * BJ_LD + y]) + sh.Xl[x * BJ_LD + y];
+          }
+          __syncthreads();
+        }
+      }
+      g.sync();
+    }
+  }
+  for (int64_t i = tid; i < m; i += nth) {
+    const double vi = P.A[i * M + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double vj = P.A[static_cast<int64_t>(j) * M + j];
+      rank += (vj > vi) || (vj == vi && j < i);
+    }
+    P.perm[i] = rank;
+    P.w_out[rank] = ldexp(vi, e2);
+  }
+  g.sync();
+  for (int64_t t = tid; t < static_cast<int64_t>(m) * m; t += nth) {
+    const int row = static_cast<int>(t / m), i = static_cast<int>(t % m);
+    P.V_out[static_cast<int64_t>(row) * P.ldv + P.perm[i]] = P.V[static_cast<int64_t>(row) * M + i];
+  }
+  if (tid == 0 && P.sweeps_out) *P.sweeps_out = sweep;
+}
+
 }  // namespace
 
 arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
-                 int64_t ldv, int32_t* sweeps, double tol) {
+                 int64_t ldv, int32_t* sweeps, double tol, bool df) {
   if (m <= 0) {
     if (sweeps) *sweeps = 0;
     return ARB_OK;
@@ -467,19 +778,21 @@ arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w
     if (sweeps) ARB_TRY(d2h_sync(ctx, sweeps, sw, sizeof(int32_t)));
     return ARB_OK;
   }
-  if (ctx->jacobi_max_blocks == 0) {
+  void* kern = df ? reinterpret_cast<void*>(jacobi_block_df_kernel) : reinterpret_cast<void*>(jacobi_block_kernel);
+  int& max_blocks = df ? ctx->jacobi_max_blocks_df : ctx->jacobi_max_blocks;
+  if (max_blocks == 0) {
     int per_sm = 0;
-    ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel, JAC_THREADS, 0));
-    ctx->jacobi_max_blocks = std::max(1, per_sm) * ctx->num_sms;
+    ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, JAC_THREADS, 0));
+    max_blocks = std::max(1, per_sm) * ctx->num_sms;
   }
   const int NB = ((m + BJ_B - 1) / BJ_B + 1) / 2 * 2;  // index blocks, even
   const int MB = NB * BJ_B;
   const int npairs = NB / 2;
   const int tasks = npairs * (npairs + 1) / 2 + (MB / BJ_S) * npairs;
-  int grid = std::max(1, std::min(tasks, ctx->jacobi_max_blocks / std::max(1, ctx->coop_share)));
+  int grid = std::max(1, std::min(tasks, max_blocks / std::max(1, ctx->coop_share)));
   // scratch: A, V (MB x MB), Q factors, reductions, permutation, sweep count
   const size_t mm = static_cast<size_t>(MB) * MB;
-  const size_t qsz = static_cast<size_t>(npairs) * BJ_S * BJ_S;
+  const size_t qsz = static_cast<size_t>(npairs) * BJ_S * BJ_S * (df ? 2 : 1);
   double* base;
   ARB_TRY(ws<double>(ctx, WS_JACOBI, 2 * mm + qsz + 2 * static_cast<size_t>(grid) + m + 8, &base));
   JacParams P = {};
@@ -498,8 +811,7 @@ arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w
   P.ldv = ldv;
   P.sweeps_out = reinterpret_cast<int32_t*>(P.red + 2 * grid + m + 2);
   void* args[] = {&P};
-  ARB_CUDA(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(jacobi_block_kernel), dim3(grid),
-                                            dim3(JAC_THREADS), args, 0, ctx->stream));
+  ARB_CUDA(ctx, cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(JAC_THREADS), args, 0, ctx->stream));
   ARB_LAUNCHED(ctx);
   if (sweeps) ARB_TRY(d2h_sync(ctx, sweeps, P.sweeps_out, sizeof(int32_t)));
   return ARB_OK;

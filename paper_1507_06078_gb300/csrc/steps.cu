@@ -201,7 +201,7 @@ static arb_status svqb_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int
   ARB_TRY(ws<int32_t>(ctx, WS_INT0, 4, &r_dev));
   ARB_TRY(gram<T>(ctx, n, Z, ldz, m, Z, ldz, m, G, m));
   ARB_TRY(svqb_prep(ctx, m, G, m, Gh, d));
-  ARB_TRY(syevj(ctx, m, Gh, m, theta, W, m, nullptr, sizeof(T) == 4 ? 1e-10 : 1e-15));
+  ARB_TRY(syevj(ctx, m, Gh, m, theta, W, m, nullptr, jac_tol<T>(ctx), jac_df<T>(ctx)));
   ARB_TRY(svqb_finish(ctx, m, theta, W, m, d, orth_tau<T>(m), Gh, r_dev));
   int32_t r = 0;
   ARB_TRY(d2h_sync(ctx, &r, r_dev, sizeof(int32_t)));
@@ -234,7 +234,7 @@ arb_status rcond_gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t n
   rc_dev = theta + ncols;
   ARB_TRY(gram<T>(ctx, n, X, ldx, ncols, X, ldx, ncols, G, ncols));
   if (xs) ARB_TRY(scale_sym(ctx, ncols, G, ncols, xs));
-  ARB_TRY(syevj(ctx, ncols, G, ncols, theta, W, ncols, nullptr, sizeof(T) == 4 ? 1e-10 : 1e-15));
+  ARB_TRY(syevj(ctx, ncols, G, ncols, theta, W, ncols, nullptr, jac_tol<T>(ctx), jac_df<T>(ctx)));
   ARB_TRY(rcond_from_eig(ctx, ncols, G, ncols, theta, W, ncols, rc_dev));
   ARB_TRY(d2h_sync(ctx, rc, rc_dev, sizeof(double)));
   return ARB_OK;
@@ -313,7 +313,7 @@ arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double o
     }
   }
   ARB_TRY(symmetrize_upper_blocks(ctx, m, H, m, off.data(), rk.data(), nblk));
-  ARB_TRY(syevj(ctx, m, H, m, theta, V, m, nullptr, sizeof(T) == 4 ? 1e-10 : 1e-15));
+  ARB_TRY(syevj(ctx, m, H, m, theta, V, m, nullptr, jac_tol<T>(ctx), jac_df<T>(ctx)));
   *m_out = m;
   return ARB_OK;
 }

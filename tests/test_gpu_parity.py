@@ -329,6 +329,41 @@ def test_gram_df_extreme_magnitudes(arb, ctx_df):
     assert np.all(np.abs(G - X.T @ X) <= 1e-13 * np.outer(nrm, nrm))
 
 
+@pytest.mark.parametrize("m", [97, 200, 256, 720])
+def test_syevj_double_float_matches_numpy(arb, ctx_df, m):
+    # orders above 96 on a double-float context: the rotations and block products carry
+    # ~2^-48 relative error per step and the sweeps stop at off(H) <= 1e-13 ||H||_F
+    rng = np.random.default_rng(1000 + m)
+    H = rng.standard_normal((m, m))
+    H = 0.5 * (H + H.T)
+    nH = np.linalg.norm(H)
+    w, V, sweeps = arb.arb_syevj(ctx_df, dev(H))
+    w, V = host(w), host(V)
+    np.testing.assert_allclose(w, np.sort(np.linalg.eigvalsh(H))[::-1], atol=2e-13 * nH)
+    np.testing.assert_allclose(V.T @ V, np.eye(m), atol=1e-12)
+    np.testing.assert_allclose(H @ V, V * w[None, :], atol=1e-12 * nH)
+    assert sweeps < 60
+
+
+@pytest.mark.parametrize("scale", [2.0 ** 90, 2.0 ** -90, 3.0e-7])
+def test_syevj_double_float_graded_and_scaled(arb, ctx_df, scale):
+    # a graded spectrum with a cluster, scaled far outside FP32's range: the kernel's exact
+    # power-of-two scaling keeps every split entry representable
+    m = 150
+    rng = np.random.default_rng(77)
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    w0 = np.concatenate([np.logspace(0, -12, m - 10), np.full(10, 0.5)]) * scale
+    H = (Q * w0[None, :]) @ Q.T
+    H = 0.5 * (H + H.T)
+    w, V, sweeps = arb.arb_syevj(ctx_df, dev(H))
+    w, V = host(w), host(V)
+    nH = np.linalg.norm(H)
+    np.testing.assert_allclose(w, np.sort(np.linalg.eigvalsh(H))[::-1], atol=2e-13 * nH)
+    np.testing.assert_allclose(V.T @ V, np.eye(m), atol=1e-12)
+    np.testing.assert_allclose(H @ V, V * w[None, :], atol=1e-12 * nH)
+    assert sweeps < 60
+
+
 def test_orth_rr_arr_in_double_float_mode(arb, ctx_df):
     rng = np.random.default_rng(4)
     Z = rng.standard_normal((5000, 20))
