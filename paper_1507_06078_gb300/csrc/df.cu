@@ -57,30 +57,39 @@ __device__ __forceinline__ dfp ldps(const df2* p) {
   return dfp{make_float2(t.x, t.y), make_float2(t.z, t.w)};
 }
 
-// Tuning defaults (measured on the 128^3 x 240 filter): gathers in flight per lane and the
-// CTAs per SM the register budget must allow.
+// Tuning defaults (measured on the 128^3 x 240 filter): gathers in flight per lane, the CTAs
+// per SM the register budget must allow, and column pairs per lane.  Measured and dropped:
+// parking the epilogue multipliers in shared memory and splitting the sum over two
+// accumulators (both slower at this occupancy), 3 CTAs per SM (spills), 2 pairs per lane.
 #ifndef ARB_DF_BATCH
 #define ARB_DF_BATCH 8
 #endif
 #ifndef ARB_DF_MIN_BLOCKS
 #define ARB_DF_MIN_BLOCKS 2
 #endif
+#ifndef ARB_DF_NP
+#define ARB_DF_NP 1
+#endif
 constexpr int DF_BATCH = ARB_DF_BATCH;
+constexpr int DF_NP = ARB_DF_NP;
+constexpr int DF_CH = 64 * DF_NP;  // columns per warp chunk
 
-// A warp owns a fixed 64-column chunk (two columns per lane, 16-byte accesses) and walks
-// its rows, gathers issued DF_BATCH at a time, as in the FP32/FP64 fused kernel.  Leading
-// dimensions are even and bases 16-byte aligned; for odd ncols the pad column (ld >=
-// ncols + 1) is read and written but never reduced.
+__device__ __forceinline__ float4 pack4(const dfp& a) { return make_float4(a.hi.x, a.hi.y, a.lo.x, a.lo.y); }
+
+// A warp owns a fixed chunk of 64 DF_NP columns - DF_NP column pairs per lane, pair u at
+// columns chunk * DF_CH + 64 u + 2 lane, so every 16-byte load of a pair is one coalesced
+// 512-byte warp access - and walks its rows, gathers issued DF_BATCH at a time, as in the
+// FP32/FP64 fused kernel.  Leading dimensions are even and bases 16-byte aligned; for odd
+// ncols the pad column (ld >= ncols + 1) is read and written but never reduced.
 // SHORT (rows of at most 32 nonzeros, blocks below 2^31 elements): row pointers loaded two
 // rows ahead, column indices and values one row ahead, 32-bit element offsets.
 template <bool RED, bool SHORT>
 __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(DfParams P) {
-  extern __shared__ double s_red[];
-  constexpr int CH = 64;
+  extern __shared__ double s_red[];  // RED: [DF_WARPS][ncols]
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int ncols = P.ncols;
-  const int nch = (ncols + CH - 1) / CH;
+  const int nch = (ncols + DF_CH - 1) / DF_CH;
   if constexpr (RED) {
     for (int c = lane; c < ncols; c += 32) s_red[static_cast<size_t>(warp) * ncols + c] = 0.0;
     __syncwarp();
@@ -90,32 +99,40 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
   const int64_t rstride = nwarps / nch;
   const int chunk = static_cast<int>(gw % nch);
   const int64_t r_first = gw / nch;
-  const int c = chunk * CH + lane * 2;
-  const bool act = (r_first < rstride) && (c < ncols);
-  const bool act1 = act && (c + 1 < ncols);  // odd ncols: the pad column is carried, not reduced
-  // lanes past the last column load columns 0-1 of the same rows (always in bounds) and
-  // discard the result, so the gathers need no per-lane predicate
-  const int cl = act ? c : 0;
+  const bool live = r_first < rstride;
+  int cp[DF_NP], cl[DF_NP];
+  bool act[DF_NP], act1[DF_NP];
+#pragma unroll
+  for (int u = 0; u < DF_NP; ++u) {
+    cp[u] = chunk * DF_CH + 64 * u + lane * 2;
+    act[u] = live && (cp[u] < ncols);
+    act1[u] = act[u] && (cp[u] + 1 < ncols);  // odd ncols: the pad column is carried, not reduced
+    // lanes past the last column load columns 0-1 of the same rows (always in bounds) and
+    // discard the result, so the gathers need no per-lane predicate
+    cl[u] = act[u] ? cp[u] : 0;
+  }
   // out = ka (A Yin) + kb Yin + kx X + kz Z with ka = sy alpha, kb = sy beta, kx = sx, kz = sz
-  dfp ka, kb, kx, kz;
+  dfp kmul[4][DF_NP];
   {
     const df2 alpha = df_from(P.alpha), beta = df_from(P.beta);
-    df2 a[2], b[2], x[2], z[2];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      const int cu = (act && c + u < ncols) ? c + u : 0;
-      const df2 sy = df_from(P.sy ? P.sy[cu] : 1.0);
-      a[u] = df_mul(sy, alpha);
-      b[u] = df_mul(sy, beta);
-      x[u] = df_from(P.X ? P.sx[cu] : 0.0);
-      z[u] = df_from(P.Z ? P.sz[cu] : 0.0);
+    for (int u = 0; u < DF_NP; ++u) {
+      df2 a[2], b[2], x[2], z[2];
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int cu = (act[u] && cp[u] + v < ncols) ? cp[u] + v : 0;
+        const df2 sy = df_from(P.sy ? P.sy[cu] : 1.0);
+        a[v] = df_mul(sy, alpha);
+        b[v] = df_mul(sy, beta);
+        x[v] = df_from(P.X ? P.sx[cu] : 0.0);
+        z[v] = df_from(P.Z ? P.sz[cu] : 0.0);
+      }
+      kmul[0][u] = dfp_of(a[0], a[1]);
+      kmul[1][u] = dfp_of(b[0], b[1]);
+      kmul[2][u] = dfp_of(x[0], x[1]);
+      kmul[3][u] = dfp_of(z[0], z[1]);
     }
-    ka = dfp_of(a[0], a[1]);
-    kb = dfp_of(b[0], b[1]);
-    kx = dfp_of(x[0], x[1]);
-    kz = dfp_of(z[0], z[1]);
   }
-  const dfp nka = neg(ka), nkb = neg(kb), nkx = neg(kx), nkz = neg(kz);
   auto off = [&](int64_t r, int64_t ld) -> int64_t {
     if constexpr (SHORT) return static_cast<int64_t>(static_cast<uint32_t>(r) * static_cast<uint32_t>(ld));
     else return r * ld;
@@ -123,10 +140,12 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
   const bool has_beta = P.beta != 0.0;  // one FP64 compare per thread, not one per row
   const bool need_yi = has_beta || (RED && P.dot_with_yin);
   const dfp zero{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-  double red[2] = {0.0, 0.0};
+  double red[DF_NP][2];
+#pragma unroll
+  for (int u = 0; u < DF_NP; ++u) red[u][0] = red[u][1] = 0.0;
   int n_jc = 0, n_cnt = 0, p_beg = 0, p_end = 0;
   float n_ah = 0.f, n_al = 0.f;
-  if (SHORT && r_first < rstride && r_first < P.n) {
+  if (SHORT && live && r_first < P.n) {
     const int b0 = __ldg(P.rowptr + r_first), e0 = __ldg(P.rowptr + r_first + 1);
     n_cnt = e0 - b0;
     if (lane < n_cnt) {
@@ -140,7 +159,7 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
       p_end = __ldg(P.rowptr + r_first + rstride + 1);
     }
   }
-  if (r_first < rstride) {
+  if (live) {
     for (int64_t row = r_first; row < P.n; row += rstride) {
       int beg = 0, end = 0, s_jc = 0;
       float s_ah = 0.f, s_al = 0.f;
@@ -171,11 +190,17 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
         end = __ldg(P.rowptr + row + 1);
       }
       // the row's own streams first, so their latency overlaps the gathers
-      dfp xv = zero, zv = zero, yi = zero;
-      if (P.X) xv = ldps(P.X + off(row, P.ldx) + cl);
-      if (P.Z) zv = ldps(P.Z + off(row, P.ldz) + cl);
-      if (need_yi) yi = ldp(P.Yin + off(row, P.ldy) + cl);
-      float2 S = make_float2(0.f, 0.f), E = make_float2(0.f, 0.f);
+      dfp xv[DF_NP], zv[DF_NP], yi[DF_NP];
+#pragma unroll
+      for (int u = 0; u < DF_NP; ++u) {
+        xv[u] = zv[u] = yi[u] = zero;
+        if (P.X) xv[u] = ldps(P.X + off(row, P.ldx) + cl[u]);
+        if (P.Z) zv[u] = ldps(P.Z + off(row, P.ldz) + cl[u]);
+        if (need_yi) yi[u] = ldp(P.Yin + off(row, P.ldy) + cl[u]);
+      }
+      float2 S[DF_NP], E[DF_NP];
+#pragma unroll
+      for (int u = 0; u < DF_NP; ++u) S[u] = E[u] = make_float2(0.f, 0.f);
       for (int base = beg; base < end; base += 32) {
         int jc = 0;
         float ah = 0.f, al = 0.f;
@@ -195,51 +220,64 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
         const int cnt = __shfl_sync(0xffffffffu, min(32, end - base), 0);  // warp-uniform
         for (int t0 = 0; t0 < cnt; t0 += DF_BATCH) {
           int jj[DF_BATCH];
-          float aah[DF_BATCH], aal[DF_BATCH];
+#pragma unroll
+          for (int t = 0; t < DF_BATCH; ++t) jj[t] = __shfl_sync(0xffffffffu, jc, t0 + t < 32 ? t0 + t : 31);
+          dfp y[DF_BATCH][DF_NP];
+#pragma unroll
+          for (int t = 0; t < DF_BATCH; ++t)
+            if (t0 + t < cnt) {
+              const df2* yr = P.Yin + off(jj[t], P.ldy);
+#pragma unroll
+              for (int u = 0; u < DF_NP; ++u) y[t][u] = ldp(yr + cl[u]);
+            }
+          // the multipliers are fetched only as each product is formed (not with the indices,
+          // before the loads), which keeps the batch's live registers to its loads
 #pragma unroll
           for (int t = 0; t < DF_BATCH; ++t) {
             const int src = t0 + t < 32 ? t0 + t : 31;
-            jj[t] = __shfl_sync(0xffffffffu, jc, src);
-            aah[t] = __shfl_sync(0xffffffffu, ah, src);
-            aal[t] = __shfl_sync(0xffffffffu, al, src);
+            const float h = __shfl_sync(0xffffffffu, ah, src);
+            const float l = __shfl_sync(0xffffffffu, al, src);
+            if (t0 + t < cnt) {
+              const dfp a{make_float2(h, h), make_float2(l, l)};
+              const dfp na{make_float2(-h, -h), make_float2(-l, -l)};
+#pragma unroll
+              for (int u = 0; u < DF_NP; ++u) dot2p(S[u], E[u], a, na, y[t][u]);
+            }
           }
-          dfp y[DF_BATCH];
-#pragma unroll
-          for (int t = 0; t < DF_BATCH; ++t)
-            if (t0 + t < cnt) y[t] = ldp(P.Yin + off(jj[t], P.ldy) + cl);
-#pragma unroll
-          for (int t = 0; t < DF_BATCH; ++t)
-            if (t0 + t < cnt)
-              dot2p(S, E, dfp{make_float2(aah[t], aah[t]), make_float2(aal[t], aal[t])},
-                    dfp{make_float2(-aah[t], -aah[t]), make_float2(-aal[t], -aal[t])}, y[t]);
         }
       }
-      if (!act) continue;
-      const dfp acc = fast_two_sum2(S, E);
-      float2 So = make_float2(0.f, 0.f), Eo = make_float2(0.f, 0.f);
-      dot2p(So, Eo, ka, nka, acc);
-      if (has_beta) dot2p(So, Eo, kb, nkb, yi);
-      if (P.X) dot2p(So, Eo, kx, nkx, xv);
-      if (P.Z) dot2p(So, Eo, kz, nkz, zv);
-      const dfp o = fast_two_sum2(So, Eo);
-      if (P.out)
-        __stcs(reinterpret_cast<float4*>(P.out + off(row, P.ldo) + c), make_float4(o.hi.x, o.hi.y, o.lo.x, o.lo.y));
-      if constexpr (RED) {
-        const double o0 = static_cast<double>(o.hi.x) + static_cast<double>(o.lo.x);
-        const double o1 = static_cast<double>(o.hi.y) + static_cast<double>(o.lo.y);
-        if (P.dot_with_yin) {
-          red[0] += o0 * (static_cast<double>(yi.hi.x) + static_cast<double>(yi.lo.x));
-          if (act1) red[1] += o1 * (static_cast<double>(yi.hi.y) + static_cast<double>(yi.lo.y));
-        } else {
-          red[0] += o0 * o0;
-          if (act1) red[1] += o1 * o1;
+      if (!act[0]) continue;
+#pragma unroll
+      for (int u = 0; u < DF_NP; ++u) {
+        const dfp acc = fast_two_sum2(S[u], E[u]);
+        float2 So = make_float2(0.f, 0.f), Eo = make_float2(0.f, 0.f);
+        dot2p(So, Eo, kmul[0][u], neg(kmul[0][u]), acc);
+        if (has_beta) dot2p(So, Eo, kmul[1][u], neg(kmul[1][u]), yi[u]);
+        if (P.X) dot2p(So, Eo, kmul[2][u], neg(kmul[2][u]), xv[u]);
+        if (P.Z) dot2p(So, Eo, kmul[3][u], neg(kmul[3][u]), zv[u]);
+        const dfp o = fast_two_sum2(So, Eo);
+        if (P.out && act[u])
+          __stcs(reinterpret_cast<float4*>(P.out + off(row, P.ldo) + cp[u]), pack4(o));
+        if constexpr (RED) {
+          const double o0 = static_cast<double>(o.hi.x) + static_cast<double>(o.lo.x);
+          const double o1 = static_cast<double>(o.hi.y) + static_cast<double>(o.lo.y);
+          if (P.dot_with_yin) {
+            if (act[u]) red[u][0] += o0 * (static_cast<double>(yi[u].hi.x) + static_cast<double>(yi[u].lo.x));
+            if (act1[u]) red[u][1] += o1 * (static_cast<double>(yi[u].hi.y) + static_cast<double>(yi[u].lo.y));
+          } else {
+            if (act[u]) red[u][0] += o0 * o0;
+            if (act1[u]) red[u][1] += o1 * o1;
+          }
         }
       }
     }
   }
   if constexpr (RED) {
-    if (act) s_red[static_cast<size_t>(warp) * ncols + c] = red[0];
-    if (act1) s_red[static_cast<size_t>(warp) * ncols + c + 1] = red[1];
+#pragma unroll
+    for (int u = 0; u < DF_NP; ++u) {
+      if (act[u]) s_red[static_cast<size_t>(warp) * ncols + cp[u]] = red[u][0];
+      if (act1[u]) s_red[static_cast<size_t>(warp) * ncols + cp[u] + 1] = red[u][1];
+    }
     __syncthreads();
     for (int cc = threadIdx.x; cc < ncols; cc += blockDim.x) {
       double sum = 0.0;
@@ -371,7 +409,7 @@ arb_status spmm_fused<df2>(arb_ctx ctx, const SpmmArgs<df2>& a) {
   ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DF_THREADS, smem));
-  const int nch = (a.ncols + 63) / 64;
+  const int nch = (a.ncols + DF_CH - 1) / DF_CH;
   const int64_t want = (P.n * nch + DF_WARPS - 1) / DF_WARPS;
   int grid = static_cast<int>(std::min<int64_t>(want, static_cast<int64_t>(ctx->num_sms) * std::max(per_sm, 1)));
   grid = std::max(grid, (nch + DF_WARPS - 1) / DF_WARPS);

@@ -34,6 +34,7 @@ constexpr int SPMM_WARPS = SPMM_THREADS / 32;
 #define ARB_SPMM_SHORT_UNROLL 4
 #endif
 
+
 template <typename T>
 struct KParams {
   int64_t n;
@@ -233,9 +234,12 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
         if constexpr (SHORT) return static_cast<int64_t>(static_cast<uint32_t>(r) * static_cast<uint32_t>(ld));
         else return r * ld;
       };
-      T xv[VEC], zv[VEC];
+      T xv[VEC], zv[VEC], yi[VEC];
       if (P.X) VecIO<T, VEC>::lds(P.X + off(row, P.ldx) + cl, xv);
       if (P.Z) VecIO<T, VEC>::lds(P.Z + off(row, P.ldz) + cl, zv);
+      // the row's own entries of Yin with them, ahead of the gathers (not after the sums)
+      const bool need_yi = P.beta != T(0) || (RED && P.dot_with_yin);
+      if (need_yi) VecIO<T, VEC>::ld(P.Yin + off(row, P.ldy) + cl, yi);
       T acc[VEC];
 #pragma unroll
       for (int u = 0; u < VEC; ++u) acc[u] = T(0);
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
           for (int t = 0; t < UNR; ++t)
             if (t0 + t < cnt) VecIO<T, VEC>::ld(P.Yin + off(jj[t], P.ldy) + cl, y[t]);
 #pragma unroll
-          for (int t = 0; t < UNR; ++t)
+          for (int t = 0; t < UNR; ++t) {
             if (t0 + t < cnt) {
               if constexpr (std::is_same<T, float>::value && VEC % 2 == 0) {
                 // packed FP32 (two lanes of one FFMA2 instruction): half the issue slots
@@ -282,13 +286,12 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
                 for (int u = 0; u < VEC; ++u) acc[u] = fma(vv[t], y[t][u], acc[u]);
               }
             }
+          }
         }
       }
       if (!act) continue;
-      T yi[VEC], o[VEC];
-      if (P.beta != T(0) || (RED && P.dot_with_yin)) {
-        VecIO<T, VEC>::ld(P.Yin + off(row, P.ldy) + c, yi);
-      } else {
+      T o[VEC];
+      if (!need_yi) {
 #pragma unroll
         for (int u = 0; u < VEC; ++u) yi[u] = T(0);
       }
