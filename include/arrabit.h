@@ -284,6 +284,20 @@ arb_status arb_gram_f32(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, int
 arb_status arb_gram_noalloc(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_t na,
                             const double* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
 
+/* Out = alpha In W + beta Out for FP32 blocks In (n x na) and Out (n x nb), row-major with
+ * leading dimensions ldi, ldo, and an FP64 matrix W (na x nb, row-major, ldw), all device
+ * pointers: the mixed path's tall-skinny products - the Ritz rotation X = U V (Alg. 1 step
+ * 4), the SVQB map and the block projections.  With na >= 8, leading dimensions that are
+ * multiples of 4 and 16-byte aligned bases it runs on the tensor cores: W is rounded to
+ * FP32, every product formed as hi*hi + hi*lo + lo*hi of TF32 parts (tcgen05.mma
+ * kind::tf32) and summed in FP32 in tensor memory, about 1e-6 relative to
+ * sum_k |In_ik| |W_kj| per entry; otherwise on CUDA cores in FP32.  beta = 0 does not read
+ * Out.  In and Out must not overlap.  Errors: ARB_INVALID_ARG; ARB_CUDA_ERROR (also if a
+ * tensor-core pipeline wait timed out). */
+arb_status arb_gemm_tall_f32(arb_ctx ctx, int64_t n, const float* In, int64_t ldi, int32_t na,
+                             const double* W, int64_t ldw, int32_t nb, double alpha, double beta,
+                             float* Out, int64_t ldo);
+
 /* Eigen-decomposition H = V diag(w) V^T of a symmetric m x m matrix (row-major, ldh) by
  * parallel cyclic Jacobi on the device (Alg. 1 step 3, reading H = V Sigma V^T).
  * w: float64[m] descending; V: m x m row-major (ldv), column j the eigenvector of w[j].

@@ -92,6 +92,7 @@ _PROTOS = {
     "arb_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
     "arb_gram_noalloc": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _i64]),
+    "arb_gemm_tall_f32": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _dbl, _dbl, _vp, _i64]),
     "arb_server_footprint": (_i64, [_i64, _i64, _i32, _i32, _i32]),
     "arb_server_create": (_i32, [C.c_int, C.c_size_t, _i32, C.POINTER(_vp)]),
     "arb_submit": (_i32, [_vp, _vp, _i32, _i32, _dbl, C.POINTER(arb_options), _vp, C.c_int, C.POINTER(_i64)]),
@@ -388,6 +389,21 @@ def arb_gram_f32(ctx: Context, X, Y, C_out=None):
     _check(ctx, load().arb_gram_f32(ctx.handle, X.shape[0], _vp(_ptr(X)), X.stride(0), X.shape[1], _vp(_ptr(Y)),
                                     Y.stride(0), Y.shape[1], _vp(_ptr(C_out)), ldc), "arb_gram_f32")
     return C_out
+
+
+def arb_gemm_tall_f32(ctx: Context, In, W, alpha=1.0, beta=0.0, Out=None):
+    """Out = alpha In W + beta Out: In, Out row-major 2D float32 CUDA tensors, W float64 (na x nb)."""
+    import torch
+    for name, T in (("In", In),) + ((("Out", Out),) if Out is not None else ()):
+        if not (T.is_cuda and T.dtype == torch.float32 and T.dim() == 2 and T.stride(1) == 1):
+            raise ValueError(f"{name}: expected a row-major 2D float32 CUDA tensor")
+    ldw = _dev2d(W, "W")
+    if Out is None:
+        Out = torch.empty((In.shape[0], W.shape[1]), dtype=torch.float32, device=In.device)
+    _check(ctx, load().arb_gemm_tall_f32(ctx.handle, In.shape[0], _vp(_ptr(In)), In.stride(0), In.shape[1],
+                                         _vp(_ptr(W)), ldw, W.shape[1], alpha, beta, _vp(_ptr(Out)),
+                                         Out.stride(0)), "arb_gemm_tall_f32")
+    return Out
 
 
 def arb_gram_noalloc(ctx: Context, X, Y, C_out):

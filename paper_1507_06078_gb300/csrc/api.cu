@@ -473,6 +473,16 @@ extern "C" arb_status arb_gram_f32(arb_ctx ctx, int64_t n, const float* X, int64
   return gram<float>(ctx, n, X, ldx, na, Y, ldy, nb, C, ldc);
 }
 
+extern "C" arb_status arb_gemm_tall_f32(arb_ctx ctx, int64_t n, const float* In, int64_t ldi, int32_t na,
+                                        const double* W, int64_t ldw, int32_t nb, double alpha, double beta,
+                                        float* Out, int64_t ldo) {
+  if (!ctx || n < 0 || na < 0 || nb < 0 || (n > 0 && nb > 0 && (!Out || ldo < nb)) ||
+      (n > 0 && na > 0 && nb > 0 && (!In || !W || ldi < na || ldw < nb)))
+    return set_error(ctx, ARB_INVALID_ARG, "gemm_tall_f32: bad arguments");
+  ARB_CUDA(ctx, cudaSetDevice(ctx->device));
+  return gemm_tall<float>(ctx, n, In, ldi, na, W, ldw, nb, alpha, beta, Out, ldo);
+}
+
 extern "C" arb_status arb_syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
                                 int64_t ldv, int32_t* sweeps) {
   if (!ctx || m < 0 || (m > 0 && (!H || !w || !V || ldh < m || ldv < m)))

@@ -63,6 +63,7 @@ enum WsSlot : int {
   WS_BATCH_TABLE,
   WS_BATCH_DESC,
   WS_TC_ERR,          // tensor-core kernels: error word
+  WS_TC_IMG,          // tensor-core tall products: packed split W
   WS_NUM_SLOTS
 };
 
@@ -280,6 +281,13 @@ bool gram_tc_supported(int64_t n, int64_t ldx, int64_t ldy, const void* X, const
 int gram_tc_rows_align();
 int gram_tc_tile_m();
 int gram_tc_tile_n();
+// Out = alpha In W + beta Out on the tensor cores (tc.cu): FP32 In (n x na), Out (n x nb), FP64 W
+// (na x nb) packed into img (gemm_tc_image_floats(na, nb) floats, 16-byte aligned) first.
+bool gemm_tc_supported(int64_t ldi, int64_t ldo, const void* In, const void* Out);
+size_t gemm_tc_image_floats(int32_t na, int32_t nb);
+arb_status gemm_tc_launch(arb_ctx ctx, int64_t n, const float* In, int64_t ldi, int32_t na, const double* W,
+                          int64_t ldw, int32_t nb, float alpha, float beta, float* Out, int64_t ldo, float* img,
+                          int* err_dev);
 arb_status gram_tc_launch(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, int32_t na, const float* Y,
                           int64_t ldy, int32_t nb, int symmetric, double* part, int64_t nsplit, int64_t rows,
                           int* err_dev);

@@ -767,6 +767,22 @@ arb_status gemm_tall(arb_ctx ctx, int64_t n, const T* In, int64_t ldi, int32_t n
       return ARB_OK;
     }
   }
+  if constexpr (std::is_same<T, float>::value) {
+    // the tensor cores for every product with an inner dimension of a full MMA step
+    if (na >= 8 && gemm_tc_supported(ldi, ldo, In, Out)) {
+      float* img;
+      int* err;
+      ARB_TRY(ws<float>(ctx, WS_TC_IMG, gemm_tc_image_floats(na, nb), &img));
+      ARB_TRY(ws<int>(ctx, WS_TC_ERR, 1, &err));
+      ARB_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+      ARB_TRY(gemm_tc_launch(ctx, n, In, ldi, na, W, ldw, nb, static_cast<float>(alpha), static_cast<float>(beta), Out,
+                             ldo, img, err));
+      int herr = 0;
+      ARB_TRY(d2h_sync(ctx, &herr, err, sizeof(int)));
+      if (herr) return set_error(ctx, ARB_CUDA_ERROR, "tall product (tensor cores): a pipeline wait timed out");
+      return ARB_OK;
+    }
+  }
   const int RN = nb <= 16 ? 1 : (nb <= 32 ? 2 : 4);
   const int TC = 16 * RN;
   dim3 grid(static_cast<unsigned>((n + 63) / 64), static_cast<unsigned>((nb + TC - 1) / TC));

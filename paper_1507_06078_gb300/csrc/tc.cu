@@ -379,6 +379,260 @@ gram_tc_kernel(int64_t n, const float* __restrict__ X, int64_t ldx, int na, cons
   }
 }
 
+// ---------------------------------------------------------------- tall-skinny products
+// Out (n x nb) = alpha In (n x na) W (na x nb) + beta Out for FP32 blocks In, Out and a
+// small FP64 matrix W: the FP32 phase's Ritz rotation X = U V (Algorithm 1), SVQB's map
+// Z W_r Theta_r^{-1/2} and the block projections X - Q (Q^T X).  Split-TF32 as in the Gram
+// product: hi*hi + hi*lo + lo*hi, three kind::tf32 MMAs per K = 8.  The tensor-memory
+// accumulation does not round to nearest (summing all of na = 720 there left errors of
+// ~1e-5 |result|, biased), so every K chunk of 16 gets a fresh accumulator (six MMAs) and
+// the threads add the chunk sums in FP32 registers, rounding to nearest.
+//
+// CTA tile: 128 rows (MMA M) x up to 256 columns of Out (MMA N, rounded up to a multiple of
+// 16); K in chunks of 16 through TG_S shared-memory stages and two tensor-memory buffers
+// (chunk c into buffer c & 1, drained while chunk c + 1's MMAs run).  W is packed once per
+// call (tg_pack_kernel) into per-chunk images of its split, transposed tile laid out exactly
+// as a stage holds it (K-major core matrices without swizzle, LBO = 128 bytes, SBO = 512
+// bytes), so one 32 KB bulk copy brings a chunk; two threads per row load the row's 16
+// entries of In for the next chunk while the current one is in flight, split them and write
+// them in the same layout.  Thread (warp w, lane l) owns row 32 (w % 4) + l of the tile
+// (the tensor-memory lane quarter its warp may read) and columns 128 (w / 4) .. +127.
+constexpr int TG_THREADS = 256;
+constexpr int TG_M = 128;                                    // rows per CTA (MMA M)
+constexpr int TG_N = 256;                                    // columns per CTA (MMA N at most)
+constexpr int TG_KS = 16;                                    // K per chunk
+constexpr int TG_S = 4;                                      // stages
+constexpr int TG_A_BYTES = TG_M * TG_KS * 4;                 // hi or lo of the In tile: 8 KB
+constexpr int TG_B_BYTES = TG_N * TG_KS * 4;                 // hi or lo of the W tile: 16 KB
+constexpr int TG_STAGE = 2 * TG_A_BYTES + 2 * TG_B_BYTES;    // 48 KB
+constexpr int TG_SMEM = TG_S * TG_STAGE + 1024;              // stages, barriers
+constexpr int TG_CHUNK_FLOATS = 2 * TG_B_BYTES / 4;          // one packed chunk of W (hi, lo)
+
+// byte offset of (row, k) in a K-major no-swizzle tile with TG_KS columns of K
+__host__ __device__ constexpr int tg_off(int row, int k) {
+  return (row >> 3) * 512 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+// img[(t * nk + c) * TG_CHUNK_FLOATS + {0, TG_B_BYTES / 4} + tg_off(j, k) / 4] = split parts of
+// W[16 c + k][256 t + j] as FP32 (zero outside na x nb)
+__global__ void tg_pack_kernel(const double* __restrict__ W, int64_t ldw, int na, int nb, int nk, int ntiles,
+                               float* __restrict__ img) {
+  const int64_t total = static_cast<int64_t>(ntiles) * nk * TG_N * TG_KS;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(e % TG_KS);
+    const int j = static_cast<int>((e / TG_KS) % TG_N);
+    const int64_t tc = e / (TG_KS * TG_N);  // t * nk + c
+    const int c = static_cast<int>(tc % nk), t = static_cast<int>(tc / nk);
+    const int kg = c * TG_KS + k, jg = t * TG_N + j;
+    const float x = (kg < na && jg < nb) ? static_cast<float>(W[static_cast<int64_t>(kg) * ldw + jg]) : 0.f;
+    float h, l;
+    split_tf32(x, h, l);
+    float* chunk = img + tc * TG_CHUNK_FLOATS;
+    chunk[tg_off(j, k) / 4] = h;
+    chunk[TG_B_BYTES / 4 + tg_off(j, k) / 4] = l;
+  }
+}
+
+// entries k0 .. k0 + 7 of a row of In (zero past na or n), k0 = 16 c + 8 (half)
+__device__ __forceinline__ void tg_load_half(const float* __restrict__ In, int64_t ldi, int64_t row, int64_t n, int na,
+                                             int c, int half, float (&a)[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) a[e] = 0.f;
+  if (row >= n) return;
+  const int k0 = c * TG_KS + 8 * half;
+  const float* p = In + row * ldi + k0;
+  const int kv = na - k0;  // valid entries from k0 (may be <= 0)
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    if (4 * g + 4 <= kv) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(p + 4 * g));
+      a[4 * g] = v.x;
+      a[4 * g + 1] = v.y;
+      a[4 * g + 2] = v.z;
+      a[4 * g + 3] = v.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (4 * g + e < kv) a[4 * g + e] = p[4 * g + e];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TG_THREADS, 1)
+gemm_tc_kernel(int64_t n, const float* __restrict__ In, int64_t ldi, int na, const float* __restrict__ img, int nk,
+               int nb, float alpha, float beta, float* __restrict__ Out, int64_t ldo, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * TG_M;
+  const int t_n = blockIdx.y, j0 = t_n * TG_N;
+  const int nbt = min(TG_N, nb - j0);            // columns of this tile
+  const int nmma = (nbt + 15) / 16 * 16;         // the MMA's N
+  unsigned long long* bar_b = reinterpret_cast<unsigned long long*>(smem + TG_S * TG_STAGE);  // [TG_S]
+  unsigned long long* bar_mma = bar_b + TG_S;                                                // [TG_S]
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(bar_mma + TG_S);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < 2 * TG_S; ++q) mbar_init(&bar_b[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = *tmem_slot;
+  const unsigned idesc = make_idesc_tf32(TG_M, nmma);
+  const float* img_t = img + static_cast<size_t>(t_n) * nk * TG_CHUNK_FLOATS;
+  // this thread's accumulator slice and running sums
+  const int q = warp & 3, ch = warp >> 2;
+  const unsigned tl = (static_cast<unsigned>(q * 32) << 16) + static_cast<unsigned>(ch * 128);
+  const int ngrp = max(0, min(4, (nbt - ch * 128 + 31) / 32));  // groups of 32 columns this thread holds
+  float sum[128];
+#pragma unroll
+  for (int e = 0; e < 128; ++e) sum[e] = 0.f;
+  // row half of In this thread stages: row tid / 2, entries 8 (tid % 2) .. +7 of each chunk
+  const int arow = tid >> 1, ahalf = tid & 1;
+
+  unsigned ph_mma = 0u, pend_mma = 0u;
+  unsigned ph_b = 0u, pend_b = 0u;  // bulk copies of W: thread 0's bookkeeping only
+  bool ok = true;
+  float a[8];
+  tg_load_half(In, ldi, r0 + arow, n, na, 0, ahalf, a);
+
+  // add chunk cc's buffer into the running sums (its MMAs are complete)
+  auto drain = [&](int cc) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned base = tmem + tl + static_cast<unsigned>((cc & 1) * TG_N);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      if (g < ngrp) {  // warp-uniform
+        float v[32];
+        tmem_ld32(base + 32 * g, v);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) sum[32 * g + e] = __fadd_rn(sum[32 * g + e], v[e]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  };
+
+  for (int c = 0; c < nk; ++c) {
+    const int s = c % TG_S;
+    unsigned char* st = smem + s * TG_STAGE;
+    // stage s was last read by chunk c - TG_S, whose MMAs every thread waited for when it
+    // drained that chunk (at iteration c - TG_S + 1 <= c - 1)
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok) break;
+    if (tid == 0) {
+      mbar_expect_tx(&bar_b[s], 2 * TG_B_BYTES);
+      bulk_g2s(st + 2 * TG_A_BYTES, img_t + static_cast<size_t>(c) * TG_CHUNK_FLOATS, 2 * TG_B_BYTES, &bar_b[s]);
+      pend_b |= 1u << s;
+    }
+    {
+      float h[8], l[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) split_tf32(a[e], h[e], l[e]);
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const int o = tg_off(arow, 8 * ahalf + 4 * g);
+        *reinterpret_cast<float4*>(st + o) = make_float4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
+        *reinterpret_cast<float4*>(st + TG_A_BYTES + o) =
+            make_float4(l[4 * g], l[4 * g + 1], l[4 * g + 2], l[4 * g + 3]);
+      }
+    }
+    if (c + 1 < nk) tg_load_half(In, ldi, r0 + arow, n, na, c + 1, ahalf, a);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // also: buffer c & 1 was drained (chunk c - 2) by every thread
+    if (tid == 0) {
+      const bool got = mbar_wait(&bar_b[s], (ph_b >> s) & 1u);
+      ok = got && ok;
+      if (got) {
+        ph_b ^= 1u << s;
+        pend_b &= ~(1u << s);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned base = smem_u32(st);
+        const unsigned long long dah = make_sdesc(base, 128, 512);
+        const unsigned long long dal = make_sdesc(base + TG_A_BYTES, 128, 512);
+        const unsigned long long dbh = make_sdesc(base + 2 * TG_A_BYTES, 128, 512);
+        const unsigned long long dbl = make_sdesc(base + 2 * TG_A_BYTES + TG_B_BYTES, 128, 512);
+        const unsigned d = tmem + static_cast<unsigned>((c & 1) * TG_N);
+#pragma unroll
+        for (int kk = 0; kk < TG_KS / 8; ++kk) {
+          const unsigned long long o = 16ull * kk;  // 256 bytes = two core matrices along K
+          mma_tf32(d, dah + o, dbh + o, idesc, kk > 0 ? 1u : 0u);
+          mma_tf32(d, dah + o, dbl + o, idesc, 1u);
+          mma_tf32(d, dal + o, dbh + o, idesc, 1u);
+        }
+      }
+      mma_commit(&bar_mma[s]);  // also after a failed wait: the barrier then completes at once
+    }
+    pend_mma |= 1u << s;
+    if (c >= 1) {  // drain chunk c - 1 while chunk c's MMAs run
+      const int sp = (c - 1) % TG_S;
+      if (mbar_wait(&bar_mma[sp], (ph_mma >> sp) & 1u)) {
+        ph_mma ^= 1u << sp;
+        pend_mma &= ~(1u << sp);
+        drain(c - 1);
+      } else {
+        ok = false;  // left pending: the clean-up below waits for it again
+      }
+    }
+  }
+  if (ok && nk > 0) {
+    const int sl = (nk - 1) % TG_S;
+    if (mbar_wait(&bar_mma[sl], (ph_mma >> sl) & 1u)) {
+      ph_mma ^= 1u << sl;
+      pend_mma &= ~(1u << sl);
+      drain(nk - 1);
+    } else {
+      ok = false;
+    }
+  }
+  // after a failed wait: let whatever is still in flight finish before the memory goes
+  for (int s = 0; s < TG_S; ++s)
+    if ((pend_mma >> s) & 1u)
+      if (!mbar_wait(&bar_mma[s], (ph_mma >> s) & 1u)) ok = false;
+  if (tid == 0)
+    for (int s = 0; s < TG_S; ++s)
+      if ((pend_b >> s) & 1u)
+        if (!mbar_wait(&bar_b[s], (ph_b >> s) & 1u)) ok = false;
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok && tid == 0) atomicExch(err, 1);
+  if (ok) {
+    const int64_t row = r0 + q * 32 + lane;
+    if (row < n) {
+      float* o = Out + row * ldo + j0 + ch * 128;
+      const int nc = min(128, nbt - ch * 128);  // columns this thread writes (<= 0: none)
+#pragma unroll
+      for (int g = 0; g < 32; ++g) {
+        const int c4 = 4 * g;
+        if (c4 + 4 <= nc) {
+          float4 r = make_float4(alpha * sum[c4], alpha * sum[c4 + 1], alpha * sum[c4 + 2], alpha * sum[c4 + 3]);
+          if (beta != 0.f) {
+            const float4 old = *reinterpret_cast<const float4*>(o + c4);
+            r.x = fmaf(beta, old.x, r.x);
+            r.y = fmaf(beta, old.y, r.y);
+            r.z = fmaf(beta, old.z, r.z);
+            r.w = fmaf(beta, old.w, r.w);
+          }
+          *reinterpret_cast<float4*>(o + c4) = r;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (c4 + e < nc) o[c4 + e] = beta != 0.f ? fmaf(beta, o[c4 + e], alpha * sum[c4 + e]) : alpha * sum[c4 + e];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 }  // namespace
 
 int gram_tc_rows_align() { return TC_KS * TC_FOLD; }
@@ -402,6 +656,31 @@ arb_status gram_tc_launch(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, i
                                                               err_dev);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
+}
+
+bool gemm_tc_supported(int64_t ldi, int64_t ldo, const void* In, const void* Out) {
+  return ldi % 4 == 0 && ldo % 4 == 0 && (reinterpret_cast<uintptr_t>(In) % 16) == 0 &&
+         (reinterpret_cast<uintptr_t>(Out) % 16) == 0;
+}
+
+arb_status gemm_tc_launch(arb_ctx ctx, int64_t n, const float* In, int64_t ldi, int32_t na, const double* W,
+                          int64_t ldw, int32_t nb, float alpha, float beta, float* Out, int64_t ldo, float* img,
+                          int* err_dev) {
+  const int nk = (na + TG_KS - 1) / TG_KS, ntiles = (nb + TG_N - 1) / TG_N;
+  const int64_t pack = static_cast<int64_t>(ntiles) * nk * TG_N * TG_KS;
+  tg_pack_kernel<<<static_cast<unsigned>(std::min<int64_t>((pack + 255) / 256, 4096)), 256, 0, ctx->stream>>>(
+      W, ldw, na, nb, nk, ntiles, img);
+  ARB_LAUNCHED(ctx);
+  ARB_CUDA(ctx, cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TG_SMEM));
+  dim3 grid(static_cast<unsigned>((n + TG_M - 1) / TG_M), static_cast<unsigned>(ntiles));
+  gemm_tc_kernel<<<grid, TG_THREADS, TG_SMEM, ctx->stream>>>(n, In, ldi, na, img, nk, nb, alpha, beta, Out, ldo,
+                                                              err_dev);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+size_t gemm_tc_image_floats(int32_t na, int32_t nb) {
+  return static_cast<size_t>((nb + TG_N - 1) / TG_N) * ((na + TG_KS - 1) / TG_KS) * TG_CHUNK_FLOATS;
 }
 
 }  // namespace arb

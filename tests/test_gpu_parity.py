@@ -209,6 +209,33 @@ def test_gram_f32_tensor_cores(arb, ctx, n, na, nb):
     assert (np.abs(G - X64.T @ X64) / np.outer(nx, nx)).max() <= 1e-6
 
 
+@pytest.mark.parametrize("n,na,nb,pad", [(1, 8, 4, 0), (300, 7, 5, 0), (1000, 17, 33, 0), (4099, 240, 240, 0),
+                                         (20000, 720, 240, 0), (5000, 100, 300, 0), (777, 64, 48, 1),
+                                         (2_097_152, 720, 240, 0)])
+def test_gemm_tall_f32_matches_numpy(arb, ctx, n, na, nb, pad):
+    # leading dimensions rounded up to multiples of 4 take the tensor cores (na >= 8); pad = 1
+    # makes them odd (CUDA cores).  Per entry within 1e-6 of sum_k |In_ik| |W_kj| (split TF32,
+    # FP32 sums); at full size on 4096 sampled rows
+    g = torch.Generator(device="cuda").manual_seed(n + na + nb)
+    la, lb = (na + 3) // 4 * 4 + pad, (nb + 3) // 4 * 4 + pad
+    In = torch.randn((n, la), dtype=torch.float32, device="cuda", generator=g)[:, :na]
+    W = torch.randn((na, nb), dtype=torch.float64, device="cuda", generator=g)
+    Out0 = torch.randn((n, lb), dtype=torch.float32, device="cuda", generator=g)[:, :nb]
+    rows = torch.arange(n, device="cuda") if n <= 20000 else torch.randint(0, n, (4096,), device="cuda", generator=g)
+    Wf = W.float().double()  # W enters as FP32
+    for alpha, beta in ((1.0, 0.0), (-1.0, 1.0)):
+        Out = Out0.clone()
+        arb.arb_gemm_tall_f32(ctx, In, W, alpha, beta, Out)
+        Is, Os, O0 = In[rows].double(), Out[rows].double(), Out0[rows].double()
+        ref = alpha * (Is @ Wf) + beta * O0
+        bound = 1e-6 * (Is.abs() @ Wf.abs()) + 1e-7 * O0.abs() + 1e-30
+        assert bool(((Os - ref).abs() <= bound).all()), float(((Os - ref).abs() / bound).max())
+    if n <= 20000:  # beta = 0 never reads Out
+        Out = torch.full((n, lb), float("nan"), dtype=torch.float32, device="cuda")[:, :nb]
+        arb.arb_gemm_tall_f32(ctx, In, W, 1.0, 0.0, Out)
+        assert bool(torch.isfinite(Out).all())
+
+
 @pytest.mark.parametrize("m", [1, 2, 3, 10, 31, 64, 65, 96, 97, 200, 256, 720])
 def test_syevj_matches_oracle_jacobi(arb, ctx, m):
     rng = np.random.default_rng(m)
