@@ -301,9 +301,9 @@ def run_ours(args):
     peak, peak_src = measured_peaks()
     achieved = fbytes / (f_ms * 1e-3) / 1e9
     # DRAM bytes per launch: ncu's dram__bytes_read.sum + dram__bytes_write.sum on a
-    # 100^3 x 240 FP32 filter pass of this kernel came to 1.003 x its algorithmic bytes
-    # (2.949 GB vs 2.94 GB); scaled to the full launch by the same ratio (the FP32 kernel only)
-    traffic = 1.003 * fbytes / W.degree if s_bytes == 4 else None
+    # 100^3 x 240 FP32 filter pass of this kernel came to 1.000 x its algorithmic bytes
+    # (2.9399 GB vs 2.9395 GB); scaled to the full launch by the same ratio (the FP32 kernel only)
+    traffic = 1.000 * fbytes / W.degree if s_bytes == 4 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": kname, "launch_ms": f_ms / W.degree,
             "algorithmic_bytes_per_launch": fbytes / W.degree, "flops_per_launch": fflops / W.degree,
@@ -415,7 +415,17 @@ def run_dense_only(args):
     U32 = torch.randn((n, m), dtype=torch.float32, device="cuda")
     AU32 = torch.randn((n, m), dtype=torch.float32, device="cuda")
     out["gram_f32_mxm_ms"] = timed(lambda: arb.arb_gram_f32(ctx, U32, AU32), reps=1)
-    del U32, AU32
+    # the FP32 phase's Ritz rotation U V (n x (q+1)p times (q+1)p x p): tensor cores, and the
+    # CUDA-core kernel on the same data with an odd leading dimension
+    Vr = torch.randn((m, p), dtype=torch.float64, device="cuda")
+    R32 = torch.empty((n, p), dtype=torch.float32, device="cuda")
+    out["gemm_tc_mxp_ms"] = timed(lambda: arb.arb_gemm_tall_f32(ctx, U32, Vr, 1.0, 0.0, R32), reps=2)
+    del AU32
+    Uo = torch.empty((n, m + 1), dtype=torch.float32, device="cuda")[:, :m]
+    Uo.copy_(U32)
+    del U32
+    out["gemm_cuda_core_mxp_ms"] = timed(lambda: arb.arb_gemm_tall_f32(ctx, Uo, Vr, 1.0, 0.0, R32), reps=1)
+    del Uo, R32
     X64 = torch.randn((n, p), dtype=torch.float64, device="cuda")
     out["gram_f64_pxp_sym_ms"] = timed(lambda: arb.arb_gram(ctx, X64, X64), reps=1)
     out["gram_df_pxp_sym_ms"] = timed(lambda: arb.arb_gram(ctx_df, X64, X64), reps=2, c=ctx_df)
