@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--dense-only", action="store_true",
                     help="only time the dense building blocks of one ARR at the workload's sizes: for profiling")
     ap.add_argument("--ncols", type=int, default=0)
+    ap.add_argument("--chung-lu", type=int, default=0,
+                    help="filter-only: the Chung-Lu normalised graph Laplacian with this many rows instead")
+    ap.add_argument("--sell", default="",
+                    help="filter-only: give the matrix a SELL-C-sigma copy, 'C,sigma' (e.g. 32,1024)")
     ap.add_argument("--degree", type=int, default=0)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
@@ -392,7 +396,8 @@ def run_dense_only(args):
     from paper_1507_06078_gb300 import build
     build.build()
     W = workload(args.grid)
-    n, p, m = W.A.n, W.p, (W.q + 1) * W.p
+    p = args.ncols or W.p
+    n, m = W.A.n, (W.q + 1) * p
     ctx = arb.Context(0)
     ctx_df = arb.Context(0)
     ctx_df.set_dense_df(True)
@@ -446,11 +451,18 @@ def run_filter_only(args):
     from paper_1507_06078_gb300 import build
     build.build()
     W = workload(args.grid)
+    A, shift, b = W.A, 12.0, 11.9  # S = 12 I - A maps the 3D Laplacian's spectrum into [0, 12]
+    if args.chung_lu:
+        A, _ = I.chung_lu_laplacian(args.chung_lu, seed=1507)
+        shift, b = 2.0, 1.9  # a normalised Laplacian's spectrum lies in [0, 2]
     ncols = args.ncols or W.p
     d = args.degree or W.degree
     ctx = arb.Context(0)
-    mat = arb.Matrix.from_csr(ctx, W.A)
-    X = arb.arb_gaussian_block(ctx, W.A.n, ncols, W.seed)
+    mat = arb.Matrix.from_csr(ctx, A)
+    if args.sell:
+        c_, s_ = (int(v) for v in args.sell.split(","))
+        mat.set_sell(c_, s_)
+    X = arb.arb_gaussian_block(ctx, A.n, ncols, W.seed)
     if args.precision == "mixed":
         X = X.float()
         f = arb.arb_filter_f32
@@ -463,18 +475,19 @@ def run_filter_only(args):
         s = 8
     Y = torch.empty_like(X)
     coef = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, d)
-    f(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, X, Y=Y)  # warm-up: workspaces, kernel attributes
+    f(ctx, mat, -1.0, shift, 0.0, b, coef, X, Y=Y)  # warm-up: workspaces, kernel attributes
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(ctx.stream)
     for _ in range(args.reps):
-        f(ctx, mat, -1.0, 12.0, 0.0, 11.9, coef, X, Y=Y)
+        f(ctx, mat, -1.0, shift, 0.0, b, coef, X, Y=Y)
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / (args.reps * d)
-    nb = filter_algorithmic_bytes(W.A.n, W.A.nnz, ncols, d, s=s, z=s) / d
-    print(json.dumps({"filter_only": True, "n": W.A.n, "ncols": ncols, "degree": d, "precision": args.precision,
+    nb = filter_algorithmic_bytes(A.n, A.nnz, ncols, d, s=s, z=s) / d
+    print(json.dumps({"filter_only": True, "n": A.n, "nnz": A.nnz, "ncols": ncols, "degree": d,
+                      "precision": args.precision, "layout": ("sell " + args.sell) if args.sell else "csr",
                       "ms_per_pass": ms, "algorithmic_GBps": nb / ms / 1e6}))
 
 

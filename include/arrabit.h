@@ -154,6 +154,38 @@ arb_status arb_matrix_create_csr_f32(arb_ctx ctx, int64_t n, int64_t nnz, const 
 arb_status arb_csr_check_symmetric(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
                                    const double* val, double rel_tol);
 arb_status arb_matrix_destroy(arb_mat mat);
+
+/* SELL-C-sigma layout (Kreutzer, Hager, Wellein, Fehske & Bishop, SIAM J. Sci. Comput. 2014)
+ * of a CSR pattern, computed on the host (no device, no context).
+ * Rows are sorted by decreasing nonzero count within each window of sigma consecutive rows
+ * (ties: lower row first).  The sorted rows are cut into chunks of C, and each chunk is
+ * stored column-major with the width of its longest row: slot cptr[c] + j*C + r holds
+ * nonzero j of the chunk's row r.
+ * Inputs: rowptr int32[n+1] (rowptr[0] = 0, nondecreasing); C >= 1; sigma >= 1.
+ * Outputs (caller-owned host arrays):
+ *  - perm int32[n]: the original row at each sorted position;
+ *  - len int32[n]: its nonzero count;
+ *  - cptr int64[ceil(n/C) + 1]: the first slot of each chunk;
+ *  - *slots: the slot count, cptr's last entry;
+ *  - src int64[slots], if non-NULL: the CSR index stored in each slot, -1 for padding.
+ * Errors: ARB_INVALID_ARG for bad arguments, a bad rowptr, or src_capacity < *slots.  In
+ * the last case *slots is still set, so a first call with src = NULL sizes src. */
+arb_status arb_sell_layout(int64_t n, const int32_t* rowptr, int32_t C, int32_t sigma,
+                           int32_t* perm, int32_t* len, int64_t* cptr, int64_t* src,
+                           int64_t src_capacity, int64_t* slots);
+/* Give a matrix a SELL-C-sigma copy (the layout above, built from its CSR arrays).  From
+ * then on every SpMM of the filter, augmentation, Rayleigh-Ritz and residual steps reads it.
+ * This covers FP64, FP32 and double-float values, all made now.
+ * Rows are processed in sorted order and written to their original block rows. Each row's
+ * nonzeros are summed in CSR order, so results equal the CSR path's. The one exception is
+ * the column reductions, which sum rows in another order.
+ * C = 0 drops the copy (CSR again). 1 <= C <= 1024 and sigma >= 1 otherwise; C = 32 with
+ * sigma a multiple of it is the usual choice.
+ * Not to be called while other calls use the matrix.  The CSR arrays are kept.
+ * Errors: ARB_INVALID_ARG, ARB_CUDA_ERROR (the matrix is then back on CSR). */
+arb_status arb_matrix_set_sell(arb_ctx ctx, arb_mat mat, int32_t C, int32_t sigma);
+/* The matrix's SELL parameters and slot count (0, 0, 0: CSR only). */
+arb_status arb_matrix_sell_info(arb_mat mat, int32_t* C, int32_t* sigma, int64_t* slots);
 /* Gershgorin interval [lo, hi] of A (host outputs); stands in for the paper's eigs
  * estimate of lambda_n (Section 5, "Estimation of lambda_n and lambda_{k+q}"). */
 arb_status arb_matrix_gershgorin(arb_ctx ctx, arb_mat mat, double* lo, double* hi);

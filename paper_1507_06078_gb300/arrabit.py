@@ -78,6 +78,9 @@ _PROTOS = {
     "arb_matrix_create_csr_f32": (_i32, [_vp, _i64, _i64, _vp, _vp, _vp, C.c_int, C.POINTER(_vp)]),
     "arb_csr_check_symmetric": (_i32, [_i64, _i64, _vp, _vp, _vp, _dbl]),
     "arb_matrix_destroy": (_i32, [_vp]),
+    "arb_sell_layout": (_i32, [_i64, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _i64, C.POINTER(_i64)]),
+    "arb_matrix_set_sell": (_i32, [_vp, _vp, _i32, _i32]),
+    "arb_matrix_sell_info": (_i32, [_vp, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i64)]),
     "arb_matrix_gershgorin": (_i32, [_vp, _vp, C.POINTER(_dbl), C.POINTER(_dbl)]),
     "arb_solve": (_i32, [_vp, _vp, _i32, _i32, _dbl, C.POINTER(arb_options), _vp, C.c_int, _vp, _vp, _i64,
                          C.c_int, C.POINTER(arb_info)]),
@@ -209,6 +212,18 @@ class Matrix:
     def from_csr(cls, ctx: Context, A) -> "Matrix":
         return cls(ctx, A.n, A.rowptr, A.col, A.val)
 
+    def set_sell(self, chunk: int = 32, sigma: int = 1024):
+        """Give the matrix a SELL-C-sigma copy (chunk = 0: back to CSR only)."""
+        _check(self.ctx, load().arb_matrix_set_sell(self.ctx.handle, self.handle, chunk, sigma),
+               "arb_matrix_set_sell")
+
+    def sell_info(self) -> tuple[int, int, int]:
+        c, s, slots = _i32(), _i32(), _i64()
+        st = load().arb_matrix_sell_info(self.handle, C.byref(c), C.byref(s), C.byref(slots))
+        if st != ARB_OK:
+            raise ArbError(st, "arb_matrix_sell_info")
+        return c.value, s.value, slots.value
+
     def close(self):
         if self.handle:
             load().arb_matrix_destroy(self.handle)
@@ -219,6 +234,27 @@ class Matrix:
             self.close()
         except Exception:
             pass
+
+
+def arb_sell_layout(rowptr, chunk: int, sigma: int):
+    """Host SELL-C-sigma layout of a CSR pattern: (perm, len, cptr, src) as numpy arrays."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    n = rowptr.shape[0] - 1
+    perm = np.zeros(max(n, 1), dtype=np.int32)
+    ln = np.zeros(max(n, 1), dtype=np.int32)
+    cptr = np.zeros((n + chunk - 1) // max(chunk, 1) + 1 if chunk > 0 else 1, dtype=np.int64)
+    slots = _i64()
+    lib = load()
+    st = lib.arb_sell_layout(n, rowptr.ctypes.data, chunk, sigma, perm.ctypes.data, ln.ctypes.data,
+                             cptr.ctypes.data, None, 0, C.byref(slots))
+    if st != ARB_OK:
+        raise ArbError(st, "arb_sell_layout")
+    src = np.zeros(max(slots.value, 1), dtype=np.int64)
+    st = lib.arb_sell_layout(n, rowptr.ctypes.data, chunk, sigma, perm.ctypes.data, ln.ctypes.data,
+                             cptr.ctypes.data, src.ctypes.data, src.shape[0], C.byref(slots))
+    if st != ARB_OK:
+        raise ArbError(st, "arb_sell_layout")
+    return perm[:n], ln[:n], cptr, src[:slots.value]
 
 
 def arb_options_default(k: int) -> arb_options:

@@ -345,6 +345,7 @@ extern "C" arb_status arb_matrix_destroy(arb_mat m) {
   cudaFree(m->val);
   if (m->val32) cudaFree(m->val32);
   if (m->valdf) cudaFree(m->valdf);
+  matrix_free_sell(m);
   delete m;
   return ARB_OK;
 }

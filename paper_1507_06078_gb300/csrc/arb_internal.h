@@ -102,6 +102,17 @@ struct arb_mat_s {
   float* val32 = nullptr;  // FP32 copy of val for the mixed-precision filter (made on demand)
   arb::df2* valdf = nullptr;  // double-float copy of val for the double-float filter (made on demand)
   int32_t max_row_nnz = -1;  // longest row (-1: unknown)
+  // SELL-C-sigma copy (arb_matrix_set_sell; sell_C = 0: CSR only).  The SpMM kernels take
+  // it when present; the CSR arrays stay for everything else.
+  int32_t sell_C = 0, sell_sigma = 0;
+  int64_t sell_slots = 0;
+  int32_t* sell_perm = nullptr;  // [n] original row at each sorted position
+  int32_t* sell_len = nullptr;   // [n] its nonzero count
+  int64_t* sell_cptr = nullptr;  // [chunks + 1] first slot of each chunk
+  int32_t* sell_col = nullptr;   // [slots] column indices (padding: 0)
+  double* sell_val = nullptr;    // [slots] values (padding: 0), and their FP32 / double-float copies
+  float* sell_val32 = nullptr;
+  arb::df2* sell_valdf = nullptr;
   bool gersh_valid = false;
   double gersh_lo = 0.0, gersh_hi = 0.0;
   std::mutex mu;  // guards the lazily made val32 / valdf and the Gershgorin cache (shared by server workers)
@@ -299,6 +310,8 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
 // w (descending), V (row-major, column j = eigenvector) of symmetric H (not modified).
 // Sweeps stop when off(A) <= tol ||H||_F: 1e-15 for FP64 data, 1e-10 where H is formed from
 // FP32 blocks and so carries FP32-level errors itself.
+// frees a matrix's SELL-C-sigma arrays (sell.cu)
+void matrix_free_sell(arb_mat m);
 // df: orders above 96 in double-float arithmetic on the FP32 pipe (stops at <= 1e-13).
 // jac_df / jac_tol: the Jacobi arithmetic and tolerance for matrices formed from element
 // type T: FP32 bases (accurate to ~1e-7) and double-float dense products take the

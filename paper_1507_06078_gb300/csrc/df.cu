@@ -45,6 +45,10 @@ struct DfParams {
   int64_t ldo;
   double* red_part;
   int dot_with_yin;
+  const int32_t* perm;  // SELL-C-sigma (MODE 2), as in the FP32/FP64 kernel
+  const int32_t* slen;
+  const int64_t* scptr;
+  int sellC;
 };
 
 // one 16-byte load of a column pair of a paired planar block
@@ -81,10 +85,13 @@ __device__ __forceinline__ float4 pack4(const dfp& a) { return make_float4(a.hi.
 // 512-byte warp access - and walks its rows, gathers issued DF_BATCH at a time, as in the
 // FP32/FP64 fused kernel.  Leading dimensions are even and bases 16-byte aligned; for odd
 // ncols the pad column (ld >= ncols + 1) is read and written but never reduced.
-// SHORT (rows of at most 32 nonzeros, blocks below 2^31 elements): row pointers loaded two
+// MODE 0: CSR; MODE 2: SELL-C-sigma (rows in sorted order, indices and values from the chunk
+// slots, block rows through perm).
+// MODE 1, SHORT (rows of at most 32 nonzeros, blocks below 2^31 elements): row pointers loaded two
 // rows ahead, column indices and values one row ahead, 32-bit element offsets.
-template <bool RED, bool SHORT>
+template <bool RED, int MODE>
 __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(DfParams P) {
+  constexpr bool SHORT = MODE == 1, SELL = MODE == 2;
   extern __shared__ double s_red[];  // RED: [DF_WARPS][ncols]
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -163,6 +170,8 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
     for (int64_t row = r_first; row < P.n; row += rstride) {
       int beg = 0, end = 0, s_jc = 0;
       float s_ah = 0.f, s_al = 0.f;
+      int64_t orow = row;  // the block row (SELL: the sorted position's original row)
+      int64_t sbase = 0;   // SELL: slot of the row's first nonzero
       if constexpr (SHORT) {
         s_jc = n_jc;
         s_ah = n_ah;
@@ -185,6 +194,10 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
           p_beg = __ldg(P.rowptr + r2);
           p_end = __ldg(P.rowptr + r2 + 1);
         }
+      } else if constexpr (SELL) {
+        orow = __ldg(P.perm + row);
+        end = __ldg(P.slen + row);
+        sbase = __ldg(P.scptr + row / P.sellC) + row % P.sellC;
       } else {
         beg = __ldg(P.rowptr + row);
         end = __ldg(P.rowptr + row + 1);
@@ -194,9 +207,9 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
 #pragma unroll
       for (int u = 0; u < DF_NP; ++u) {
         xv[u] = zv[u] = yi[u] = zero;
-        if (P.X) xv[u] = ldps(P.X + off(row, P.ldx) + cl[u]);
-        if (P.Z) zv[u] = ldps(P.Z + off(row, P.ldz) + cl[u]);
-        if (need_yi) yi[u] = ldp(P.Yin + off(row, P.ldy) + cl[u]);
+        if (P.X) xv[u] = ldps(P.X + off(orow, P.ldx) + cl[u]);
+        if (P.Z) zv[u] = ldps(P.Z + off(orow, P.ldz) + cl[u]);
+        if (need_yi) yi[u] = ldp(P.Yin + off(orow, P.ldy) + cl[u]);
       }
       float2 S[DF_NP], E[DF_NP];
 #pragma unroll
@@ -211,8 +224,9 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
         } else {
           const int e = base + lane;
           if (e < end) {
-            jc = __ldg(P.col + e);
-            const float2 v = __ldg(reinterpret_cast<const float2*>(P.val) + e);
+            const int64_t idx = SELL ? sbase + static_cast<int64_t>(e) * P.sellC : static_cast<int64_t>(e);
+            jc = __ldg(P.col + idx);
+            const float2 v = __ldg(reinterpret_cast<const float2*>(P.val) + idx);
             ah = v.x;
             al = v.y;
           }
@@ -257,7 +271,7 @@ __global__ void __launch_bounds__(DF_THREADS, ARB_DF_MIN_BLOCKS) spmm_df_kernel(
         if (P.Z) dot2p(So, Eo, kmul[3][u], neg(kmul[3][u]), zv[u]);
         const dfp o = fast_two_sum2(So, Eo);
         if (P.out && act[u])
-          __stcs(reinterpret_cast<float4*>(P.out + off(row, P.ldo) + cp[u]), pack4(o));
+          __stcs(reinterpret_cast<float4*>(P.out + off(orow, P.ldo) + cp[u]), pack4(o));
         if constexpr (RED) {
           const double o0 = static_cast<double>(o.hi.x) + static_cast<double>(o.lo.x);
           const double o1 = static_cast<double>(o.hi.y) + static_cast<double>(o.lo.y);
@@ -371,15 +385,21 @@ template <>
 arb_status spmm_fused<df2>(arb_ctx ctx, const SpmmArgs<df2>& a) {
   const arb_mat_s* A = a.A;
   if (a.ncols <= 0 || A->n <= 0) return ARB_OK;
-  if (!A->valdf) return set_error(ctx, ARB_INVALID_ARG, "spmm(df): matrix has no double-float values");
+  const bool sell = A->sell_C > 0;
+  if (!(sell ? A->sell_valdf : A->valdf))
+    return set_error(ctx, ARB_INVALID_ARG, "spmm(df): matrix has no double-float values");
   const bool even = (a.ldy % 2 == 0) && (!a.X || a.ldx % 2 == 0) && (!a.Z || a.ldz % 2 == 0) &&
                     (!a.out || a.ldo % 2 == 0);
   if (!even) return set_error(ctx, ARB_INVALID_ARG, "spmm(df): leading dimensions must be even");
   DfParams P;
   P.n = A->n;
   P.rowptr = A->rowptr;
-  P.col = A->col;
-  P.val = A->valdf;
+  P.col = sell ? A->sell_col : A->col;
+  P.val = sell ? A->sell_valdf : A->valdf;
+  P.perm = A->sell_perm;
+  P.slen = A->sell_len;
+  P.scptr = A->sell_cptr;
+  P.sellC = A->sell_C;
   P.ncols = a.ncols;
   P.Yin = a.Yin;
   P.ldy = a.ldy;
@@ -404,8 +424,10 @@ arb_status spmm_fused<df2>(arb_ctx ctx, const SpmmArgs<df2>& a) {
   if (a.Z) ld_max = std::max(ld_max, a.ldz);
   if (a.out) ld_max = std::max(ld_max, a.ldo);
   const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32 && A->n * ld_max < (int64_t(1) << 31);
-  void (*kern)(DfParams) = short_rows ? (want_red ? spmm_df_kernel<true, true> : spmm_df_kernel<false, true>)
-                                      : (want_red ? spmm_df_kernel<true, false> : spmm_df_kernel<false, false>);
+  const int mode = sell ? 2 : (short_rows ? 1 : 0);
+  void (*kern)(DfParams) = mode == 2   ? (want_red ? spmm_df_kernel<true, 2> : spmm_df_kernel<false, 2>)
+                           : mode == 1 ? (want_red ? spmm_df_kernel<true, 1> : spmm_df_kernel<false, 1>)
+                                       : (want_red ? spmm_df_kernel<true, 0> : spmm_df_kernel<false, 0>);
   ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DF_THREADS, smem));

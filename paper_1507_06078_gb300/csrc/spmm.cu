@@ -56,6 +56,12 @@ struct KParams {
   int64_t ldo;
   double* red_part;  // [gridDim.x][ncols] per-block partial column reductions, or NULL
   int dot_with_yin;
+  // SELL-C-sigma (MODE 2): sorted position i holds block row perm[i], of slen[i] nonzeros
+  // stored at slots scptr[i / sellC] + i % sellC + e * sellC (e = 0 .. slen[i] - 1)
+  const int32_t* perm;
+  const int32_t* slen;
+  const int64_t* scptr;
+  int sellC;
 };
 
 // VEC consecutive elements as one 8/16-byte access
@@ -148,13 +154,18 @@ struct VecIO<float, 4> {
 // RED adds the column reduction (sum of out^2 or out*Yin) in FP64 registers, combined per
 // CTA through shared memory.
 //
-// SHORT (every row has at most 32 nonzeros, e.g. stencils, and every block has fewer than
+// MODE 0: CSR.  MODE 2: SELL-C-sigma - rows taken in their sorted order (longest first within
+// each sigma window, so the warps of a CTA get rows of similar length), each row's indices
+// and values read from its chunk's column-major slots; the block rows it reads and writes
+// are the original ones (perm), so the result is the same, summed in the same order.
+// MODE 1, SHORT (every row has at most 32 nonzeros, e.g. stencils, and every block has fewer than
 // 2^31 elements): the index loads of a row are software-pipelined across the warp's rows -
 // the row pointers two rows ahead, the column indices and values one row ahead - so a row
 // waits only on its gathers, not on the chain rowptr -> col -> Yin of three dependent
 // loads; element offsets are 32-bit products.
-template <typename T, int VEC, bool RED, bool SHORT>
+template <typename T, int VEC, bool RED, int MODE>
 __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_kernel(KParams<T> P) {
+  constexpr bool SHORT = MODE == 1, SELL = MODE == 2;
   extern __shared__ double s_red[];  // [SPMM_WARPS][ncols] when RED
   constexpr int CH = 32 * VEC;
   constexpr int UNR = SHORT ? ARB_SPMM_SHORT_UNROLL : ARB_SPMM_UNROLL;
@@ -206,6 +217,8 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
     for (int64_t row = r_first; row < P.n; row += rstride) {
       int beg = 0, end = 0, s_jc = 0;
       T s_av = T(0);
+      int64_t orow = row;  // the block row (SELL: the sorted position's original row)
+      int64_t sbase = 0;   // SELL: slot of the row's first nonzero
       if constexpr (SHORT) {
         s_jc = n_jc;
         s_av = n_av;
@@ -225,6 +238,10 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
           p_beg = __ldg(P.rowptr + r2);
           p_end = __ldg(P.rowptr + r2 + 1);
         }
+      } else if constexpr (SELL) {
+        orow = __ldg(P.perm + row);
+        end = __ldg(P.slen + row);
+        sbase = __ldg(P.scptr + row / P.sellC) + row % P.sellC;
       } else {
         beg = __ldg(P.rowptr + row);
         end = __ldg(P.rowptr + row + 1);
@@ -235,11 +252,11 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
         else return r * ld;
       };
       T xv[VEC], zv[VEC], yi[VEC];
-      if (P.X) VecIO<T, VEC>::lds(P.X + off(row, P.ldx) + cl, xv);
-      if (P.Z) VecIO<T, VEC>::lds(P.Z + off(row, P.ldz) + cl, zv);
+      if (P.X) VecIO<T, VEC>::lds(P.X + off(orow, P.ldx) + cl, xv);
+      if (P.Z) VecIO<T, VEC>::lds(P.Z + off(orow, P.ldz) + cl, zv);
       // the row's own entries of Yin with them, ahead of the gathers (not after the sums)
       const bool need_yi = P.beta != T(0) || (RED && P.dot_with_yin);
-      if (need_yi) VecIO<T, VEC>::ld(P.Yin + off(row, P.ldy) + cl, yi);
+      if (need_yi) VecIO<T, VEC>::ld(P.Yin + off(orow, P.ldy) + cl, yi);
       T acc[VEC];
 #pragma unroll
       for (int u = 0; u < VEC; ++u) acc[u] = T(0);
@@ -252,8 +269,9 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
         } else {
           const int e = base + lane;
           if (e < end) {
-            jc = __ldg(P.col + e);
-            av = __ldg(P.val + e);
+            const int64_t idx = SELL ? sbase + static_cast<int64_t>(e) * P.sellC : static_cast<int64_t>(e);
+            jc = __ldg(P.col + idx);
+            av = __ldg(P.val + idx);
           }
         }
         const int cnt = __shfl_sync(0xffffffffu, min(32, end - base), 0);  // warp-uniform
@@ -320,7 +338,7 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
           for (int u = 0; u < VEC; ++u) o[u] = fma(csz[u], zv[u], o[u]);
         }
       }
-      if (P.out) VecIO<T, VEC>::sts(P.out + off(row, P.ldo) + c, o);
+      if (P.out) VecIO<T, VEC>::sts(P.out + off(orow, P.ldo) + c, o);
       if constexpr (RED) {
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
@@ -428,11 +446,12 @@ __global__ void col_sumsq_kernel(int64_t n, const double* __restrict__ X, int64_
 // second, partly empty wave of CTAs runs at the end.  With want_red, the per-CTA partial
 // column sums go to a workspace of grid x ncols doubles (returned with the grid).
 template <typename T, int VEC>
-arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, bool short_rows, int* grid_out,
+arb_status launch_spmm(arb_ctx ctx, KParams<T> P, size_t smem, bool want_red, int mode, int* grid_out,
                        double** part_out) {
   void (*kern)(KParams<T>) =
-      short_rows ? (want_red ? spmm_fused_kernel<T, VEC, true, true> : spmm_fused_kernel<T, VEC, false, true>)
-                 : (want_red ? spmm_fused_kernel<T, VEC, true, false> : spmm_fused_kernel<T, VEC, false, false>);
+      mode == 2   ? (want_red ? spmm_fused_kernel<T, VEC, true, 2> : spmm_fused_kernel<T, VEC, false, 2>)
+      : mode == 1 ? (want_red ? spmm_fused_kernel<T, VEC, true, 1> : spmm_fused_kernel<T, VEC, false, 1>)
+                  : (want_red ? spmm_fused_kernel<T, VEC, true, 0> : spmm_fused_kernel<T, VEC, false, 0>);
   ARB_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SPMM_THREADS, smem));
@@ -456,11 +475,11 @@ template <typename T>
 const T* values_of(const arb_mat_s* A);
 template <>
 const double* values_of<double>(const arb_mat_s* A) {
-  return A->val;
+  return A->sell_C > 0 ? A->sell_val : A->val;
 }
 template <>
 const float* values_of<float>(const arb_mat_s* A) {
-  return A->val32;
+  return A->sell_C > 0 ? A->sell_val32 : A->val32;
 }
 
 }  // namespace
@@ -489,8 +508,12 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   KParams<T> P;
   P.n = A->n;
   P.rowptr = A->rowptr;
-  P.col = A->col;
+  P.col = A->sell_C > 0 ? A->sell_col : A->col;
   P.val = values_of<T>(A);
+  P.perm = A->sell_perm;
+  P.slen = A->sell_len;
+  P.scptr = A->sell_cptr;
+  P.sellC = A->sell_C;
   P.ncols = a.ncols;
   P.Yin = a.Yin;
   P.ldy = a.ldy;
@@ -529,19 +552,20 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   if (a.Z) ld_max = std::max(ld_max, a.ldz);
   if (a.out) ld_max = std::max(ld_max, a.ldo);
   const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32 && A->n * ld_max < (int64_t(1) << 31);
+  const int mode = A->sell_C > 0 ? 2 : (short_rows ? 1 : 0);
   if constexpr (sizeof(T) == 4) {
     if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
-      ARB_TRY((launch_spmm<T, 4>(ctx, P, smem, want_red, short_rows, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 4>(ctx, P, smem, want_red, mode, &grid, &part)));
     } else if (fits(2)) {
-      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, short_rows, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, mode, &grid, &part)));
     } else {
-      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, short_rows, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, mode, &grid, &part)));
     }
   } else {
     if (fits(2)) {
-      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, short_rows, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, mode, &grid, &part)));
     } else {
-      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, short_rows, &grid, &part)));
+      ARB_TRY((launch_spmm<T, 1>(ctx, P, smem, want_red, mode, &grid, &part)));
     }
   }
   if (want_red) {

@@ -500,6 +500,57 @@ def test_solve_chung_lu_scaled(arb, ctx, precision):
     assert np.linalg.norm(R, axis=0).max() <= 1e-8 * 8.0
 
 
+@pytest.mark.parametrize("which", ["chung_lu", "laplace3d"])
+def test_sell_spmm_and_filters_match_csr(arb, ctx, which):
+    # SELL-C-sigma (C = 32, sigma = 1024) walks the rows in sorted order but sums each row's
+    # nonzeros in CSR order: SpMM and all three filter arithmetics are bitwise equal to the
+    # CSR kernels (power-law rows of 2 to hundreds of nonzeros; 7-point stencil rows)
+    if which == "chung_lu":
+        A, _ = I.chung_lu_laplacian(20000, seed=3)
+        shift, b = 2.0, 1.9
+    else:
+        A = I.laplacian_3d(24)
+        shift, b = 12.0, 11.9
+    m_csr = arb.Matrix.from_csr(ctx, A)
+    m_sell = arb.Matrix.from_csr(ctx, A)
+    m_sell.set_sell(32, 1024)
+    c, sg, slots = m_sell.sell_info()
+    assert (c, sg) == (32, 1024) and A.nnz <= slots < 2 * A.nnz + 32 * 1024
+    X = dev(I.gaussian_block(A.n, 40, 7))
+    y_csr = host(arb.arb_spmm(ctx, m_csr, 1.0, 0.0, X))
+    y_sell = host(arb.arb_spmm(ctx, m_sell, 1.0, 0.0, X))
+    np.testing.assert_array_equal(y_sell, y_csr)
+    Xh = host(X)
+    ref = scipy_of(A) @ Xh
+    np.testing.assert_allclose(y_sell, ref, atol=1e-13 * (abs(scipy_of(A)) @ abs(Xh)).max())
+    coef = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, 8)
+    for f, Xin in ((arb.arb_filter, X), (arb.arb_filter_f32, X.float()), (arb.arb_filter_df, X)):
+        a = host(f(ctx, m_csr, -1.0, shift, 0.0, b, coef, Xin))
+        s_ = host(f(ctx, m_sell, -1.0, shift, 0.0, b, coef, Xin))
+        np.testing.assert_array_equal(s_, a)
+    m_sell.set_sell(0, 0)
+    assert m_sell.sell_info() == (0, 0, 0)
+    np.testing.assert_array_equal(host(arb.arb_spmm(ctx, m_sell, 1.0, 0.0, X)), y_csr)
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_solve_chung_lu_sell(arb, ctx, precision):
+    # the scaled Chung-Lu solve on the SELL-C-sigma copy: k smallest against LAPACK
+    A, _ = I.chung_lu_laplacian(3000, seed=11)
+    k, p = 20, 30
+    X0 = I.gaussian_block(A.n, p, 5)
+    mat = arb.Matrix.from_csr(ctx, A)
+    mat.set_sell(32, 256)
+    o = arb.arb_options_default(k)
+    o.p, o.q, o.degree, o.precision = p, 1, 15, precision
+    r = arb.arb_solve(ctx, mat, k, 1, 1e-8, o, x0=X0, evecs="host")
+    assert r.status == arb.ARB_OK, r.info
+    lam = np.linalg.eigvalsh(A.to_dense())[:k]
+    np.testing.assert_allclose(r.evals, lam, atol=1e-9)
+    R = scipy_of(A) @ r.evecs - r.evecs * r.evals[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= 1e-8 * 8.0
+
+
 def test_matrix_from_fp32_values(arb, ctx):
     # FP32 values widened on the device give the same matrix (and solve) as the FP64 upload
     # of the same numbers; device-pointer uploads record the longest row too

@@ -87,3 +87,55 @@ def test_symmetry_check_host_only(lib):
     bad = A.rowptr.copy()
     bad[-1] += 1
     assert arb.arb_csr_check_symmetric(A.n, bad, A.col, A.val) == arb.ARB_INVALID_ARG
+
+
+# A worked SELL-C-sigma example from the format's definition (Kreutzer et al. 2014, Sec. 2),
+# derived by hand: 6 rows of lengths 1, 3, 2, 0, 2, 1 (CSR entries 0..8), C = 2, sigma = 4.
+# Window rows 0-3 sorted longest first: 1 (3), 2 (2), 0 (1), 3 (0); window rows 4-5: 4 (2),
+# 5 (1).  Chunks: positions {0, 1} width 3 -> 6 slots, {2, 3} width 1 -> 2 slots, {4, 5}
+# width 2 -> 4 slots.  Column-major slots: chunk 0 holds row 1's entries 1, 2, 3 at slots
+# 0, 2, 4 and row 2's entries 4, 5 at slots 1, 3; chunk 1 row 0's entry 0 at slot 6; chunk 2
+# row 4's entries 6, 7 at slots 8, 10 and row 5's entry 8 at slot 9.
+SELL_EXAMPLE = dict(rowptr=[0, 1, 4, 6, 6, 8, 9], C=2, sigma=4, perm=[1, 2, 0, 3, 4, 5], length=[3, 2, 1, 0, 2, 1],
+                    chunk_start=[0, 6, 8, 12], src=[1, 4, 2, 5, 3, -1, 0, -1, 6, 8, 7, -1])
+
+
+def test_sell_layout_worked_example(lib):
+    from oracle import sell_oracle as S
+    ex = SELL_EXAMPLE
+    for got in (S.sell_c_sigma(ex["rowptr"], ex["C"], ex["sigma"]),
+                arb.arb_sell_layout(np.array(ex["rowptr"]), ex["C"], ex["sigma"])):
+        perm, ln, cptr, src = got
+        assert perm.tolist() == ex["perm"] and ln.tolist() == ex["length"]
+        assert cptr.tolist() == ex["chunk_start"] and src.tolist() == ex["src"]
+
+
+@pytest.mark.parametrize("C,sigma", [(32, 1024), (4, 8), (1, 1), (32, 1), (7, 100), (64, 5000)])
+def test_sell_layout_matches_oracle_on_power_law_rows(lib, C, sigma):
+    # the library's host layout equals the oracle's, integer for integer; the layout
+    # reproduces A x from its slots alone and stores every nonzero exactly once
+    from oracle import sell_oracle as S
+    A, _ = I.chung_lu_laplacian(3000, seed=5)
+    lo = S.sell_c_sigma(A.rowptr, C, sigma)
+    li = arb.arb_sell_layout(A.rowptr, C, sigma)
+    for a, b in zip(lo, li):
+        np.testing.assert_array_equal(a, b)
+    perm, ln, cptr, src = lo
+    assert sorted(src[src >= 0].tolist()) == list(range(A.nnz))
+    x = np.random.default_rng(C + sigma).standard_normal(A.n)
+    dense = A.to_dense()
+    np.testing.assert_allclose(S.sell_matvec(perm, ln, cptr, src, A.col, A.val, C, x), dense @ x, atol=1e-12)
+    # lengths never increase inside a window
+    for w0 in range(0, A.n, sigma):
+        seg = ln[w0:w0 + sigma]
+        assert np.all(np.diff(seg) <= 0)
+
+
+def test_sell_layout_rejects_bad_arguments(lib):
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    with pytest.raises(arb.ArbError):
+        arb.arb_sell_layout(rp, 0, 4)
+    with pytest.raises(arb.ArbError):
+        arb.arb_sell_layout(rp, 2, 0)
+    with pytest.raises(arb.ArbError):
+        arb.arb_sell_layout(np.array([0, 2, 1], dtype=np.int32), 2, 4)

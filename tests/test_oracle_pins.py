@@ -313,3 +313,18 @@ def test_lanczos_bounds_enclose_the_spectrum(which):
     # far tighter than Gershgorin on the graph Laplacian
     if which == "chung_lu":
         assert hi < 0.5 * O.gershgorin_bounds(A)[1]
+
+
+def test_sell_oracle_pins():
+    # SELL-C-sigma oracle against properties fixed by the format's definition: a diagonal
+    # pattern (every row length 1) keeps the identity order and has no padding; C = 1 with
+    # sigma = n is a global sort by decreasing length; sigma = 1 keeps the original order
+    from oracle import sell_oracle as S
+    perm, ln, cptr, src = S.sell_c_sigma(list(range(11)), 4, 8)
+    assert perm.tolist() == list(range(10)) and cptr[-1] == 12 and (src >= 0).sum() == 10
+    rowptr = [0, 2, 2, 7, 8, 11]
+    perm, ln, cptr, src = S.sell_c_sigma(rowptr, 1, 5)
+    assert perm.tolist() == [2, 4, 0, 3, 1] and ln.tolist() == [5, 3, 2, 1, 0]
+    assert cptr.tolist() == [0, 5, 8, 10, 11, 11]
+    perm, ln, cptr, src = S.sell_c_sigma(rowptr, 2, 1)
+    assert perm.tolist() == [0, 1, 2, 3, 4] and cptr.tolist() == [0, 4, 14, 20]
