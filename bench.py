@@ -58,6 +58,12 @@ def parse():
                     help="only apply the filter (--reps times) to an n x --ncols block: for profiling")
     ap.add_argument("--dense-only", action="store_true",
                     help="only time the dense building blocks of one ARR at the workload's sizes: for profiling")
+    ap.add_argument("--serve", action="store_true",
+                    help="served mix: a seeded Poisson stream of solve requests against one server; "
+                         "prints p50/p99 latency and solves/s")
+    ap.add_argument("--rate", type=float, default=4.0, help="--serve: arrivals per second")
+    ap.add_argument("--requests", type=int, default=48, help="--serve: number of requests")
+    ap.add_argument("--slots", type=int, default=4, help="--serve: concurrent solves of the server")
     ap.add_argument("--ncols", type=int, default=0)
     ap.add_argument("--chung-lu", type=int, default=0,
                     help="filter-only: the Chung-Lu normalised graph Laplacian with this many rows instead")
@@ -491,10 +497,74 @@ def run_filter_only(args):
                       "ms_per_pass": ms, "algorithmic_GBps": nb / ms / 1e6}))
 
 
+def run_serve(args):
+    """Served mix, bounded: a seeded Poisson stream (seed 4242) of solve requests in equal
+    thirds of 2D 64^2 Laplacian problems (k = 20, p = 30, d = 10, q = 1), variable-coefficient
+    diffusion instances (sides 32-256, k 8-64, p = 1.5k, d = 10, q = 1) and a 1/8-scale
+    Chung-Lu graph Laplacian (n ~ 125k, k 10-100, p = 1.2k, d = 15, q = 1), all to relative
+    residual 1e-8 with the FP32 filter and double-float refinement, against one server with
+    --slots concurrent solves.  Latency is the library's submit-to-completion wall time;
+    solves/s counts requests over first submission to last completion."""
+    from paper_1507_06078_gb300 import arrabit as arb
+    from paper_1507_06078_gb300 import build
+    build.build()
+    ctx = arb.Context(0)
+    rng = np.random.Generator(np.random.Philox(4242))
+    w0 = I.workload_2d64()
+    lap2d = arb.Matrix.from_csr(ctx, w0.A)
+    diff = I.batched_diffusion_instances(count=4, base_seed=42420, side_range=(32, 256))
+    diff_m = [arb.Matrix.from_csr(ctx, w.A) for w in diff]
+    cl, _ = I.chung_lu_laplacian(125000, seed=4242)
+    cl_m = arb.Matrix.from_csr(ctx, cl)
+    reqs = []
+    for _ in range(args.requests):
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            reqs.append(("laplace2d_64", lap2d, 20, 30, 10))
+        elif kind == 1:
+            j = int(rng.integers(0, len(diff)))
+            reqs.append((diff[j].name, diff_m[j], diff[j].k, diff[j].p, 10))
+        else:
+            k = int(rng.integers(10, 101))
+            reqs.append(("chung_lu_125k", cl_m, k, int(round(1.2 * k)), 15))
+    gaps = rng.exponential(1.0 / args.rate, size=args.requests)
+    srv = arb.Server(0, hbm_budget_bytes=64 << 30, max_slots=args.slots)
+    tickets, t_sub = [], []
+    t0 = time.perf_counter()
+    t_next = t0
+    for (name, mat, k, p, d), g in zip(reqs, gaps):
+        t_next += g
+        delay = t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        o = arb.arb_options_default(k)
+        o.p, o.q, o.degree, o.precision = p, 1, d, arb.ARB_MIXED_DF
+        t_sub.append(time.perf_counter())
+        tickets.append(srv.submit(mat, k, arb.ARB_SMALLEST, 1e-8, o, want_evecs=False))
+    lat, ok, worst = [], 0, 0.0
+    for t in tickets:
+        r = srv.wait(t)
+        lat.append(r.info["latency_s"])
+        ok += int(r.status == arb.ARB_OK)
+        worst = max(worst, r.info["maxres"])
+    srv.close()
+    done = max(ts + lt for ts, lt in zip(t_sub, lat))
+    lat = np.array(lat)
+    print(json.dumps({"serve": True, "rate_per_s": args.rate, "requests": args.requests, "slots": args.slots,
+                      "converged": ok, "max_maxres": worst, "p50_s": float(np.percentile(lat, 50)),
+                      "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+                      "solves_per_s": args.requests / (done - t_sub[0]),
+                      "mix": {nm: sum(1 for r in reqs if r[0] == nm) for nm in sorted({r[0] for r in reqs})},
+                      "precision": "mixed_df", "tol": 1e-8}))
+
+
 def main():
     args = parse()
     if args.filter_only:
         run_filter_only(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
     if args.dense_only:
         run_dense_only(args)
