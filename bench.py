@@ -542,11 +542,17 @@ def run_serve(args):
         t_sub.append(time.perf_counter())
         tickets.append(srv.submit(mat, k, arb.ARB_SMALLEST, 1e-8, o, want_evecs=False))
     lat, ok, worst = [], 0, 0.0
-    for t in tickets:
+    per_kind = {}
+    for (name, *_), t in zip(reqs, tickets):
         r = srv.wait(t)
         lat.append(r.info["latency_s"])
         ok += int(r.status == arb.ARB_OK)
         worst = max(worst, r.info["maxres"])
+        kd = per_kind.setdefault(name, {"requests": 0, "converged": 0, "max_maxres": 0.0, "stops": {}})
+        kd["requests"] += 1
+        kd["converged"] += int(r.status == arb.ARB_OK)
+        kd["max_maxres"] = max(kd["max_maxres"], r.info["maxres"])
+        kd["stops"][r.info["stop_reason"]] = kd["stops"].get(r.info["stop_reason"], 0) + 1
     srv.close()
     done = max(ts + lt for ts, lt in zip(t_sub, lat))
     lat = np.array(lat)
@@ -554,7 +560,7 @@ def run_serve(args):
                       "converged": ok, "max_maxres": worst, "p50_s": float(np.percentile(lat, 50)),
                       "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
                       "solves_per_s": args.requests / (done - t_sub[0]),
-                      "mix": {nm: sum(1 for r in reqs if r[0] == nm) for nm in sorted({r[0] for r in reqs})},
+                      "by_kind": per_kind,
                       "precision": "mixed_df", "tol": 1e-8}))
 
 
