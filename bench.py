@@ -23,6 +23,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -102,7 +103,9 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_dev{device}.csv")
+        # the raw samples go to $ARB_BENCH_OUT (default: the system temp directory)
+        out = os.environ.get("ARB_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"clocks_dev{device}.csv")
 
     def __enter__(self):
         try:
