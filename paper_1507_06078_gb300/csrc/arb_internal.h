@@ -64,6 +64,8 @@ enum WsSlot : int {
   WS_BATCH_DESC,
   WS_TC_ERR,          // tensor-core kernels: error word
   WS_TC_IMG,          // tensor-core tall products: packed split W
+  WS_ORTH_NORM,       // orth's recovery of truncated directions: column norms, column list
+  WS_ORTH_IDX,
   WS_NUM_SLOTS
 };
 
@@ -229,6 +231,8 @@ arb_status gemm_tall(arb_ctx ctx, int64_t n, const T* In, int64_t ldi, int32_t n
                      int64_t ldw, int32_t nb, double alpha, double beta, T* Out, int64_t ldo);
 // dst[:, j] = src[:, idx[j]] for j < ncols (idx on device)
 template <typename T>
+arb_status col_norms2(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t m, double* out);
+template <typename T>
 arb_status gather_cols(arb_ctx ctx, int64_t n, const T* src, int64_t lds, const int32_t* idx,
                        int32_t ncols, T* dst, int64_t ldd);
 // dst[:, j] = idx[j] >= 0 ? srcA[:, idx[j]] : srcB[:, -idx[j]-1]
@@ -345,11 +349,14 @@ arb_status filter_apply(arb_ctx ctx, arb_mat mat, const FilterPlan& plan, const 
                         int32_t ncols, const double* xscale, T* W1, T* W2, int64_t ldw, T* Y,
                         int64_t ldy, double* colss, T** result);
 
-// Orthonormal basis of range(Z) (two eigen-truncated Gram passes).  U must not alias Z.
-// tmp: n x m work block.  *rank on host.
+// Orthonormal basis of range(Z) (two eigen-truncated Gram passes).  U must not alias Z and
+// has room for m columns; tmp: n x m work block.  *rank on host.  recover: when the Gram
+// passes truncated directions, project Z off the basis and orthonormalise what is left
+// above rounding level (up to two rounds), so a block whose singular values span more
+// than the Gram passes resolve (~1e-6 of the largest) keeps its small directions.
 template <typename T>
 arb_status orth(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* U, int64_t ldu, T* tmp,
-                int64_t ldt, int32_t* rank);
+                int64_t ldt, int32_t* rank, bool recover = false);
 
 // Reciprocal 1-norm condition number of diag(xs) X^T X diag(xs) (host result).
 template <typename T>

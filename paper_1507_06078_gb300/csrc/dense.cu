@@ -797,6 +797,33 @@ arb_status gemm_tall(arb_ctx ctx, int64_t n, const T* In, int64_t ldi, int32_t n
   return ARB_OK;
 }
 
+// out[c] = sum_r X[r][c]^2, FP64 sums, one CTA per column and a fixed reduction tree
+template <typename T>
+__global__ void col_norm2_kernel(int64_t n, const T* __restrict__ X, int64_t ldx, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+    const double x = static_cast<double>(X[r * ldx + c]);
+    s = fma(x, x, s);
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+template <typename T>
+arb_status col_norms2(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t m, double* out) {
+  if (m <= 0) return ARB_OK;
+  col_norm2_kernel<T><<<static_cast<unsigned>(m), 256, 0, ctx->stream>>>(n, X, ldx, out);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
 template <typename T>
 arb_status gather_cols(arb_ctx ctx, int64_t n, const T* src, int64_t lds, const int32_t* idx, int32_t ncols,
                        T* dst, int64_t ldd) {
@@ -832,6 +859,8 @@ template arb_status gemm_tall<double>(arb_ctx, int64_t, const double*, int64_t, 
                                       int32_t, double, double, double*, int64_t);
 template arb_status gemm_tall<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, const double*, int64_t,
                                      int32_t, double, double, float*, int64_t);
+template arb_status col_norms2<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, double*);
+template arb_status col_norms2<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, double*);
 template arb_status gather_cols<double>(arb_ctx, int64_t, const double*, int64_t, const int32_t*, int32_t,
                                         double*, int64_t);
 template arb_status gather_cols<float>(arb_ctx, int64_t, const float*, int64_t, const int32_t*, int32_t, float*,

@@ -212,14 +212,55 @@ static arb_status svqb_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int
 
 template <typename T>
 arb_status orth(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* U, int64_t ldu, T* tmp,
-                int64_t ldt, int32_t* rank) {
+                int64_t ldt, int32_t* rank, bool recover) {
   *rank = 0;
   if (m <= 0) return ARB_OK;
   int32_t r1 = 0, r2 = 0;
   ARB_TRY(svqb_pass<T>(ctx, n, Z, ldz, m, tmp, ldt, &r1));
   if (r1 == 0) return ARB_OK;
   ARB_TRY(svqb_pass<T>(ctx, n, tmp, ldt, r1, U, ldu, &r2));
-  *rank = r2;
+  int32_t r = r2;
+  // A Gram pass resolves singular values down to ~sqrt(tau) of the largest.  A filtered
+  // block can span far more (one isolated extreme eigenvalue amplified by the filter), and
+  // the directions the passes dropped are then the ones still to converge.  Recover them:
+  // the residual Z - U U^T Z (projected twice) keeps each column's part outside the basis;
+  // its columns above rounding level (64 m u of the largest column of Z), largest first
+  // and at most m - r, are orthonormalised and appended.
+  if (recover && r < m) {
+    double* nrm;
+    int32_t* idx;
+    ARB_TRY(ws<double>(ctx, WS_ORTH_NORM, static_cast<size_t>(m), &nrm));
+    std::vector<double> zn(m), rn(m);
+    ARB_TRY(col_norms2<T>(ctx, n, Z, ldz, m, nrm));
+    ARB_TRY(d2h_sync(ctx, zn.data(), nrm, m * sizeof(double)));
+    const double zmax = std::sqrt(*std::max_element(zn.begin(), zn.end()));
+    const double thr = 64.0 * m * (sizeof(T) == 4 ? 6e-8 : 1.11e-16) * zmax;
+    for (int round = 0; round < 2 && r < m; ++round) {
+      ARB_TRY((copy_block<T, T>(ctx, n, Z, ldz, m, tmp, ldt)));
+      for (int pass = 0; pass < 2; ++pass) ARB_TRY(project_out<T>(ctx, n, U, ldu, r, tmp, ldt, m));
+      ARB_TRY(col_norms2<T>(ctx, n, tmp, ldt, m, nrm));
+      ARB_TRY(d2h_sync(ctx, rn.data(), nrm, m * sizeof(double)));
+      std::vector<int32_t> keep;
+      for (int32_t j = 0; j < m; ++j)
+        if (std::sqrt(rn[j]) > thr) keep.push_back(j);
+      if (keep.empty()) break;
+      std::stable_sort(keep.begin(), keep.end(), [&](int32_t a, int32_t b) { return rn[a] > rn[b]; });
+      if (static_cast<int32_t>(keep.size()) > m - r) keep.resize(m - r);
+      const int32_t ns = static_cast<int32_t>(keep.size());
+      ARB_TRY(ws<int32_t>(ctx, WS_ORTH_IDX, static_cast<size_t>(ns), &idx));
+      ARB_CUDA(ctx, cudaMemcpyAsync(idx, keep.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+      ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      ARB_TRY(gather_cols<T>(ctx, n, tmp, ldt, idx, ns, U + r, ldu));  // columns r .. r+ns-1 of U
+      int32_t ra = 0, rb = 0;
+      ARB_TRY(svqb_pass<T>(ctx, n, U + r, ldu, ns, tmp, ldt, &ra));
+      if (ra == 0) break;
+      for (int pass = 0; pass < 2; ++pass) ARB_TRY(project_out<T>(ctx, n, U, ldu, r, tmp, ldt, ra));
+      ARB_TRY(svqb_pass<T>(ctx, n, tmp, ldt, ra, U + r, ldu, &rb));
+      if (rb == 0) break;
+      r += rb;
+    }
+  }
+  *rank = r;
   return ARB_OK;
 }
 
@@ -256,7 +297,7 @@ arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double o
   if (sizeof(T) == 4) ARB_TRY(ensure_val32(ctx, mat));
   if (nl > 0) ARB_TRY(project_out<T>(ctx, n, Qc, ldqc, nl, X, ldx, w));
   int32_t r0 = 0;
-  ARB_TRY(orth(ctx, n, static_cast<const T*>(X), ldx, w, wk.U, wk.ldu, wk.T1, wk.ldt, &r0));
+  ARB_TRY(orth(ctx, n, static_cast<const T*>(X), ldx, w, wk.U, wk.ldu, wk.T1, wk.ldt, &r0, true));
   if (r0 == 0) return set_error(ctx, ARB_BREAKDOWN, "ARR: iterate has no numerical rank");
   std::vector<int32_t> off{0}, rk{r0};
   int32_t m = r0;
@@ -326,9 +367,9 @@ template arb_status filter_apply<float>(arb_ctx, arb_mat, const FilterPlan&, con
 template arb_status filter_apply<df2>(arb_ctx, arb_mat, const FilterPlan&, const df2*, int64_t, int32_t, const double*,
                                       df2*, df2*, int64_t, df2*, int64_t, double*, df2**);
 template arb_status orth<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, double*, int64_t, double*,
-                                 int64_t, int32_t*);
+                                 int64_t, int32_t*, bool);
 template arb_status orth<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, float*, int64_t, float*,
-                                int64_t, int32_t*);
+                                int64_t, int32_t*, bool);
 template arb_status rcond_gram<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, const double*, double*);
 template arb_status rcond_gram<float>(arb_ctx, int64_t, const float*, int64_t, int32_t, const double*, double*);
 template arb_status project_out<double>(arb_ctx, int64_t, const double*, int64_t, int32_t, double*, int64_t,

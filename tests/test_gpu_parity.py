@@ -551,6 +551,33 @@ def test_solve_chung_lu_sell(arb, ctx, precision):
     assert np.linalg.norm(R, axis=0).max() <= 1e-8 * 8.0
 
 
+@pytest.fixture(scope="module")
+def chung_lu_125k():
+    return I.chung_lu_laplacian(125000, seed=4242)[0]
+
+
+def test_solve_chung_lu_125k_keeps_small_directions(arb, ctx, chung_lu_125k):
+    # 1/8 of the C2 scale, k = 50: the first filter leaves the block's singular values
+    # spread far beyond what a Gram pass resolves (the near-zero eigenvalue dominates);
+    # orth must recover the truncated directions or the basis collapses to rank ~2 and the
+    # solve stalls at maxres 0.25 (the oracle, with pivoted QR, converges in 4 outer
+    # iterations).  Checked by properties: residuals within the near-tolerance stop rule's
+    # bound, orthogonality, and the smallest eigenvalue near 0 (the connected graph's
+    # Laplacian has an exact 0, which the FP32 rounding of the values perturbs by ~u32)
+    A = chung_lu_125k
+    k, p = 50, 60
+    mat = arb.Matrix.from_csr(ctx, A)
+    o = arb.arb_options_default(k)
+    o.p, o.q, o.degree = p, 1, 15
+    r = arb.arb_solve(ctx, mat, k, 1, 1e-8, o, x0=I.gaussian_block(A.n, p, 5), evecs="host")
+    assert r.status == arb.ARB_OK, r.info
+    Q, lam = r.evecs, r.evals
+    assert abs(lam[0]) <= 1e-7 and np.all(np.diff(lam) >= -1e-12)
+    R = scipy_of(A) @ Q - Q * lam[None, :]
+    assert np.linalg.norm(R, axis=0).max() <= 1e-8 * 10.0
+    np.testing.assert_allclose(Q.T @ Q, np.eye(k), atol=1e-10)
+
+
 def test_matrix_from_fp32_values(arb, ctx):
     # FP32 values widened on the device give the same matrix (and solve) as the FP64 upload
     # of the same numbers; device-pointer uploads record the longest row too
