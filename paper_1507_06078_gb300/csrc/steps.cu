@@ -297,7 +297,10 @@ arb_status arr_basis_and_eig(arb_ctx ctx, arb_mat mat, double op_scale, double o
   if (sizeof(T) == 4) ARB_TRY(ensure_val32(ctx, mat));
   if (nl > 0) ARB_TRY(project_out<T>(ctx, n, Qc, ldqc, nl, X, ldx, w));
   int32_t r0 = 0;
-  ARB_TRY(orth(ctx, n, static_cast<const T*>(X), ldx, w, wk.U, wk.ldu, wk.T1, wk.ldt, &r0, true));
+  // FP32 blocks resolve no more than their Gram pass does (the recovery threshold 64 m u32
+  // of the largest column is about the pass's own cut), so only FP64 bases recover
+  ARB_TRY(orth(ctx, n, static_cast<const T*>(X), ldx, w, wk.U, wk.ldu, wk.T1, wk.ldt, &r0,
+               std::is_same<T, double>::value));
   if (r0 == 0) return set_error(ctx, ARB_BREAKDOWN, "ARR: iterate has no numerical rank");
   std::vector<int32_t> off{0}, rk{r0};
   int32_t m = r0;
