@@ -139,3 +139,14 @@ def test_sell_layout_rejects_bad_arguments(lib):
         arb.arb_sell_layout(rp, 2, 0)
     with pytest.raises(arb.ArbError):
         arb.arb_sell_layout(np.array([0, 2, 1], dtype=np.int32), 2, 4)
+
+
+@pytest.mark.parametrize("rowptr,C,sigma", [([0], 32, 1024), ([0, 3], 32, 1024), ([0, 0, 0], 4, 2),
+                                            ([0, 2, 3, 7], 8, 2), ([0, 1, 1, 4, 4, 6], 2, 100)])
+def test_sell_layout_edge_cases_match_oracle(lib, rowptr, C, sigma):
+    # empty matrix, one row, empty rows, a chunk wider than the matrix, a window wider than it
+    from oracle import sell_oracle as S
+    lo = S.sell_c_sigma(rowptr, C, sigma)
+    li = arb.arb_sell_layout(np.array(rowptr), C, sigma)
+    for a, b in zip(lo, li):
+        np.testing.assert_array_equal(np.asarray(a), np.asarray(b))
