@@ -299,16 +299,19 @@ arb_status arb_gram(arb_ctx ctx, int64_t n, const double* X, int64_t ldx, int32_
 arb_status arb_gram_f32(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, int32_t na,
                         const float* Y, int64_t ldy, int32_t nb, double* C, int64_t ldc);
 
-/* arb_gram for callers that cannot allocate device memory (for example code running
- * while a stream is captured into a CUDA graph, or applications whose device memory is
- * owned by their own pool): the same product C = X^T Y, but its split-K partial sums live
- * in a static device array of 1,048,576 doubles (8 MiB) that the library holds on every
- * device it is loaded on, so the call allocates nothing.  The paper has no counterpart;
- * this is an interface variant only.
+/* arb_gram for callers that cannot let a library allocate device memory: applications
+ * whose device memory is owned by their own pool allocator (which may hold all free memory
+ * and must see every allocation), and latency-bound loops that must not meet the implicit
+ * device synchronisation of cudaMalloc / cudaFree.  The same product C = X^T Y, but its
+ * split-K partial sums live in a static device array of 1,048,576 doubles (8 MiB) that
+ * the library holds on every device it is loaded on until the process exits, so the call
+ * allocates nothing.  The paper has no counterpart; this is an interface variant only.
  *  - Limit: na * nb <= 1048576, else ARB_INVALID_ARG (nothing is launched).  Larger
  *    shapes go through arb_gram.  The row split shrinks so the partial sums fit.
  *  - The first call on a device looks up the array's device address (with that device
- *    current) and caches it; make that first call before any stream capture.
+ *    current) and caches it for the process; make that first call before any stream
+ *    capture.  cudaDeviceReset discards the array with the device's context, so do not
+ *    call this after resetting a device it was used on.
  *  - Every call shares the one array: calls whose kernels overlap on the GPU (different
  *    streams, or two contexts on one device) race on it and must be serialised by the
  *    caller.  Each call overwrites every partial sum it reads, so no clearing is needed.

@@ -384,7 +384,9 @@ def lanczos_bounds(A: sp.csr_matrix, steps: int, seed: int) -> tuple[float, floa
     return float(lo), float(hi)
 
 
-# the library draws the Lanczos start column from stream seed + 0x9E3779B97F4A7C15 (mod 2^64)
+# Input convention shared with the library, not arithmetic of the method: the Lanczos start
+# column is the Gaussian stream number seed + 0x9E3779B97F4A7C15 (mod 2^64), so that both
+# sides start the spectrum estimate from the same column of the seeded input generator
 BOUND_SEED_OFFSET = 0x9E3779B97F4A7C15
 
 

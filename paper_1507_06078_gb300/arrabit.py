@@ -401,8 +401,21 @@ def arb_spmm(ctx: Context, mat: Matrix, op_scale: float, op_shift: float, X, Y=N
     return Y
 
 
+def _gram_shapes(X, Y, C_out):
+    """X^T Y needs X and Y with the same row count and, when given, C_out of shape
+    (X columns, Y columns); checked before any pointer reaches the library, whose
+    arguments carry no row count for Y and no row count for C."""
+    if X.dim() != 2 or Y.dim() != 2:
+        raise ValueError("X and Y must be 2D")
+    if Y.shape[0] != X.shape[0]:
+        raise ValueError(f"Y has {Y.shape[0]} rows, X has {X.shape[0]}")
+    if C_out is not None and tuple(C_out.shape) != (X.shape[1], Y.shape[1]):
+        raise ValueError(f"C_out must be {X.shape[1]} x {Y.shape[1]}, got {tuple(C_out.shape)}")
+
+
 def arb_gram(ctx: Context, X, Y, C_out=None):
     import torch
+    _gram_shapes(X, Y, C_out)
     ldx = _dev2d(X, "X")
     ldy = _dev2d(Y, "Y")
     if C_out is None:
@@ -416,6 +429,7 @@ def arb_gram(ctx: Context, X, Y, C_out=None):
 def arb_gram_f32(ctx: Context, X, Y, C_out=None):
     """C = X^T Y for FP32 CUDA tensors (row-major 2D), FP64 result."""
     import torch
+    _gram_shapes(X, Y, C_out)
     for name, T in (("X", X), ("Y", Y)):
         if not (T.is_cuda and T.dtype == torch.float32 and T.dim() == 2 and T.stride(1) == 1):
             raise ValueError(f"{name}: expected a row-major 2D float32 CUDA tensor")
@@ -445,6 +459,9 @@ def arb_gemm_tall_f32(ctx: Context, In, W, alpha=1.0, beta=0.0, Out=None):
 def arb_gram_noalloc(ctx: Context, X, Y, C_out):
     """C = X^T Y without any device allocation by the library (partial sums in its static
     scratch); C_out must be given."""
+    if C_out is None:
+        raise ValueError("C_out must be given (the call allocates nothing)")
+    _gram_shapes(X, Y, C_out)
     ldx = _dev2d(X, "X")
     ldy = _dev2d(Y, "Y")
     ldc = _dev2d(C_out, "C")

@@ -1,13 +1,12 @@
 // Gram product for callers that cannot allocate device memory.
 //
 // arb_gram's split-K partial sums normally live in a workspace the context allocates on
-// first use.  Some callers cannot let a library call cudaMalloc: code that runs while a
-// stream is being captured into a CUDA graph (an allocation there is not recorded and
-// may synchronise), applications whose device memory is owned by their own pool
-// allocator, and latency-critical loops that must not hit the implicit synchronisation
-// of cudaMalloc/cudaFree.  arb_gram_noalloc serves them: its partial sums go to a
-// file-scope device array that exists as long as the library is loaded, so the call
-// itself allocates nothing.
+// first use.  Some callers cannot let a library call cudaMalloc: applications whose device
+// memory is owned by their own pool allocator (it may hold all free memory, and it must
+// account for every allocation), and latency-critical loops that must not hit the
+// implicit synchronisation of cudaMalloc/cudaFree.  arb_gram_noalloc serves them: its
+// partial sums go to a file-scope device array that exists as long as the library is
+// loaded, so the call itself allocates nothing.
 #include <mutex>
 
 #include "arb_internal.h"

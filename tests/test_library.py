@@ -150,3 +150,20 @@ def test_sell_layout_edge_cases_match_oracle(lib, rowptr, C, sigma):
     li = arb.arb_sell_layout(np.array(rowptr), C, sigma)
     for a, b in zip(lo, li):
         np.testing.assert_array_equal(np.asarray(a), np.asarray(b))
+
+
+@pytest.mark.parametrize("fn", ["arb_gram", "arb_gram_f32", "arb_gram_noalloc"])
+def test_gram_bindings_refuse_mismatched_shapes_before_any_launch(fn):
+    # the C entry points take no row count for Y and none for C: a short Y or a small C
+    # would be read or written out of bounds, so the binding refuses them before it
+    # touches a pointer (host tensors here: nothing reaches the library)
+    torch = pytest.importorskip("torch")
+    f = getattr(arb, fn)
+    dt = torch.float32 if fn == "arb_gram_f32" else torch.float64
+    X = torch.zeros((100, 4), dtype=dt)
+    with pytest.raises(ValueError, match="rows"):
+        f(None, X, torch.zeros((99, 3), dtype=dt), torch.zeros((4, 3), dtype=torch.float64))
+    with pytest.raises(ValueError, match="C_out"):
+        f(None, X, torch.zeros((100, 3), dtype=dt), torch.zeros((4, 2), dtype=torch.float64))
+    with pytest.raises(ValueError, match="C_out"):
+        f(None, X, torch.zeros((100, 3), dtype=dt), torch.zeros((3, 4), dtype=torch.float64))

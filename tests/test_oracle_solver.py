@@ -98,13 +98,116 @@ def test_oracle_horner_path_matches():
 
 
 def test_oracle_locking_path():
-    # a tolerance tight enough that continuation runs and pairs get locked
+    # Deflation (eq. defl, Algorithm 8): with the first continuation tolerance tol_1 = 1e-3
+    # the lock threshold is tol_1^2 = 1e-6, so the leading pairs, which converge first, are
+    # locked while the rest iterate; the later outer iterations then run with a non-empty
+    # Q_c (projection of X and Z, merge of locked and new Ritz pairs)
     A = I.laplacian_2d(20)
     X0 = I.gaussian_block(A.n, 14, 8)
-    r = O.arrabit_mpm(_scipy(A), 12, X0, which="smallest", tol=1e-12, q=1, degree=8)
+    B = _scipy(A)
+    r = O.arrabit_mpm(B, 12, X0, which="smallest", tol=1e-10, q=1, degree=8, tol1=1e-3)
     assert r.converged
-    np.testing.assert_allclose(r.evals, laplacian_2d_eigs(20)[:12], atol=1e-11)
-    assert any(h.n_locked > 0 for h in r.history) or r.outer_iters <= 3
+    assert any(h.n_locked > 0 for h in r.history)
+    lam = laplacian_2d_eigs(20)[:12]
+    np.testing.assert_allclose(r.evals, lam, atol=1e-12)
+    # the merged set stays orthonormal to rounding level (a partial projection against the
+    # locked block leaves ~1e-13 of it in the free block)
+    assert np.abs(r.evecs.T @ r.evecs - np.eye(12)).max() <= 1e-13
+    _check_invariants(B, r, 1e-10, 8.0)
+
+
+def test_oracle_locking_grows_to_all_locked():
+    # k = p and a tolerance below what FP64 residuals reach: the pairs lock as they pass the
+    # floor of the threshold (1e-14), until the whole block is locked (the all-locked exit)
+    A = I.laplacian_2d(20)
+    X0 = I.gaussian_block(A.n, 10, 8)
+    r = O.arrabit_mpm(_scipy(A), 10, X0, which="smallest", tol=1e-15, q=1, degree=8, tol1=1e-2)
+    assert r.stop_reason == "all_locked"
+    assert max(h.n_locked for h in r.history) > 0
+    np.testing.assert_allclose(r.evals, laplacian_2d_eigs(20)[:10], atol=1e-13)
+    np.testing.assert_allclose(r.evecs.T @ r.evecs, np.eye(10), atol=1e-13)
+
+
+@pytest.mark.parametrize("slip", ["dropped", "sign", "half", "transposed"])
+def test_planted_project_out_slip_is_caught(monkeypatch, slip):
+    # each plausible mistake in X - Q_c (Q_c^T X) fails one of the locking-path pins above:
+    # the solve raises, misses an eigenvalue, or loses orthogonality of the merged set
+    def bad(Qc, X):
+        if Qc is None or Qc.shape[1] == 0:
+            return X
+        if slip == "dropped":
+            return X
+        if slip == "sign":
+            return X + Qc @ (Qc.T @ X)
+        if slip == "half":
+            return X - 0.5 * Qc @ (Qc.T @ X)
+        return X - Qc[:, ::-1] @ (Qc.T @ X)
+
+    monkeypatch.setattr(O, "project_out", bad)
+    A = I.laplacian_2d(20)
+    X0 = I.gaussian_block(A.n, 14, 8)
+    lam = laplacian_2d_eigs(20)[:12]
+    try:
+        r = O.arrabit_mpm(_scipy(A), 12, X0, which="smallest", tol=1e-10, q=1, degree=8, tol1=1e-3)
+    except RuntimeError:
+        return
+    err = np.max(np.abs(r.evals - lam))
+    orth = np.abs(r.evecs.T @ r.evecs - np.eye(12)).max()
+    assert err > 1e-10 or orth > 1e-13
+
+
+def test_pad_ritz_invariants():
+    # completing a short Ritz set: the first columns and values are kept, the new columns
+    # are orthonormal and orthogonal to the kept ones, and their values are Rayleigh
+    # quotients (so they lie inside the spectrum of B)
+    A = _scipy(I.laplacian_2d(12))
+    wref, Vref = np.linalg.eigh(A.toarray())
+    Y, w = Vref[:, -3:][:, ::-1], wref[-3:][::-1]
+    pool = I.gaussian_block(A.shape[0], 6, 41)
+    Yp, wp = O.pad_ritz(A, Y, w, 7, pool)
+    assert Yp.shape == (A.shape[0], 7) and wp.shape == (7,)
+    np.testing.assert_array_equal(Yp[:, :3], Y)
+    np.testing.assert_array_equal(wp[:3], w)
+    np.testing.assert_allclose(Yp.T @ Yp, np.eye(7), atol=1e-13)
+    assert np.all(wp[3:] >= wref[0] - 1e-12) and np.all(wp[3:] <= wref[-1] + 1e-12)
+    # a full set is returned unchanged; a short one without a pool is an error
+    Yf, wf = O.pad_ritz(A, Yp, wp, 7, None)
+    assert Yf is Yp and wf is wp
+    with pytest.raises(RuntimeError):
+        O.pad_ritz(A, Y, w, 7, None)
+
+
+def test_oracle_rank_deficient_start_block_is_padded():
+    # duplicated start columns: X keeps rank 5 through the filter, the q = 1 subspace has
+    # dimension 10 < p = 14, so the Ritz set is completed from the pool; the solve still
+    # reaches the dense eigenvalues
+    n, k, p = 400, 8, 14
+    A = _random_sparse_spd(n, 0.02, 77)
+    wref = np.linalg.eigvalsh(A.toarray())
+    G = I.gaussian_block(n, 5, 32)
+    X0 = np.hstack([G, G, G[:, :4]])
+    pool = I.gaussian_block(n, p, 33)
+    r = O.arrabit_mpm(A, k, X0, which="largest", tol=1e-10, q=1, degree=10, pad_pool=pool)
+    assert r.history[0].rank == 10
+    assert r.converged
+    np.testing.assert_allclose(r.evals, wref[::-1][:k], atol=1e-9 * np.abs(wref).max())
+
+
+def test_residual_denominators_use_the_original_eigenvalue():
+    # eq. resi divides by max(1, |lambda_i|) with lambda_i an eigenvalue of A.  For the
+    # smallest pairs of A = L + 200 I the method runs on sigma I - A, whose Ritz values
+    # mu_i = sigma - lambda_i are near 8, far from lambda_i near 200: the reported
+    # residuals must equal ||A x_i - lambda_i x_i|| / |lambda_i| recomputed from the pairs
+    L = _scipy(I.laplacian_2d(16))
+    A = (L + 200.0 * sp.identity(L.shape[0])).tocsr()
+    X0 = I.gaussian_block(L.shape[0], 12, 13)
+    r = O.arrabit_mpm(A, 10, X0, which="smallest", tol=1e-6, q=1, degree=4)
+    assert r.converged
+    direct = np.linalg.norm(A @ r.evecs - r.evecs * r.evals[None, :], axis=0) / np.abs(r.evals)
+    big = r.res > 1e-11  # far above the ~1e-16 rounding of the recomputation
+    assert big.sum() >= 5
+    np.testing.assert_allclose(r.res[big], direct[big], rtol=0.01)
+    np.testing.assert_allclose(r.evals, 200.0 + laplacian_2d_eigs(16)[:10], rtol=1e-9)
 
 
 def test_augmentation_helps():
@@ -150,3 +253,36 @@ def test_oracle_b_every_arr_reading():
     np.testing.assert_allclose(r_arr.evals, lam, atol=1e-9)
     np.testing.assert_allclose(r_lit.evals, lam, atol=1e-9)
     assert r_arr.history[-1].b > r_arr.history[0].b  # b moved towards lambda_{k+q} of B
+
+
+def test_planted_residual_denominator_slip_is_caught(monkeypatch):
+    # dividing by max(1, |mu_i|) of the shifted operator instead of max(1, |lambda_i|)
+    # makes the reported residuals ~25x too large on the shifted Laplacian above
+    real = O.residual_norms
+    monkeypatch.setattr(O, "residual_norms", lambda B, X, mu, lam: real(B, X, mu, mu))
+    L = _scipy(I.laplacian_2d(16))
+    A = (L + 200.0 * sp.identity(L.shape[0])).tocsr()
+    X0 = I.gaussian_block(L.shape[0], 12, 13)
+    r = O.arrabit_mpm(A, 10, X0, which="smallest", tol=1e-6, q=1, degree=4)
+    direct = np.linalg.norm(A @ r.evecs - r.evecs * r.evals[None, :], axis=0) / np.abs(r.evals)
+    big = r.res > 1e-11
+    assert not np.allclose(r.res[big], direct[big], rtol=0.01)
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_arr_exact_on_a_krylov_invariant_subspace(q):
+    # Algorithm 5 on a diagonal B: a column supported on q + 1 coordinates spans, with its
+    # first q powers, exactly those coordinate vectors, so ARR returns exactly the q + 1
+    # diagonal entries there (descending) with the unit vectors as Ritz vectors
+    n = 50
+    dvals = np.linspace(-1.0, 3.0, n) ** 3
+    B = sp.diags(dvals).tocsr()
+    support = [3, 17, 41][: q + 1]
+    X = np.zeros((n, 1))
+    X[support, 0] = [1.0, -2.0, 0.5][: q + 1]
+    Y, w = O.arr(B, X, q, npairs=q + 1)
+    want = np.sort(dvals[support])[::-1]
+    np.testing.assert_allclose(w, want, atol=1e-13)
+    for j in range(q + 1):
+        i = support[int(np.argmin(np.abs(dvals[support] - w[j])))]
+        assert abs(abs(Y[i, j]) - 1.0) <= 1e-12

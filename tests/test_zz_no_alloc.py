@@ -1,8 +1,10 @@
-"""arb_gram_noalloc: the Gram product for callers that cannot allocate device memory
-(graph-capturing code, applications with their own memory pool).  Its partial sums live
-in the library's static device scratch; it must give arb_gram's result, also on a second
-call that reuses the scratch, and refuse shapes that do not fit.  Collected last so a
-stop-at-first-failure run has already run every other test."""
+"""arb_gram_noalloc: the Gram product for callers that cannot let a library allocate
+device memory (applications whose device memory belongs to their own pool allocator, and
+latency-bound loops that must not meet cudaMalloc's implicit synchronisation).  Its
+partial sums live in the library's static device scratch.  It must give the host product
+X^T Y and arb_gram's result, also on a second call that reuses the scratch, allocate no
+device memory, and refuse shapes that do not fit.  Collected last so a stop-at-first-
+failure run has already run every other test."""
 import numpy as np
 import pytest
 
@@ -36,13 +38,21 @@ def test_noalloc_gram_matches_gram_on_two_calls(env, n, na, nb, same):
         Y = X if same else _blk(n, nb, 10 * call + 2)
         ref = arb.arb_gram(ctx, X, Y)
         C = torch.full((na, nb), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         arb.arb_gram_noalloc(ctx, X, Y, C)
         torch.cuda.synchronize()
-        # same products, sums split differently over rows: the Gram tolerance of the parity
-        # tests, 1e-13 ||x_i|| ||y_j|| per entry
-        bound = 1e-13 * torch.outer(X.norm(dim=0), Y.norm(dim=0))
-        assert torch.isfinite(C).all()
-        assert bool(((C - ref).abs() <= bound).all())
+        if call == 1:  # once the library's module is loaded, a call takes no device memory
+            assert torch.cuda.mem_get_info()[0] == free0
+        # the host product in FP64, and arb_gram's: same products, sums split differently
+        # over rows - the Gram tolerance of the parity tests, 1e-13 ||x_i|| ||y_j||
+        Xh, Yh = X.cpu().numpy(), Y.cpu().numpy()
+        host = Xh.T @ Yh
+        bound = 1e-13 * np.outer(np.linalg.norm(Xh, axis=0), np.linalg.norm(Yh, axis=0))
+        Ch = C.cpu().numpy()
+        assert np.isfinite(Ch).all()
+        assert np.all(np.abs(Ch - host) <= bound)
+        assert np.all(np.abs(Ch - ref.cpu().numpy()) <= bound)
 
 
 def test_noalloc_gram_refuses_shapes_beyond_scratch(env):
