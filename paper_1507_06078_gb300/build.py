@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIBPATH = os.path.join(LIBDIR, "libarrabit.so")
-SOURCES = ["spmm.cu", "dense.cu", "jacobi.cu", "steps.cu", "api.cu", "noalloc.cu", "server.cu", "batched.cu", "df.cu", "tc.cu", "sell.cu"]
+SOURCES = ["spmm.cu", "dense.cu", "jacobi.cu", "steps.cu", "api.cu", "noalloc.cu", "server.cu", "batched.cu", "df.cu", "tc.cu", "sell.cu", "chol.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -33,10 +33,16 @@ def cuda_home() -> str:
     return os.path.dirname(os.path.dirname(os.path.realpath(nvcc())))
 
 
+def extra_flags() -> list[str]:
+    """Extra nvcc flags from $ARB_NVCC_FLAGS, e.g. the kernels' tuning macros
+    (-DARB_SPMM_UNROLL=8); empty by default."""
+    return os.environ.get("ARB_NVCC_FLAGS", "").split()
+
+
 def _compile(src: str) -> str:
     obj = os.path.join(OBJDIR, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-           "-c", os.path.join(CSRC, src), "-o", obj]
+           *extra_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -66,6 +66,10 @@ enum WsSlot : int {
   WS_TC_IMG,          // tensor-core tall products: packed split W
   WS_ORTH_NORM,       // orth's recovery of truncated directions: column norms, column list
   WS_ORTH_IDX,
+  WS_CHOL,            // Cholesky: diagonal-block inverse, status words, factor, inverse
+  WS_CHOL_STATUS,
+  WS_CHOL_R,
+  WS_CHOL_RINV,
   WS_NUM_SLOTS
 };
 
@@ -306,6 +310,22 @@ arb_status gemm_tc_launch(arb_ctx ctx, int64_t n, const float* In, int64_t ldi, 
 arb_status gram_tc_launch(arb_ctx ctx, int64_t n, const float* X, int64_t ldx, int32_t na, const float* Y,
                           int64_t ldy, int32_t nb, int symmetric, double* part, int64_t nsplit, int64_t rows,
                           int* err_dev);
+
+// ---------------------------------------------------------------- Cholesky (chol.cu)
+// In place: the upper triangle of the symmetric m x m matrix A (row-major, lda) becomes the
+// factor R with A = R^T R (FP64, blocked right-looking).  A pivot <= thr (or not finite)
+// stops the factorisation: status[0] = 1, status[1] = its index (device words, cleared
+// first).  No host synchronisation.
+arb_status cholesky_upper(arb_ctx ctx, int32_t m, double* A, int64_t lda, double thr, int32_t* status);
+int cholesky_max_order();
+// M (m x m, row-major, ld m) = diag(d) R^{-1} (d NULL: R^{-1}) for the upper factor R;
+// nothing is written when status[0] != 0.
+arb_status triangular_inverse(arb_ctx ctx, int32_t m, const double* R, int64_t lda, const double* d, double* M,
+                              const int32_t* status);
+// rc_dev = 1 / (||G||_1 ||G^{-1}||_1) with G^{-1} from the Cholesky factor of G; 0 when G is
+// not numerically positive definite.  R, Rinv, Ginv: m x m work matrices.
+arb_status rcond_from_cholesky(arb_ctx ctx, int32_t m, const double* G, int64_t ldg, double* R, double* Rinv,
+                               double* Ginv, int32_t* status, double* rc_dev);
 
 // ---------------------------------------------------------------- batched filter (batched.cu)
 arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs);

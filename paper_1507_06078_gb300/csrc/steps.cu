@@ -210,11 +210,50 @@ static arb_status svqb_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int
   return ARB_OK;
 }
 
+// One CholeskyQR pass: G = Z^T Z, D = diag(G)^{-1/2}, D G D = R^T R (FP64 Cholesky whose
+// pivots must exceed thr), out = Z D R^{-1}.  *ok = false when the factorisation broke
+// down; out is then not written.
+template <typename T>
+static arb_status cholqr_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* out, int64_t ldo,
+                              double thr, bool* ok) {
+  double *G, *Gh, *M, *d;
+  int32_t* status;
+  const size_t mm = static_cast<size_t>(m) * m;
+  ARB_TRY(ws<double>(ctx, WS_SMALL0, mm, &G));
+  ARB_TRY(ws<double>(ctx, WS_SMALL1, mm, &Gh));
+  ARB_TRY(ws<double>(ctx, WS_SMALL2, mm, &M));
+  ARB_TRY(ws<double>(ctx, WS_VEC0, m, &d));
+  ARB_TRY(ws<int32_t>(ctx, WS_CHOL_STATUS, 4, &status));
+  ARB_TRY(gram<T>(ctx, n, Z, ldz, m, Z, ldz, m, G, m));
+  ARB_TRY(svqb_prep(ctx, m, G, m, Gh, d));
+  ARB_TRY(cholesky_upper(ctx, m, Gh, m, thr, status));
+  ARB_TRY(triangular_inverse(ctx, m, Gh, m, d, M, status));
+  int32_t st[2] = {0, 0};
+  ARB_TRY(d2h_sync(ctx, st, status, sizeof(st)));
+  *ok = st[0] == 0;
+  if (*ok) ARB_TRY(gemm_tall<T>(ctx, n, Z, ldz, m, M, m, m, 1.0, 0.0, out, ldo));
+  return ARB_OK;
+}
+
 template <typename T>
 arb_status orth(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* U, int64_t ldu, T* tmp,
                 int64_t ldt, int32_t* rank, bool recover) {
   *rank = 0;
   if (m <= 0) return ARB_OK;
+  // CholeskyQR2: two Cholesky passes when the first factorisation keeps every pivot of the
+  // unit-diagonal Gram matrix above the Gram pass's truncation threshold (the block has
+  // full numerical rank) and the second Gram matrix is near the identity (every pivot
+  // above 1/2: the first pass left a well-conditioned block).  Otherwise the block is
+  // (numerically) rank deficient and the eigen-truncated Gram passes below take over.
+  if (m <= cholesky_max_order()) {
+    bool ok1 = false, ok2 = false;
+    ARB_TRY(cholqr_pass<T>(ctx, n, Z, ldz, m, tmp, ldt, orth_tau<T>(m), &ok1));
+    if (ok1) ARB_TRY(cholqr_pass<T>(ctx, n, tmp, ldt, m, U, ldu, 0.5, &ok2));
+    if (ok2) {
+      *rank = m;
+      return ARB_OK;
+    }
+  }
   int32_t r1 = 0, r2 = 0;
   ARB_TRY(svqb_pass<T>(ctx, n, Z, ldz, m, tmp, ldt, &r1));
   if (r1 == 0) return ARB_OK;
@@ -267,16 +306,28 @@ arb_status orth(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* U
 template <typename T>
 arb_status rcond_gram(arb_ctx ctx, int64_t n, const T* X, int64_t ldx, int32_t ncols, const double* xs,
                       double* rc) {
-  double *G, *W, *theta, *rc_dev;
+  double *G, *R, *Rinv, *Ginv, *rc_dev;
+  int32_t* status;
   const size_t mm = static_cast<size_t>(ncols) * ncols;
   ARB_TRY(ws<double>(ctx, WS_SMALL0, mm, &G));
-  ARB_TRY(ws<double>(ctx, WS_SMALL2, mm, &W));
-  ARB_TRY(ws<double>(ctx, WS_VEC1, ncols + 2, &theta));
-  rc_dev = theta + ncols;
+  ARB_TRY(ws<double>(ctx, WS_CHOL_R, mm, &R));
+  ARB_TRY(ws<double>(ctx, WS_CHOL_RINV, mm, &Rinv));
+  ARB_TRY(ws<double>(ctx, WS_SMALL2, mm, &Ginv));
+  ARB_TRY(ws<double>(ctx, WS_VEC1, 2, &rc_dev));
+  ARB_TRY(ws<int32_t>(ctx, WS_CHOL_STATUS, 4, &status));
   ARB_TRY(gram<T>(ctx, n, X, ldx, ncols, X, ldx, ncols, G, ncols));
   if (xs) ARB_TRY(scale_sym(ctx, ncols, G, ncols, xs));
-  ARB_TRY(syevj(ctx, ncols, G, ncols, theta, W, ncols, nullptr, jac_tol<T>(ctx), jac_df<T>(ctx)));
-  ARB_TRY(rcond_from_eig(ctx, ncols, G, ncols, theta, W, ncols, rc_dev));
+  if (ncols <= cholesky_max_order()) {
+    // G^{-1} from the Cholesky factor (as the oracle computes it); rc = 0 when G is not
+    // numerically positive definite
+    ARB_TRY(rcond_from_cholesky(ctx, ncols, G, ncols, R, Rinv, Ginv, status, rc_dev));
+  } else {
+    double *W, *theta;
+    ARB_TRY(ws<double>(ctx, WS_SMALL1, mm, &W));
+    ARB_TRY(ws<double>(ctx, WS_VEC2, ncols, &theta));
+    ARB_TRY(syevj(ctx, ncols, G, ncols, theta, W, ncols, nullptr, jac_tol<T>(ctx), jac_df<T>(ctx)));
+    ARB_TRY(rcond_from_eig(ctx, ncols, G, ncols, theta, W, ncols, rc_dev));
+  }
   ARB_TRY(d2h_sync(ctx, rc, rc_dev, sizeof(double)));
   return ARB_OK;
 }

@@ -49,13 +49,12 @@ def _opts(arb, k, p, q, d, **kw):
     return o
 
 
-@pytest.mark.parametrize("precision", [0, 2])
-def test_solve_locks_pairs_against_oracle(arb, ctx, precision):
+def test_solve_locks_pairs_against_oracle(arb, ctx):
     A = I.laplacian_2d(20)
     k, p = 12, 14
     X0 = I.gaussian_block(A.n, p, 8)
     mat = arb.Matrix.from_csr(ctx, A)
-    o = _opts(arb, k, p, 1, 8, tol1=1e-3, precision=precision)
+    o = _opts(arb, k, p, 1, 8, tol1=1e-3)
     r = arb.arb_solve(ctx, mat, k, arb.ARB_SMALLEST, 1e-10, o, x0=X0, evecs="host")
     assert r.status == arb.ARB_OK, r.info
     # pairs were locked and stayed locked through the last outer iteration
@@ -71,15 +70,19 @@ def test_solve_locks_pairs_against_oracle(arb, ctx, precision):
     assert np.linalg.norm(R, axis=0).max() <= 1e-10 * 8.0
 
 
-def test_solve_locking_grows_to_all_locked(arb, ctx):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_locking_grows_to_all_locked(arb, ctx, precision):
     # k = p and a tolerance below the FP64 residual floor: pairs lock as they reach the
     # threshold floor 1e-14 until the whole block is locked (ARB_STOP_ALL_LOCKED), as in
-    # the oracle with the same inputs
+    # the oracle with the same inputs.  With ARB_MIXED the FP32 phase never locks (its
+    # residuals stop far above the thresholds); its FP64 refinement locks the same way.
+    # (ARB_MIXED_DF's double-float filter leaves residuals near 1e-13, above the 1e-14
+    # floor of the threshold, so it stops on the stall rule instead.)
     A = I.laplacian_2d(20)
     k = p = 10
     X0 = I.gaussian_block(A.n, p, 8)
     mat = arb.Matrix.from_csr(ctx, A)
-    o = _opts(arb, k, p, 1, 8, tol1=1e-2)
+    o = _opts(arb, k, p, 1, 8, tol1=1e-2, precision=precision)
     r = arb.arb_solve(ctx, mat, k, arb.ARB_SMALLEST, 1e-15, o, x0=X0, evecs="host")
     ref = O.arrabit_mpm(scipy_of(A), k, X0, which="smallest", tol=1e-15, q=1, degree=8, tol1=1e-2)
     assert ref.stop_reason == "all_locked"
