@@ -104,6 +104,8 @@ typedef struct {
   int32_t stop_reason;  /* arb_stop_reason */
   int32_t last_rank;    /* dimension of the last Rayleigh-Ritz subspace */
   int32_t outer_iters_fp32; /* ARB_MIXED: outer iterations of the FP32 phase */
+  int32_t max_locked;   /* largest locked set of any outer iteration (eq. defl) */
+  int32_t reserved0;
 } arb_info;
 
 /* ---------------------------------------------------------------- context, matrices */

@@ -56,7 +56,8 @@ class arb_info(C.Structure):
                 ("sigma", C.c_double), ("t_total", C.c_double), ("t_filter", C.c_double),
                 ("t_arr", C.c_double), ("spmm_cols", C.c_int64), ("outer_iters", C.c_int32),
                 ("n_filters", C.c_int32), ("n_locked", C.c_int32), ("stop_reason", C.c_int32),
-                ("last_rank", C.c_int32), ("outer_iters_fp32", C.c_int32)]
+                ("last_rank", C.c_int32), ("outer_iters_fp32", C.c_int32), ("max_locked", C.c_int32),
+                ("reserved0", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}

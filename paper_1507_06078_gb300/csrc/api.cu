@@ -957,6 +957,7 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
       }
     }
     S.nl = static_cast<int32_t>(lock_idx.size());
+    S.info.max_locked = std::max(S.info.max_locked, S.nl);
     S.w = p - S.nl;
     if (S.w == 0) {
       S.stop = ARB_STOP_ALL_LOCKED;
