@@ -322,8 +322,39 @@ def pad_ritz(B, Y: np.ndarray, w: np.ndarray, want: int, pool: np.ndarray | None
     return np.hstack([Y, P]), np.concatenate([w, rq])
 
 
+def gn_step(apply_filter, X: np.ndarray) -> np.ndarray:
+    """One Gauss-Newton inner step of Algorithm 8 (the GN branch; Algorithm 4 with the
+    polynomial accelerator in place of A): Y = X (X^T X)^{-1}, Z = poly(A - aI, Y, ...),
+    X+ = Z - X (Y^T Z - I) / 2.  (X^T X)^{-1} comes from a Cholesky factorisation; a
+    rank-deficient X (failed factorisation) raises numpy.linalg.LinAlgError."""
+    G = X.T @ X
+    c = sla.cho_factor(0.5 * (G + G.T), lower=False, check_finite=True)
+    Y = sla.cho_solve(c, X.T).T
+    Z = apply_filter(Y)
+    return Z - X @ (Y.T @ Z - np.eye(X.shape[1])) / 2.0
+
+
+def filter_value(coef: np.ndarray, mu, a: float, b: float):
+    """rho_d(mu) for the filter Algorithm 8 applies, poly(B - aI, ., 0, b - a, Gamma_d):
+    psi_d at the image of mu - a under the map of [0, b - a] onto [-1, 1]."""
+    return eval_cheb_series(coef, 2.0 * (np.asarray(mu, dtype=np.float64) - a) / (b - a) - 1.0)
+
+
+def next_degree(filter_kind: str, mu_k: float, mu_kq: float, a: float, b: float, d_max: int) -> int:
+    """The polynomial degree rule of Section 5 (eqs. hat-d and degree): the smallest d >= 3
+    with rho_d(mu*_{k+q}) / rho_d(mu*_k) < 0.9, capped at d_max (d_max when no d up to
+    d_max qualifies)."""
+    for d in range(3, d_max + 1):
+        coef = interpolant_cheb_coeffs(d) if filter_kind == "chebinterp" else chebyshev_T_coeffs(d)
+        rk = float(filter_value(coef, mu_k, a, b))
+        rkq = float(filter_value(coef, mu_kq, a, b))
+        if rk > 0.0 and np.isfinite(rk) and np.isfinite(rkq) and rkq / rk < 0.9:
+            return d
+    return d_max
+
+
 # -------------------------------------------------------------------------------------
-# Algorithm 8 (MPM inner solver)
+# Algorithm 8 (MPM or GN inner solver)
 # -------------------------------------------------------------------------------------
 @dataclass
 class OuterRecord:
@@ -336,6 +367,8 @@ class OuterRecord:
     b: float
     n_locked: int
     rank: int
+    q: int = 1       # augmentation blocks of this iteration's ARR
+    degree: int = 0  # polynomial degree of this iteration's filters
 
 
 @dataclass
@@ -396,14 +429,18 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
                 filter_kind: str = "chebinterp", sigma: float | None = None,
                 inner_fixed: int = 0, pad_pool: np.ndarray | None = None,
                 poly_eval: str = "clenshaw", b_update: str = "continuation",
-                seed: int = 20150722) -> OracleResult:
+                seed: int = 20150722, inner: str = "mpm", adapt_q: bool = False, q_max: int = 3,
+                adapt_d: bool = False, d_max: int = 15) -> OracleResult:
     """ARRABIT with the multi-power inner solver, Algorithm 8, for the k largest (or, via
     B = sigma I - A, smallest) eigenpairs of symmetric A.  The block width is
     p = X0.shape[1] = k + guard vectors.  ``inner_fixed`` > 0 replaces the inner stop rule
-    by exactly that many filter applications per outer iteration (for lock-step tests).
+    by exactly that many inner steps per outer iteration (for lock-step tests).
     ``b_update`` = "continuation" refreshes b = mu_{k+q} only at a continuation step, as
     Algorithm 8 does; "every_arr" refreshes it after every ARR projection, as the
-    estimation paragraph of Section 5 describes.
+    estimation paragraph of Section 5 describes.  ``inner`` = "gn" takes Algorithm 8's GN
+    branch instead of MPM.  ``adapt_q`` raises q by one (up to q_max) after an ARR when
+    eq. block holds; ``adapt_d`` sets the degree after every ARR by eqs. hat-d and degree
+    (cap d_max); ``degree`` and ``q`` are then the initial values.
     """
     A = sp.csr_matrix(A, dtype=np.float64)
     n, p = X0.shape
@@ -438,20 +475,26 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
     b = float(jacobi_eigh(H0)[0][-1])
     b0 = b
     n_spmm_cols = U0.shape[1]
-    if filter_kind == "chebinterp":
-        coef = interpolant_cheb_coeffs(degree)
-    elif filter_kind == "chebyshev":
-        coef = chebyshev_T_coeffs(degree)
-    else:
+    if filter_kind not in ("chebinterp", "chebyshev"):
         raise ValueError(filter_kind)
-    gamma = cheb_to_monomial(coef)
+    if inner not in ("mpm", "gn"):
+        raise ValueError(inner)
+
+    def coefficients(d):
+        return interpolant_cheb_coeffs(d) if filter_kind == "chebinterp" else chebyshev_T_coeffs(d)
 
     def apply_filter(X):
-        # Alg. 8 calls poly(B - aI, X, 0, b - a, Gamma_d)
+        # Alg. 8 calls poly(B - aI, X, 0, b - a, Gamma_d) with the current degree
         Bs = B - a * sp.identity(n, format="csr")
+        coef = coefficients(degree)
         if poly_eval == "horner":
-            return poly_alg7(Bs, X, 0.0, b - a, gamma)
+            return poly_alg7(Bs, X, 0.0, b - a, cheb_to_monomial(coef))
         return poly_clenshaw(Bs, X, 0.0, b - a, coef)
+
+    # the augmentation count may grow only while (q + 1) p < n (Algorithm 5's requirement)
+    q_cap = max(q, min(q_max, (n - 1) // p - 1)) if adapt_q else q
+    mu_best = None
+    maxres_prev = None
 
     if tol1 is None:
         tol1 = max(1e-6, tol) if tol <= 1e-8 else tol
@@ -474,12 +517,22 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
         i1_max = maxit1 if inner_fixed <= 0 else 1
         for _ in range(i1_max):
             n_inner = maxit2 if inner_fixed <= 0 else inner_fixed
+            lost_rank = False
             for _ in range(n_inner):
-                X = normalize_columns(apply_filter(X))
+                if inner == "mpm":
+                    X = normalize_columns(apply_filter(X))
+                else:
+                    try:
+                        X = gn_step(apply_filter, X)
+                    except np.linalg.LinAlgError:
+                        # X^T X is not numerically positive definite: the GN step is
+                        # undefined; end the inner loop and let the ARR step take over
+                        lost_rank = True
+                        break
                 X = project_out(Qc, X)
                 nf += 1
                 n_spmm_cols += degree * X.shape[1]
-            if inner_fixed > 0:
+            if inner_fixed > 0 or lost_rank:
                 break
             rcp = rc
             rc = rcond_spd(X.T @ X)
@@ -506,7 +559,8 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
         maxres = float(np.max(res[:k]))
         if maxres < best:
             best, best_iter = maxres, j
-        rec = OuterRecord(nf, rcs, maxres, tol_t, b, Qc.shape[1], rank)
+            mu_best = (float(mu[k - 1]), float(mu[p - 1]))  # the most accurate Ritz values so far
+        rec = OuterRecord(nf, rcs, maxres, tol_t, b, Qc.shape[1], rank, q, degree)
         history.append(rec)
         # outer stop rules (eq. out-stop and cases (i)-(iii))
         h = int(np.sum(res[:k] < 0.1 * tol))
@@ -534,6 +588,16 @@ def arrabit_mpm(A: sp.csr_matrix, k: int, X0: np.ndarray, which: str = "smallest
         if X.shape[1] == 0:
             stop_reason = "all_locked"
             break
+        # augmentation blocks (eq. block): small decay of the relevant Ritz values of the
+        # shifted operator B - aI the inner solver works on, and a disappointing decrease
+        # of the residuals
+        if adapt_q and maxres_prev is not None and q < q_cap:
+            if (mu[p - 1] - a) / (mu[k - 1] - a) > 0.95 and maxres / maxres_prev > 0.1:
+                q += 1
+        maxres_prev = maxres
+        # polynomial degree (eqs. hat-d, degree) from the most accurate Ritz values so far
+        if adapt_d and mu_best is not None:
+            degree = next_degree(filter_kind, mu_best[0], mu_best[1], a, b, d_max)
     # report the k leading pairs in the original problem's terms
     Xk = Xall[:, :k]
     lam_rq = np.einsum("ij,ij->j", Xk, A @ Xk)

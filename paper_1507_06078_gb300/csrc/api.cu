@@ -79,12 +79,31 @@ arb_status host_stage(arb_ctx ctx, size_t bytes, void** out) {
   return ARB_OK;
 }
 
+arb_status device_error_word(arb_ctx ctx, int32_t** out) {
+  if (!ctx->err_dev) {
+    ARB_CUDA(ctx, cudaMalloc(&ctx->err_dev, 4 * sizeof(int32_t)));
+    ARB_CUDA(ctx, cudaMemsetAsync(ctx->err_dev, 0, 4 * sizeof(int32_t), ctx->stream));
+  }
+  *out = ctx->err_dev;
+  return ARB_OK;
+}
+
+// The read-back also fetches the device error word: a pipelined kernel whose bounded wait
+// gave up since the last synchronisation turns this call into ARB_CUDA_ERROR.
 arb_status d2h_sync(arb_ctx ctx, void* host, const void* dev, size_t bytes) {
   void* st;
-  ARB_TRY(host_stage(ctx, std::max<size_t>(bytes, 4096), &st));
+  const size_t off = (bytes + 15) / 16 * 16;
+  ARB_TRY(host_stage(ctx, std::max<size_t>(off + 16, 4096), &st));
   ARB_CUDA(ctx, cudaMemcpyAsync(st, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  int32_t* herr = reinterpret_cast<int32_t*>(static_cast<char*>(st) + off);
+  *herr = 0;
+  if (ctx->err_dev) ARB_CUDA(ctx, cudaMemcpyAsync(herr, ctx->err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   memcpy(host, st, bytes);
+  if (*herr != 0) {
+    ARB_CUDA(ctx, cudaMemsetAsync(ctx->err_dev, 0, sizeof(int32_t), ctx->stream));
+    return set_error(ctx, ARB_CUDA_ERROR, "a pipelined kernel's bounded wait gave up (results of the call are void)");
+  }
   return ARB_OK;
 }
 
@@ -169,6 +188,7 @@ extern "C" arb_status arb_ctx_destroy(arb_ctx ctx) {
     }
   cudaStreamSynchronize(ctx->stream);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  if (ctx->err_dev) cudaFree(ctx->err_dev);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return ARB_OK;

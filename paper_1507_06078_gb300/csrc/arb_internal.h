@@ -96,6 +96,9 @@ struct arb_ctx_s {
   // FP64 Gram and tall-skinny products in double-float arithmetic on the FP32 pipe
   // (arb_ctx_set_dense_df; ARB_MIXED_DF solves set it for their refinement phase)
   bool dense_df = false;
+  // device error word of pipelined kernels whose bounded waits gave up (two ints, zeroed);
+  // read and cleared at every host synchronisation of d2h_sync
+  int32_t* err_dev = nullptr;
 };
 
 struct arb_mat_s {
@@ -165,6 +168,8 @@ size_t solve_footprint(int64_t n, int64_t nnz, int32_t p, int32_t q, int32_t pre
 arb_status solve_on(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol, const arb_options* opts,
                     const double* x0, int x0_on_device, double* evals, double* evecs, int64_t ldq,
                     int evecs_on_device, arb_info* info);
+// The context's device error word (allocated and zeroed on first use).
+arb_status device_error_word(arb_ctx ctx, int32_t** out);
 // Pinned host staging of at least `bytes`.
 arb_status host_stage(arb_ctx ctx, size_t bytes, void** out);
 // Copy `bytes` from device to a host pointer through the stream and wait.
@@ -199,6 +204,12 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a);
 // double-float blocks (df.cu): leading dimensions even, 16-byte aligned bases
 template <>
 arb_status spmm_fused<df2>(arb_ctx ctx, const SpmmArgs<df2>& a);
+// The FP32 product by the bulk-copy pipelined kernel (spmm_bulk.cu) when the operands allow
+// it (rows of at most 32 nonzeros, CSR, ncols a multiple of 4, 16-byte aligned rows);
+// *launched = false leaves the work to the caller.  want_red: per-CTA partial column sums
+// into *part (grid x ncols, *grid_out CTAs).
+arb_status spmm_bulk_f32(arb_ctx ctx, const arb_mat_s* A, const SpmmArgs<float>& a, const float* val, bool want_red,
+                         bool* launched, int* grid_out, double** part);
 // FP32 copy of A's values (kept with the matrix).
 arb_status ensure_val32(arb_ctx ctx, arb_mat mat);
 

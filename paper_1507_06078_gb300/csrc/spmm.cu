@@ -554,7 +554,11 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   const bool short_rows = A->max_row_nnz >= 0 && A->max_row_nnz <= 32 && A->n * ld_max < (int64_t(1) << 31);
   const int mode = A->sell_C > 0 ? 2 : (short_rows ? 1 : 0);
   if constexpr (sizeof(T) == 4) {
-    if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
+    bool bulk = false;
+    if (mode == 1) ARB_TRY(spmm_bulk_f32(ctx, A, a, P.val, want_red, &bulk, &grid, &part));
+    if (bulk) {
+      // done by the bulk-copy pipelined kernel
+    } else if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
       ARB_TRY((launch_spmm<T, 4>(ctx, P, smem, want_red, mode, &grid, &part)));
     } else if (fits(2)) {
       ARB_TRY((launch_spmm<T, 2>(ctx, P, smem, want_red, mode, &grid, &part)));

@@ -286,3 +286,129 @@ def test_arr_exact_on_a_krylov_invariant_subspace(q):
     for j in range(q + 1):
         i = support[int(np.argmin(np.abs(dvals[support] - w[j])))]
         assert abs(abs(Y[i, j]) - 1.0) <= 1e-12
+
+
+# ---------------------------------------------------------------- GN inner solver (Algorithm 4)
+def _filter_of(B, coef, a, b):
+    return lambda Y: O.poly_clenshaw(B - a * sp.identity(B.shape[0], format="csr"), Y, 0.0, b - a, coef)
+
+
+def test_gn_step_fixed_points():
+    # GN minimises ||X X^T - F||_F for F = rho(B): X* = V_S diag(sqrt(f_S)) Q (eigenvectors
+    # of any subset S of positive eigenvalues f_S of F, any orthogonal Q) is a fixed point
+    n = 40
+    dvals = np.linspace(0.0, 3.0, n)
+    B = sp.diags(dvals).tocsr()
+    coef = O.interpolant_cheb_coeffs(6)
+    F = _filter_of(B, coef, 0.0, 2.5)
+    f = O.filter_value(coef, dvals, 0.0, 2.5)
+    S = [39, 37, 35, 34]
+    assert np.all(f[S] > 0)
+    Xs = np.zeros((n, 4))
+    Xs[S, range(4)] = np.sqrt(f[S])
+    Q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((4, 4)))
+    for X in (Xs, Xs @ Q):
+        np.testing.assert_allclose(O.gn_step(F, X), X, rtol=0, atol=1e-12 * np.abs(X).max())
+
+
+def test_gn_step_equals_section_2_closed_form():
+    # Section 2.5 writes the GN step as X + (I - X (X^T X)^{-1} X^T / 2)(F X (X^T X)^{-1} - X);
+    # Algorithm 4 writes it as Z - X (Y^T Z - I)/2 with Y = X (X^T X)^{-1}, Z = F Y
+    A = _scipy(I.laplacian_2d(9))
+    coef = O.interpolant_cheb_coeffs(5)
+    F = _filter_of(A, coef, 0.0, 6.0)
+    X = np.random.default_rng(2).standard_normal((A.shape[0], 5))
+    Gi = np.linalg.inv(X.T @ X)
+    closed = X + (np.eye(A.shape[0]) - 0.5 * X @ Gi @ X.T) @ (F(X @ Gi) - X)
+    np.testing.assert_allclose(O.gn_step(F, X), closed, rtol=0, atol=1e-10 * np.abs(closed).max())
+
+
+@pytest.mark.parametrize("slip", ["half_dropped", "sign", "no_identity"])
+def test_planted_gn_slips_are_caught(slip):
+    n = 30
+    dvals = np.linspace(0.0, 2.0, n)
+    B = sp.diags(dvals).tocsr()
+    coef = O.interpolant_cheb_coeffs(4)
+    F = _filter_of(B, coef, 0.0, 1.5)
+    f = O.filter_value(coef, dvals, 0.0, 1.5)
+    X = np.zeros((n, 3))
+    X[[29, 25, 7], range(3)] = np.sqrt(np.abs(f[[29, 25, 7]]))
+
+    def bad(Fn, X):
+        Y = X @ np.linalg.inv(X.T @ X)
+        Z = Fn(Y)
+        if slip == "half_dropped":
+            return Z - X @ (Y.T @ Z - np.eye(3))
+        if slip == "sign":
+            return Z + X @ (Y.T @ Z - np.eye(3)) / 2
+        return Z - X @ (Y.T @ Z) / 2
+
+    Xr = np.random.default_rng(3).standard_normal((n, 3))
+    # the slip either moves the fixed point or changes the step on a generic X
+    assert (not np.allclose(bad(F, X), X, atol=1e-10)) or (not np.allclose(bad(F, Xr), O.gn_step(F, Xr), atol=1e-10))
+
+
+@pytest.mark.parametrize("m,k,p", [(20, 12, 14), (32, 12, 16)])
+def test_oracle_gn_inner_solver_closed_form(m, k, p):
+    A = _scipy(I.laplacian_2d(m))
+    X0 = I.gaussian_block(A.shape[0], p, 8)
+    r = O.arrabit_mpm(A, k, X0, which="smallest", tol=1e-10, q=1, degree=8, inner="gn")
+    assert r.converged
+    np.testing.assert_allclose(r.evals, laplacian_2d_eigs(m)[:k], rtol=0, atol=1e-10)
+    _check_invariants(A, r, 1e-10, 8.0)
+
+
+def test_oracle_gn_bruteforce_random_sparse():
+    n, k, p = 400, 8, 12
+    A = _random_sparse_spd(n, 0.02, 77)
+    wref = np.linalg.eigvalsh(A.toarray())
+    r = O.arrabit_mpm(A, k, I.gaussian_block(n, p, 31), which="largest", tol=1e-10, q=1, degree=10, inner="gn")
+    assert r.converged
+    np.testing.assert_allclose(r.evals, wref[::-1][:k], atol=1e-9 * np.abs(wref).max())
+
+
+# ---------------------------------------------------------------- adaptive q and d (Section 5)
+def test_degree_rule_special_cases():
+    # rho_d(a) = psi_d(-1) = f_d(-1) = 0 (t = -1 is an interpolation node), so mu*_{k+q} = a
+    # gives the ratio 0 and the smallest degree, 3; equal Ritz values give the ratio 1 and
+    # the cap
+    assert O.next_degree("chebinterp", 5.0, 0.0, 0.0, 4.0, 15) == 3
+    assert O.next_degree("chebinterp", 3.0, 3.0, 0.0, 4.0, 15) == 15
+    assert O.next_degree("chebinterp", 3.0, 3.0, 0.0, 4.0, 7) == 7
+    # a gap just above b needs a higher degree than a wide one
+    d_close = O.next_degree("chebinterp", 4.02, 4.0, 0.0, 4.0, 40)
+    d_wide = O.next_degree("chebinterp", 4.5, 4.0, 0.0, 4.0, 40)
+    assert 3 <= d_wide < d_close <= 40
+
+
+def test_degree_rule_against_brute_force_ratios():
+    # the chosen degree is the first d >= 3 whose ratio of interpolant values (computed
+    # here by numpy's Chebyshev series, not the oracle's recurrence) is below 0.9
+    import numpy.polynomial.chebyshev as npc
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        a, b = 0.0, rng.uniform(1.0, 5.0)
+        mkq = b * rng.uniform(0.8, 1.05)
+        mk = mkq + b * rng.uniform(0.0, 0.2)
+        d = O.next_degree("chebinterp", mk, mkq, a, b, 25)
+        ratio = lambda dd: (npc.chebval(2 * (mkq - a) / (b - a) - 1, O.interpolant_cheb_coeffs(dd))  # noqa: E731
+                            / npc.chebval(2 * (mk - a) / (b - a) - 1, O.interpolant_cheb_coeffs(dd)))
+        if d < 25:
+            assert ratio(d) < 0.9
+        for dd in range(3, d):
+            assert not ratio(dd) < 0.9
+
+
+def test_oracle_adaptive_degree_and_blocks():
+    A = _scipy(I.laplacian_3d(16))
+    X0 = I.gaussian_block(A.shape[0], 36, 3)
+    lam = laplacian_3d_eigs(16)[:30]
+    r = O.arrabit_mpm(A, 30, X0, which="smallest", tol=1e-10, q=1, degree=3, adapt_q=True, adapt_d=True)
+    assert r.converged
+    np.testing.assert_allclose(r.evals, lam, rtol=0, atol=1e-10)
+    ds = [h.degree for h in r.history]
+    assert ds[0] == 3 and max(ds) > 3 and max(ds) <= 15
+    r2 = O.arrabit_mpm(A, 30, X0, which="smallest", tol=1e-10, q=1, degree=3, adapt_q=True)
+    qs = [h.q for h in r2.history]
+    assert qs[0] == 1 and max(qs) > 1 and max(qs) <= 3 and qs == sorted(qs)
+    np.testing.assert_allclose(r2.evals, lam, rtol=0, atol=1e-10)
