@@ -366,6 +366,7 @@ extern "C" arb_status arb_matrix_destroy(arb_mat m) {
   if (m->val32) cudaFree(m->val32);
   if (m->valdf) cudaFree(m->valdf);
   matrix_free_sell(m);
+  matrix_free_bulk(m);
   delete m;
   return ARB_OK;
 }

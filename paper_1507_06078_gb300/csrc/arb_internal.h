@@ -122,6 +122,8 @@ struct arb_mat_s {
   double* sell_val = nullptr;    // [slots] values (padding: 0), and their FP32 / double-float copies
   float* sell_val32 = nullptr;
   arb::df2* sell_valdf = nullptr;
+  // group table of the bulk-copy FP32 SpMM (spmm_bulk.cu), made on first use
+  int32_t* bulk_tab = nullptr;
   bool gersh_valid = false;
   double gersh_lo = 0.0, gersh_hi = 0.0;
   std::mutex mu;  // guards the lazily made val32 / valdf and the Gershgorin cache (shared by server workers)
@@ -347,6 +349,8 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
 // FP32 blocks and so carries FP32-level errors itself.
 // frees a matrix's SELL-C-sigma arrays (sell.cu)
 void matrix_free_sell(arb_mat m);
+// frees a matrix's bulk-copy group table (spmm_bulk.cu)
+void matrix_free_bulk(arb_mat m);
 // df: orders above 96 in double-float arithmetic on the FP32 pipe (stops at <= 1e-13).
 // jac_df / jac_tol: the Jacobi arithmetic and tolerance for matrices formed from element
 // type T: FP32 bases (accurate to ~1e-7) and double-float dense products take the

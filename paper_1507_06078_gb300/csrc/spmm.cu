@@ -33,6 +33,16 @@ constexpr int SPMM_WARPS = SPMM_THREADS / 32;
 #ifndef ARB_SPMM_SHORT_UNROLL
 #define ARB_SPMM_SHORT_UNROLL 4
 #endif
+// 1: short-row FP32 products by the bulk-copy pipelined kernel (spmm_bulk.cu); measured at
+// 2.6-2.8 ms per 128^3 x 240 filter pass against 2.0 ms for this kernel, so off by default
+#ifndef ARB_SPMM_BULK
+#define ARB_SPMM_BULK 0
+#endif
+// 1: every CTA walks a contiguous range of rows (neighbouring rows' gathers meet in its L1)
+// instead of the grid sweeping the rows as one interleaved front
+#ifndef ARB_SPMM_CONTIG
+#define ARB_SPMM_CONTIG 0
+#endif
 
 
 template <typename T>
@@ -177,13 +187,21 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
     for (int c = lane; c < ncols; c += 32) s_red[static_cast<size_t>(warp) * ncols + c] = 0.0;
     __syncwarp();
   }
+  // ARB_SPMM_CONTIG: every CTA walks its own contiguous range of rows, SPMM_WARPS / nch rows
+  // at a time (when every chunk gets a warp); otherwise the grid sweeps the rows as one
+  // interleaved front, warp gw taking rows gw / nch + k (nwarps / nch)
+  const bool contig = ARB_SPMM_CONTIG && nch <= SPMM_WARPS;
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * SPMM_WARPS + warp;
   const int64_t nwarps = static_cast<int64_t>(gridDim.x) * SPMM_WARPS;
-  const int64_t rstride = nwarps / nch;  // warps per chunk
-  const int chunk = static_cast<int>(gw % nch);
-  const int64_t r_first = gw / nch;
+  const int wpc = SPMM_WARPS / nch;  // warps per chunk in a CTA (contiguous ranges)
+  const int64_t rows_per_cta = (P.n + gridDim.x - 1) / gridDim.x;
+  const int chunk = contig ? warp % nch : static_cast<int>(gw % nch);
+  const int64_t r_first = contig ? static_cast<int64_t>(blockIdx.x) * rows_per_cta + warp / nch : gw / nch;
+  const int64_t rstride = contig ? static_cast<int64_t>(wpc) : nwarps / nch;
+  const int64_t r_end = contig ? min(P.n, static_cast<int64_t>(blockIdx.x + 1) * rows_per_cta) : P.n;
+  const bool live = contig ? warp < wpc * nch : r_first < rstride;
   const int c = chunk * CH + lane * VEC;
-  const bool act = (r_first < rstride) && (c < ncols);
+  const bool act = live && (c < ncols);
   // lanes past the last column load column 0 of the same rows (always in bounds) and
   // discard the result, so the gathers need no per-lane predicate
   const int cl = act ? c : 0;
@@ -201,20 +219,20 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
   // SHORT pipeline state: indices of the next row, row pointers of the one after
   int n_jc = 0, n_cnt = 0, p_beg = 0, p_end = 0;
   T n_av = T(0);
-  if (SHORT && r_first < rstride && r_first < P.n) {
+  if (SHORT && live && r_first < r_end) {
     const int b0 = __ldg(P.rowptr + r_first), e0 = __ldg(P.rowptr + r_first + 1);
     n_cnt = e0 - b0;
     if (lane < n_cnt) {
       n_jc = __ldg(P.col + b0 + lane);
       n_av = __ldg(P.val + b0 + lane);
     }
-    if (r_first + rstride < P.n) {
+    if (r_first + rstride < r_end) {
       p_beg = __ldg(P.rowptr + r_first + rstride);
       p_end = __ldg(P.rowptr + r_first + rstride + 1);
     }
   }
-  if (r_first < rstride) {
-    for (int64_t row = r_first; row < P.n; row += rstride) {
+  if (live) {
+    for (int64_t row = r_first; row < r_end; row += rstride) {
       int beg = 0, end = 0, s_jc = 0;
       T s_av = T(0);
       int64_t orow = row;  // the block row (SELL: the sorted position's original row)
@@ -227,14 +245,14 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
         n_cnt = 0;
         n_jc = 0;
         n_av = T(0);
-        if (r1 < P.n) {
+        if (r1 < r_end) {
           n_cnt = p_end - p_beg;
           if (lane < n_cnt) {
             n_jc = __ldg(P.col + p_beg + lane);
             n_av = __ldg(P.val + p_beg + lane);
           }
         }
-        if (r2 < P.n) {
+        if (r2 < r_end) {
           p_beg = __ldg(P.rowptr + r2);
           p_end = __ldg(P.rowptr + r2 + 1);
         }
@@ -555,7 +573,9 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
   const int mode = A->sell_C > 0 ? 2 : (short_rows ? 1 : 0);
   if constexpr (sizeof(T) == 4) {
     bool bulk = false;
+#if ARB_SPMM_BULK
     if (mode == 1) ARB_TRY(spmm_bulk_f32(ctx, A, a, P.val, want_red, &bulk, &grid, &part));
+#endif
     if (bulk) {
       // done by the bulk-copy pipelined kernel
     } else if (ARB_SPMM_F32_MAX_VEC >= 4 && fits(4)) {
