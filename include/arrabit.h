@@ -90,7 +90,18 @@ typedef struct {
                            phase also ends when an outer iteration fails to halve maxres.  The
                            FP64 phase starts from the FP32 Ritz block with b = mu_{k+q}. */
   uint64_t seed;        /* stream for padding columns (Philox4x32-10 + Box-Muller) */
+  int32_t inner;        /* arb_inner_solver: ARB_INNER_MPM (default) or ARB_INNER_GN (Algorithm 8's branches) */
+  int32_t adapt;        /* bit 0 (ARB_ADAPT_Q): raise q by one after an ARR when eq. block holds, up to
+                           q_max; bit 1 (ARB_ADAPT_DEGREE): set the degree after every ARR by eqs. hat-d
+                           and degree, up to d_max; q and degree are then the initial values */
+  int32_t q_max;        /* cap of the adaptive q (0: 3, Section 5), also capped so that (q+1) p < n */
+  int32_t d_max;        /* cap of the adaptive degree (0: 15, Section 5) */
 } arb_options;
+
+/* Inner solver of Algorithm 8: the multi-power method (Section 3) or Gauss-Newton
+ * (Algorithm 4, Section 2.5). */
+typedef enum { ARB_INNER_MPM = 0, ARB_INNER_GN = 1 } arb_inner_solver;
+enum { ARB_ADAPT_Q = 1, ARB_ADAPT_DEGREE = 2 };
 
 typedef struct {
   double maxres;        /* max_{i<=k} res_i, eq. resi */
@@ -105,6 +116,8 @@ typedef struct {
   int32_t last_rank;    /* dimension of the last Rayleigh-Ritz subspace */
   int32_t outer_iters_fp32; /* ARB_MIXED: outer iterations of the FP32 phase */
   int32_t max_locked;   /* largest locked set of any outer iteration (eq. defl) */
+  int32_t final_q;      /* augmentation blocks of the last ARR (differs from opts->q with ARB_ADAPT_Q) */
+  int32_t final_d;      /* polynomial degree at exit (differs from opts->degree with ARB_ADAPT_DEGREE) */
   int32_t reserved0;
 } arb_info;
 

@@ -27,6 +27,8 @@ ARB_NOT_SYMMETRIC, ARB_BREAKDOWN, ARB_CUDA_ERROR, ARB_TIMEOUT, ARB_REJECTED = -3
 ARB_LARGEST, ARB_SMALLEST = 0, 1
 ARB_FP64, ARB_MIXED, ARB_MIXED_DF = 0, 1, 2
 ARB_FILTER_CHEBINTERP, ARB_FILTER_CHEBYSHEV = 0, 1
+ARB_INNER_MPM, ARB_INNER_GN = 0, 1
+ARB_ADAPT_Q, ARB_ADAPT_DEGREE = 1, 2
 STOP_REASONS = {0: "converged", 1: "near_tol", 2: "stalled", 3: "maxit", 4: "all_locked"}
 
 
@@ -41,7 +43,8 @@ class arb_options(C.Structure):
                 ("maxit1", C.c_int32), ("maxit2", C.c_int32), ("inner_fixed", C.c_int32),
                 ("filter", C.c_int32), ("precision", C.c_int32), ("b_update", C.c_int32),
                 ("tol1", C.c_double), ("shift_sigma", C.c_double), ("tol_switch", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("inner", C.c_int32), ("adapt", C.c_int32), ("q_max", C.c_int32),
+                ("d_max", C.c_int32)]
 
 
 class arb_filter_job(C.Structure):
@@ -57,7 +60,7 @@ class arb_info(C.Structure):
                 ("t_arr", C.c_double), ("spmm_cols", C.c_int64), ("outer_iters", C.c_int32),
                 ("n_filters", C.c_int32), ("n_locked", C.c_int32), ("stop_reason", C.c_int32),
                 ("last_rank", C.c_int32), ("outer_iters_fp32", C.c_int32), ("max_locked", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("final_q", C.c_int32), ("final_d", C.c_int32), ("reserved0", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_ if not f.startswith("reserved")}

@@ -631,6 +631,12 @@ struct SolveState {
   double best = std::numeric_limits<double>::infinity();
   int best_iter = 0;
   int outer = 0;  // outer iterations done in the current phase
+  // adaptive augmentation and degree (Section 5): the cap of q, the previous maxres, and
+  // mu_k, mu_{k+q} of the most accurate iteration so far
+  int32_t q_cap = 0;
+  double maxres_prev = -1.0;
+  bool have_best_mu = false;
+  double mu_best_k = 0.0, mu_best_kq = 0.0;
   int stop = ARB_STOP_MAXIT;
   arb_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -785,6 +791,80 @@ arb_status pad_ritz_block(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& 
   return ARB_OK;
 }
 
+// The polynomial degree rule of Section 5 (eqs. hat-d and degree): the smallest d >= 3 with
+// rho_d(mu_kq) / rho_d(mu_k) < 0.9, capped at d_max, rho_d the filter Algorithm 8 applies
+// (psi_d on the map of [0, b - a] onto [-1, 1], evaluated by the three-term recurrence).
+int next_degree(int filter, double mu_k, double mu_kq, double a, double b, int d_max) {
+  auto psi = [&](int d, double mu) {
+    double c[64];
+    arb_filter_coefficients(filter, d, c);
+    const double t = 2.0 * (mu - a) / (b - a) - 1.0;
+    double tp = 1.0, tc = t, sum = c[0] + c[1] * t;
+    for (int j = 2; j <= d; ++j) {
+      const double tn = 2.0 * t * tc - tp;
+      sum += c[j] * tn;
+      tp = tc;
+      tc = tn;
+    }
+    return sum;
+  };
+  for (int d = 3; d <= d_max; ++d) {
+    const double rk = psi(d, mu_k), rkq = psi(d, mu_kq);
+    if (rk > 0.0 && std::isfinite(rk) && std::isfinite(rkq) && rkq / rk < 0.9) return d;
+  }
+  return d_max;
+}
+
+// One Gauss-Newton inner step (Algorithm 8's GN branch, Algorithm 4 with the accelerator):
+// Y = X (X^T X)^{-1}, Z = poly(B - aI, Y, 0, b - a, Gamma_d), X <- Z - X (Y^T Z - I) / 2.
+// (X^T X)^{-1} through an FP64 Cholesky factorisation; *ok = false (X unchanged) when X^T X
+// is not numerically positive definite.
+template <typename T>
+arb_status gn_step(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, const FilterPlan& plan, bool* ok) {
+  const int64_t n = S.n;
+  const int32_t w = S.w;
+  const size_t ww = static_cast<size_t>(w) * w;
+  double *G, *R, *Rinv, *Ginv;
+  int32_t* status;
+  ARB_TRY(ws<double>(ctx, WS_SMALL0, ww, &G));
+  ARB_TRY(ws<double>(ctx, WS_CHOL_R, ww, &R));
+  ARB_TRY(ws<double>(ctx, WS_CHOL_RINV, ww, &Rinv));
+  ARB_TRY(ws<double>(ctx, WS_SMALL1, ww, &Ginv));
+  ARB_TRY(ws<int32_t>(ctx, WS_CHOL_STATUS, 4, &status));
+  ARB_TRY(gram<T>(ctx, n, B.X, B.ld, w, B.X, B.ld, w, G, w));
+  ARB_TRY(spd_inverse(ctx, w, G, w, R, Rinv, Ginv, status));
+  int32_t st[2] = {0, 0};
+  ARB_TRY(d2h_sync(ctx, st, status, sizeof(st)));
+  *ok = st[0] == 0;
+  if (!*ok) return ARB_OK;
+  T* Y = B.wk.T2;  // free during the inner loop
+  ARB_TRY(gemm_tall<T>(ctx, n, B.X, B.ld, w, Ginv, w, w, 1.0, 0.0, Y, B.ld));
+  T* Z = nullptr;
+  bool filtered = false;
+  if constexpr (std::is_same<T, double>::value) {
+    if (S.df_filter) {
+      df2* Yd = reinterpret_cast<df2*>(B.wk.T1);
+      df2* Rd = nullptr;
+      ARB_TRY(to_df(ctx, n, Y, B.ld, w, Yd, B.ld));
+      ARB_TRY(filter_apply<df2>(ctx, mat, plan, Yd, B.ld, w, nullptr, reinterpret_cast<df2*>(B.W1),
+                                reinterpret_cast<df2*>(B.W2), B.ld, nullptr, 0, nullptr, &Rd));
+      ARB_TRY(from_df(ctx, n, Rd, B.ld, w, B.wk.T1, B.ld));  // Yd is no longer needed
+      Z = B.wk.T1;
+      filtered = true;
+    }
+  }
+  if (!filtered) ARB_TRY(filter_apply<T>(ctx, mat, plan, Y, B.ld, w, nullptr, B.W1, B.W2, B.ld, nullptr, 0, nullptr, &Z));
+  double* M = G;  // Y^T Z - I
+  ARB_TRY(gram<T>(ctx, n, Y, B.ld, w, Z, B.ld, w, M, w));
+  ARB_TRY(add_diagonal(ctx, w, M, w, -1.0));
+  ARB_TRY(gemm_tall<T>(ctx, n, B.X, B.ld, w, M, w, w, -0.5, 1.0, Z, B.ld));
+  // X <- Z: exchange the buffers (all are n x ld blocks of the solve)
+  if (Z == B.W1) std::swap(B.X, B.W1);
+  else if (Z == B.W2) std::swap(B.X, B.W2);
+  else std::swap(B.X, B.wk.T1);
+  return ARB_OK;
+}
+
 // Outer iterations of Algorithm 8 with blocks of type T until the outer stop rule holds for
 // `tol_phase` (or a stall / maxit / all-locked stop).  rc_floor bounds the inner-stop
 // threshold from below (reading c7: 100 u of the filter precision); lock = false disables
@@ -800,6 +880,8 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
   S.best_iter = 0;
   S.outer = 0;
   S.stop = ARB_STOP_MAXIT;
+  S.maxres_prev = -1.0;
+  S.have_best_mu = false;
   float ms = 0.f;
   double prev_maxres = std::numeric_limits<double>::infinity();
   for (int j = 1; j <= S.o.maxit; ++j) {
@@ -812,9 +894,22 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     const int n_checks = S.o.inner_fixed > 0 ? 1 : S.o.maxit1;
     const int n_steps = S.o.inner_fixed > 0 ? S.o.inner_fixed : S.o.maxit2;
     const double rc_thr = std::max(S.tol_t, rc_floor);
+    bool lost_rank = false;
     for (int i1 = 0; i1 < n_checks; ++i1) {
       for (int i2 = 0; i2 < n_steps; ++i2) {
         const FilterPlan plan = make_filter_plan(S.op_scale, S.op_shift, S.a, S.b, S.d, S.coef);
+        if (S.o.inner == ARB_INNER_GN) {
+          bool ok = true;
+          ARB_TRY(gn_step<T>(ctx, mat, S, B, plan, &ok));
+          if (!ok) {  // X^T X not positive definite: the GN step is undefined, go to the ARR step
+            lost_rank = true;
+            break;
+          }
+          if (S.nl > 0) ARB_TRY(project_out<T>(ctx, n, B.Qc, B.ld, S.nl, B.X, B.ld, S.w));
+          S.info.n_filters++;
+          S.info.spmm_cols += static_cast<int64_t>(S.d) * S.w;
+          continue;
+        }
         T* result = nullptr;
         bool filtered = false;
         if constexpr (std::is_same<T, double>::value) {
@@ -840,7 +935,7 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
         S.info.n_filters++;
         S.info.spmm_cols += static_cast<int64_t>(S.d) * S.w;
       }
-      if (S.o.inner_fixed > 0) break;
+      if (S.o.inner_fixed > 0 || lost_rank) break;
       const double rcp = rc;
       bool done_rc = false;
       if constexpr (std::is_same<T, double>::value) {
@@ -933,6 +1028,9 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     if (maxres < S.best) {
       S.best = maxres;
       S.best_iter = j;
+      S.have_best_mu = true;
+      S.mu_best_k = S.h_mu[k - 1];
+      S.mu_best_kq = S.h_mu[p - 1];
     }
     if (maxres <= tol_phase) {
       S.stop = ARB_STOP_CONVERGED;
@@ -992,6 +1090,22 @@ arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, do
     ARB_TRY(upload_ints(ctx, S.iidx, free_idx));
     ARB_TRY(gather_cols<T>(ctx, n, B.Xall, B.ld, S.iidx, S.w, B.X, B.ld));
     ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
+    // augmentation blocks (eq. block): little decay of the relevant Ritz values of B - aI
+    // (the operator the inner solver works on) and a disappointing residual decrease
+    if ((S.o.adapt & ARB_ADAPT_Q) && S.maxres_prev > 0.0 && S.q < S.q_cap) {
+      const double ratio = (S.h_mu[p - 1] - S.a) / (S.h_mu[k - 1] - S.a);
+      if (ratio > 0.95 && maxres / S.maxres_prev > 0.1) S.q++;
+    }
+    S.maxres_prev = maxres;
+    // polynomial degree (eqs. hat-d, degree) from the most accurate Ritz values so far
+    if ((S.o.adapt & ARB_ADAPT_DEGREE) && S.have_best_mu) {
+      const int d = next_degree(S.o.filter, S.mu_best_k, S.mu_best_kq, S.a, S.b, S.o.d_max > 0 ? S.o.d_max : 15);
+      if (d != S.d) {
+        S.d = d;
+        if (arb_filter_coefficients(S.o.filter, S.d, S.coef) != ARB_OK)
+          return set_error(ctx, ARB_INVALID_ARG, "solve: bad filter kind");
+      }
+    }
   }
   return ARB_OK;
 }
@@ -1016,6 +1130,9 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
   if (o.precision != ARB_FP64 && o.precision != ARB_MIXED && o.precision != ARB_MIXED_DF)
     return set_error(ctx, ARB_INVALID_ARG, "solve: unknown precision");
   if (o.b_update != 0 && o.b_update != 1) return set_error(ctx, ARB_INVALID_ARG, "solve: b_update must be 0 or 1");
+  if (o.inner != ARB_INNER_MPM && o.inner != ARB_INNER_GN) return set_error(ctx, ARB_INVALID_ARG, "solve: bad inner solver");
+  if ((o.adapt & ~(ARB_ADAPT_Q | ARB_ADAPT_DEGREE)) != 0 || o.q_max < 0 || o.d_max < 0 || o.d_max > 60)
+    return set_error(ctx, ARB_INVALID_ARG, "solve: bad adaptation options");
   if (which != ARB_LARGEST && which != ARB_SMALLEST) return set_error(ctx, ARB_INVALID_ARG, "solve: bad which");
   if (evecs && ldq < n) return set_error(ctx, ARB_INVALID_ARG, "solve: ldq < n");
   S.smallest = (which == ARB_SMALLEST);
@@ -1038,8 +1155,13 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
     S.a = lo_A;
   }
 
-  // device buffers
-  S.mcap = static_cast<int64_t>(S.q + 1) * p;
+  // device buffers (room for the largest q the adaptation may reach, (q+1) p < n)
+  S.q_cap = S.q;
+  if (o.adapt & ARB_ADAPT_Q) {
+    const int64_t fit = (n - 1) / p - 1;
+    S.q_cap = static_cast<int32_t>(std::max<int64_t>(S.q, std::min<int64_t>(o.q_max > 0 ? o.q_max : 3, fit)));
+  }
+  S.mcap = static_cast<int64_t>(S.q_cap + 1) * p;
   BlockSet<double> D;
   BlockSet<float> F;
   ARB_TRY(alloc_blocks<double>(ctx, S, D));
@@ -1180,6 +1302,8 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
   S.info.stop_reason = S.stop;
   S.info.b_final = S.b;
   S.info.n_locked = S.nl;
+  S.info.final_q = S.q;
+  S.info.final_d = S.d;
 
   // ---------------- outputs: Rayleigh quotients on A, order, sign, column-major copy
   {

@@ -335,6 +335,12 @@ int cholesky_max_order();
 // nothing is written when status[0] != 0.
 arb_status triangular_inverse(arb_ctx ctx, int32_t m, const double* R, int64_t lda, const double* d, double* M,
                               const int32_t* status);
+// Ginv (m x m, ld m) = G^{-1} of a symmetric positive definite G through its Cholesky factor
+// (R, Rinv: m x m work); status[0] != 0 (device) when G is not numerically positive definite.
+arb_status spd_inverse(arb_ctx ctx, int32_t m, const double* G, int64_t ldg, double* R, double* Rinv, double* Ginv,
+                       int32_t* status);
+// M[i][i] += s for i < m
+arb_status add_diagonal(arb_ctx ctx, int32_t m, double* M, int64_t ldm, double s);
 // rc_dev = 1 / (||G||_1 ||G^{-1}||_1) with G^{-1} from the Cholesky factor of G; 0 when G is
 // not numerically positive definite.  R, Rinv, Ginv: m x m work matrices.
 arb_status rcond_from_cholesky(arb_ctx ctx, int32_t m, const double* G, int64_t ldg, double* R, double* Rinv,

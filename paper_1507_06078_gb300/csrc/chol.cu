@@ -218,6 +218,12 @@ __global__ void rcond_chol_kernel(int m, const double* __restrict__ G, int64_t l
   }
 }
 
+// M[i][i] += s
+__global__ void add_diagonal_kernel(int m, double* __restrict__ M, int64_t ldm, double s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) M[static_cast<int64_t>(i) * ldm + i] += s;
+}
+
 __global__ void clear_status_kernel(int32_t* status) {
   if (threadIdx.x < 2) status[threadIdx.x] = 0;
 }
@@ -268,6 +274,29 @@ arb_status rcond_from_cholesky(arb_ctx ctx, int32_t m, const double* G, int64_t 
   inverse_from_factor_kernel<<<static_cast<int>((mm + 255) / 256), 256, 0, ctx->stream>>>(m, Rinv, Ginv, status);
   ARB_LAUNCHED(ctx);
   rcond_chol_kernel<<<1, 256, 0, ctx->stream>>>(m, G, ldg, Ginv, status, rc_dev);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+}  // namespace arb
+
+namespace arb {
+
+arb_status spd_inverse(arb_ctx ctx, int32_t m, const double* G, int64_t ldg, double* R, double* Rinv, double* Ginv,
+                       int32_t* status) {
+  ARB_CUDA(ctx, cudaMemcpy2DAsync(R, m * sizeof(double), G, ldg * sizeof(double), m * sizeof(double), m,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  ARB_TRY(cholesky_upper(ctx, m, R, m, 0.0, status));
+  ARB_TRY(triangular_inverse(ctx, m, R, m, nullptr, Rinv, status));
+  const int64_t mm = static_cast<int64_t>(m) * m;
+  inverse_from_factor_kernel<<<static_cast<int>((mm + 255) / 256), 256, 0, ctx->stream>>>(m, Rinv, Ginv, status);
+  ARB_LAUNCHED(ctx);
+  return ARB_OK;
+}
+
+arb_status add_diagonal(arb_ctx ctx, int32_t m, double* M, int64_t ldm, double s) {
+  if (m <= 0) return ARB_OK;
+  add_diagonal_kernel<<<(m + 127) / 128, 128, 0, ctx->stream>>>(m, M, ldm, s);
   ARB_LAUNCHED(ctx);
   return ARB_OK;
 }

@@ -168,7 +168,13 @@ extern "C" arb_status arb_submit(arb_server srv, arb_mat mat, int32_t k, arb_whi
   const int32_t p = req->opts.p > 0 ? req->opts.p : k + static_cast<int32_t>(std::lround(0.1 * k));
   if (x0) req->x0.assign(x0, x0 + static_cast<size_t>(mat->n) * p);
   req->want_vecs = want_evecs != 0;
-  req->footprint = arb::solve_footprint(mat->n, mat->nnz, p, req->opts.q, req->opts.precision);
+  // an adaptive q may grow to q_max (3 by default, and (q+1) p < n): admit for the largest
+  int32_t qf = req->opts.q;
+  if (req->opts.adapt & ARB_ADAPT_Q) {
+    const int64_t fit = (mat->n - 1) / std::max<int32_t>(p, 1) - 1;
+    qf = static_cast<int32_t>(std::max<int64_t>(qf, std::min<int64_t>(req->opts.q_max > 0 ? req->opts.q_max : 3, fit)));
+  }
+  req->footprint = arb::solve_footprint(mat->n, mat->nnz, p, qf, req->opts.precision);
   std::lock_guard<std::mutex> lock(srv->mu);
   if (srv->stop) return ARB_REJECTED;
   if (req->footprint > srv->budget) {

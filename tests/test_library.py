@@ -31,8 +31,8 @@ def test_status_strings_and_defaults(lib):
     o = arb.arb_options_default(20)
     assert (o.p, o.q, o.degree, o.maxit, o.maxit1, o.maxit2) == (22, 1, 3, 30, 10, 5)
     assert np.isnan(o.shift_sigma)
-    assert ctypes.sizeof(arb.arb_options) == 4 * 10 + 8 * 4
-    assert ctypes.sizeof(arb.arb_info) == 8 * 8 + 8 + 4 * 8
+    assert ctypes.sizeof(arb.arb_options) == 4 * 10 + 8 * 4 + 4 * 4
+    assert ctypes.sizeof(arb.arb_info) == 8 * 8 + 8 + 4 * 10
 
 
 @pytest.mark.parametrize("d", [1, 3, 10, 15, 20])
