@@ -440,9 +440,11 @@ def run_ours(args):
 
     served = None
     if rank == 0 and world == 1 and args.serve_mix:
-        mix = served_mix(arb.ARB_MIXED_DF, args.rate, args.requests, args.slots)
+        # the mixed form with an FP64 refinement: on the Chung-Lu kind the double-float
+        # refinement stalls where FP64 converges (see the design notes)
+        mix = served_mix(arb.ARB_MIXED, args.rate, args.requests, args.slots)
         mix64 = served_mix(arb.ARB_FP64, args.rate, args.requests, args.slots)
-        served = {"mixed_df": mix, "fp64": mix64,
+        served = {"mixed": mix, "fp64": mix64,
                   "p99_speedup_vs_fp64": mix64["p99_s"] / mix["p99_s"],
                   "solves_per_s_speedup_vs_fp64": mix["solves_per_s"] / max(mix64["solves_per_s"], 1e-30)}
 
@@ -580,13 +582,14 @@ def run_filter_only(args):
 
 def served_mix(precision, rate, requests, slots, seed=4242):
     """Served mix, bounded: a seeded Poisson stream of solve requests in equal thirds of 2D
-    64^2 Laplacian problems (k = 20, p = 30, d = 10, q = 1), variable-coefficient diffusion
-    instances (sides 32-256, k 8-64, p = 1.5k, d = 10, q = 1) and a 1/8-scale Chung-Lu
-    graph Laplacian (n ~ 125k, k 10-100, p = 1.2k, d = 15, q = 1), all to relative residual
-    1e-8 in the given precision (arb_precision), against one server with `slots` concurrent
-    solves.  Latency is the library's submit-to-completion wall time; p50/p99 are over the
-    requests that converged (the others are counted per kind); solves/s counts converged
-    requests over first submission to last completion."""
+    64^2 Laplacian problems (k = 20, p = 30, d = 10), variable-coefficient diffusion
+    instances (sides 32-256, k 8-64, p = 1.5k, d = 20) and a 1/8-scale Chung-Lu graph
+    Laplacian (n ~ 125k, k 10-60, p = 1.2k, d = 15), all with q = 1, b refreshed after every
+    ARR (Section 5) and relative residual 1e-8 in the given precision (arb_precision),
+    against one server with `slots` concurrent solves.  Latency is the library's
+    submit-to-completion wall time; p50/p99 are over the requests that converged (the others
+    are counted per kind); solves/s counts converged requests over first submission to last
+    completion."""
     from paper_1507_06078_gb300 import arrabit as arb
     ctx = arb.Context(0)
     rng = np.random.Generator(np.random.Philox(seed))
@@ -603,9 +606,9 @@ def served_mix(precision, rate, requests, slots, seed=4242):
             reqs.append(("laplace2d_64", lap2d, 20, 30, 10))
         elif kind == 1:
             j = int(rng.integers(0, len(diff)))
-            reqs.append((diff[j].name, diff_m[j], diff[j].k, diff[j].p, 10))
+            reqs.append((diff[j].name, diff_m[j], diff[j].k, diff[j].p, 20))
         else:
-            k = int(rng.integers(10, 101))
+            k = int(rng.integers(10, 61))
             reqs.append(("chung_lu_125k", cl_m, k, int(round(1.2 * k)), 15))
     gaps = rng.exponential(1.0 / rate, size=requests)
     srv = arb.Server(0, hbm_budget_bytes=64 << 30, max_slots=slots)
@@ -618,7 +621,7 @@ def served_mix(precision, rate, requests, slots, seed=4242):
         if delay > 0:
             time.sleep(delay)
         o = arb.arb_options_default(k)
-        o.p, o.q, o.degree, o.precision = p, 1, d, precision
+        o.p, o.q, o.degree, o.precision, o.b_update = p, 1, d, precision, 1
         t_sub.append(time.perf_counter())
         tickets.append(srv.submit(mat, k, arb.ARB_SMALLEST, 1e-8, o, want_evecs=False))
     lat, conv, worst = [], [], 0.0

@@ -423,6 +423,56 @@ arb_status arb_solve_batched(arb_ctx ctx, int32_t nb, const arb_mat* mats, const
                              const double* const* x0, double* const* evals, double* const* evecs,
                              const int64_t* ldq, arb_info* info, int32_t max_concurrent);
 
+/* ---------------------------------------------------------------- lock-step batching */
+
+/* Autotuner of the fused block SpMM for one matrix, by measurement: every candidate row
+ * layout - CSR, or SELL-C-sigma with C = 8 (sigma = 256) or C = 32 (sigma = 1024) - and
+ * vector width per lane - 4, 2 or 1 FP32 columns, so a warp covers a column slice of 128,
+ * 64 or 32 per row - is timed on one fused filter-like pass over an n x ncols FP32 block
+ * (gathers plus the X and Z streams of the Clenshaw recurrence; CUDA events on the
+ * context's stream, best of 3), and the fastest is kept with the matrix: its SELL copy is
+ * made or dropped (as by arb_matrix_set_sell) and the width caps every later fused SpMM on
+ * it, batched or not.  choice (host int32[2], may be NULL) receives {C (0: CSR), width};
+ * ms (host, may be NULL) the candidate's time per pass.  Not to be called while other
+ * calls use the matrix.  The paper tunes nothing of this kind (its products are MKL
+ * calls); the degree is chosen by the paper's own rule (ARB_ADAPT_DEGREE).
+ * Errors: ARB_INVALID_ARG, ARB_CUDA_ERROR. */
+arb_status arb_matrix_autotune(arb_ctx ctx, arb_mat mat, int32_t ncols, int32_t* choice, double* ms);
+
+typedef struct {
+  int64_t rounds;            /* inner-step rounds of the lock-step loop */
+  int64_t batched_launches;  /* persistent batched filter launches, direct or from graphs */
+  int64_t graph_launches;    /* rounds replayed from a captured CUDA graph */
+  int64_t graphs_captured;   /* distinct round shapes captured */
+  int64_t single_steps;      /* inner steps run for one instance alone (GN, double-float filter) */
+  double t_total;            /* seconds spent in the call */
+} arb_batch_stats;
+
+enum { ARB_BATCH_GRAPHS = 1, ARB_BATCH_AUTOTUNE = 2 };
+
+/* Solve nb independent problems (Algorithm 8 each, uneven sizes, widths and degrees) in
+ * lock step: every instance runs its own outer iterations, stop rules and precision
+ * phases, but in each round every instance that is in its inner loop takes one
+ * multi-power step, and the filters of all those steps run as ONE persistent cooperative
+ * launch (the batched filter of arb_filter_batched: all passes of all instances, a
+ * grid-wide barrier between passes).  Instances whose step cannot join the batch (the GN
+ * inner solver, the double-float refinement filter of ARB_MIXED_DF) take it alone in the
+ * same round.  flags: ARB_BATCH_GRAPHS captures the device work of a round into a CUDA
+ * graph the second time the same round shape occurs (the same instances, buffers and
+ * degrees) and replays it afterwards, with the round's descriptors re-uploaded before
+ * each replay; ARB_BATCH_AUTOTUNE runs arb_matrix_autotune on every distinct matrix first
+ * (width p of its first problem).  The work runs on a stream of its own, ordered after the
+ * context's stream; each instance has workspaces of its own for the duration of the call.
+ * Arguments and outputs per instance as for arb_solve (x0[i] host n_i x p_i or NULL;
+ * evecs[i] host column-major or NULL; ldq may be NULL for ldq[i] = n_i; opts, info and
+ * stats may be NULL).  Returns ARB_OK when every instance converged, else the first
+ * failing status (or ARB_NOT_CONVERGED).  The paper solves one problem at a time; the
+ * lock-step batch is this library's. */
+arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat* mats, const int32_t* k, const arb_which* which,
+                              const double* tol, const arb_options* opts, const double* const* x0,
+                              double* const* evals, double* const* evecs, const int64_t* ldq, arb_info* info,
+                              int32_t flags, arb_batch_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,6 +29,7 @@ ARB_FP64, ARB_MIXED, ARB_MIXED_DF = 0, 1, 2
 ARB_FILTER_CHEBINTERP, ARB_FILTER_CHEBYSHEV = 0, 1
 ARB_INNER_MPM, ARB_INNER_GN = 0, 1
 ARB_ADAPT_Q, ARB_ADAPT_DEGREE = 1, 2
+ARB_BATCH_GRAPHS, ARB_BATCH_AUTOTUNE = 1, 2
 STOP_REASONS = {0: "converged", 1: "near_tol", 2: "stalled", 3: "maxit", 4: "all_locked"}
 
 
@@ -52,6 +53,14 @@ class arb_filter_job(C.Structure):
                 ("b", C.c_double), ("degree", C.c_int32), ("fp32", C.c_int32), ("coef", C.c_void_p),
                 ("X", C.c_void_p), ("ldx", C.c_int64), ("ncols", C.c_int32), ("reserved0", C.c_int32),
                 ("xscale", C.c_void_p), ("Y", C.c_void_p), ("ldy", C.c_int64), ("colss", C.c_void_p)]
+
+
+class arb_batch_stats(C.Structure):
+    _fields_ = [("rounds", C.c_int64), ("batched_launches", C.c_int64), ("graph_launches", C.c_int64),
+                ("graphs_captured", C.c_int64), ("single_steps", C.c_int64), ("t_total", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class arb_info(C.Structure):
@@ -106,6 +115,9 @@ _PROTOS = {
     "arb_wait": (_i32, [_vp, _i64, _i32, _vp, _vp, _i64, C.POINTER(arb_info), C.POINTER(_dbl)]),
     "arb_server_destroy": (_i32, [_vp]),
     "arb_solve_batched": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32]),
+    "arb_solve_lockstep": (_i32, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32,
+                                  C.POINTER(arb_batch_stats)]),
+    "arb_matrix_autotune": (_i32, [_vp, _vp, _i32, _vp, C.POINTER(_dbl)]),
     "arb_syevj": (_i32, [_vp, _i32, _vp, _i64, _vp, _vp, _i64, C.POINTER(_i32)]),
     "arb_rcond_gram": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, C.POINTER(_dbl)]),
     "arb_orth": (_i32, [_vp, _i64, _vp, _i64, _i32, _vp, _i64, C.POINTER(_i32)]),
@@ -636,3 +648,50 @@ def arb_solve_batched(ctx: Context, problems: list[dict], max_concurrent: int = 
                                   C.cast(vcp, _vp) if evecs else None, None, C.cast(infos, _vp), max_concurrent)
     _check(ctx, st, "arb_solve_batched")
     return st, [SolveResult(ARB_OK, evs[i], vecs[i].T if evecs else None, infos[i].as_dict()) for i in range(nb)]
+
+
+def _batch_args(problems, evecs):
+    nb = len(problems)
+    mats = (_vp * nb)(*[p["mat"].handle.value for p in problems])
+    ks = (_i32 * nb)(*[p["k"] for p in problems])
+    wh = (_i32 * nb)(*[p["which"] for p in problems])
+    tl = (_dbl * nb)(*[p["tol"] for p in problems])
+    opts = (arb_options * nb)(*[p.get("opts") or arb_options_default(p["k"]) for p in problems])
+    keep = []
+    x0s = (_vp * nb)()
+    for i, p in enumerate(problems):
+        if p.get("x0") is not None:
+            x = np.ascontiguousarray(p["x0"], dtype=np.float64)
+            keep.append(x)
+            x0s[i] = x.ctypes.data
+    evs = [np.zeros(p["k"]) for p in problems]
+    vecs = [np.zeros((p["k"], p["mat"].n)) for p in problems] if evecs else None
+    evp = (_vp * nb)(*[e.ctypes.data for e in evs])
+    vcp = (_vp * nb)(*[v.ctypes.data for v in vecs]) if evecs else None
+    return nb, mats, ks, wh, tl, opts, keep, x0s, evs, vecs, evp, vcp
+
+
+def arb_solve_lockstep(ctx: Context, problems: list[dict], flags: int = ARB_BATCH_GRAPHS, evecs: bool = True):
+    """Lock-step batched solve: problems as for arb_solve_batched.  Returns (status,
+    [SolveResult], stats dict)."""
+    nb, mats, ks, wh, tl, opts, keep, x0s, evs, vecs, evp, vcp = _batch_args(problems, evecs)
+    infos = (arb_info * nb)()
+    stats = arb_batch_stats()
+    st = load().arb_solve_lockstep(ctx.handle, nb, C.cast(mats, _vp), C.cast(ks, _vp), C.cast(wh, _vp),
+                                   C.cast(tl, _vp), C.cast(opts, _vp), C.cast(x0s, _vp), C.cast(evp, _vp),
+                                   C.cast(vcp, _vp) if evecs else None, None, C.cast(infos, _vp), flags,
+                                   C.byref(stats))
+    _check(ctx, st, "arb_solve_lockstep")
+    del keep
+    return st, [SolveResult(ARB_OK, evs[i], vecs[i].T if evecs else None, infos[i].as_dict()) for i in range(nb)], \
+        stats.as_dict()
+
+
+def arb_matrix_autotune(ctx: Context, mat: Matrix, ncols: int) -> dict:
+    """Time the fused SpMM layouts and widths on this matrix and keep the fastest:
+    {"sell_C": C (0 = CSR), "vec": width, "ms": time per pass}."""
+    choice = (_i32 * 2)()
+    ms = _dbl()
+    _check(ctx, load().arb_matrix_autotune(ctx.handle, mat.handle, ncols, C.cast(choice, _vp), C.byref(ms)),
+           "arb_matrix_autotune")
+    return {"sell_C": choice[0], "vec": choice[1], "ms": ms.value}

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIBPATH = os.path.join(LIBDIR, "libarrabit.so")
-SOURCES = ["spmm.cu", "dense.cu", "jacobi.cu", "steps.cu", "api.cu", "noalloc.cu", "server.cu", "batched.cu", "df.cu", "tc.cu", "sell.cu", "chol.cu", "spmm_bulk.cu"]
+SOURCES = ["spmm.cu", "dense.cu", "jacobi.cu", "steps.cu", "api.cu", "noalloc.cu", "server.cu", "batched.cu", "df.cu", "tc.cu", "sell.cu", "chol.cu", "spmm_bulk.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -8,6 +8,9 @@
 #include <cstring>
 #include <limits>
 #include <type_traits>
+#include <memory>
+#include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "arb_internal.h"
@@ -643,7 +646,10 @@ struct SolveState {
   bool trace = false;  // ARB_TRACE set in the environment: one line per outer iteration on stderr
   bool df_filter = false;  // FP64 phase filters in double-float arithmetic (ARB_MIXED_DF)
   // mixed paths: an idle FP32 n x ld32 block the FP64 phase uses for FP32 Gram products of
-  // its inner stop rule (rcond thresholds >= 1e-6 are far above what FP32 Grams resolve)
+  // its inner stop rule while the rcond threshold is >= 1e-4.  An FP32 Gram entry is good to
+  // ~1e-8 of ||x_i|| ||x_j||, so its smallest eigenvalue carries errors up to ~p 1e-8: at the
+  // threshold 1e-6 it cannot tell rc from 0, the inner loop then ran on past the point where
+  // the block lost rank (measured on the Chung-Lu Laplacian, k = 90).
   float* x32 = nullptr;
   int64_t ld32 = 0;
 };
@@ -865,491 +871,1016 @@ arb_status gn_step(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, cons
   return ARB_OK;
 }
 
-// Outer iterations of Algorithm 8 with blocks of type T until the outer stop rule holds for
-// `tol_phase` (or a stall / maxit / all-locked stop).  rc_floor bounds the inner-stop
-// threshold from below (reading c7: 100 u of the filter precision); lock = false disables
-// deflation (thresholds of eq. defl are below what FP32 blocks resolve).  When
-// continue_on_phase_tol is set, reaching tol_phase performs one continuation step (b and
-// tol_t updated as in eq. contin) before returning.
+// One phase of Algorithm 8 with blocks of type T (the FP32 phase or the FP64 phase of a
+// solve), run until the outer stop rule holds for `tol_phase` (or a stall / maxit /
+// all-locked stop).  rc_floor bounds the inner-stop threshold from below (reading c7: 100 u
+// of the filter precision); lock = false disables deflation (thresholds of eq. defl are
+// below what FP32 blocks resolve).  When cont_on_tol is set, reaching tol_phase performs one
+// continuation step (b and tol_t updated as in eq. contin) before the phase ends.
+//
+// The phase is resumable at the points the lock-step batched driver needs: the start of an
+// outer iteration, every inner step (whose filter the caller may have applied for many
+// instances at once), the inner stop check, and the ARR / stop-rule tail.
 template <typename T>
-arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, double tol_phase, double rc_floor,
-                     bool lock, bool continue_on_phase_tol, bool stop_on_stagnation = false) {
-  const int64_t n = S.n;
-  const int32_t p = S.p, k = S.k;
-  S.best = std::numeric_limits<double>::infinity();
-  S.best_iter = 0;
-  S.outer = 0;
-  S.stop = ARB_STOP_MAXIT;
-  S.maxres_prev = -1.0;
-  S.have_best_mu = false;
-  float ms = 0.f;
+struct Phase {
+  arb_ctx ctx;
+  arb_mat mat;
+  SolveState* S;
+  BlockSet<T>* B;
+  double tol_phase = 0.0, rc_floor = 0.0;
+  bool lock = true, cont_on_tol = false, stop_on_stag = false;
+  int j = 0;                 // outer iteration in progress
+  int i1 = 0, i2 = 0;        // inner check and step counters of the current outer iteration
+  int n_checks = 0, n_steps = 0;
+  double rc = 0.0, rc_thr = 0.0;
   double prev_maxres = std::numeric_limits<double>::infinity();
-  for (int j = 1; j <= S.o.maxit; ++j) {
-    S.outer = j;
-    S.info.outer_iters++;
-    const int nf0 = S.info.n_filters;
-    // ---------------- inner loop: multi-power steps (Algorithm 8, MPM branch)
-    ARB_CUDA(ctx, cudaEventRecord(S.ev0, ctx->stream));
-    double rc = std::numeric_limits<double>::infinity();
-    const int n_checks = S.o.inner_fixed > 0 ? 1 : S.o.maxit1;
-    const int n_steps = S.o.inner_fixed > 0 ? S.o.inner_fixed : S.o.maxit2;
-    const double rc_thr = std::max(S.tol_t, rc_floor);
-    bool lost_rank = false;
-    for (int i1 = 0; i1 < n_checks; ++i1) {
-      for (int i2 = 0; i2 < n_steps; ++i2) {
-        const FilterPlan plan = make_filter_plan(S.op_scale, S.op_shift, S.a, S.b, S.d, S.coef);
-        if (S.o.inner == ARB_INNER_GN) {
-          bool ok = true;
-          ARB_TRY(gn_step<T>(ctx, mat, S, B, plan, &ok));
-          if (!ok) {  // X^T X not positive definite: the GN step is undefined, go to the ARR step
-            lost_rank = true;
-            break;
-          }
-          if (S.nl > 0) ARB_TRY(project_out<T>(ctx, n, B.Qc, B.ld, S.nl, B.X, B.ld, S.w));
-          S.info.n_filters++;
-          S.info.spmm_cols += static_cast<int64_t>(S.d) * S.w;
-          continue;
-        }
-        T* result = nullptr;
-        bool filtered = false;
-        if constexpr (std::is_same<T, double>::value) {
-          if (S.df_filter) {
-            // double-float filter: X rounded into T1 (free during the inner loop), the passes
-            // run in W1 / W2 (same bytes per element as FP64), the result read back into X
-            df2* Xd = reinterpret_cast<df2*>(B.wk.T1);
-            df2* R = nullptr;
-            ARB_TRY(to_df(ctx, n, B.X, B.ld, S.w, Xd, B.ld));
-            ARB_TRY(filter_apply<df2>(ctx, mat, plan, Xd, B.ld, S.w, S.xs, reinterpret_cast<df2*>(B.W1),
-                                      reinterpret_cast<df2*>(B.W2), B.ld, nullptr, 0, S.ss, &R));
-            ARB_TRY(from_df(ctx, n, R, B.ld, S.w, B.X, B.ld));
-            filtered = true;
-          }
-        }
-        if (!filtered) {
-          ARB_TRY(filter_apply<T>(ctx, mat, plan, B.X, B.ld, S.w, S.xs, B.W1, B.W2, B.ld, nullptr, 0, S.ss, &result));
-          if (result == B.W1) std::swap(B.X, B.W1);
-          else std::swap(B.X, B.W2);
-        }
-        ARB_TRY(inv_sqrt(ctx, S.w, S.ss, S.xs));  // column normalisation, applied lazily
-        if (S.nl > 0) ARB_TRY(project_out<T>(ctx, n, B.Qc, B.ld, S.nl, B.X, B.ld, S.w));
-        S.info.n_filters++;
-        S.info.spmm_cols += static_cast<int64_t>(S.d) * S.w;
-      }
-      if (S.o.inner_fixed > 0 || lost_rank) break;
-      const double rcp = rc;
-      bool done_rc = false;
-      if constexpr (std::is_same<T, double>::value) {
-        if (S.x32 && rc_thr >= 1e-6) {
-          ARB_TRY((copy_block<double, float>(ctx, n, B.X, B.ld, S.w, S.x32, S.ld32)));
-          ARB_TRY(rcond_gram<float>(ctx, n, S.x32, S.ld32, S.w, S.xs, &rc));
-          done_rc = true;
-        }
-      }
-      if (!done_rc) ARB_TRY(rcond_gram<T>(ctx, n, B.X, B.ld, S.w, S.xs, &rc));
-      if (rc <= rc_thr || rc / rcp > 0.99) break;  // eq. inn-stop
-    }
-    ARB_CUDA(ctx, cudaEventRecord(S.ev1, ctx->stream));
-    ARB_CUDA(ctx, cudaEventSynchronize(S.ev1));
-    ARB_CUDA(ctx, cudaEventElapsedTime(&ms, S.ev0, S.ev1));
-    S.info.t_filter += ms * 1e-3;
+  bool in_inner = false;     // the inner loop of outer iteration j is running
+  bool done = false;         // the phase has ended (S->stop says why)
+  int nf0 = 0;
 
+  arb_status begin() {
+    S->best = std::numeric_limits<double>::infinity();
+    S->best_iter = 0;
+    S->outer = 0;
+    S->stop = ARB_STOP_MAXIT;
+    S->maxres_prev = -1.0;
+    S->have_best_mu = false;
+    j = 0;
+    done = false;
+    return ARB_OK;
+  }
+
+  // start outer iteration j + 1 (or end the phase at maxit)
+  arb_status outer_begin() {
+    if (j >= S->o.maxit) {
+      done = true;
+      return ARB_OK;
+    }
+    ++j;
+    S->outer = j;
+    S->info.outer_iters++;
+    nf0 = S->info.n_filters;
+    ARB_CUDA(ctx, cudaEventRecord(S->ev0, ctx->stream));
+    rc = std::numeric_limits<double>::infinity();
+    n_checks = S->o.inner_fixed > 0 ? 1 : S->o.maxit1;
+    n_steps = S->o.inner_fixed > 0 ? S->o.inner_fixed : S->o.maxit2;
+    rc_thr = std::max(S->tol_t, rc_floor);
+    i1 = i2 = 0;
+    in_inner = true;
+    return ARB_OK;
+  }
+
+  FilterPlan plan() const { return make_filter_plan(S->op_scale, S->op_shift, S->a, S->b, S->d, S->coef); }
+
+  // MPM steps whose filter an external batched launch performs: the filter reads X with
+  // the lazy column scaling xs and writes the result, with its column sums of squares in
+  // ss, to filter_out(); step_post() then takes it over as the iterate
+  bool batchable() const {
+    if (S->o.inner != ARB_INNER_MPM) return false;
+    if constexpr (std::is_same<T, double>::value) return !S->df_filter;
+    return true;
+  }
+  T* filter_out() const { return B->W1; }
+
+  // one inner step, filter included
+  arb_status step() {
+    const int64_t n = S->n;
+    const FilterPlan pl = plan();
+    if (S->o.inner == ARB_INNER_GN) {
+      bool ok = true;
+      ARB_TRY(gn_step<T>(ctx, mat, *S, *B, pl, &ok));
+      if (!ok) {  // X^T X not positive definite: the GN step is undefined, go to the ARR step
+        in_inner = false;
+        return ARB_OK;
+      }
+      if (S->nl > 0) ARB_TRY(project_out<T>(ctx, n, B->Qc, B->ld, S->nl, B->X, B->ld, S->w));
+      return count_step();
+    }
+    bool filtered = false;
+    if constexpr (std::is_same<T, double>::value) {
+      if (S->df_filter) {
+        // double-float filter: X rounded into T1 (free during the inner loop), the passes
+        // run in W1 / W2 (same bytes per element as FP64), the result read back into X
+        df2* Xd = reinterpret_cast<df2*>(B->wk.T1);
+        df2* R = nullptr;
+        ARB_TRY(to_df(ctx, n, B->X, B->ld, S->w, Xd, B->ld));
+        ARB_TRY(filter_apply<df2>(ctx, mat, pl, Xd, B->ld, S->w, S->xs, reinterpret_cast<df2*>(B->W1),
+                                  reinterpret_cast<df2*>(B->W2), B->ld, nullptr, 0, S->ss, &R));
+        ARB_TRY(from_df(ctx, n, R, B->ld, S->w, B->X, B->ld));
+        filtered = true;
+      }
+    }
+    if (!filtered) {
+      T* result = nullptr;
+      ARB_TRY(filter_apply<T>(ctx, mat, pl, B->X, B->ld, S->w, S->xs, B->W1, B->W2, B->ld, nullptr, 0, S->ss, &result));
+      if (result == B->W1) std::swap(B->X, B->W1);
+      else std::swap(B->X, B->W2);
+    }
+    return normalise_project_count();
+  }
+
+  // after an external filter wrote the filtered block into filter_out() (and its column
+  // sums of squares into S->ss): it becomes the iterate
+  arb_status step_post_external() {
+    std::swap(B->X, B->W1);
+    return normalise_project_count();
+  }
+
+  arb_status normalise_project_count() {
+    ARB_TRY(inv_sqrt(ctx, S->w, S->ss, S->xs));  // column normalisation, applied lazily
+    if (S->nl > 0) ARB_TRY(project_out<T>(ctx, S->n, B->Qc, B->ld, S->nl, B->X, B->ld, S->w));
+    return count_step();
+  }
+
+  arb_status count_step() {
+    S->info.n_filters++;
+    S->info.spmm_cols += static_cast<int64_t>(S->d) * S->w;
+    ++i2;
+    return ARB_OK;
+  }
+
+  bool step_due() const { return in_inner && i2 < n_steps; }
+
+  // after n_steps steps: the inner stop rule (eq. inn-stop), or the end of a fixed schedule
+  arb_status check() {
+    i2 = 0;
+    ++i1;
+    if (S->o.inner_fixed > 0) {
+      in_inner = false;
+      return ARB_OK;
+    }
+    const int64_t n = S->n;
+    const double rcp = rc;
+    bool done_rc = false;
+    if constexpr (std::is_same<T, double>::value) {
+      if (S->x32 && rc_thr >= 1e-4) {
+        ARB_TRY((copy_block<double, float>(ctx, n, B->X, B->ld, S->w, S->x32, S->ld32)));
+        ARB_TRY(rcond_gram<float>(ctx, n, S->x32, S->ld32, S->w, S->xs, &rc));
+        done_rc = true;
+      }
+    }
+    if (!done_rc) ARB_TRY(rcond_gram<T>(ctx, n, B->X, B->ld, S->w, S->xs, &rc));
+    if (rc <= rc_thr || rc / rcp > 0.99 || i1 >= n_checks) in_inner = false;
+    return ARB_OK;
+  }
+
+  // augmentation + projection + RR, residuals, stop rules, continuation, deflation and the
+  // adaptive rules of the outer iteration j
+  arb_status outer_tail() {
+    arb_status st = outer_tail_impl();
+    if (st != ARB_OK) done = true;
+    return st;
+  }
+
+  arb_status outer_tail_impl() {
+    SolveState& Sr = *S;
+    BlockSet<T>& Br = *B;
+    const int64_t n = Sr.n;
+    const int32_t p = Sr.p, k = Sr.k;
+    float ms = 0.f;
+    ARB_CUDA(ctx, cudaEventRecord(Sr.ev1, ctx->stream));
+    ARB_CUDA(ctx, cudaEventSynchronize(Sr.ev1));
+    ARB_CUDA(ctx, cudaEventElapsedTime(&ms, Sr.ev0, Sr.ev1));
+    Sr.info.t_filter += ms * 1e-3;
     // ---------------- augmentation + projection + RR (Algorithm 5 inside Algorithm 8)
-    ARB_CUDA(ctx, cudaEventRecord(S.ev0, ctx->stream));
+    ARB_CUDA(ctx, cudaEventRecord(Sr.ev0, ctx->stream));
     int32_t m = 0;
-    ARB_TRY(arr_basis_and_eig<T>(ctx, mat, S.op_scale, S.op_shift, n, B.X, B.ld, S.w, B.Qc, B.ld, S.nl, S.q,
-                                 B.wk, &m, S.theta, S.V));
-    S.info.last_rank = m;
-    S.info.spmm_cols += m;
+    ARB_TRY(arr_basis_and_eig<T>(ctx, mat, Sr.op_scale, Sr.op_shift, n, Br.X, Br.ld, Sr.w, Br.Qc, Br.ld, Sr.nl, Sr.q,
+                                 Br.wk, &m, Sr.theta, Sr.V));
+    Sr.info.last_rank = m;
+    Sr.info.spmm_cols += m;
     // the p leading pairs of (Q_c, Sigma_c) and (U V, theta)
-    ARB_TRY(select_top(ctx, S.sigc, S.nl, S.theta, m, p, S.imap, S.mu));
-    ARB_TRY(d2h_sync(ctx, S.h_map.data(), S.imap, p * sizeof(int32_t)));
+    ARB_TRY(select_top(ctx, Sr.sigc, Sr.nl, Sr.theta, m, p, Sr.imap, Sr.mu));
+    ARB_TRY(d2h_sync(ctx, Sr.h_map.data(), Sr.imap, p * sizeof(int32_t)));
     int32_t count = 0;  // Ritz pairs available (the rest of the block is padded below)
-    while (count < p && S.h_map[count] >= 0) ++count;
+    while (count < p && Sr.h_map[count] >= 0) ++count;
     // mu_{k+q} is an estimate of lambda_{k+q} only when it is a Ritz value: after padding
     // (a Rayleigh quotient of a random column) b keeps its previous value
     const bool b_ok = (count == p);
     if (count == 0) return set_error(ctx, ARB_BREAKDOWN, "solve: no Ritz pairs");
     std::vector<int32_t> newcols, src(count);
     for (int s = 0; s < count; ++s) {
-      if (S.h_map[s] < S.nl) {
-        src[s] = -S.h_map[s] - 1;  // locked column
+      if (Sr.h_map[s] < Sr.nl) {
+        src[s] = -Sr.h_map[s] - 1;  // locked column
       } else {
         src[s] = static_cast<int32_t>(newcols.size());
-        newcols.push_back(S.h_map[s] - S.nl);
+        newcols.push_back(Sr.h_map[s] - Sr.nl);
       }
     }
     const int32_t pn = static_cast<int32_t>(newcols.size());
     if (pn > 0) {
-      ARB_TRY(upload_ints(ctx, S.iidx, newcols));
-      ARB_TRY(gather_cols<double>(ctx, m, S.V, m, S.iidx, pn, S.Vsel, pn));  // V: m x m, ld m
-      ARB_TRY(gemm_tall<T>(ctx, n, B.wk.U, B.ldm, m, S.Vsel, pn, pn, 1.0, 0.0, B.wk.T1, B.ld));
+      ARB_TRY(upload_ints(ctx, Sr.iidx, newcols));
+      ARB_TRY(gather_cols<double>(ctx, m, Sr.V, m, Sr.iidx, pn, Sr.Vsel, pn));  // V: m x m, ld m
+      ARB_TRY(gemm_tall<T>(ctx, n, Br.wk.U, Br.ldm, m, Sr.Vsel, pn, pn, 1.0, 0.0, Br.wk.T1, Br.ld));
     }
-    ARB_TRY(upload_ints(ctx, S.imap, src));
-    ARB_TRY(gather_cols2<T>(ctx, n, B.wk.T1, B.ld, B.Qc, B.ld, S.imap, count, B.Xall, B.ld));
-    if (count < p) ARB_TRY(pad_ritz_block(ctx, mat, S, B, count, j));
+    ARB_TRY(upload_ints(ctx, Sr.imap, src));
+    ARB_TRY(gather_cols2<T>(ctx, n, Br.wk.T1, Br.ld, Br.Qc, Br.ld, Sr.imap, count, Br.Xall, Br.ld));
+    if (count < p) ARB_TRY(pad_ritz_block(ctx, mat, Sr, Br, count, j));
     // residuals (eq. resi): ||B x - mu x|| with the sign folded (-B x + mu x)
     {
       SpmmArgs<T> sa;
       sa.A = mat;
       sa.ncols = p;
-      sa.Yin = B.Xall;
-      sa.ldy = B.ld;
-      sa.alpha = -S.op_scale;
-      sa.beta = -S.op_shift;
-      sa.X = B.Xall;
-      sa.ldx = B.ld;
-      sa.sx = S.mu;
-      sa.colred = S.ss;
+      sa.Yin = Br.Xall;
+      sa.ldy = Br.ld;
+      sa.alpha = -Sr.op_scale;
+      sa.beta = -Sr.op_shift;
+      sa.X = Br.Xall;
+      sa.ldx = Br.ld;
+      sa.sx = Sr.mu;
+      sa.colred = Sr.ss;
       ARB_TRY(spmm_fused<T>(ctx, sa));
-      ARB_TRY(residual_finish(ctx, p, S.ss, S.mu, S.smallest ? 1 : 0, S.sigma, S.res));
-      S.info.spmm_cols += p;
+      ARB_TRY(residual_finish(ctx, p, Sr.ss, Sr.mu, Sr.smallest ? 1 : 0, Sr.sigma, Sr.res));
+      Sr.info.spmm_cols += p;
     }
-    ARB_TRY(d2h_sync(ctx, S.h_mu.data(), S.mu, p * sizeof(double)));
-    ARB_TRY(d2h_sync(ctx, S.h_res.data(), S.res, p * sizeof(double)));
-    ARB_CUDA(ctx, cudaEventRecord(S.ev1, ctx->stream));
-    ARB_CUDA(ctx, cudaEventSynchronize(S.ev1));
-    ARB_CUDA(ctx, cudaEventElapsedTime(&ms, S.ev0, S.ev1));
-    S.info.t_arr += ms * 1e-3;
+    ARB_TRY(d2h_sync(ctx, Sr.h_mu.data(), Sr.mu, p * sizeof(double)));
+    ARB_TRY(d2h_sync(ctx, Sr.h_res.data(), Sr.res, p * sizeof(double)));
+    ARB_CUDA(ctx, cudaEventRecord(Sr.ev1, ctx->stream));
+    ARB_CUDA(ctx, cudaEventSynchronize(Sr.ev1));
+    ARB_CUDA(ctx, cudaEventElapsedTime(&ms, Sr.ev0, Sr.ev1));
+    Sr.info.t_arr += ms * 1e-3;
 
     // ---------------- outer stop rules, continuation, deflation (Section 5)
     double maxres = 0.0;
     int h = 0;
     for (int i = 0; i < k; ++i) {
-      maxres = std::max(maxres, std::isnan(S.h_res[i]) ? std::numeric_limits<double>::infinity() : S.h_res[i]);
-      h += S.h_res[i] < 0.1 * tol_phase;
+      maxres = std::max(maxres, std::isnan(Sr.h_res[i]) ? std::numeric_limits<double>::infinity() : Sr.h_res[i]);
+      h += Sr.h_res[i] < 0.1 * tol_phase;
     }
-    if (S.trace)
+    if (Sr.trace)
       fprintf(stderr,
               "[arb] %s outer %d: filters %d (total %d) rc %.3e rank %d maxres %.3e b %.9g tol_t %.1e locked %d "
               "t_filter %.3fs t_arr %.3fs\n",
-              sizeof(T) == 4 ? "fp32" : "fp64", j, S.info.n_filters - nf0, S.info.n_filters, rc,
-              m, maxres, S.b, S.tol_t, S.nl, S.info.t_filter, S.info.t_arr);
-    S.info.maxres = maxres;
-    if (maxres < S.best) {
-      S.best = maxres;
-      S.best_iter = j;
-      S.have_best_mu = true;
-      S.mu_best_k = S.h_mu[k - 1];
-      S.mu_best_kq = S.h_mu[p - 1];
+              sizeof(T) == 4 ? "fp32" : "fp64", j, Sr.info.n_filters - nf0, Sr.info.n_filters, rc,
+              m, maxres, Sr.b, Sr.tol_t, Sr.nl, Sr.info.t_filter, Sr.info.t_arr);
+    Sr.info.maxres = maxres;
+    if (maxres < Sr.best) {
+      Sr.best = maxres;
+      Sr.best_iter = j;
+      Sr.have_best_mu = true;
+      Sr.mu_best_k = Sr.h_mu[k - 1];
+      Sr.mu_best_kq = Sr.h_mu[p - 1];
     }
     if (maxres <= tol_phase) {
-      S.stop = ARB_STOP_CONVERGED;
-      if (continue_on_phase_tol && tol_phase > S.tol) {
-        if (b_ok) S.b = S.h_mu[p - 1];
-        if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+      Sr.stop = ARB_STOP_CONVERGED;
+      if (cont_on_tol && tol_phase > Sr.tol) {
+        if (b_ok) Sr.b = Sr.h_mu[p - 1];
+        if (!(Sr.b > Sr.a)) Sr.b = Sr.a + 1e-3 * std::max(1.0, std::fabs(Sr.a));
       }
+      done = true;
       return ARB_OK;
     }
     // mixed path: the FP32 iterate has reached its accuracy floor when an outer iteration
     // no longer halves maxres; hand over to FP64 with the best interval estimate
-    if (stop_on_stagnation && j >= 2 && maxres > 0.5 * prev_maxres) {
-      S.stop = ARB_STOP_STALLED;
-      if (b_ok) S.b = S.h_mu[p - 1];
-      if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+    if (stop_on_stag && j >= 2 && maxres > 0.5 * prev_maxres) {
+      Sr.stop = ARB_STOP_STALLED;
+      if (b_ok) Sr.b = Sr.h_mu[p - 1];
+      if (!(Sr.b > Sr.a)) Sr.b = Sr.a + 1e-3 * std::max(1.0, std::fabs(Sr.a));
+      done = true;
       return ARB_OK;
     }
     prev_maxres = maxres;
     if (maxres < (1.0 + 9.0 * h / k) * tol_phase) {
-      S.stop = ARB_STOP_NEAR_TOL;
+      Sr.stop = ARB_STOP_NEAR_TOL;
+      done = true;
       return ARB_OK;
     }
-    if (j - S.best_iter >= 3) {
-      S.stop = ARB_STOP_STALLED;
+    if (j - Sr.best_iter >= 3) {
+      Sr.stop = ARB_STOP_STALLED;
+      done = true;
       return ARB_OK;
     }
-    if (maxres <= S.tol_t) {  // continuation, eq. contin
-      S.tol_t = std::max(1e-2 * S.tol_t, S.tol);
-      if (b_ok) S.b = S.h_mu[p - 1];
-    } else if (S.o.b_update == 1) {  // Section 5: a better estimate of lambda_{k+q} after each ARR
-      if (b_ok) S.b = S.h_mu[p - 1];
+    if (maxres <= Sr.tol_t) {  // continuation, eq. contin
+      Sr.tol_t = std::max(1e-2 * Sr.tol_t, Sr.tol);
+      if (b_ok) Sr.b = Sr.h_mu[p - 1];
+    } else if (Sr.o.b_update == 1) {  // Section 5: a better estimate of lambda_{k+q} after each ARR
+      if (b_ok) Sr.b = Sr.h_mu[p - 1];
     }
-    if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
-    const double thr = std::max(1e-14, S.tol_t * S.tol_t);  // eq. defl
+    if (!(Sr.b > Sr.a)) Sr.b = Sr.a + 1e-3 * std::max(1.0, std::fabs(Sr.a));
+    const double thr = std::max(1e-14, Sr.tol_t * Sr.tol_t);  // eq. defl
     std::vector<int32_t> lock_idx, free_idx;
-    S.h_sigc.clear();
+    Sr.h_sigc.clear();
     for (int s = 0; s < p; ++s) {
-      if (lock && s < k && S.h_res[s] <= thr) {
+      if (lock && s < k && Sr.h_res[s] <= thr) {
         lock_idx.push_back(s);
-        S.h_sigc.push_back(S.h_mu[s]);
+        Sr.h_sigc.push_back(Sr.h_mu[s]);
       } else {
         free_idx.push_back(s);
       }
     }
-    S.nl = static_cast<int32_t>(lock_idx.size());
-    S.info.max_locked = std::max(S.info.max_locked, S.nl);
-    S.w = p - S.nl;
-    if (S.w == 0) {
-      S.stop = ARB_STOP_ALL_LOCKED;
+    Sr.nl = static_cast<int32_t>(lock_idx.size());
+    Sr.info.max_locked = std::max(Sr.info.max_locked, Sr.nl);
+    Sr.w = p - Sr.nl;
+    if (Sr.w == 0) {
+      Sr.stop = ARB_STOP_ALL_LOCKED;
+      done = true;
       return ARB_OK;
     }
-    if (S.nl > 0) {
-      ARB_TRY(upload_ints(ctx, S.iidx, lock_idx));
-      ARB_TRY(gather_cols<T>(ctx, n, B.Xall, B.ld, S.iidx, S.nl, B.Qc, B.ld));
-      ARB_TRY(h2d(ctx, S.sigc, S.h_sigc.data(), S.nl * sizeof(double)));
+    if (Sr.nl > 0) {
+      ARB_TRY(upload_ints(ctx, Sr.iidx, lock_idx));
+      ARB_TRY(gather_cols<T>(ctx, n, Br.Xall, Br.ld, Sr.iidx, Sr.nl, Br.Qc, Br.ld));
+      ARB_TRY(h2d(ctx, Sr.sigc, Sr.h_sigc.data(), Sr.nl * sizeof(double)));
     }
-    ARB_TRY(upload_ints(ctx, S.iidx, free_idx));
-    ARB_TRY(gather_cols<T>(ctx, n, B.Xall, B.ld, S.iidx, S.w, B.X, B.ld));
-    ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
+    ARB_TRY(upload_ints(ctx, Sr.iidx, free_idx));
+    ARB_TRY(gather_cols<T>(ctx, n, Br.Xall, Br.ld, Sr.iidx, Sr.w, Br.X, Br.ld));
+    ARB_TRY(fill(ctx, Sr.xs, Sr.w, 1.0));
     // augmentation blocks (eq. block): little decay of the relevant Ritz values of B - aI
     // (the operator the inner solver works on) and a disappointing residual decrease
-    if ((S.o.adapt & ARB_ADAPT_Q) && S.maxres_prev > 0.0 && S.q < S.q_cap) {
-      const double ratio = (S.h_mu[p - 1] - S.a) / (S.h_mu[k - 1] - S.a);
-      if (ratio > 0.95 && maxres / S.maxres_prev > 0.1) S.q++;
+    if ((Sr.o.adapt & ARB_ADAPT_Q) && Sr.maxres_prev > 0.0 && Sr.q < Sr.q_cap) {
+      const double ratio = (Sr.h_mu[p - 1] - Sr.a) / (Sr.h_mu[k - 1] - Sr.a);
+      if (ratio > 0.95 && maxres / Sr.maxres_prev > 0.1) Sr.q++;
     }
-    S.maxres_prev = maxres;
+    Sr.maxres_prev = maxres;
     // polynomial degree (eqs. hat-d, degree) from the most accurate Ritz values so far
-    if ((S.o.adapt & ARB_ADAPT_DEGREE) && S.have_best_mu) {
-      const int d = next_degree(S.o.filter, S.mu_best_k, S.mu_best_kq, S.a, S.b, S.o.d_max > 0 ? S.o.d_max : 15);
-      if (d != S.d) {
-        S.d = d;
-        if (arb_filter_coefficients(S.o.filter, S.d, S.coef) != ARB_OK)
+    if ((Sr.o.adapt & ARB_ADAPT_DEGREE) && Sr.have_best_mu) {
+      const int d = next_degree(Sr.o.filter, Sr.mu_best_k, Sr.mu_best_kq, Sr.a, Sr.b, Sr.o.d_max > 0 ? Sr.o.d_max : 15);
+      if (d != Sr.d) {
+        Sr.d = d;
+        if (arb_filter_coefficients(Sr.o.filter, Sr.d, Sr.coef) != ARB_OK)
           return set_error(ctx, ARB_INVALID_ARG, "solve: bad filter kind");
       }
     }
+    return ARB_OK;
+  }
+};
+
+template <typename T>
+arb_status run_outer(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, double tol_phase, double rc_floor,
+                     bool lock, bool continue_on_phase_tol, bool stop_on_stagnation = false) {
+  Phase<T> ph;
+  ph.ctx = ctx;
+  ph.mat = mat;
+  ph.S = &S;
+  ph.B = &B;
+  ph.tol_phase = tol_phase;
+  ph.rc_floor = rc_floor;
+  ph.lock = lock;
+  ph.cont_on_tol = continue_on_phase_tol;
+  ph.stop_on_stag = stop_on_stagnation;
+  ARB_TRY(ph.begin());
+  for (;;) {
+    ARB_TRY(ph.outer_begin());
+    if (ph.done) break;
+    while (ph.in_inner) {
+      while (ph.step_due()) ARB_TRY(ph.step());
+      if (ph.in_inner) ARB_TRY(ph.check());
+    }
+    ARB_TRY(ph.outer_tail());
+    if (ph.done) break;
   }
   return ARB_OK;
 }
 
+// One arb_solve: set-up (spectrum bounds, workspaces, start block, first b), the phases of
+// Algorithm 8 (an FP32 phase and an FP64 refinement on the mixed paths, one FP64 phase
+// otherwise) and the outputs.  solve_impl runs the phases back to back; the lock-step
+// batched driver advances the phases of many solves together.
+struct Solve {
+  arb_ctx ctx = nullptr;
+  arb_mat mat = nullptr;
+  Timer total;
+  SolveState S;
+  BlockSet<double> D;
+  BlockSet<float> F;
+  bool mixed = false;
+  double lo_A = 0.0, hi_A = 0.0;
+  double tol_phase32 = 0.0, tol_t64 = 0.0;
+  int stage = 0;  // 0: FP32 phase, 1: FP64 phase, 2: phases over
+  Phase<float> p32;
+  Phase<double> p64;
+  bool dense_set = false, dense_saved = false;
+
+  ~Solve() {
+    if (S.ev0) cudaEventDestroy(S.ev0);
+    if (S.ev1) cudaEventDestroy(S.ev1);
+    if (dense_set) ctx->dense_df = dense_saved;
+  }
+
+  arb_status setup(int32_t k, arb_which which, double tol, const arb_options& o, const double* x0, int x0_on_device,
+                   double* evecs, int64_t ldq) {
+    S.o = o;
+    S.n = mat->n;
+    S.k = k;
+    S.p = o.p > 0 ? o.p : k + static_cast<int32_t>(std::lround(0.1 * k));
+    S.q = o.q;
+    S.d = o.degree;
+    S.tol = tol;
+    const int64_t n = S.n;
+    const int32_t p = S.p;
+    if (k <= 0 || k > p || S.q < 0 || S.d < 1 || S.d > 60 || o.maxit < 1 || o.maxit1 < 1 || o.maxit2 < 1 ||
+        static_cast<int64_t>(S.q + 1) * p >= n || !(tol > 0.0))
+      return set_error(ctx, ARB_INVALID_ARG, "solve: need 0 < k <= p, (q+1) p < n, 1 <= degree <= 60, tol > 0");
+    if (o.precision != ARB_FP64 && o.precision != ARB_MIXED && o.precision != ARB_MIXED_DF)
+      return set_error(ctx, ARB_INVALID_ARG, "solve: unknown precision");
+    if (o.b_update != 0 && o.b_update != 1) return set_error(ctx, ARB_INVALID_ARG, "solve: b_update must be 0 or 1");
+    if (o.inner != ARB_INNER_MPM && o.inner != ARB_INNER_GN) return set_error(ctx, ARB_INVALID_ARG, "solve: bad inner solver");
+    if ((o.adapt & ~(ARB_ADAPT_Q | ARB_ADAPT_DEGREE)) != 0 || o.q_max < 0 || o.d_max < 0 || o.d_max > 60)
+      return set_error(ctx, ARB_INVALID_ARG, "solve: bad adaptation options");
+    if (which != ARB_LARGEST && which != ARB_SMALLEST) return set_error(ctx, ARB_INVALID_ARG, "solve: bad which");
+    if (evecs && ldq < n) return set_error(ctx, ARB_INVALID_ARG, "solve: ldq < n");
+    S.smallest = (which == ARB_SMALLEST);
+    mixed = (o.precision == ARB_MIXED || o.precision == ARB_MIXED_DF);
+    S.df_filter = (o.precision == ARB_MIXED_DF);
+    S.trace = getenv("ARB_TRACE") != nullptr;
+
+    // operator B = op_scale A + op_shift I whose largest eigenpairs are wanted; the far end
+    // of A's spectrum from the tighter of Gershgorin's bound and a Lanczos estimate
+    double glo, ghi, llo, lhi;
+    ARB_TRY(gershgorin(ctx, mat, &glo, &ghi));
+    ARB_TRY(lanczos_bounds(ctx, mat, 32, o.seed + 0x9E3779B97F4A7C15ull, &llo, &lhi));
+    hi_A = std::min(ghi, lhi);
+    lo_A = std::max(glo, llo);
+    if (S.smallest) {
+      S.sigma = std::isnan(o.shift_sigma) ? hi_A : o.shift_sigma;
+      S.op_scale = -1.0;
+      S.op_shift = S.sigma;
+      S.a = S.sigma - hi_A;  // lower bound of sigma I - A
+    } else {
+      S.a = lo_A;
+    }
+
+    // device buffers (room for the largest q the adaptation may reach, (q+1) p < n)
+    S.q_cap = S.q;
+    if (o.adapt & ARB_ADAPT_Q) {
+      const int64_t fit = (n - 1) / p - 1;
+      S.q_cap = static_cast<int32_t>(std::max<int64_t>(S.q, std::min<int64_t>(o.q_max > 0 ? o.q_max : 3, fit)));
+    }
+    S.mcap = static_cast<int64_t>(S.q_cap + 1) * p;
+    ARB_TRY(alloc_blocks<double>(ctx, S, D));
+    if (mixed) {
+      ARB_TRY(alloc_blocks<float>(ctx, S, F));
+      ARB_TRY(ensure_val32(ctx, mat));
+      if (S.df_filter) ARB_TRY(ensure_valdf(ctx, mat));
+    }
+    ARB_TRY(ws<double>(ctx, WS_S_V, static_cast<size_t>(S.mcap) * S.mcap, &S.V));
+    ARB_TRY(ws<double>(ctx, WS_S_VSEL, static_cast<size_t>(S.mcap) * p, &S.Vsel));
+    double* vec;
+    ARB_TRY(ws<double>(ctx, WS_S_VEC, static_cast<size_t>(S.mcap) + 8 * static_cast<size_t>(p) + 64, &vec));
+    S.theta = vec;
+    S.mu = S.theta + S.mcap;
+    S.sigc = S.mu + p;
+    S.ss = S.sigc + p;
+    S.res = S.ss + p;
+    S.xs = S.res + p;
+    S.imap = reinterpret_cast<int32_t*>(S.xs + p);
+    S.iidx = S.imap + p + (p & 1);
+    S.sgn = reinterpret_cast<double*>(S.iidx + p + (p & 1));
+    S.h_mu.resize(p);
+    S.h_res.resize(p);
+    S.h_map.resize(p);
+
+    // start block X0 (Algorithm 8: i.i.d. Gaussian n x (k+q)), held in the FP64 iterate
+    if (x0) {
+      ARB_CUDA(ctx, cudaMemcpy2DAsync(D.X, D.ld * sizeof(double), x0, p * sizeof(double), p * sizeof(double), n,
+                                      x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                      ctx->stream));
+    } else {
+      ARB_TRY(gaussian_fill(ctx, n, p, o.seed, D.X, D.ld));
+    }
+
+    // b: smallest Ritz value of orth(X0) (Section 5, "Estimation of lambda_n and lambda_{k+q}");
+    // an estimate, so the mixed paths take it from FP32 blocks
+    auto initial_b = [&](auto& Bk) -> arb_status {
+      using E = typename std::remove_reference<decltype(*Bk.X)>::type;
+      int32_t r = 0;
+      ARB_TRY(orth<E>(ctx, n, Bk.X, Bk.ld, p, Bk.wk.U, Bk.ldm, Bk.wk.T1, Bk.ld, &r));
+      if (r == 0) return set_error(ctx, ARB_BREAKDOWN, "solve: start block has no numerical rank");
+      SpmmArgs<E> sa;
+      sa.A = mat;
+      sa.ncols = r;
+      sa.Yin = Bk.wk.U;
+      sa.ldy = Bk.ldm;
+      sa.alpha = S.op_scale;
+      sa.beta = S.op_shift;
+      sa.out = Bk.wk.AU;
+      sa.ldo = Bk.ldm;
+      ARB_TRY(spmm_fused<E>(ctx, sa));
+      double* H;
+      ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(r) * r, &H));
+      ARB_TRY(gram<E>(ctx, n, Bk.wk.U, Bk.ldm, r, Bk.wk.AU, Bk.ldm, r, H, r));
+      ARB_TRY(symmetrize(ctx, r, H, r));
+      ARB_TRY(syevj(ctx, r, H, r, S.theta, S.V, r, nullptr, jac_tol<E>(ctx), jac_df<E>(ctx)));
+      ARB_TRY(d2h_sync(ctx, &S.b, S.theta + (r - 1), sizeof(double)));
+      S.info.spmm_cols += r;
+      return ARB_OK;
+    };
+    if (mixed) {
+      ARB_TRY((copy_block<double, float>(ctx, n, D.X, D.ld, p, F.X, F.ld)));
+      ARB_TRY(initial_b(F));
+      S.x32 = F.wk.T2;
+      S.ld32 = F.ld;
+    } else {
+      ARB_TRY(initial_b(D));
+    }
+    S.info.a = S.a;
+    S.info.b0 = S.b;
+    S.info.sigma = S.sigma;
+    if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+
+    if (arb_filter_coefficients(o.filter, S.d, S.coef) != ARB_OK)
+      return set_error(ctx, ARB_INVALID_ARG, "solve: bad filter kind");
+    const double tol1 = o.tol1 > 0.0 ? o.tol1 : (tol <= 1e-8 ? std::max(1e-6, tol) : tol);
+    S.tol_t = std::max(tol1, tol);
+    S.w = p;
+    S.nl = 0;
+    ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
+    ARB_CUDA(ctx, cudaEventCreate(&S.ev0));
+    ARB_CUDA(ctx, cudaEventCreate(&S.ev1));
+
+    return ARB_OK;
+  }
+
+  // the first phase: FP32 on the mixed paths (reading c7: inner-stop threshold >= 100 u32;
+  // the FP32 residual floor ~ 32 u32 ||B||, ||B|| bounded by the spectrum estimates, ends it,
+  // as do tol_switch and an outer iteration that fails to halve maxres), else FP64
+  arb_status start() {
+    if (mixed) {
+      const double normB = std::max(std::fabs(S.sigma - lo_A), std::fabs(S.sigma - hi_A));
+      const double floor32 = 32.0 * 5.96e-8 * (S.smallest ? normB : std::max(std::fabs(lo_A), std::fabs(hi_A)));
+      const double sw = std::max(S.o.tol_switch > 0.0 ? S.o.tol_switch : 1e-5, floor32);
+      tol_phase32 = std::max(sw, S.tol);
+      tol_t64 = S.tol_t;  // the FP64 phase starts the paper's continuation at tol_1
+      S.tol_t = std::max(S.tol_t, tol_phase32);
+      init_phase(p32, F, tol_phase32, 100.0 * 5.96e-8, false, true, true);
+      stage = 0;
+      return p32.begin();
+    }
+    init_phase(p64, D, S.tol, 0.0, true, false, false);
+    stage = 1;
+    return p64.begin();
+  }
+
+  template <typename T>
+  void init_phase(Phase<T>& ph, BlockSet<T>& B, double tol_phase, double rc_floor, bool lock, bool cont, bool stag) {
+    ph.ctx = ctx;
+    ph.mat = mat;
+    ph.S = &S;
+    ph.B = &B;
+    ph.tol_phase = tol_phase;
+    ph.rc_floor = rc_floor;
+    ph.lock = lock;
+    ph.cont_on_tol = cont;
+    ph.stop_on_stag = stag;
+  }
+
+  // the current phase has ended: from the FP32 phase to the FP64 refinement (Algorithm 8
+  // continued in FP64 from the FP32 Ritz block), or the end of the phases
+  arb_status phase_ended() {
+    const int64_t n = S.n;
+    const int32_t p = S.p;
+    if (stage == 0) {
+      S.info.outer_iters_fp32 = S.info.outer_iters;
+      S.tol_t = tol_t64;
+      const bool done32 = (S.stop == ARB_STOP_CONVERGED || S.stop == ARB_STOP_NEAR_TOL) && tol_phase32 <= S.tol;
+      // If the FP32 phase made no usable progress - its block lost rank (the filter's
+      // dynamic range outran FP32 before the inner stop rule could see it, e.g. an isolated
+      // extreme eigenvalue and a crude first b) or maxres stayed above 1e-2 - the refinement
+      // starts over from X0 with the first interval estimate, as the FP64 method would.
+      const bool fp32_failed = !(S.info.maxres <= 1e-2) || S.info.last_rank < p;
+      if (fp32_failed) {
+        S.b = S.info.b0;
+        if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
+        S.tol_t = tol_t64;
+      } else {
+        ARB_TRY((copy_block<float, double>(ctx, n, F.Xall, F.ld, p, D.Xall, D.ld)));
+      }
+      if (!done32 || fp32_failed) {
+        // D.X still holds X0 (the FP32 phase ran on its own blocks)
+        if (!fp32_failed) ARB_TRY((copy_block<double, double>(ctx, n, D.Xall, D.ld, p, D.X, D.ld)));
+        S.w = p;
+        S.nl = 0;
+        ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
+        // ARB_MIXED_DF: the refinement's dense products in double-float arithmetic too
+        if (S.df_filter) {
+          dense_set = true;
+          dense_saved = ctx->dense_df;
+          ctx->dense_df = true;
+        }
+        init_phase(p64, D, S.tol, 0.0, true, false, false);
+        stage = 1;
+        return p64.begin();
+      }
+      stage = 2;
+      return ARB_OK;
+    }
+    if (dense_set) {
+      ctx->dense_df = dense_saved;
+      dense_set = false;
+    }
+    stage = 2;
+    return ARB_OK;
+  }
+
+  // every phase to its end, back to back
+  arb_status run() {
+    ARB_TRY(start());
+    while (stage < 2) {
+      if (stage == 0) ARB_TRY(run_phase(p32));
+      else ARB_TRY(run_phase(p64));
+      ARB_TRY(phase_ended());
+    }
+    return ARB_OK;
+  }
+
+  template <typename T>
+  static arb_status run_phase(Phase<T>& ph) {
+    for (;;) {
+      ARB_TRY(ph.outer_begin());
+      if (ph.done) return ARB_OK;
+      while (ph.in_inner) {
+        while (ph.step_due()) ARB_TRY(ph.step());
+        if (ph.in_inner) ARB_TRY(ph.check());
+      }
+      ARB_TRY(ph.outer_tail());
+      if (ph.done) return ARB_OK;
+    }
+  }
+
+  // outputs: Rayleigh quotients on A, order, sign, column-major copy
+  arb_status finish(double* evals, double* evecs, int64_t ldq, int evecs_on_device, arb_info* info_out) {
+    const int64_t n = S.n;
+    const int32_t p = S.p, k = S.k;
+    S.info.stop_reason = S.stop;
+    S.info.b_final = S.b;
+    S.info.n_locked = S.nl;
+    S.info.final_q = S.q;
+    S.info.final_d = S.d;
+
+    // ---------------- outputs: Rayleigh quotients on A, order, sign, column-major copy
+    {
+      SpmmArgs<double> sa;
+      sa.A = mat;
+      sa.ncols = k;
+      sa.Yin = D.Xall;
+      sa.ldy = D.ld;
+      sa.alpha = 1.0;
+      sa.beta = 0.0;
+      sa.colred = S.ss;
+      sa.dot_with_yin = true;
+      ARB_TRY(spmm_fused<double>(ctx, sa));
+      S.info.spmm_cols += k;
+    }
+    std::vector<double> rq(k);
+    ARB_TRY(d2h_sync(ctx, rq.data(), S.ss, k * sizeof(double)));
+    std::vector<int32_t> perm(k);
+    for (int i = 0; i < k; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(),
+                     [&](int x, int y) { return S.smallest ? rq[x] < rq[y] : rq[x] > rq[y]; });
+    if (evals)
+      for (int i = 0; i < k; ++i) evals[i] = rq[perm[i]];
+    if (evecs) {
+      ARB_TRY(column_signs(ctx, n, D.Xall, D.ld, p, S.sgn));
+      std::vector<double> hs(p);
+      ARB_TRY(d2h_sync(ctx, hs.data(), S.sgn, p * sizeof(double)));
+      std::vector<double> sgn_perm(k);
+      for (int i = 0; i < k; ++i) sgn_perm[i] = hs[perm[i]];
+      ARB_TRY(upload_ints(ctx, S.iidx, perm));
+      ARB_TRY(h2d(ctx, S.res, sgn_perm.data(), k * sizeof(double)));
+      if (evecs_on_device) {
+        ARB_TRY(write_colmajor(ctx, n, D.Xall, D.ld, S.iidx, S.res, k, evecs, ldq));
+      } else {
+        // stage through a device block (W1 is free now), then one strided copy to the host
+        ARB_TRY(write_colmajor(ctx, n, D.Xall, D.ld, S.iidx, S.res, k, D.W1, n));
+        ARB_CUDA(ctx, cudaMemcpy2DAsync(evecs, ldq * sizeof(double), D.W1, n * sizeof(double), n * sizeof(double), k,
+                                        cudaMemcpyDeviceToHost, ctx->stream));
+      }
+    }
+    ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    S.info.t_total = total.sec();
+    if (info_out) *info_out = S.info;
+    const bool ok = (S.stop == ARB_STOP_CONVERGED || S.stop == ARB_STOP_NEAR_TOL);
+    return ok ? ARB_OK : ARB_NOT_CONVERGED;
+  }
+};
+
 arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, double tol, const arb_options& o,
                       const double* x0, int x0_on_device, double* evals, double* evecs, int64_t ldq,
                       int evecs_on_device, arb_info* info_out) {
-  Timer total;
-  SolveState S;
-  S.o = o;
-  S.n = mat->n;
-  S.k = k;
-  S.p = o.p > 0 ? o.p : k + static_cast<int32_t>(std::lround(0.1 * k));
-  S.q = o.q;
-  S.d = o.degree;
-  S.tol = tol;
-  const int64_t n = S.n;
-  const int32_t p = S.p;
-  if (k <= 0 || k > p || S.q < 0 || S.d < 1 || S.d > 60 || o.maxit < 1 || o.maxit1 < 1 || o.maxit2 < 1 ||
-      static_cast<int64_t>(S.q + 1) * p >= n || !(tol > 0.0))
-    return set_error(ctx, ARB_INVALID_ARG, "solve: need 0 < k <= p, (q+1) p < n, 1 <= degree <= 60, tol > 0");
-  if (o.precision != ARB_FP64 && o.precision != ARB_MIXED && o.precision != ARB_MIXED_DF)
-    return set_error(ctx, ARB_INVALID_ARG, "solve: unknown precision");
-  if (o.b_update != 0 && o.b_update != 1) return set_error(ctx, ARB_INVALID_ARG, "solve: b_update must be 0 or 1");
-  if (o.inner != ARB_INNER_MPM && o.inner != ARB_INNER_GN) return set_error(ctx, ARB_INVALID_ARG, "solve: bad inner solver");
-  if ((o.adapt & ~(ARB_ADAPT_Q | ARB_ADAPT_DEGREE)) != 0 || o.q_max < 0 || o.d_max < 0 || o.d_max > 60)
-    return set_error(ctx, ARB_INVALID_ARG, "solve: bad adaptation options");
-  if (which != ARB_LARGEST && which != ARB_SMALLEST) return set_error(ctx, ARB_INVALID_ARG, "solve: bad which");
-  if (evecs && ldq < n) return set_error(ctx, ARB_INVALID_ARG, "solve: ldq < n");
-  S.smallest = (which == ARB_SMALLEST);
-  const bool mixed = (o.precision == ARB_MIXED || o.precision == ARB_MIXED_DF);
-  S.df_filter = (o.precision == ARB_MIXED_DF);
-  S.trace = getenv("ARB_TRACE") != nullptr;
-
-  // operator B = op_scale A + op_shift I whose largest eigenpairs are wanted; the far end
-  // of A's spectrum from the tighter of Gershgorin's bound and a Lanczos estimate
-  double glo, ghi, llo, lhi;
-  ARB_TRY(gershgorin(ctx, mat, &glo, &ghi));
-  ARB_TRY(lanczos_bounds(ctx, mat, 32, o.seed + 0x9E3779B97F4A7C15ull, &llo, &lhi));
-  const double hi_A = std::min(ghi, lhi), lo_A = std::max(glo, llo);
-  if (S.smallest) {
-    S.sigma = std::isnan(o.shift_sigma) ? hi_A : o.shift_sigma;
-    S.op_scale = -1.0;
-    S.op_shift = S.sigma;
-    S.a = S.sigma - hi_A;  // lower bound of sigma I - A
-  } else {
-    S.a = lo_A;
-  }
-
-  // device buffers (room for the largest q the adaptation may reach, (q+1) p < n)
-  S.q_cap = S.q;
-  if (o.adapt & ARB_ADAPT_Q) {
-    const int64_t fit = (n - 1) / p - 1;
-    S.q_cap = static_cast<int32_t>(std::max<int64_t>(S.q, std::min<int64_t>(o.q_max > 0 ? o.q_max : 3, fit)));
-  }
-  S.mcap = static_cast<int64_t>(S.q_cap + 1) * p;
-  BlockSet<double> D;
-  BlockSet<float> F;
-  ARB_TRY(alloc_blocks<double>(ctx, S, D));
-  if (mixed) {
-    ARB_TRY(alloc_blocks<float>(ctx, S, F));
-    ARB_TRY(ensure_val32(ctx, mat));
-    if (S.df_filter) ARB_TRY(ensure_valdf(ctx, mat));
-  }
-  ARB_TRY(ws<double>(ctx, WS_S_V, static_cast<size_t>(S.mcap) * S.mcap, &S.V));
-  ARB_TRY(ws<double>(ctx, WS_S_VSEL, static_cast<size_t>(S.mcap) * p, &S.Vsel));
-  double* vec;
-  ARB_TRY(ws<double>(ctx, WS_S_VEC, static_cast<size_t>(S.mcap) + 8 * static_cast<size_t>(p) + 64, &vec));
-  S.theta = vec;
-  S.mu = S.theta + S.mcap;
-  S.sigc = S.mu + p;
-  S.ss = S.sigc + p;
-  S.res = S.ss + p;
-  S.xs = S.res + p;
-  S.imap = reinterpret_cast<int32_t*>(S.xs + p);
-  S.iidx = S.imap + p + (p & 1);
-  S.sgn = reinterpret_cast<double*>(S.iidx + p + (p & 1));
-  S.h_mu.resize(p);
-  S.h_res.resize(p);
-  S.h_map.resize(p);
-
-  // start block X0 (Algorithm 8: i.i.d. Gaussian n x (k+q)), held in the FP64 iterate
-  if (x0) {
-    ARB_CUDA(ctx, cudaMemcpy2DAsync(D.X, D.ld * sizeof(double), x0, p * sizeof(double), p * sizeof(double), n,
-                                    x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                    ctx->stream));
-  } else {
-    ARB_TRY(gaussian_fill(ctx, n, p, o.seed, D.X, D.ld));
-  }
-
-  // b: smallest Ritz value of orth(X0) (Section 5, "Estimation of lambda_n and lambda_{k+q}");
-  // an estimate, so the mixed paths take it from FP32 blocks
-  auto initial_b = [&](auto& Bk) -> arb_status {
-    using E = typename std::remove_reference<decltype(*Bk.X)>::type;
-    int32_t r = 0;
-    ARB_TRY(orth<E>(ctx, n, Bk.X, Bk.ld, p, Bk.wk.U, Bk.ldm, Bk.wk.T1, Bk.ld, &r));
-    if (r == 0) return set_error(ctx, ARB_BREAKDOWN, "solve: start block has no numerical rank");
-    SpmmArgs<E> sa;
-    sa.A = mat;
-    sa.ncols = r;
-    sa.Yin = Bk.wk.U;
-    sa.ldy = Bk.ldm;
-    sa.alpha = S.op_scale;
-    sa.beta = S.op_shift;
-    sa.out = Bk.wk.AU;
-    sa.ldo = Bk.ldm;
-    ARB_TRY(spmm_fused<E>(ctx, sa));
-    double* H;
-    ARB_TRY(ws<double>(ctx, WS_SMALL0, static_cast<size_t>(r) * r, &H));
-    ARB_TRY(gram<E>(ctx, n, Bk.wk.U, Bk.ldm, r, Bk.wk.AU, Bk.ldm, r, H, r));
-    ARB_TRY(symmetrize(ctx, r, H, r));
-    ARB_TRY(syevj(ctx, r, H, r, S.theta, S.V, r, nullptr, jac_tol<E>(ctx), jac_df<E>(ctx)));
-    ARB_TRY(d2h_sync(ctx, &S.b, S.theta + (r - 1), sizeof(double)));
-    S.info.spmm_cols += r;
-    return ARB_OK;
-  };
-  if (mixed) {
-    ARB_TRY((copy_block<double, float>(ctx, n, D.X, D.ld, p, F.X, F.ld)));
-    ARB_TRY(initial_b(F));
-    S.x32 = F.wk.T2;
-    S.ld32 = F.ld;
-  } else {
-    ARB_TRY(initial_b(D));
-  }
-  S.info.a = S.a;
-  S.info.b0 = S.b;
-  S.info.sigma = S.sigma;
-  if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
-
-  if (arb_filter_coefficients(o.filter, S.d, S.coef) != ARB_OK)
-    return set_error(ctx, ARB_INVALID_ARG, "solve: bad filter kind");
-  const double tol1 = o.tol1 > 0.0 ? o.tol1 : (tol <= 1e-8 ? std::max(1e-6, tol) : tol);
-  S.tol_t = std::max(tol1, tol);
-  S.w = p;
-  S.nl = 0;
-  ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
-  ARB_CUDA(ctx, cudaEventCreate(&S.ev0));
-  ARB_CUDA(ctx, cudaEventCreate(&S.ev1));
-  struct EvGuard {
-    SolveState& s;
-    ~EvGuard() {
-      if (s.ev0) cudaEventDestroy(s.ev0);
-      if (s.ev1) cudaEventDestroy(s.ev1);
-    }
-  } guard{S};
-
-  if (mixed) {
-    // Phase 1: FP32 blocks until the continuation tolerance of the FP32 phase is met
-    // (reading c7: inner-stop threshold >= 100 u32; precision switches when continuation
-    // tightens tol_t below what FP32 resolves).
-    // FP32 residual floor ~ 32 u32 ||B|| (||B|| bounded by Gershgorin): the FP32 phase ends
-    // there, at tol_switch, or as soon as an outer iteration stops halving maxres.
-    const double normB = std::max(std::fabs(S.sigma - lo_A), std::fabs(S.sigma - hi_A));
-    const double floor32 = 32.0 * 5.96e-8 * (S.smallest ? normB : std::max(std::fabs(lo_A), std::fabs(hi_A)));
-    const double sw = std::max(o.tol_switch > 0.0 ? o.tol_switch : 1e-5, floor32);
-    const double tol_phase = std::max(sw, tol);
-    const double tol_t64 = S.tol_t;  // the FP64 phase starts the paper's continuation at tol_1
-    S.tol_t = std::max(S.tol_t, tol_phase);
-    ARB_TRY(run_outer<float>(ctx, mat, S, F, tol_phase, 100.0 * 5.96e-8, false, true, true));
-    S.info.outer_iters_fp32 = S.info.outer_iters;
-    S.tol_t = tol_t64;
-    const bool done32 = (S.stop == ARB_STOP_CONVERGED || S.stop == ARB_STOP_NEAR_TOL) && tol_phase <= tol;
-    // Phase 2: FP64 refinement from the FP32 Ritz block (Algorithm 8 continued in FP64).
-    // If the FP32 phase made no usable progress - its block lost rank (the filter's dynamic
-    // range outran FP32 before the inner stop rule could see it, e.g. an isolated extreme
-    // eigenvalue and a crude first b) or maxres stayed above 1e-2 - the refinement starts
-    // over from X0 with the first interval estimate instead, as the FP64 method would.
-    const bool fp32_failed = !(S.info.maxres <= 1e-2) || S.info.last_rank < p;
-    if (fp32_failed) {
-      S.b = S.info.b0;
-      if (!(S.b > S.a)) S.b = S.a + 1e-3 * std::max(1.0, std::fabs(S.a));
-      S.tol_t = tol_t64;
-    } else {
-      ARB_TRY((copy_block<float, double>(ctx, n, F.Xall, F.ld, p, D.Xall, D.ld)));
-    }
-    if (!done32 || fp32_failed) {
-      // D.X still holds X0 (the FP32 phase ran on its own blocks)
-      if (!fp32_failed) ARB_TRY((copy_block<double, double>(ctx, n, D.Xall, D.ld, p, D.X, D.ld)));
-      S.w = p;
-      S.nl = 0;
-      ARB_TRY(fill(ctx, S.xs, S.w, 1.0));
-      // ARB_MIXED_DF: the refinement's dense products in double-float arithmetic too
-      struct DenseGuard {
-        arb_ctx c;
-        bool saved;
-        ~DenseGuard() { c->dense_df = saved; }
-      } dg{ctx, ctx->dense_df};
-      if (S.df_filter) ctx->dense_df = true;
-      ARB_TRY(run_outer<double>(ctx, mat, S, D, tol, 0.0, true, false));
-    }
-  } else {
-    ARB_TRY(run_outer<double>(ctx, mat, S, D, tol, 0.0, true, false));
-  }
-  S.info.stop_reason = S.stop;
-  S.info.b_final = S.b;
-  S.info.n_locked = S.nl;
-  S.info.final_q = S.q;
-  S.info.final_d = S.d;
-
-  // ---------------- outputs: Rayleigh quotients on A, order, sign, column-major copy
-  {
-    SpmmArgs<double> sa;
-    sa.A = mat;
-    sa.ncols = k;
-    sa.Yin = D.Xall;
-    sa.ldy = D.ld;
-    sa.alpha = 1.0;
-    sa.beta = 0.0;
-    sa.colred = S.ss;
-    sa.dot_with_yin = true;
-    ARB_TRY(spmm_fused<double>(ctx, sa));
-    S.info.spmm_cols += k;
-  }
-  std::vector<double> rq(k);
-  ARB_TRY(d2h_sync(ctx, rq.data(), S.ss, k * sizeof(double)));
-  std::vector<int32_t> perm(k);
-  for (int i = 0; i < k; ++i) perm[i] = i;
-  std::stable_sort(perm.begin(), perm.end(),
-                   [&](int x, int y) { return S.smallest ? rq[x] < rq[y] : rq[x] > rq[y]; });
-  if (evals)
-    for (int i = 0; i < k; ++i) evals[i] = rq[perm[i]];
-  if (evecs) {
-    ARB_TRY(column_signs(ctx, n, D.Xall, D.ld, p, S.sgn));
-    std::vector<double> hs(p);
-    ARB_TRY(d2h_sync(ctx, hs.data(), S.sgn, p * sizeof(double)));
-    std::vector<double> sgn_perm(k);
-    for (int i = 0; i < k; ++i) sgn_perm[i] = hs[perm[i]];
-    ARB_TRY(upload_ints(ctx, S.iidx, perm));
-    ARB_TRY(h2d(ctx, S.res, sgn_perm.data(), k * sizeof(double)));
-    if (evecs_on_device) {
-      ARB_TRY(write_colmajor(ctx, n, D.Xall, D.ld, S.iidx, S.res, k, evecs, ldq));
-    } else {
-      // stage through a device block (W1 is free now), then one strided copy to the host
-      ARB_TRY(write_colmajor(ctx, n, D.Xall, D.ld, S.iidx, S.res, k, D.W1, n));
-      ARB_CUDA(ctx, cudaMemcpy2DAsync(evecs, ldq * sizeof(double), D.W1, n * sizeof(double), n * sizeof(double), k,
-                                      cudaMemcpyDeviceToHost, ctx->stream));
-    }
-  }
-  ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  S.info.t_total = total.sec();
-  if (info_out) *info_out = S.info;
-  const bool ok = (S.stop == ARB_STOP_CONVERGED || S.stop == ARB_STOP_NEAR_TOL);
-  return ok ? ARB_OK : ARB_NOT_CONVERGED;
+  Solve sv;
+  sv.ctx = ctx;
+  sv.mat = mat;
+  ARB_TRY(sv.setup(k, which, tol, o, x0, x0_on_device, evecs, ldq));
+  ARB_TRY(sv.run());
+  return sv.finish(evals, evecs, ldq, evecs_on_device, info_out);
 }
+
+// ---------------------------------------------------------------- lock-step batched driver
+// A context of the lock-step driver: the caller's device, its own stream and workspaces.
+arb_ctx make_sub_context(arb_ctx parent, cudaStream_t stream) {
+  arb_ctx c = new arb_ctx_s();
+  c->device = parent->device;
+  c->stream = stream;
+  c->own_stream = false;
+  c->num_sms = parent->num_sms;
+  c->coop_share = 1;
+  return c;
+}
+
+void drop_sub_context(arb_ctx c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (int i = 0; i < WS_NUM_SLOTS; ++i)
+    if (c->ws[i]) cudaFree(c->ws[i]);
+  if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  if (c->err_dev) cudaFree(c->err_dev);
+  delete c;
+}
+
+// What the driver needs of the current phase of a solve, whatever its element type.
+struct PhaseView {
+  Solve* sv;
+  template <typename F>
+  auto with(F&& f) -> decltype(f(sv->p64)) {
+    if (sv->stage == 0) return f(sv->p32);
+    return f(sv->p64);
+  }
+};
+
+// The filter job of the current inner step of an instance (its batched form).
+template <typename T>
+arb_filter_job job_of(const Phase<T>& ph) {
+  const SolveState& S = *ph.S;
+  arb_filter_job J{};
+  J.mat = ph.mat;
+  J.op_scale = S.op_scale;
+  J.op_shift = S.op_shift;
+  J.a = S.a;
+  J.b = S.b;
+  J.degree = S.d;
+  J.fp32 = sizeof(T) == 4 ? 1 : 0;
+  J.coef = S.coef;
+  J.X = ph.B->X;
+  J.ldx = ph.B->ld;
+  J.ncols = S.w;
+  J.xscale = S.xs;
+  J.Y = ph.filter_out();
+  J.ldy = ph.B->ld;
+  J.colss = S.ss;
+  return J;
+}
+
+// key of a round's captured graph: everything the recorded kernels bake in
+std::string round_key(const BatchPlan& plan) {
+  std::string key;
+  auto put = [&](const void* p, size_t b) { key.append(static_cast<const char*>(p), b); };
+  put(&plan.dj, sizeof(plan.dj));
+  put(&plan.dp, sizeof(plan.dp));
+  put(&plan.doff, sizeof(plan.doff));
+  put(&plan.part, sizeof(plan.part));
+  put(&plan.coop_grid, sizeof(plan.coop_grid));
+  put(&plan.dmax, sizeof(plan.dmax));
+  for (const auto& J : plan.jobs) {
+    put(&J.mat, sizeof(J.mat));
+    put(&J.X, sizeof(J.X));
+    put(&J.Y, sizeof(J.Y));
+    put(&J.ncols, sizeof(J.ncols));
+    put(&J.degree, sizeof(J.degree));
+    put(&J.fp32, sizeof(J.fp32));
+    put(&J.xscale, sizeof(J.xscale));
+    put(&J.colss, sizeof(J.colss));
+    put(&J.ldx, sizeof(J.ldx));
+    put(&J.ldy, sizeof(J.ldy));
+  }
+  for (const auto& t : plan.tables) {
+    put(&t.table, sizeof(t.table));
+    put(t.cc.c, sizeof(double) * (t.d + 1));
+  }
+  return key;
+}
+
+int64_t round_kernels(const BatchPlan& plan) {
+  int64_t k = static_cast<int64_t>(plan.tables.size()) + 1;
+  for (const auto& J : plan.jobs)
+    if (J.colss) k += 2;
+  return k;
+}
+
+}  // namespace
+
+extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat* mats, const int32_t* k,
+                                         const arb_which* which, const double* tol, const arb_options* opts,
+                                         const double* const* x0, double* const* evals, double* const* evecs,
+                                         const int64_t* ldq, arb_info* info, int32_t flags, arb_batch_stats* stats) {
+  if (!ctx || nb < 0 || (nb > 0 && (!mats || !k || !which || !tol || !evals)) || (flags & ~3) != 0)
+    return set_error(ctx, ARB_INVALID_ARG, "solve_lockstep: bad arguments");
+  Timer total;
+  arb_batch_stats bs{};
+  if (nb == 0) {
+    if (stats) *stats = bs;
+    return ARB_OK;
+  }
+  for (int32_t i = 0; i < nb; ++i)
+    if (!mats[i] || mats[i]->device != ctx->device)
+      return set_error(ctx, ARB_INVALID_ARG, "solve_lockstep: matrix missing or on another device");
+  ARB_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t stream = nullptr;
+  ARB_CUDA(ctx, cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+  cudaEvent_t order = nullptr;
+  cudaEventCreateWithFlags(&order, cudaEventDisableTiming);
+  cudaEventRecord(order, ctx->stream);  // the caller's earlier work first
+  cudaStreamWaitEvent(stream, order, 0);
+  arb_ctx bctx = make_sub_context(ctx, stream);  // the batched filter's workspaces
+  std::vector<arb_ctx> subs(nb, nullptr);
+  std::vector<std::unique_ptr<Solve>> sv(nb);
+  std::vector<arb_status> st(nb, ARB_OK);
+  std::vector<bool> live(nb, false), in_outer(nb, false);
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+  };
+  std::unordered_map<std::string, Graph> graphs;
+  std::unordered_map<std::string, int> seen;
+  bool graphs_ok = (flags & ARB_BATCH_GRAPHS) != 0;
+  arb_status fatal = ARB_OK;
+  auto cleanup = [&]() {
+    for (auto& g : graphs)
+      if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
+    sv.clear();
+    for (arb_ctx c : subs) drop_sub_context(c);
+    drop_sub_context(bctx);
+    cudaStreamSynchronize(stream);
+    cudaEventRecord(order, stream);  // the caller's later work after ours
+    cudaStreamWaitEvent(ctx->stream, order, 0);
+    cudaEventDestroy(order);
+    cudaStreamDestroy(stream);
+  };
+  // autotuned SpMM settings per distinct matrix (width of its first problem)
+  if (flags & ARB_BATCH_AUTOTUNE) {
+    for (int32_t i = 0; i < nb && fatal == ARB_OK; ++i) {
+      if (mats[i]->tuned) continue;
+      arb_options o;
+      if (opts) o = opts[i];
+      else arb_options_default(&o, k[i]);
+      const int32_t p = o.p > 0 ? o.p : k[i] + static_cast<int32_t>(std::lround(0.1 * k[i]));
+      fatal = arb_matrix_autotune(bctx, mats[i], p, nullptr, nullptr);
+    }
+    if (fatal != ARB_OK) {
+      set_error(ctx, fatal, std::string("solve_lockstep: autotune: ") + bctx->last_error);
+      cleanup();
+      return fatal;
+    }
+  }
+  // set-up and first phase of every instance
+  for (int32_t i = 0; i < nb; ++i) {
+    subs[i] = make_sub_context(ctx, stream);
+    sv[i].reset(new Solve());
+    sv[i]->ctx = subs[i];
+    sv[i]->mat = mats[i];
+    arb_options o;
+    if (opts) o = opts[i];
+    else arb_options_default(&o, k[i]);
+    st[i] = sv[i]->setup(k[i], which[i], tol[i], o, x0 ? x0[i] : nullptr, 0, evecs ? evecs[i] : nullptr,
+                         ldq ? ldq[i] : mats[i]->n);
+    if (st[i] == ARB_OK) st[i] = sv[i]->start();
+    live[i] = st[i] == ARB_OK;
+  }
+  // the lock-step loop
+  for (;;) {
+    // phase transitions and the start of outer iterations
+    bool any = false;
+    for (int32_t i = 0; i < nb; ++i) {
+      while (live[i] && !in_outer[i]) {
+        Solve& s = *sv[i];
+        if (s.stage >= 2) {
+          live[i] = false;
+          break;
+        }
+        PhaseView pv{&s};
+        const bool ended = pv.with([](auto& ph) { return ph.done; });
+        if (ended) {
+          st[i] = s.phase_ended();
+          if (st[i] != ARB_OK) live[i] = false;
+          continue;
+        }
+        st[i] = pv.with([](auto& ph) { return ph.outer_begin(); });
+        if (st[i] != ARB_OK) {
+          live[i] = false;
+          break;
+        }
+        if (!pv.with([](auto& ph) { return ph.done; })) in_outer[i] = true;
+      }
+      any = any || live[i];
+    }
+    if (!any) break;
+    // one inner step of every instance whose inner loop runs: the batchable ones together
+    std::vector<arb_filter_job> jobs;
+    std::vector<int32_t> who;
+    for (int32_t i = 0; i < nb; ++i) {
+      if (!live[i] || !in_outer[i]) continue;
+      PhaseView pv{sv[i].get()};
+      if (!pv.with([](auto& ph) { return ph.step_due(); })) continue;
+      if (pv.with([](auto& ph) { return ph.batchable(); })) {
+        jobs.push_back(pv.with([](auto& ph) { return job_of(ph); }));
+        who.push_back(i);
+      } else {
+        st[i] = pv.with([](auto& ph) { return ph.step(); });
+        bs.single_steps++;
+        if (st[i] != ARB_OK) live[i] = false;
+      }
+    }
+    if (!jobs.empty()) {
+      BatchPlan plan;
+      fatal = filter_batched_prepare(bctx, static_cast<int32_t>(jobs.size()), jobs.data(), &plan);
+      if (fatal != ARB_OK) break;
+      bool ran = false;
+      if (graphs_ok) {
+        const std::string key = round_key(plan);
+        auto g = graphs.find(key);
+        if (g != graphs.end()) {
+          if (cudaGraphLaunch(g->second.exec, stream) == cudaSuccess) {
+            bctx->launches += g->second.kernels;
+            bs.graph_launches++;
+            ran = true;
+          } else {
+            cudaGetLastError();
+            graphs_ok = false;
+          }
+        } else if (++seen[key] >= 2) {
+          // the second occurrence of this round shape: its workspaces exist, capture it
+          cudaGraph_t graph = nullptr;
+          bool captured = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+          arb_status ls = ARB_OK;
+          if (captured) {
+            const int64_t l0 = bctx->launches;
+            ls = filter_batched_launch(bctx, plan);
+            bctx->launches = l0;
+            captured = cudaStreamEndCapture(stream, &graph) == cudaSuccess && ls == ARB_OK && graph;
+          }
+          Graph gx;
+          if (captured && cudaGraphInstantiate(&gx.exec, graph, 0) == cudaSuccess &&
+              cudaGraphLaunch(gx.exec, stream) == cudaSuccess) {
+            gx.kernels = round_kernels(plan);
+            bctx->launches += gx.kernels;
+            graphs[key] = gx;
+            bs.graphs_captured++;
+            bs.graph_launches++;
+            ran = true;
+          } else {
+            // capture is not available here: run the rounds directly from now on
+            if (gx.exec) cudaGraphExecDestroy(gx.exec);
+            cudaGetLastError();
+            graphs_ok = false;
+          }
+          if (graph) cudaGraphDestroy(graph);
+        }
+      }
+      if (!ran) {
+        fatal = filter_batched_launch(bctx, plan);
+        if (fatal != ARB_OK) break;
+      }
+      bs.batched_launches++;
+      for (int32_t i : who) {
+        PhaseView pv{sv[i].get()};
+        st[i] = pv.with([](auto& ph) { return ph.step_post_external(); });
+        if (st[i] != ARB_OK) live[i] = false;
+      }
+    }
+    bs.rounds++;
+    // inner stop checks, then the ARR tails of the instances whose inner loop has ended
+    for (int32_t i = 0; i < nb; ++i) {
+      if (!live[i] || !in_outer[i]) continue;
+      PhaseView pv{sv[i].get()};
+      const bool due = pv.with([](auto& ph) { return ph.in_inner && !ph.step_due(); });
+      if (due) {
+        st[i] = pv.with([](auto& ph) { return ph.check(); });
+        if (st[i] != ARB_OK) {
+          live[i] = false;
+          continue;
+        }
+      }
+      if (!pv.with([](auto& ph) { return ph.in_inner; })) {
+        st[i] = pv.with([](auto& ph) { return ph.outer_tail(); });
+        in_outer[i] = false;
+        if (st[i] != ARB_OK) live[i] = false;
+      }
+    }
+  }
+  if (fatal != ARB_OK) {
+    set_error(ctx, fatal, std::string("solve_lockstep: batched filter: ") + bctx->last_error);
+    ctx->launches += bctx->launches;
+    cleanup();
+    return fatal;
+  }
+  // outputs
+  arb_status worst = ARB_OK;
+  for (int32_t i = 0; i < nb; ++i) {
+    if (st[i] == ARB_OK) {
+      st[i] = sv[i]->finish(evals[i], evecs ? evecs[i] : nullptr, ldq ? ldq[i] : mats[i]->n, 0,
+                            info ? &info[i] : nullptr);
+    } else if (subs[i]) {
+      set_error(ctx, st[i], std::string("solve_lockstep: instance ") + std::to_string(i) + ": " + subs[i]->last_error);
+    }
+    if (st[i] != ARB_OK && (worst == ARB_OK || (worst == ARB_NOT_CONVERGED && st[i] < 0))) worst = st[i];
+    if (subs[i]) ctx->launches += subs[i]->launches;
+  }
+  ctx->launches += bctx->launches;
+  bs.t_total = total.sec();
+  if (stats) *stats = bs;
+  cleanup();
+  return worst;
+}
+
+namespace {
 
 }  // namespace
 

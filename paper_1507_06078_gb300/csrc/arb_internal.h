@@ -124,6 +124,10 @@ struct arb_mat_s {
   arb::df2* sell_valdf = nullptr;
   // group table of the bulk-copy FP32 SpMM (spmm_bulk.cu), made on first use
   int32_t* bulk_tab = nullptr;
+  // autotuned SpMM settings (arb_matrix_autotune): widest vector access per lane of the
+  // FP32 / FP64 fused SpMM kernels (0: the widest the operands allow), tuned flag
+  int32_t tune_vec = 0;
+  bool tuned = false;
   bool gersh_valid = false;
   double gersh_lo = 0.0, gersh_hi = 0.0;
   std::mutex mu;  // guards the lazily made val32 / valdf and the Gershgorin cache (shared by server workers)
@@ -347,6 +351,32 @@ arb_status rcond_from_cholesky(arb_ctx ctx, int32_t m, const double* G, int64_t 
                                double* Ginv, int32_t* status, double* rc_dev);
 
 // ---------------------------------------------------------------- batched filter (batched.cu)
+struct CoefTable {
+  double c[64];
+};
+// A prepared batched filter: descriptors on the device, per-job coefficient-table launches,
+// workspaces.  filter_batched_launch issues kernels only (capturable into a CUDA graph).
+struct BatchPlan {
+  struct Table {
+    bool fp32;
+    int d, ncols, blocks;
+    CoefTable cc;
+    const double* xscale;
+    void* table;
+  };
+  int32_t njobs = 0;
+  int dmax = 0;
+  int coop_grid = 1;
+  std::vector<arb_filter_job> jobs;
+  std::vector<Table> tables;
+  std::vector<double> coef;
+  const void* dj = nullptr;  // device job and pass descriptors, pass offsets
+  const void* dp = nullptr;
+  const int64_t* doff = nullptr;
+  double* part = nullptr;    // column-sum partials
+};
+arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs, BatchPlan* plan);
+arb_status filter_batched_launch(arb_ctx ctx, const BatchPlan& plan);
 arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs);
 
 // ---------------------------------------------------------------- Jacobi (jacobi.cu)

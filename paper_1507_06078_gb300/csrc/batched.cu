@@ -184,13 +184,9 @@ __global__ void __launch_bounds__(BT_THREADS) batched_filter_kernel(const BJob* 
   }
 }
 
-struct ChebCoefB {
-  double c[64];
-};
-
 // table[(3 t + {0,1,2}) * ncols + c] = {sy, sx, sz} of pass t, in the job's element type
 template <typename T>
-__global__ void batched_table_kernel(int d, ChebCoefB cc, const double* __restrict__ xs, int ncols, T* table) {
+__global__ void batched_table_kernel(int d, CoefTable cc, const double* __restrict__ xs, int ncols, T* table) {
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (idx >= static_cast<int64_t>(d) * ncols) return;
   const int t = static_cast<int>(idx / ncols), c = static_cast<int>(idx % ncols);
@@ -238,7 +234,17 @@ inline bool al(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p)
 
 }  // namespace
 
-arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs) {
+// The batched filter in two parts: prepare() validates the jobs, sizes the workspaces and
+// uploads the descriptors (it synchronises the stream); launch() issues the per-job
+// coefficient tables, the one persistent cooperative launch and the per-job column sums -
+// kernels only, with no allocation and no synchronisation, so that a caller may capture it
+// into a CUDA graph and replay it while the descriptors (re-uploaded by prepare) keep
+// their device addresses.
+arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs, BatchPlan* out) {
+  out->njobs = njobs;
+  out->jobs.assign(jobs, jobs + njobs);
+  out->tables.clear();
+  out->coef.clear();
   if (njobs <= 0) return ARB_OK;
   int dmax = 0;
   size_t work_bytes = 0, table_bytes = 0;
@@ -274,18 +280,16 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
     char* tab = tables + to;
     to += (3 * static_cast<size_t>(J.degree) * J.ncols * es + 255) / 256 * 256;
     const FilterPlan plan = make_filter_plan(J.op_scale, J.op_shift, J.a, J.b, J.degree, J.coef);
-    ChebCoefB cc;
+    CoefTable cc;
     for (int i = 0; i < 64; ++i) cc.c[i] = (i <= J.degree) ? plan.coef[i] : 0.0;
     const int64_t cnt = static_cast<int64_t>(J.degree) * J.ncols;
     const int tb = static_cast<int>((cnt + 255) / 256);
-    if (f) batched_table_kernel<float><<<tb, 256, 0, ctx->stream>>>(J.degree, cc, J.xscale, J.ncols, reinterpret_cast<float*>(tab));
-    else batched_table_kernel<double><<<tb, 256, 0, ctx->stream>>>(J.degree, cc, J.xscale, J.ncols, reinterpret_cast<double*>(tab));
-    ARB_LAUNCHED(ctx);
+    out->tables.push_back(BatchPlan::Table{f, J.degree, J.ncols, tb, cc, J.xscale, tab});
     // vector width: 16-byte lanes when the columns, leading dimensions and bases allow
     int vec = 1;
     const int want = f ? 4 : 2;
     if (J.ncols % want == 0 && J.ldx % want == 0 && J.ldy % want == 0 && ldw[j] % want == 0 && al(J.X, 16) &&
-        al(J.Y, 16) && J.ncols > 32 * (want / 2))
+        al(J.Y, 16) && J.ncols > 32 * (want / 2) && (J.mat->tune_vec == 0 || J.mat->tune_vec >= want))
       vec = want;
     const int nch = (J.ncols + 32 * vec - 1) / (32 * vec);
     hj[j] = BJob{n, J.mat->rowptr, J.mat->col, f ? static_cast<const void*>(J.mat->val32) : J.mat->val, J.ncols, nch,
@@ -359,9 +363,43 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
   const BJob* dj = reinterpret_cast<const BJob*>(desc);
   const BPass* dp = reinterpret_cast<const BPass*>(desc + bj);
   const int64_t* doff = reinterpret_cast<const int64_t*>(desc + bj + bp);
+  out->dmax = dmax;
   int per_sm = 0;
   ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_filter_kernel, BT_THREADS, 0));
-  const int grid = std::max(1, std::max(1, per_sm) * ctx->num_sms / std::max(1, ctx->coop_share));
+  out->coop_grid = std::max(1, std::max(1, per_sm) * ctx->num_sms / std::max(1, ctx->coop_share));
+  out->dj = dj;
+  out->dp = dp;
+  out->doff = doff;
+  // column-sum partials: the largest any job needs
+  size_t part_max = 0;
+  for (int j = 0; j < njobs; ++j) {
+    if (!jobs[j].colss) continue;
+    const int64_t n = jobs[j].mat->n;
+    const int64_t rows = std::max<int64_t>(256, (n + 4 * ctx->num_sms - 1) / (4 * ctx->num_sms));
+    part_max = std::max(part_max, static_cast<size_t>((n + rows - 1) / rows) * jobs[j].ncols);
+  }
+  if (part_max) ARB_TRY(ws<double>(ctx, WS_SS_PART, part_max, &out->part));
+  return ARB_OK;
+}
+
+arb_status filter_batched_launch(arb_ctx ctx, const BatchPlan& plan) {
+  const int32_t njobs = plan.njobs;
+  if (njobs <= 0) return ARB_OK;
+  for (const auto& tb : plan.tables) {
+    if (tb.fp32)
+      batched_table_kernel<float><<<tb.blocks, 256, 0, ctx->stream>>>(tb.d, tb.cc, tb.xscale, tb.ncols,
+                                                                      static_cast<float*>(tb.table));
+    else
+      batched_table_kernel<double><<<tb.blocks, 256, 0, ctx->stream>>>(tb.d, tb.cc, tb.xscale, tb.ncols,
+                                                                       static_cast<double*>(tb.table));
+    ARB_LAUNCHED(ctx);
+  }
+  const BJob* dj = static_cast<const BJob*>(plan.dj);
+  const BPass* dp = static_cast<const BPass*>(plan.dp);
+  const int64_t* doff = plan.doff;
+  int dmax = plan.dmax;
+  const arb_filter_job* jobs = plan.jobs.data();
+  const int grid = plan.coop_grid;
   int nj = njobs;
   void* args[] = {&dj, &dp, &doff, &nj, &dmax};
   ARB_CUDA(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(batched_filter_kernel), dim3(grid),
@@ -374,8 +412,7 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
     const int64_t n = J.mat->n;
     const int64_t rows = std::max<int64_t>(256, (n + 4 * ctx->num_sms - 1) / (4 * ctx->num_sms));
     const int nb = static_cast<int>((n + rows - 1) / rows);
-    double* part;
-    ARB_TRY(ws<double>(ctx, WS_SS_PART, static_cast<size_t>(nb) * J.ncols, &part));
+    double* part = plan.part;
     if (J.fp32)
       colss_kernel<float><<<nb, 128, 0, ctx->stream>>>(n, static_cast<const float*>(J.Y), J.ldy, J.ncols, rows, part);
     else
@@ -385,6 +422,13 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
     ARB_LAUNCHED(ctx);
   }
   return ARB_OK;
+}
+
+
+arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs) {
+  BatchPlan plan;
+  ARB_TRY(filter_batched_prepare(ctx, njobs, jobs, &plan));
+  return filter_batched_launch(ctx, plan);
 }
 
 }  // namespace arb

@@ -561,6 +561,8 @@ arb_status spmm_fused(arb_ctx ctx, const SpmmArgs<T>& a) {
     if (a.X) ok = ok && (a.ldx % v == 0) && aligned(a.X, bytes);
     if (a.Z) ok = ok && (a.ldz % v == 0) && aligned(a.Z, bytes);
     if (a.out) ok = ok && (a.ldo % v == 0) && aligned(a.out, bytes);
+    // the matrix's tuned width caps the access (arb_matrix_autotune)
+    if (A->tune_vec > 0 && v > A->tune_vec) return false;
     return ok && a.ncols > 32 * (v / 2);
   };
   int grid = 0;
