@@ -66,6 +66,13 @@ def parse():
     ap.add_argument("--no-serve-mix", dest="serve_mix", action="store_false",
                     help="skip the bounded served mix (p50/p99 latency, mixed and plain FP64) of the default run")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the batched workload (256 diffusion instances in one lock-step solve)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched workload: --instances instances, --precision, graph/autotune flags")
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--adapt-degree", action="store_true", help="batched workload: the paper's degree rule")
+    ap.add_argument("--batch-flags", type=int, default=3, help="lock-step flags: 1 graphs, 2 autotune")
     ap.add_argument("--no-strict", dest="strict", action="store_false",
                     help="skip the tol 1e-9 solve whose residuals are all strictly within 1e-8")
     ap.add_argument("--filter-only", action="store_true",
@@ -438,6 +445,16 @@ def run_ours(args):
         d2h = W.k * W.A.n * 8 + W.k * 8
         e2e = {"value": world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    # the workload's ~76 GB of workspaces go back before the served mix and the batch
+    mat.close()
+    ctx.close()
+    torch.cuda.empty_cache()
+
+    batched = None
+    if rank == 0 and world == 1 and args.batched:
+        from paper_1507_06078_gb300 import arrabit as arbm
+        batched = batched_c3(256, arbm.ARB_MIXED, arbm.ARB_BATCH_GRAPHS | arbm.ARB_BATCH_AUTOTUNE)
+
     served = None
     if rank == 0 and world == 1 and args.serve_mix:
         # the mixed form with an FP64 refinement: on the Chung-Lu kind the double-float
@@ -465,6 +482,7 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "gpu_launches": int(launches), "fp64_path": fp64_cmp, "strict_1e-8": strict, "served": served,
+                "batched_c3": batched,
                 "solve": {"eig_rel_err_vs_closed_form": eig_err, "maxres": info["maxres"],
                           "outer_iters": info["outer_iters"], "n_filters": info["n_filters"],
                           "spmm_cols": info["spmm_cols"], "t_filter_s": info["t_filter"],
@@ -648,6 +666,69 @@ def served_mix(precision, rate, requests, slots, seed=4242):
             "solves_per_s": float(conv.sum()) / (done - t_sub[0]), "by_kind": per_kind, "tol": 1e-8}
 
 
+def batched_c3(instances, precision, flags, sides=(32, 512), degree=20, adapt_degree=False):
+    """Batched workload: `instances` 2D variable-coefficient diffusion operators (5-point,
+    lognormal edge coefficients, seeds 30000 + i, sides uniform in `sides`, k uniform in
+    8..64, p = 1.5 k), smallest pairs to relative residual 1e-8, q = 1, b refreshed after
+    every ARR, degree 20 (or the paper's adaptive rule from `degree`, cap 20), solved together by
+    arb_solve_lockstep (one batched filter launch per round, rounds replayed from CUDA
+    graphs, SpMM layout autotuned per matrix).  Returns the whole batch's solves/s (CUDA
+    events around the call), convergence, launch statistics and a dense-eigenvalue check of
+    the two smallest instances."""
+    import torch
+    from paper_1507_06078_gb300 import arrabit as arb
+    ctx = arb.Context(0)
+    ws = I.batched_diffusion_instances(count=instances, base_seed=30000, side_range=sides)
+    probs = []
+    for w in ws:
+        o = arb.arb_options_default(w.k)
+        o.p, o.q, o.degree, o.precision, o.b_update = w.p, 1, degree, precision, 1
+        if adapt_degree:
+            o.adapt, o.d_max = arb.ARB_ADAPT_DEGREE, 20
+        probs.append(dict(mat=arb.Matrix.from_csr(ctx, w.A), k=w.k, which=arb.ARB_SMALLEST, tol=1e-8, opts=o,
+                          x0=I.gaussian_block(w.A.n, w.p, w.seed)))
+    # every instance of a lock-step call holds its workspaces for the whole call: the batch
+    # goes in chunks whose summed footprints stay within a budget of HBM
+    chunks, cur, used = [], [], 0
+    budget = 100 << 30
+    for pr, w in zip(probs, ws):
+        f = arb.arb_server_footprint(w.A.n, w.A.nnz, w.p, 1, precision) + 8 * w.A.n * ((w.p + 3) // 4 * 4)
+        if cur and used + f > budget:
+            chunks.append(cur)
+            cur, used = [], 0
+        cur.append(pr)
+        used += f
+    chunks.append(cur)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(ctx.stream)
+    res, st, stats = [], arb.ARB_OK, {}
+    for ch in chunks:
+        st_c, res_c, stats_c = arb.arb_solve_lockstep(ctx, ch, flags=flags, evecs=False)
+        res += res_c
+        st = st if st != arb.ARB_OK else st_c
+        for key, v in stats_c.items():
+            stats[key] = stats.get(key, 0) + v
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = e0.elapsed_time(e1)
+    conv = sum(r.info["stop_reason"] in ("converged", "near_tol") for r in res)
+    small = sorted(range(len(ws)), key=lambda i: ws[i].A.n)[:2]
+    err = 0.0
+    for i in small:
+        lam = np.linalg.eigvalsh(ws[i].A.to_dense())[:ws[i].k]
+        err = max(err, float(np.max(np.abs(res[i].evals - lam) / np.maximum(1.0, np.abs(lam)))))
+    return {"instances": instances, "precision": {0: "fp64", 1: "mixed", 2: "mixed_df"}[precision],
+            "solves_per_s": instances / (ms * 1e-3), "ms": ms, "wall_s": wall, "converged": int(conv),
+            "max_maxres": float(max(r.info["maxres"] for r in res)),
+            "n_total": int(sum(w.A.n for w in ws)), "k_total": int(sum(w.k for w in ws)),
+            "final_degrees": sorted({r.info["final_d"] for r in res}),
+            "eig_rel_err_two_smallest_vs_dense": err, "stats": stats, "status": st, "chunks": len(chunks)}
+
+
 def run_serve(args):
     """--serve: the served mix at --rate / --requests / --slots in the chosen precision."""
     from paper_1507_06078_gb300 import build
@@ -658,8 +739,21 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def run_batched_only(args):
+    from paper_1507_06078_gb300 import build
+    build.build()
+    prec = {"mixed": 1, "mixed_df": 2, "fp64": 0}[args.precision]
+    out = batched_c3(args.instances, prec, args.batch_flags, degree=args.degree or 20,
+                     adapt_degree=args.adapt_degree)
+    out["batched_only"] = True
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.batched_only:
+        run_batched_only(args)
+        return
     if args.filter_only:
         run_filter_only(args)
         return

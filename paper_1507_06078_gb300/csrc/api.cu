@@ -8,8 +8,12 @@
 #include <cstring>
 #include <limits>
 #include <type_traits>
+#include <condition_variable>
+#include <functional>
 #include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -1566,13 +1570,28 @@ arb_status solve_impl(arb_ctx ctx, arb_mat mat, int32_t k, arb_which which, doub
 
 // ---------------------------------------------------------------- lock-step batched driver
 // A context of the lock-step driver: the caller's device, its own stream and workspaces.
-arb_ctx make_sub_context(arb_ctx parent, cudaStream_t stream) {
+// A context of the lock-step driver: the caller's device, a stream of its own (or the given
+// one) and workspaces of its own.  coop_share: the cooperative launches of this many such
+// contexts may run at once (each grid takes 1/coop_share of the device).
+arb_ctx make_sub_context(arb_ctx parent, cudaStream_t stream, int coop_share) {
   arb_ctx c = new arb_ctx_s();
   c->device = parent->device;
-  c->stream = stream;
-  c->own_stream = false;
   c->num_sms = parent->num_sms;
-  c->coop_share = 1;
+  c->coop_share = std::max(1, coop_share);
+  if (stream) {
+    c->stream = stream;
+    c->own_stream = false;
+  } else if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) == cudaSuccess) {
+    c->own_stream = true;
+  } else {
+    delete c;
+    return nullptr;
+  }
+  if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return nullptr;
+  }
   return c;
 }
 
@@ -1583,8 +1602,65 @@ void drop_sub_context(arb_ctx c) {
     if (c->ws[i]) cudaFree(c->ws[i]);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   if (c->err_dev) cudaFree(c->err_dev);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
+
+// A fixed pool of host threads running one parallel loop at a time: run(count, f) calls
+// f(i) for i < count, spread over the workers, and returns when all calls have returned.
+class WorkerPool {
+ public:
+  explicit WorkerPool(int n) {
+    for (int t = 0; t < n; ++t) threads_.emplace_back([this] { work(); });
+  }
+  ~WorkerPool() {
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+  }
+  void run(int count, const std::function<void(int)>& f) {
+    if (count <= 0) return;
+    std::unique_lock<std::mutex> l(mu_);
+    f_ = &f;
+    count_ = count;
+    next_ = 0;
+    left_ = count;
+    ++gen_;
+    cv_.notify_all();
+    done_.wait(l, [this] { return left_ == 0; });
+    f_ = nullptr;
+  }
+
+ private:
+  void work() {
+    uint64_t seen = 0;
+    std::unique_lock<std::mutex> l(mu_);
+    for (;;) {
+      cv_.wait(l, [&] { return stop_ || gen_ != seen; });
+      if (stop_) return;
+      seen = gen_;
+      while (next_ < count_) {
+        const int i = next_++;
+        const std::function<void(int)>* f = f_;
+        l.unlock();
+        (*f)(i);
+        l.lock();
+        if (--left_ == 0) done_.notify_all();
+      }
+    }
+  }
+  std::vector<std::thread> threads_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)>* f_ = nullptr;
+  int count_ = 0, next_ = 0, left_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
 
 // What the driver needs of the current phase of a solve, whatever its element type.
 struct PhaseView {
@@ -1679,7 +1755,11 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
   cudaEventCreateWithFlags(&order, cudaEventDisableTiming);
   cudaEventRecord(order, ctx->stream);  // the caller's earlier work first
   cudaStreamWaitEvent(stream, order, 0);
-  arb_ctx bctx = make_sub_context(ctx, stream);  // the batched filter's workspaces
+  // the instances' per-instance work (inner stop checks, ARR tails, steps that do not join
+  // the batch) runs on a pool of host threads, each instance on a stream of its own; their
+  // cooperative launches (block Jacobi) share the device among the workers
+  const int workers = std::max(1, std::min<int>(nb, 16));
+  arb_ctx bctx = make_sub_context(ctx, stream, 1);  // the batched filter's workspaces and stream
   std::vector<arb_ctx> subs(nb, nullptr);
   std::vector<std::unique_ptr<Solve>> sv(nb);
   std::vector<arb_status> st(nb, ARB_OK);
@@ -1699,7 +1779,7 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
     for (arb_ctx c : subs) drop_sub_context(c);
     drop_sub_context(bctx);
     cudaStreamSynchronize(stream);
-    cudaEventRecord(order, stream);  // the caller's later work after ours
+    cudaEventRecord(order, stream);  // the caller's later work after ours (the instances' streams are drained)
     cudaStreamWaitEvent(ctx->stream, order, 0);
     cudaEventDestroy(order);
     cudaStreamDestroy(stream);
@@ -1722,7 +1802,12 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
   }
   // set-up and first phase of every instance
   for (int32_t i = 0; i < nb; ++i) {
-    subs[i] = make_sub_context(ctx, stream);
+    subs[i] = make_sub_context(ctx, nullptr, workers);
+    if (!subs[i]) {
+      st[i] = set_error(ctx, ARB_CUDA_ERROR, "solve_lockstep: stream creation");
+      continue;
+    }
+    cudaStreamWaitEvent(subs[i]->stream, order, 0);
     sv[i].reset(new Solve());
     sv[i]->ctx = subs[i];
     sv[i]->mat = mats[i];
@@ -1734,6 +1819,7 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
     if (st[i] == ARB_OK) st[i] = sv[i]->start();
     live[i] = st[i] == ARB_OK;
   }
+  WorkerPool pool(workers);
   // the lock-step loop
   for (;;) {
     // phase transitions and the start of outer iterations
@@ -1762,9 +1848,10 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
       any = any || live[i];
     }
     if (!any) break;
-    // one inner step of every instance whose inner loop runs: the batchable ones together
+    // one inner step of every instance whose inner loop runs: the batchable ones together,
+    // the others alone on the worker pool
     std::vector<arb_filter_job> jobs;
-    std::vector<int32_t> who;
+    std::vector<int32_t> who, alone;
     for (int32_t i = 0; i < nb; ++i) {
       if (!live[i] || !in_outer[i]) continue;
       PhaseView pv{sv[i].get()};
@@ -1773,12 +1860,24 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
         jobs.push_back(pv.with([](auto& ph) { return job_of(ph); }));
         who.push_back(i);
       } else {
-        st[i] = pv.with([](auto& ph) { return ph.step(); });
-        bs.single_steps++;
-        if (st[i] != ARB_OK) live[i] = false;
+        alone.push_back(i);
       }
     }
+    pool.run(static_cast<int>(alone.size()), [&](int t) {
+      const int32_t i = alone[t];
+      PhaseView pv{sv[i].get()};
+      st[i] = pv.with([](auto& ph) { return ph.step(); });
+    });
+    for (int32_t i : alone) {
+      bs.single_steps++;
+      if (st[i] != ARB_OK) live[i] = false;
+    }
     if (!jobs.empty()) {
+      // the batch reads the instances' blocks: their streams' work first
+      for (int32_t i : who) {
+        cudaEventRecord(subs[i]->ev_join, subs[i]->stream);
+        cudaStreamWaitEvent(stream, subs[i]->ev_join, 0);
+      }
       BatchPlan plan;
       fatal = filter_batched_prepare(bctx, static_cast<int32_t>(jobs.size()), jobs.data(), &plan);
       if (fatal != ARB_OK) break;
@@ -1829,30 +1928,43 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
         if (fatal != ARB_OK) break;
       }
       bs.batched_launches++;
+      // and the instances' next work reads its results; the batch ends before the workers'
+      // cooperative launches start, so those never share the device with it
+      cudaEventRecord(bctx->ev_join, stream);
       for (int32_t i : who) {
+        cudaStreamWaitEvent(subs[i]->stream, bctx->ev_join, 0);
         PhaseView pv{sv[i].get()};
         st[i] = pv.with([](auto& ph) { return ph.step_post_external(); });
         if (st[i] != ARB_OK) live[i] = false;
       }
+      if (cudaStreamSynchronize(stream) != cudaSuccess) {
+        fatal = cuda_error(bctx, cudaGetLastError(), "batched filter", __FILE__, __LINE__);
+        break;
+      }
     }
     bs.rounds++;
-    // inner stop checks, then the ARR tails of the instances whose inner loop has ended
-    for (int32_t i = 0; i < nb; ++i) {
-      if (!live[i] || !in_outer[i]) continue;
+    // inner stop checks, then the ARR tails of the instances whose inner loop has ended,
+    // on the worker pool
+    std::vector<int32_t> busy;
+    for (int32_t i = 0; i < nb; ++i)
+      if (live[i] && in_outer[i]) busy.push_back(i);
+    std::vector<char> tail_done(nb, 0);
+    pool.run(static_cast<int>(busy.size()), [&](int t) {
+      const int32_t i = busy[t];
       PhaseView pv{sv[i].get()};
       const bool due = pv.with([](auto& ph) { return ph.in_inner && !ph.step_due(); });
       if (due) {
         st[i] = pv.with([](auto& ph) { return ph.check(); });
-        if (st[i] != ARB_OK) {
-          live[i] = false;
-          continue;
-        }
+        if (st[i] != ARB_OK) return;
       }
       if (!pv.with([](auto& ph) { return ph.in_inner; })) {
         st[i] = pv.with([](auto& ph) { return ph.outer_tail(); });
-        in_outer[i] = false;
-        if (st[i] != ARB_OK) live[i] = false;
+        tail_done[i] = 1;
       }
+    });
+    for (int32_t i : busy) {
+      if (tail_done[i]) in_outer[i] = false;
+      if (st[i] != ARB_OK) live[i] = false;
     }
   }
   if (fatal != ARB_OK) {
@@ -1862,12 +1974,14 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
     return fatal;
   }
   // outputs
-  arb_status worst = ARB_OK;
-  for (int32_t i = 0; i < nb; ++i) {
-    if (st[i] == ARB_OK) {
+  pool.run(nb, [&](int i) {
+    if (st[i] == ARB_OK)
       st[i] = sv[i]->finish(evals[i], evecs ? evecs[i] : nullptr, ldq ? ldq[i] : mats[i]->n, 0,
                             info ? &info[i] : nullptr);
-    } else if (subs[i]) {
+  });
+  arb_status worst = ARB_OK;
+  for (int32_t i = 0; i < nb; ++i) {
+    if (st[i] != ARB_OK && subs[i]) {
       set_error(ctx, st[i], std::string("solve_lockstep: instance ") + std::to_string(i) + ": " + subs[i]->last_error);
     }
     if (st[i] != ARB_OK && (worst == ARB_OK || (worst == ARB_NOT_CONVERGED && st[i] < 0))) worst = st[i];

@@ -99,6 +99,8 @@ struct arb_ctx_s {
   // device error word of pipelined kernels whose bounded waits gave up (two ints, zeroed);
   // read and cleared at every host synchronisation of d2h_sync
   int32_t* err_dev = nullptr;
+  // ordering event of the lock-step driver's contexts (made with them)
+  cudaEvent_t ev_join = nullptr;
 };
 
 struct arb_mat_s {
