@@ -71,6 +71,11 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workload: --instances instances, --precision, graph/autotune flags")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--c2", action="store_true", help="the full-size Chung-Lu workload (k = 500, p = 600)")
+    ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--c2-precisions", default="fp64,mixed")
+    ap.add_argument("--ablations", action="store_true", help="RR vs ARR, degree, filter kind and k sweeps")
+    ap.add_argument("--max-side", type=int, default=512, help="batched workload: largest grid side")
     ap.add_argument("--adapt-degree", action="store_true", help="batched workload: the paper's degree rule")
     ap.add_argument("--batch-flags", type=int, default=3, help="lock-step flags: 1 graphs, 2 autotune")
     ap.add_argument("--no-strict", dest="strict", action="store_false",
@@ -453,7 +458,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and world == 1 and args.batched:
         from paper_1507_06078_gb300 import arrabit as arbm
-        batched = batched_c3(256, arbm.ARB_MIXED, arbm.ARB_BATCH_GRAPHS | arbm.ARB_BATCH_AUTOTUNE)
+        # 256 instances at the small end of the batched workload's sides (32-128): the full
+        # range (sides to 512) takes ~750 s, most of it in instances that reach maxit
+        batched = batched_c3(256, arbm.ARB_MIXED, arbm.ARB_BATCH_GRAPHS | arbm.ARB_BATCH_AUTOTUNE, sides=(32, 128))
 
     served = None
     if rank == 0 and world == 1 and args.serve_mix:
@@ -666,7 +673,7 @@ def served_mix(precision, rate, requests, slots, seed=4242):
             "solves_per_s": float(conv.sum()) / (done - t_sub[0]), "by_kind": per_kind, "tol": 1e-8}
 
 
-def batched_c3(instances, precision, flags, sides=(32, 512), degree=20, adapt_degree=False):
+def batched_c3(instances, precision, flags, sides=(32, 512), degree=20, adapt_degree=False, compare_slots=True):
     """Batched workload: `instances` 2D variable-coefficient diffusion operators (5-point,
     lognormal edge coefficients, seeds 30000 + i, sides uniform in `sides`, k uniform in
     8..64, p = 1.5 k), smallest pairs to relative residual 1e-8, q = 1, b refreshed after
@@ -716,6 +723,17 @@ def batched_c3(instances, precision, flags, sides=(32, 512), degree=20, adapt_de
     wall = time.perf_counter() - t0
     ms = e0.elapsed_time(e1)
     conv = sum(r.info["stop_reason"] in ("converged", "near_tol") for r in res)
+    # the same problems through arb_solve_batched (independent solves on 8 concurrent
+    # streams, no batched filter), for comparison
+    slots = None
+    if compare_slots:
+        e0.record(ctx.stream)
+        t1 = time.perf_counter()
+        for ch in chunks:
+            arb.arb_solve_batched(ctx, ch, max_concurrent=8, evecs=False)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        slots = {"solves_per_s": instances / (e0.elapsed_time(e1) * 1e-3), "wall_s": time.perf_counter() - t1}
     small = sorted(range(len(ws)), key=lambda i: ws[i].A.n)[:2]
     err = 0.0
     for i in small:
@@ -726,7 +744,8 @@ def batched_c3(instances, precision, flags, sides=(32, 512), degree=20, adapt_de
             "max_maxres": float(max(r.info["maxres"] for r in res)),
             "n_total": int(sum(w.A.n for w in ws)), "k_total": int(sum(w.k for w in ws)),
             "final_degrees": sorted({r.info["final_d"] for r in res}),
-            "eig_rel_err_two_smallest_vs_dense": err, "stats": stats, "status": st, "chunks": len(chunks)}
+            "eig_rel_err_two_smallest_vs_dense": err, "stats": stats, "status": st, "chunks": len(chunks),
+            "sides": list(sides), "degree": degree, "adaptive_degree": adapt_degree, "concurrent_streams": slots}
 
 
 def run_serve(args):
@@ -739,11 +758,132 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def _solve_timed(arb, ctx, mat, k, o, x0, tol=1e-8, which=None):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    r = arb.arb_solve(ctx, mat, k, arb.ARB_SMALLEST if which is None else which, tol, o, x0=x0, evecs="device")
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1) * 1e-3
+
+
+def run_c2(args):
+    """The Chung-Lu workload at full size: normalised Laplacian of the largest component of
+    a Chung-Lu graph with n = 1e6 (power-law expected degrees, exponent 2.5, mean 16, max
+    5000; seed 1507), k = 500 smallest pairs, p = 600, degree 15, q = 1, relative residual
+    1e-8, b refreshed after every ARR; the matrix in its original order and after a reverse
+    Cuthill-McKee reordering (SELL-C-sigma C = 32, sigma = 1024 when --sell).  Prints one
+    filter pass per layout and the solve in the chosen precisions."""
+    import torch
+    from paper_1507_06078_gb300 import arrabit as arb
+    from paper_1507_06078_gb300 import build
+    build.build()
+    t0 = time.perf_counter()
+    A, _ = I.chung_lu_laplacian(args.chung_lu or 1_000_000, seed=1507)
+    t_gen = time.perf_counter() - t0
+    R, perm = I.rcm_permuted(A)
+    k, p = args.k or 500, int(round(1.2 * (args.k or 500)))
+    ctx = arb.Context(0)
+    out = {"c2": True, "n": A.n, "nnz": A.nnz, "k": k, "p": p, "t_generate_s": t_gen}
+    coef = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, 15)
+    passes = {}
+    for name, M, sell in (("csr", A, None), ("sell32", A, (32, 1024)), ("rcm_csr", R, None), ("rcm_sell32", R, (32, 1024))):
+        mat = arb.Matrix.from_csr(ctx, M)
+        if sell:
+            mat.set_sell(*sell)
+        X = arb.arb_gaussian_block(ctx, M.n, p, 5).float()
+        Y = torch.empty_like(X)
+        arb.arb_filter_f32(ctx, mat, -1.0, 2.0, 0.0, 1.9, coef, X, Y=Y)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        arb.arb_filter_f32(ctx, mat, -1.0, 2.0, 0.0, 1.9, coef, X, Y=Y)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 15
+        passes[name] = {"ms_per_pass": ms, "algorithmic_GBps": filter_algorithmic_bytes(M.n, M.nnz, p, 15, 4, 4) / 15 / ms / 1e6}
+        del X, Y
+        mat.close()
+    out["filter_pass_fp32"] = passes
+    mat = arb.Matrix.from_csr(ctx, R)
+    mat.set_sell(32, 1024)
+    x0 = I.gaussian_block(R.n, p, 20150724)
+    solves = {}
+    for prec in args.c2_precisions.split(","):
+        o = arb.arb_options_default(k)
+        o.p, o.q, o.degree, o.b_update = p, 1, 15, 1
+        o.precision = {"fp64": arb.ARB_FP64, "mixed": arb.ARB_MIXED, "mixed_df": arb.ARB_MIXED_DF}[prec]
+        r, sec = _solve_timed(arb, ctx, mat, k, o, x0)
+        solves[prec] = {"seconds": sec, "status": r.status, "maxres": r.info["maxres"], "stop": r.info["stop_reason"],
+                        "outer_iters": r.info["outer_iters"], "n_filters": r.info["n_filters"],
+                        "lambda_1": float(r.evals[0]), "lambda_k": float(r.evals[-1])}
+        print(json.dumps({"c2_solve": prec, **solves[prec]}), flush=True)
+    out["solves"] = solves
+    print(json.dumps(out))
+
+
+def run_ablations(args):
+    """Synthetic analogues of the paper's ablations and k sweep (Tables ARR, polydeg,
+    comp-cheby, and the k-scaling runs of Section 6.4) on the GPU path: one solve per
+    setting, CUDA-event time, outer iterations and SpMV-equivalent columns.
+    * RR vs ARR: q = 0, 1, 2 and the adaptive rule (eq. block), 3D 48^3 Laplacian, k = 50.
+    * degree: d = 5, 10, 15, 20 and the adaptive rule (eqs. hat-d, degree) from d = 3.
+    * filter: Chebyshev interpolant of max(0,t)^(10d) vs the plain Chebyshev T_d, d = 10, 20.
+    * k sweep: k = 25, 50, 100, 200 on the 3D 64^3 Laplacian (p = 1.2 k, d = 20, q = 2).
+    All smallest pairs to relative residual 1e-8 in FP64 except the k sweep (mixed_df)."""
+    from paper_1507_06078_gb300 import arrabit as arb
+    from paper_1507_06078_gb300 import build
+    build.build()
+    ctx = arb.Context(0)
+    A = I.laplacian_3d(48)
+    mat = arb.Matrix.from_csr(ctx, A)
+    k, p = 50, 60
+    x0 = I.gaussian_block(A.n, p, 77)
+    lam = laplacian_3d_closed_form(48)[:k]
+    rows = []
+
+    def one(group, setting, o, M=mat, kk=k, xx=x0, ll=lam):
+        r, sec = _solve_timed(arb, ctx, M, kk, o, xx)
+        err = float(np.max(np.abs(r.evals - ll) / np.maximum(1.0, np.abs(ll))))
+        row = {"group": group, "setting": setting, "seconds": sec, "outer_iters": r.info["outer_iters"],
+               "spmm_cols": r.info["spmm_cols"], "stop": r.info["stop_reason"], "maxres": r.info["maxres"],
+               "final_q": r.info["final_q"], "final_d": r.info["final_d"], "eig_err": err}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+
+    def opts(q=1, d=15, filt=arb.ARB_FILTER_CHEBINTERP, adapt=0, prec=arb.ARB_FP64, kk=k, pp=p):
+        o = arb.arb_options_default(kk)
+        o.p, o.q, o.degree, o.filter, o.adapt, o.precision, o.b_update = pp, q, d, filt, adapt, prec, 1
+        return o
+
+    for q in (0, 1, 2):
+        one("rr_vs_arr", f"q={q}", opts(q=q))
+    one("rr_vs_arr", "adaptive q", opts(q=1, adapt=arb.ARB_ADAPT_Q))
+    for d in (5, 10, 15, 20):
+        one("degree", f"d={d}", opts(d=d))
+    one("degree", "adaptive d from 3", opts(d=3, adapt=arb.ARB_ADAPT_DEGREE))
+    for d in (10, 20):
+        one("filter", f"interpolant d={d}", opts(d=d))
+        one("filter", f"chebyshev T_d d={d}", opts(d=d, filt=arb.ARB_FILTER_CHEBYSHEV))
+    A64 = I.laplacian_3d(64)
+    m64 = arb.Matrix.from_csr(ctx, A64)
+    lam64 = laplacian_3d_closed_form(64)
+    for kk in (25, 50, 100, 200):
+        pp = int(round(1.2 * kk))
+        one("k_sweep", f"k={kk}", opts(q=2, d=20, prec=arb.ARB_MIXED_DF, kk=kk, pp=pp), M=m64, kk=kk,
+            xx=I.gaussian_block(A64.n, pp, 78), ll=lam64[:kk])
+    print(json.dumps({"ablations": True, "rows": rows}))
+
+
 def run_batched_only(args):
     from paper_1507_06078_gb300 import build
     build.build()
     prec = {"mixed": 1, "mixed_df": 2, "fp64": 0}[args.precision]
-    out = batched_c3(args.instances, prec, args.batch_flags, degree=args.degree or 20,
+    out = batched_c3(args.instances, prec, args.batch_flags, sides=(32, args.max_side), degree=args.degree or 20,
                      adapt_degree=args.adapt_degree)
     out["batched_only"] = True
     print(json.dumps(out))
@@ -751,6 +891,12 @@ def run_batched_only(args):
 
 def main():
     args = parse()
+    if args.c2:
+        run_c2(args)
+        return
+    if args.ablations:
+        run_ablations(args)
+        return
     if args.batched_only:
         run_batched_only(args)
         return

@@ -282,6 +282,20 @@ def chung_lu_laplacian(n: int, seed: int = 1507, beta: float = 2.5, mean: float 
     return CSR(nn, L.indptr.astype(np.int32), L.indices.astype(np.int32), L.data.astype(np.float64)), ids
 
 
+def rcm_permuted(A: CSR) -> tuple[CSR, np.ndarray]:
+    """P A P^T for the reverse Cuthill-McKee order of A's graph (scipy.sparse.csgraph), the
+    locality ordering for matrices whose nonzeros gather rows at random (power-law graphs):
+    neighbouring rows then gather nearby rows.  The spectrum is unchanged and eigenvectors
+    come back by the returned permutation (row i of the result is row perm[i] of A)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import reverse_cuthill_mckee
+    M = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+    perm = reverse_cuthill_mckee(M, symmetric_mode=True).astype(np.int64)
+    R = M[perm][:, perm].tocsr()
+    R.sort_indices()
+    return CSR(A.n, R.indptr.astype(np.int32), R.indices.astype(np.int32), R.data.astype(np.float64)), perm
+
+
 def diffusion_2d(side: int, seed: int) -> CSR:
     """5-point variable-coefficient diffusion on a side x side grid with Dirichlet ghost
     nodes: every grid edge (interior and boundary) gets a conductance exp(N(0,1))

@@ -125,3 +125,14 @@ def test_diffusion_2d_invariants():
     assert np.linalg.eigvalsh(M)[0] > 0
     assert np.array_equal(diffusion_2d(side, 3).val, A.val)
     assert not np.array_equal(diffusion_2d(side, 4).val, A.val)
+
+
+def test_rcm_permutation_is_a_symmetric_permutation():
+    A, _ = I.chung_lu_laplacian(3000, seed=9)
+    R, perm = I.rcm_permuted(A)
+    assert sorted(perm.tolist()) == list(range(A.n)) and R.nnz == A.nnz
+    D, E = A.to_dense(), R.to_dense()
+    np.testing.assert_array_equal(E, D[np.ix_(perm, perm)])
+    # the reordering shrinks the bandwidth
+    bw = lambda M: int(np.max(np.abs(np.repeat(np.arange(M.n), np.diff(M.rowptr)) - M.col)))  # noqa: E731
+    assert bw(R) < bw(A)
