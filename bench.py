@@ -464,8 +464,8 @@ def run_ours(args):
 
     served = None
     if rank == 0 and world == 1 and args.serve_mix:
-        # the mixed form with an FP64 refinement: on the Chung-Lu kind the double-float
-        # refinement stalls where FP64 converges (see the design notes)
+        # the mixed form with an FP64 refinement: on the 125k-row Chung-Lu kind the
+        # double-float refinement stalls near 1e-7 where FP64 converges
         mix = served_mix(arb.ARB_MIXED, args.rate, args.requests, args.slots)
         mix64 = served_mix(arb.ARB_FP64, args.rate, args.requests, args.slots)
         served = {"mixed": mix, "fp64": mix64,
@@ -661,6 +661,11 @@ def served_mix(precision, rate, requests, slots, seed=4242):
         kd["converged"] += int(r.status == arb.ARB_OK)
         kd["max_maxres"] = max(kd["max_maxres"], r.info["maxres"])
         kd["stops"][r.info["stop_reason"]] = kd["stops"].get(r.info["stop_reason"], 0) + 1
+        kd.setdefault("latencies_s", []).append(r.info["latency_s"])
+        kd.setdefault("solve_s", []).append(r.info["t_total"])
+    for kd in per_kind.values():
+        kd["mean_latency_s"] = float(np.mean(kd.pop("latencies_s")))
+        kd["mean_solve_s"] = float(np.mean(kd.pop("solve_s")))
     srv.close()
     done = max(ts + lt for ts, lt in zip(t_sub, lat))
     lat = np.array(lat)

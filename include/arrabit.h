@@ -446,6 +446,12 @@ typedef struct {
   int64_t graphs_captured;   /* distinct round shapes captured */
   int64_t single_steps;      /* inner steps run for one instance alone (GN, double-float filter) */
   double t_total;            /* seconds spent in the call */
+  double t_batched;          /* host seconds from forming a round's batch to its completion */
+  double t_single;           /* host seconds in the rounds' single-instance steps */
+  double t_checks;           /* host seconds in the inner stop checks and ARR tails */
+  double t_batch_kernel;     /* device seconds of the batched filter launches (CUDA events) */
+  double t_prepare;          /* host seconds forming the batches (descriptors, upload) */
+  int64_t batched_jobs;      /* instance steps filtered by the batched launches, summed over rounds */
 } arb_batch_stats;
 
 enum { ARB_BATCH_GRAPHS = 1, ARB_BATCH_AUTOTUNE = 2 };

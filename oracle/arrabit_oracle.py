@@ -10,8 +10,7 @@ Everything is float64.  Library primitives used as single steps: scipy.sparse ma
 products, scipy's pivoted Householder QR, Cholesky factor/solve, and numpy's Chebyshev
 basis conversion.  The dense symmetric eigensolver is a hand-written cyclic Jacobi.
 
-Readings of the paper taken where it is silent or inconsistent (each is repeated in the
-design notes of the repository):
+Readings of the paper taken where it is silent or inconsistent:
 
 * Alg. 1 writes H = V^T Sigma V but Y = U V; we take H = V Sigma V^T with the columns of
   V the eigenvectors, sorted by descending Ritz value (ties keep index order).

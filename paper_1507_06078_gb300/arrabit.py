@@ -57,7 +57,9 @@ class arb_filter_job(C.Structure):
 
 class arb_batch_stats(C.Structure):
     _fields_ = [("rounds", C.c_int64), ("batched_launches", C.c_int64), ("graph_launches", C.c_int64),
-                ("graphs_captured", C.c_int64), ("single_steps", C.c_int64), ("t_total", C.c_double)]
+                ("graphs_captured", C.c_int64), ("single_steps", C.c_int64), ("t_total", C.c_double),
+                ("t_batched", C.c_double), ("t_single", C.c_double), ("t_checks", C.c_double),
+                ("t_batch_kernel", C.c_double), ("t_prepare", C.c_double), ("batched_jobs", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

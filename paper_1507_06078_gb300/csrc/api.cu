@@ -1701,33 +1701,20 @@ std::string round_key(const BatchPlan& plan) {
   auto put = [&](const void* p, size_t b) { key.append(static_cast<const char*>(p), b); };
   put(&plan.dj, sizeof(plan.dj));
   put(&plan.dp, sizeof(plan.dp));
-  put(&plan.doff, sizeof(plan.doff));
-  put(&plan.part, sizeof(plan.part));
-  put(&plan.coop_grid, sizeof(plan.coop_grid));
   put(&plan.dmax, sizeof(plan.dmax));
-  for (const auto& J : plan.jobs) {
-    put(&J.mat, sizeof(J.mat));
-    put(&J.X, sizeof(J.X));
-    put(&J.Y, sizeof(J.Y));
-    put(&J.ncols, sizeof(J.ncols));
-    put(&J.degree, sizeof(J.degree));
-    put(&J.fp32, sizeof(J.fp32));
-    put(&J.xscale, sizeof(J.xscale));
-    put(&J.colss, sizeof(J.colss));
-    put(&J.ldx, sizeof(J.ldx));
-    put(&J.ldy, sizeof(J.ldy));
-  }
-  for (const auto& t : plan.tables) {
-    put(&t.table, sizeof(t.table));
-    put(t.cc.c, sizeof(double) * (t.d + 1));
+  for (const auto& c : plan.cls) {
+    put(&c.first, sizeof(c.first));
+    put(&c.count, sizeof(c.count));
+    put(&c.grid, sizeof(c.grid));
+    put(&c.doff, sizeof(c.doff));
+    put(&c.dcs, sizeof(c.dcs));
   }
   return key;
 }
 
 int64_t round_kernels(const BatchPlan& plan) {
-  int64_t k = static_cast<int64_t>(plan.tables.size()) + 1;
-  for (const auto& J : plan.jobs)
-    if (J.colss) k += 2;
+  int64_t k = 0;
+  for (const auto& c : plan.cls) k += c.count > 0 ? 1 : 0;
   return k;
 }
 
@@ -1751,8 +1738,10 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
   ARB_CUDA(ctx, cudaSetDevice(ctx->device));
   cudaStream_t stream = nullptr;
   ARB_CUDA(ctx, cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
-  cudaEvent_t order = nullptr;
+  cudaEvent_t order = nullptr, kev0 = nullptr, kev1 = nullptr;
   cudaEventCreateWithFlags(&order, cudaEventDisableTiming);
+  cudaEventCreate(&kev0);
+  cudaEventCreate(&kev1);
   cudaEventRecord(order, ctx->stream);  // the caller's earlier work first
   cudaStreamWaitEvent(stream, order, 0);
   // the instances' per-instance work (inner stop checks, ARR tails, steps that do not join
@@ -1782,6 +1771,8 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
     cudaEventRecord(order, stream);  // the caller's later work after ours (the instances' streams are drained)
     cudaStreamWaitEvent(ctx->stream, order, 0);
     cudaEventDestroy(order);
+    cudaEventDestroy(kev0);
+    cudaEventDestroy(kev1);
     cudaStreamDestroy(stream);
   };
   // autotuned SpMM settings per distinct matrix (width of its first problem)
@@ -1863,6 +1854,7 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
         alone.push_back(i);
       }
     }
+    Timer t_single;
     pool.run(static_cast<int>(alone.size()), [&](int t) {
       const int32_t i = alone[t];
       PhaseView pv{sv[i].get()};
@@ -1872,15 +1864,20 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
       bs.single_steps++;
       if (st[i] != ARB_OK) live[i] = false;
     }
+    bs.t_single += t_single.sec();
     if (!jobs.empty()) {
+      Timer t_batch;
       // the batch reads the instances' blocks: their streams' work first
       for (int32_t i : who) {
         cudaEventRecord(subs[i]->ev_join, subs[i]->stream);
         cudaStreamWaitEvent(stream, subs[i]->ev_join, 0);
       }
       BatchPlan plan;
+      Timer t_prep;
       fatal = filter_batched_prepare(bctx, static_cast<int32_t>(jobs.size()), jobs.data(), &plan);
       if (fatal != ARB_OK) break;
+      bs.t_prepare += t_prep.sec();
+      cudaEventRecord(kev0, stream);
       bool ran = false;
       if (graphs_ok) {
         const std::string key = round_key(plan);
@@ -1928,6 +1925,8 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
         if (fatal != ARB_OK) break;
       }
       bs.batched_launches++;
+      bs.batched_jobs += static_cast<int64_t>(jobs.size());
+      cudaEventRecord(kev1, stream);
       // and the instances' next work reads its results; the batch ends before the workers'
       // cooperative launches start, so those never share the device with it
       cudaEventRecord(bctx->ev_join, stream);
@@ -1941,6 +1940,9 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
         fatal = cuda_error(bctx, cudaGetLastError(), "batched filter", __FILE__, __LINE__);
         break;
       }
+      bs.t_batched += t_batch.sec();
+      float kms = 0.f;
+      if (cudaEventElapsedTime(&kms, kev0, kev1) == cudaSuccess) bs.t_batch_kernel += kms * 1e-3;
     }
     bs.rounds++;
     // inner stop checks, then the ARR tails of the instances whose inner loop has ended,
@@ -1949,6 +1951,7 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
     for (int32_t i = 0; i < nb; ++i)
       if (live[i] && in_outer[i]) busy.push_back(i);
     std::vector<char> tail_done(nb, 0);
+    Timer t_checks;
     pool.run(static_cast<int>(busy.size()), [&](int t) {
       const int32_t i = busy[t];
       PhaseView pv{sv[i].get()};
@@ -1962,6 +1965,7 @@ extern "C" arb_status arb_solve_lockstep(arb_ctx ctx, int32_t nb, const arb_mat*
         tail_done[i] = 1;
       }
     });
+    bs.t_checks += t_checks.sec();
     for (int32_t i : busy) {
       if (tail_done[i]) in_outer[i] = false;
       if (st[i] != ARB_OK) live[i] = false;

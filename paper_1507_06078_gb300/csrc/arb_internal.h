@@ -59,8 +59,7 @@ enum WsSlot : int {
   WS_F32_AU,
   WS_F32_T,
   WS_F32_T2,
-  WS_BATCH_WORK,      // batched filter: per-instance work blocks, tables, descriptors
-  WS_BATCH_TABLE,
+  WS_BATCH_WORK,      // batched filter: per-instance work blocks and multiplier tables
   WS_BATCH_DESC,
   WS_TC_ERR,          // tensor-core kernels: error word
   WS_TC_IMG,          // tensor-core tall products: packed split W
@@ -353,28 +352,22 @@ arb_status rcond_from_cholesky(arb_ctx ctx, int32_t m, const double* G, int64_t 
                                double* Ginv, int32_t* status, double* rc_dev);
 
 // ---------------------------------------------------------------- batched filter (batched.cu)
-struct CoefTable {
-  double c[64];
-};
-// A prepared batched filter: descriptors on the device, per-job coefficient-table launches,
-// workspaces.  filter_batched_launch issues kernels only (capturable into a CUDA graph).
+// A prepared batched filter: descriptors on the device, workspaces.  filter_batched_launch
+// issues one kernel per job class present (capturable into a CUDA graph).
 struct BatchPlan {
-  struct Table {
-    bool fp32;
-    int d, ncols, blocks;
-    CoefTable cc;
-    const double* xscale;
-    void* table;
+  struct Class {             // jobs of one element type and vector width: 0 FP32 x4, 1 FP32 x1,
+    int first = 0;           // 2 FP64 x2, 3 FP64 x1 (in class order on the device)
+    int count = 0;
+    int grid = 0;
+    const int64_t* doff = nullptr;  // pass and table-prologue offsets over the class's jobs
+    const int64_t* dcs = nullptr;   // column-sum offsets over the class's columns
   };
   int32_t njobs = 0;
   int dmax = 0;
-  int coop_grid = 1;
   std::vector<arb_filter_job> jobs;
-  std::vector<Table> tables;
-  std::vector<double> coef;
-  const void* dj = nullptr;  // device job and pass descriptors, pass offsets
+  Class cls[4];
+  const void* dj = nullptr;  // device job and pass descriptors
   const void* dp = nullptr;
-  const int64_t* doff = nullptr;
   double* part = nullptr;    // column-sum partials
 };
 arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs, BatchPlan* plan);

@@ -1,19 +1,32 @@
 // Batched filter: the Chebyshev-interpolant filter (Algorithm 7, evaluated by Clenshaw's
 // recurrence) applied to many independent instances - different matrices, block widths,
-// degrees and precisions - in ONE persistent cooperative launch.
+// degrees and precisions - in persistent cooperative launches, one per element type and
+// vector width present in the batch.
 //
-// Every pass t of the recurrence is a set of work items: (instance, row, column chunk)
-// for each instance whose degree exceeds t.  The items of pass t are numbered by
-// per-pass prefix sums over the instances; warps take items in grid-stride order, find
-// the instance by binary search, and run the same fused gather + Clenshaw epilogue as
-// the single-instance kernel.  A grid-wide barrier separates passes (pass t+1 gathers
-// rows that pass t wrote).  Each instance's multipliers are tabulated per pass in its
-// own element type, and its buffer rotation (b_j over b_{j+2}) is fixed in a pass table,
-// so the kernel reads plain pointers.
+// Every pass t of the recurrence is a set of tiles: (instance, run of rows) for each
+// instance whose degree exceeds t.  The tiles of pass t are numbered by per-pass prefix
+// sums over the instances; warps take tiles in grid-stride order and find the instance by
+// one binary search per tile.  Inside a tile a warp is split into groups of G lanes (G the
+// power of two that covers the block's width in 16-byte vectors, at most 32), one row per
+// group, so a 12-column block keeps 8 rows in flight per warp instead of idling 20 lanes.
+// A group walks its rows software-pipelined: the nonzeros of the next row and the bounds
+// of the one after are fetched while the current row gathers.  Each lane sums its
+// columns' products over the row's nonzeros in CSR order and applies the same Clenshaw
+// epilogue as the single-instance kernel.  The per-column multipliers of every pass follow
+// from the instance's coefficients and column scale in FP64; a prologue of the launch
+// tabulates them in the instance's element type, so the row loop runs no FP64 instruction
+// for FP32 instances (FP64 issues at a small fraction of the FP32 rate on this GPU).  A
+// grid-wide barrier separates passes (pass t+1 gathers rows that pass t wrote).  In an
+// instance's last pass every tile also leaves the column sums of squares of its rows (the
+// MPM normalisation of Algorithm 7's output; FP32 instances sum in double-float: FP32
+// pairs with error-free product and sum transforms); after the last barrier one warp per
+// (instance, column) adds the tiles' partial sums in tile order, so the result does not
+// depend on the grid.
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "arb_internal.h"
@@ -25,13 +38,31 @@ namespace {
 
 constexpr int BT_THREADS = 256;
 constexpr int BT_WARPS = BT_THREADS / 32;
+// nonzeros of the next row fetched ahead (rows up to this length take one round trip)
+#ifndef BT_PF
+#define BT_PF 4
+#endif
+// CTAs per SM the register budget must allow (2: 128 registers a thread)
+#ifndef ARB_BATCH_MIN_BLOCKS
+#define ARB_BATCH_MIN_BLOCKS 2
+#endif
 
 struct BJob {
   int64_t n;
   const int32_t* rowptr;
   const int32_t* col;
   const void* val;
+  const double* coef;  // c_0..c_d of the instance's interpolant in terms of S (device)
+  const double* xs;    // per-column scale of X, or NULL
+  double* colss;       // column sums of squares of the result, or NULL
+  double* part;        // [tiles][ncols] partial sums of the last pass (colss only)
+  void* tab;           // [degree][3][ldt] multipliers (sy, sx, sz) of every pass, element type
+  int64_t tiles;       // tiles of one pass
+  int32_t tile_rows;
   int32_t ncols, nch, vec, fp32;
+  int32_t glog;        // lanes per row = 1 << glog
+  int32_t degree;
+  int32_t ldt;         // ncols rounded up to 4
 };
 
 struct BPass {
@@ -39,216 +70,325 @@ struct BPass {
   const void* X;
   const void* Z;
   void* out;
-  const void* sy;  // per-column multipliers in the job's element type
-  const void* sx;
-  const void* sz;
   int64_t ldy, ldx, ldz, ldo;
   double alpha, beta;
 };
 
+// VEC consecutive elements of a row; those at or past `valid` are left alone / zero
 template <typename T, int VEC>
-__device__ __forceinline__ void vload(const T* p, T (&r)[VEC]) {
+__device__ __forceinline__ void vload(const T* p, int valid, T (&r)[VEC]) {
+  if (valid >= VEC) {
+    if constexpr (VEC == 4 && sizeof(T) == 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p);
+      r[0] = t.x;
+      r[1] = t.y;
+      r[2] = t.z;
+      r[3] = t.w;
+      return;
+    } else if constexpr (VEC == 2 && sizeof(T) == 8) {
+      const double2 t = *reinterpret_cast<const double2*>(p);
+      r[0] = t.x;
+      r[1] = t.y;
+      return;
+    }
+  }
 #pragma unroll
-  for (int u = 0; u < VEC; ++u) r[u] = p[u];
-}
-
-template <>
-__device__ __forceinline__ void vload<float, 4>(const float* p, float (&r)[4]) {
-  const float4 t = *reinterpret_cast<const float4*>(p);
-  r[0] = t.x;
-  r[1] = t.y;
-  r[2] = t.z;
-  r[3] = t.w;
-}
-
-template <>
-__device__ __forceinline__ void vload<double, 2>(const double* p, double (&r)[2]) {
-  const double2 t = *reinterpret_cast<const double2*>(p);
-  r[0] = t.x;
-  r[1] = t.y;
+  for (int u = 0; u < VEC; ++u) r[u] = u < valid ? p[u] : T(0);
 }
 
 template <typename T, int VEC>
-__device__ __forceinline__ void vstore(T* p, const T (&r)[VEC]) {
+__device__ __forceinline__ void vstore(T* p, int valid, const T (&r)[VEC]) {
+  if (valid >= VEC) {
+    if constexpr (VEC == 4 && sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+      return;
+    } else if constexpr (VEC == 2 && sizeof(T) == 8) {
+      *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+      return;
+    }
+  }
 #pragma unroll
-  for (int u = 0; u < VEC; ++u) p[u] = r[u];
+  for (int u = 0; u < VEC; ++u)
+    if (u < valid) p[u] = r[u];
 }
 
-template <>
-__device__ __forceinline__ void vstore<float, 4>(float* p, const float (&r)[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+// multipliers of column c in pass t (Clenshaw's b_j = 2 S b_{j+1} - b_{j+2} + c_j X with
+// the first and last passes folded in), in FP64 as the single-instance filter's tables
+__device__ __forceinline__ void pass_multipliers(const BJob& J, int t, int c, double& sy, double& sx, double& sz) {
+  const double s = J.xs ? J.xs[c] : 1.0;
+  const int d = J.degree;
+  const int j = d - 1 - t;
+  if (d == 1) {
+    sy = J.coef[1] * s;
+    sx = J.coef[0] * s;
+    sz = 0.0;
+  } else {
+    sy = (t == 0) ? 2.0 * J.coef[d] * s : (t == d - 1 ? 1.0 : 2.0);
+    sx = J.coef[j] * s;
+    sz = (j + 2 == d) ? -J.coef[d] * s : -1.0;
+  }
 }
 
-template <>
-__device__ __forceinline__ void vstore<double, 2>(double* p, const double (&r)[2]) {
-  *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
+// (hi, lo) += o^2 with the rounding errors of the product and of the sum carried in lo
+__device__ __forceinline__ void df_add_square(float o, float& hi, float& lo) {
+  const float p = o * o;
+  const float pe = fmaf(o, o, -p);
+  const float s = hi + p;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (p - bp);
+  hi = s;
+  lo += e + pe;
 }
 
-// out[row, chunk] = sy*(alpha*(A Yin)[row] + beta*Yin[row]) + sx*X[row] + sz*Z[row]
+__device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2) {
+  const float s = hi + h2;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (h2 - bp);
+  hi = s;
+  lo = lo + l2 + e;
+}
+
+// one tile of pass t: out[row, c] = sy*(alpha*(A Yin)[row] + beta*Yin[row]) + sx*X[row] + sz*Z[row]
 template <typename T, int VEC>
-__device__ void batched_item(const BJob& J, const BPass& P, int64_t row, int chunk, int lane) {
-  const int c = chunk * 32 * VEC + lane * VEC;
-  const bool act = c < J.ncols;
+__device__ void batched_tile(const BJob& J, const BPass& P, int t, int64_t tile, int lane, bool last) {
+  const int glog = J.glog;
+  const int G = 1 << glog;
+  const int R = 32 >> glog;
+  const int grp = lane >> glog, gl = lane & (G - 1);
+  const int64_t r0 = tile * J.tile_rows;
+  const int64_t r1 = min(J.n, r0 + J.tile_rows);
+  const bool want_ss = last && J.colss != nullptr;  // warp-uniform
   const T* Yin = static_cast<const T*>(P.Yin);
   const T* X = static_cast<const T*>(P.X);
   const T* Z = static_cast<const T*>(P.Z);
+  T* out = static_cast<T*>(P.out);
   const T* val = static_cast<const T*>(J.val);
-  T xv[VEC], zv[VEC];
-  if (X && act) vload<T, VEC>(X + row * P.ldx + c, xv);
-  if (Z && act) vload<T, VEC>(Z + row * P.ldz + c, zv);
-  T acc[VEC];
-#pragma unroll
-  for (int u = 0; u < VEC; ++u) acc[u] = T(0);
-  const int beg = J.rowptr[row], end = J.rowptr[row + 1];
-  for (int base = beg; base < end; base += 32) {
-    const int e = base + lane;
-    int jc = 0;
-    T av = T(0);
-    if (e < end) {
-      jc = J.col[e];
-      av = val[e];
-    }
-    const int cnt = min(32, end - base);
-    for (int t0 = 0; t0 < cnt; t0 += 4) {
-      int jj[4];
-      T vv[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        jj[t] = __shfl_sync(0xffffffffu, jc, t0 + t < 32 ? t0 + t : 31);
-        vv[t] = __shfl_sync(0xffffffffu, av, t0 + t < 32 ? t0 + t : 31);
-      }
-      T y[4][VEC];
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (act && t0 + t < cnt) vload<T, VEC>(Yin + static_cast<int64_t>(jj[t]) * P.ldy + c, y[t]);
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (act && t0 + t < cnt)
-#pragma unroll
-          for (int u = 0; u < VEC; ++u) acc[u] = fma(vv[t], y[t][u], acc[u]);
-    }
-  }
-  if (!act) return;
   const T alpha = static_cast<T>(P.alpha), beta = static_cast<T>(P.beta);
-  const T* sy = static_cast<const T*>(P.sy);
-  const T* sx = static_cast<const T*>(P.sx);
-  const T* sz = static_cast<const T*>(P.sz);
-  T yi[VEC], o[VEC];
-  if (beta != T(0)) {
-    vload<T, VEC>(Yin + row * P.ldy + c, yi);
-  } else {
+  // column sums of squares of the tile's rows: FP64 for FP64 instances, double-float
+  // (hi, lo) for FP32 ones
+  using Acc = typename std::conditional<sizeof(T) == 4, float, double>::type;
+  for (int ch = 0; ch < J.nch; ++ch) {
+    const int c = (ch * G + gl) * VEC;
+    const int valid = min(VEC, J.ncols - c);  // <= 0: the lane has no column here
+    Acc ss[VEC], sl[VEC];
 #pragma unroll
-    for (int u = 0; u < VEC; ++u) yi[u] = T(0);
-  }
+    for (int u = 0; u < VEC; ++u) ss[u] = sl[u] = Acc(0);
+    const T* tab = static_cast<const T*>(J.tab) + static_cast<int64_t>(t) * 3 * J.ldt + c;
+    if (valid > 0) {
+      int64_t row = r0 + grp;
+      int cb = 0, ce = 0, nb = 0, ne = 0;
+      int cj[BT_PF];
+      T cv[BT_PF];
+      if (row < r1) {
+        cb = J.rowptr[row];
+        ce = J.rowptr[row + 1];
+      }
 #pragma unroll
-  for (int u = 0; u < VEC; ++u) {
-    o[u] = sy[c + u] * fma(alpha, acc[u], beta * yi[u]);
-    if (X) o[u] = fma(sx[c + u], xv[u], o[u]);
-    if (Z) o[u] = fma(sz[c + u], zv[u], o[u]);
+      for (int q = 0; q < BT_PF; ++q) {
+        const bool in = cb + q < ce;
+        cj[q] = in ? J.col[cb + q] : 0;
+        cv[q] = in ? val[cb + q] : T(0);
+      }
+      if (row + R < r1) {
+        nb = J.rowptr[row + R];
+        ne = J.rowptr[row + R + 1];
+      }
+      for (; row < r1; row += R) {
+        int pb = 0, pe = 0;
+        if (row + 2 * R < r1) {
+          pb = J.rowptr[row + 2 * R];
+          pe = J.rowptr[row + 2 * R + 1];
+        }
+        int nj[BT_PF];
+        T nv[BT_PF];
+#pragma unroll
+        for (int q = 0; q < BT_PF; ++q) {
+          const bool in = nb + q < ne;
+          nj[q] = in ? J.col[nb + q] : 0;
+          nv[q] = in ? val[nb + q] : T(0);
+        }
+        T xv[VEC], zv[VEC], yi[VEC];
+        if (X) vload<T, VEC>(X + row * P.ldx + c, valid, xv);
+        if (Z) vload<T, VEC>(Z + row * P.ldz + c, valid, zv);
+        if (beta != T(0)) vload<T, VEC>(Yin + row * P.ldy + c, valid, yi);
+        T acc[VEC];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) acc[u] = T(0);
+        {
+          T y[BT_PF][VEC];
+#pragma unroll
+          for (int q = 0; q < BT_PF; ++q)
+            if (cb + q < ce) vload<T, VEC>(Yin + static_cast<int64_t>(cj[q]) * P.ldy + c, valid, y[q]);
+#pragma unroll
+          for (int q = 0; q < BT_PF; ++q)
+            if (cb + q < ce)
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) acc[u] = fma(cv[q], y[q][u], acc[u]);
+        }
+        for (int e = cb + BT_PF; e < ce; e += 4) {  // rows longer than the prefetched part
+          int jj[4];
+          T vv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool in = e + q < ce;
+            jj[q] = in ? J.col[e + q] : 0;
+            vv[q] = in ? val[e + q] : T(0);
+          }
+          T y[4][VEC];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (e + q < ce) vload<T, VEC>(Yin + static_cast<int64_t>(jj[q]) * P.ldy + c, valid, y[q]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (e + q < ce)
+#pragma unroll
+              for (int u = 0; u < VEC; ++u) acc[u] = fma(vv[q], y[q][u], acc[u]);
+        }
+        // the pass's multipliers from the table (cached reads, not held in registers
+        // across the gathers)
+        T my[VEC], mx[VEC], mz[VEC];
+        vload<T, VEC>(tab, valid, my);
+        vload<T, VEC>(tab + J.ldt, valid, mx);
+        vload<T, VEC>(tab + 2 * J.ldt, valid, mz);
+        T o[VEC];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          o[u] = my[u] * fma(alpha, acc[u], beta != T(0) ? beta * yi[u] : T(0));
+          if (X) o[u] = fma(mx[u], xv[u], o[u]);
+          if (Z) o[u] = fma(mz[u], zv[u], o[u]);
+        }
+        vstore<T, VEC>(out + row * P.ldo + c, valid, o);
+        if (want_ss) {
+#pragma unroll
+          for (int u = 0; u < VEC; ++u) {
+            if constexpr (sizeof(T) == 4) df_add_square(o[u], ss[u], sl[u]);
+            else ss[u] = fma(o[u], o[u], ss[u]);
+          }
+        }
+        cb = nb;
+        ce = ne;
+        nb = pb;
+        ne = pe;
+#pragma unroll
+        for (int q = 0; q < BT_PF; ++q) {
+          cj[q] = nj[q];
+          cv[q] = nv[q];
+        }
+      }
+    }
+    if (want_ss) {
+      // the R groups' sums of the tile's rows, then one lane per column writes them
+#pragma unroll
+      for (int u = 0; u < VEC; ++u)
+        for (int m = G; m < 32; m <<= 1) {
+          const Acc h2 = __shfl_xor_sync(0xffffffffu, ss[u], m);
+          if constexpr (sizeof(T) == 4) {
+            const Acc l2 = __shfl_xor_sync(0xffffffffu, sl[u], m);
+            df_add(ss[u], sl[u], h2, l2);
+          } else {
+            ss[u] += h2;
+          }
+        }
+      if (grp == 0)
+#pragma unroll
+        for (int u = 0; u < VEC; ++u)
+          if (u < valid) J.part[tile * J.ncols + c + u] = static_cast<double>(ss[u]) + static_cast<double>(sl[u]);
+    }
   }
-  vstore<T, VEC>(static_cast<T*>(P.out) + row * P.ldo + c, o);
 }
 
-__global__ void __launch_bounds__(BT_THREADS) batched_filter_kernel(const BJob* __restrict__ jobs,
-                                                                     const BPass* __restrict__ passes,
-                                                                     const int64_t* __restrict__ offsets, int njobs,
-                                                                     int dmax) {
+// one launch per element type and vector width present in the batch: a kernel that held
+// all four tile variants would need the registers of their union and spill.
+// offsets: dmax rows of per-pass tile offsets, then one row of table-prologue offsets
+// (degree x ncols per job), each of njobs + 1 entries; csoff: column-sum offsets.
+template <typename T, int VEC>
+__global__ void __launch_bounds__(BT_THREADS, ARB_BATCH_MIN_BLOCKS)
+    batched_filter_kernel(const BJob* __restrict__ jobs, const BPass* __restrict__ passes,
+                          const int64_t* __restrict__ offsets, int njobs, int dmax,
+                          const int64_t* __restrict__ csoff) {
   cg::grid_group g = cg::this_grid();
   const int lane = threadIdx.x & 31;
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * BT_WARPS + (threadIdx.x >> 5);
   const int64_t nw = static_cast<int64_t>(gridDim.x) * BT_WARPS;
+  auto job_of = [&](const int64_t* off, int64_t item) {
+    int lo = 0, hi = njobs - 1;  // last job with off[j] <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (off[mid] <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  };
+  // prologue: every job's multiplier table, then a barrier
+  {
+    const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nt = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t* toff = offsets + static_cast<int64_t>(dmax) * (njobs + 1);
+    for (int64_t item = gt; item < toff[njobs]; item += nt) {
+      const int j = job_of(toff, item);
+      const BJob& J = jobs[j];
+      const int64_t local = item - toff[j];
+      const int tt = static_cast<int>(local / J.ncols), c = static_cast<int>(local % J.ncols);
+      double my, mx, mz;
+      pass_multipliers(J, tt, c, my, mx, mz);
+      T* tab = static_cast<T*>(J.tab) + static_cast<int64_t>(tt) * 3 * J.ldt + c;
+      tab[0] = static_cast<T>(my);
+      tab[J.ldt] = static_cast<T>(mx);
+      tab[2 * J.ldt] = static_cast<T>(mz);
+    }
+    g.sync();
+  }
   for (int t = 0; t < dmax; ++t) {
     const int64_t* off = offsets + static_cast<int64_t>(t) * (njobs + 1);
     const int64_t total = off[njobs];
     for (int64_t item = gw; item < total; item += nw) {
-      int lo = 0, hi = njobs - 1;  // last job with off[j] <= item
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (off[mid] <= item) lo = mid;
-        else hi = mid - 1;
-      }
-      const BJob& J = jobs[lo];
-      const BPass& P = passes[static_cast<int64_t>(lo) * dmax + t];
-      const int64_t local = item - off[lo];
-      const int64_t row = local / J.nch;
-      const int chunk = static_cast<int>(local % J.nch);
-      if (J.fp32) {
-        if (J.vec == 4) batched_item<float, 4>(J, P, row, chunk, lane);
-        else batched_item<float, 1>(J, P, row, chunk, lane);
-      } else {
-        if (J.vec == 2) batched_item<double, 2>(J, P, row, chunk, lane);
-        else batched_item<double, 1>(J, P, row, chunk, lane);
-      }
+      const int j = job_of(off, item);
+      const BJob& J = jobs[j];
+      const BPass& P = passes[static_cast<int64_t>(j) * dmax + t];
+      batched_tile<T, VEC>(J, P, t, item - off[j], lane, t == J.degree - 1);
     }
     g.sync();
   }
-}
-
-// table[(3 t + {0,1,2}) * ncols + c] = {sy, sx, sz} of pass t, in the job's element type
-template <typename T>
-__global__ void batched_table_kernel(int d, CoefTable cc, const double* __restrict__ xs, int ncols, T* table) {
-  const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (idx >= static_cast<int64_t>(d) * ncols) return;
-  const int t = static_cast<int>(idx / ncols), c = static_cast<int>(idx % ncols);
-  const double s = xs ? xs[c] : 1.0;
-  const int j = d - 1 - t;
-  double sy, sx, sz;
-  if (d == 1) {
-    sy = cc.c[1] * s;
-    sx = cc.c[0] * s;
-    sz = 0.0;
-  } else {
-    sy = (t == 0) ? 2.0 * cc.c[d] * s : (t == d - 1 ? 1.0 : 2.0);
-    sx = cc.c[j] * s;
-    sz = (j + 2 == d) ? -cc.c[d] * s : -1.0;
-  }
-  table[(3 * static_cast<int64_t>(t) + 0) * ncols + c] = static_cast<T>(sy);
-  table[(3 * static_cast<int64_t>(t) + 1) * ncols + c] = static_cast<T>(sx);
-  table[(3 * static_cast<int64_t>(t) + 2) * ncols + c] = static_cast<T>(sz);
-}
-
-// per-job column sums of squares: block b of job j sums rows [b*R, (b+1)*R)
-template <typename T>
-__global__ void colss_kernel(int64_t n, const T* __restrict__ Y, int64_t ldy, int ncols, int64_t rows,
-                             double* __restrict__ part) {
-  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows, r1 = min(n, r0 + rows);
-  for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+  // column sums of squares: one warp per (job, column), tiles strided over the lanes and
+  // added in a fixed tree
+  const int64_t ctotal = csoff[njobs];
+  for (int64_t item = gw; item < ctotal; item += nw) {
+    const int j = job_of(csoff, item);
+    const BJob& J = jobs[j];
+    const int c = static_cast<int>(item - csoff[j]);
     double s = 0.0;
-    for (int64_t r = r0; r < r1; ++r) {
-      const double v = static_cast<double>(Y[r * ldy + c]);
-      s = fma(v, v, s);
-    }
-    part[static_cast<size_t>(blockIdx.x) * ncols + c] = s;
+    for (int64_t tile = lane; tile < J.tiles; tile += 32) s += J.part[tile * J.ncols + c];
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) J.colss[c] = s;
   }
-}
-
-__global__ void colss_reduce_kernel(const double* __restrict__ part, int nb, int ncols, double* __restrict__ out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncols) return;
-  double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += part[static_cast<size_t>(b) * ncols + c];
-  out[c] = s;
 }
 
 inline bool al(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// kernel of a job class: 0 FP32 x4, 1 FP32 x1, 2 FP64 x2, 3 FP64 x1
+const void* class_kernel(int cls) {
+  switch (cls) {
+    case 0: return reinterpret_cast<const void*>(batched_filter_kernel<float, 4>);
+    case 1: return reinterpret_cast<const void*>(batched_filter_kernel<float, 1>);
+    case 2: return reinterpret_cast<const void*>(batched_filter_kernel<double, 2>);
+    default: return reinterpret_cast<const void*>(batched_filter_kernel<double, 1>);
+  }
+}
+
 }  // namespace
 
 // The batched filter in two parts: prepare() validates the jobs, sizes the workspaces and
-// uploads the descriptors (it synchronises the stream); launch() issues the per-job
-// coefficient tables, the one persistent cooperative launch and the per-job column sums -
-// kernels only, with no allocation and no synchronisation, so that a caller may capture it
-// into a CUDA graph and replay it while the descriptors (re-uploaded by prepare) keep
-// their device addresses.
+// uploads the descriptors (it synchronises the stream); launch() issues the persistent
+// cooperative launches (one per job class present) - kernels only, with no allocation and
+// no synchronisation, so that a caller may capture them into a CUDA graph and replay it
+// while the descriptors (re-uploaded by prepare) keep their device addresses.
 arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs, BatchPlan* out) {
   out->njobs = njobs;
   out->jobs.assign(jobs, jobs + njobs);
-  out->tables.clear();
-  out->coef.clear();
+  for (auto& c : out->cls) c = BatchPlan::Class{};
   if (njobs <= 0) return ARB_OK;
   int dmax = 0;
-  size_t work_bytes = 0, table_bytes = 0;
-  std::vector<int64_t> ldw(njobs);
+  size_t work_bytes = 0, ncoef = 0;
   for (int j = 0; j < njobs; ++j) {
     const arb_filter_job& J = jobs[j];
     if (!J.mat || !J.coef || !J.X || !J.Y || J.ncols <= 0 || J.ldx < J.ncols || J.ldy < J.ncols || !(J.b > J.a) ||
@@ -256,46 +396,84 @@ arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_j
       return set_error(ctx, ARB_INVALID_ARG, "filter_batched: bad job");
     dmax = std::max(dmax, J.degree);
     const size_t es = J.fp32 ? 4 : 8;
-    ldw[j] = (J.ncols + 3) / 4 * 4;
-    work_bytes += 2 * static_cast<size_t>(J.mat->n) * ldw[j] * es + 256;
-    table_bytes += 3 * static_cast<size_t>(J.degree) * J.ncols * es + 256;
+    const size_t ldw = (J.ncols + 3) / 4 * 4;
+    work_bytes += 2 * static_cast<size_t>(J.mat->n) * ldw * es + 512;
+    work_bytes += 3 * static_cast<size_t>(J.degree) * ldw * es + 256;  // multiplier table
+    ncoef += static_cast<size_t>(J.degree) + 1;
     if (J.fp32) ARB_TRY(ensure_val32(ctx, J.mat));
   }
-  char *work, *tables;
+  char* work;
   ARB_TRY(ws<char>(ctx, WS_BATCH_WORK, work_bytes, &work));
-  ARB_TRY(ws<char>(ctx, WS_BATCH_TABLE, table_bytes, &tables));
+  // class of every job (element type; 16-byte lanes when the leading dimensions and bases
+  // allow, a ragged last vector of a row being read and written element by element), and
+  // the jobs in class order
+  std::vector<int> cls(njobs), order;
+  for (int j = 0; j < njobs; ++j) {
+    const arb_filter_job& J = jobs[j];
+    const int want = J.fp32 ? 4 : 2;
+    const int64_t ldw = (J.ncols + 3) / 4 * 4;
+    const bool wide = J.ldx % want == 0 && J.ldy % want == 0 && ldw % want == 0 && al(J.X, 16) && al(J.Y, 16);
+    cls[j] = (J.fp32 ? 0 : 2) + (wide ? 0 : 1);
+  }
+  for (int k = 0; k < 4; ++k)
+    for (int j = 0; j < njobs; ++j)
+      if (cls[j] == k) order.push_back(j);
   std::vector<BJob> hj(njobs);
   std::vector<BPass> hp(static_cast<size_t>(njobs) * dmax);
-  std::vector<int64_t> hoff(static_cast<size_t>(dmax) * (njobs + 1), 0);
-  size_t wo = 0, to = 0;
-  for (int j = 0; j < njobs; ++j) {
+  std::vector<double> hcoef;
+  hcoef.reserve(ncoef);
+  std::vector<size_t> coef_at(njobs), part_at(njobs);
+  size_t wo = 0, part_total = 0;
+  for (int o = 0; o < njobs; ++o) {
+    const int j = order[o];
     const arb_filter_job& J = jobs[j];
     const bool f = J.fp32 != 0;
     const size_t es = f ? 4 : 8;
     const int64_t n = J.mat->n;
+    const int64_t ldw = (J.ncols + 3) / 4 * 4;
     char* W1 = work + wo;
-    wo += (static_cast<size_t>(n) * ldw[j] * es + 255) / 256 * 256;
+    wo += (static_cast<size_t>(n) * ldw * es + 255) / 256 * 256;
     char* W2 = work + wo;
-    wo += (static_cast<size_t>(n) * ldw[j] * es + 255) / 256 * 256;
-    char* tab = tables + to;
-    to += (3 * static_cast<size_t>(J.degree) * J.ncols * es + 255) / 256 * 256;
+    wo += (static_cast<size_t>(n) * ldw * es + 255) / 256 * 256;
+    char* tab = work + wo;
+    wo += (3 * static_cast<size_t>(J.degree) * ldw * es + 255) / 256 * 256;
     const FilterPlan plan = make_filter_plan(J.op_scale, J.op_shift, J.a, J.b, J.degree, J.coef);
-    CoefTable cc;
-    for (int i = 0; i < 64; ++i) cc.c[i] = (i <= J.degree) ? plan.coef[i] : 0.0;
-    const int64_t cnt = static_cast<int64_t>(J.degree) * J.ncols;
-    const int tb = static_cast<int>((cnt + 255) / 256);
-    out->tables.push_back(BatchPlan::Table{f, J.degree, J.ncols, tb, cc, J.xscale, tab});
-    // vector width: 16-byte lanes when the columns, leading dimensions and bases allow
-    int vec = 1;
-    const int want = f ? 4 : 2;
-    if (J.ncols % want == 0 && J.ldx % want == 0 && J.ldy % want == 0 && ldw[j] % want == 0 && al(J.X, 16) &&
-        al(J.Y, 16) && J.ncols > 32 * (want / 2) && (J.mat->tune_vec == 0 || J.mat->tune_vec >= want))
-      vec = want;
-    const int nch = (J.ncols + 32 * vec - 1) / (32 * vec);
-    hj[j] = BJob{n, J.mat->rowptr, J.mat->col, f ? static_cast<const void*>(J.mat->val32) : J.mat->val, J.ncols, nch,
-                 vec, f ? 1 : 0};
+    coef_at[o] = hcoef.size();
+    for (int i = 0; i <= J.degree; ++i) hcoef.push_back(plan.coef[i]);
+    const int vec = (cls[j] & 1) ? 1 : (f ? 4 : 2);
+    // lanes per row: the power of two covering the row's vectors, at most a warp
+    const int lanes = (J.ncols + vec - 1) / vec;
+    int glog = 0;
+    while ((1 << glog) < lanes && glog < 5) ++glog;
+    const int G = 1 << glog, R = 32 >> glog;
+    const int nch = (J.ncols + G * vec - 1) / (G * vec);
+    // 8 to 64 row steps per tile: the instance lookup is amortised and a large instance
+    // leaves at most ~1024 tiles of partial column sums
+    const int64_t iters = std::min<int64_t>(64, std::max<int64_t>(8, (n + R * 1024 - 1) / (R * 1024)));
+    const int32_t tile_rows = static_cast<int32_t>(R * iters);
+    const int64_t tiles = (n + tile_rows - 1) / tile_rows;
+    part_at[o] = part_total;
+    if (J.colss) part_total += static_cast<size_t>(tiles) * J.ncols;
+    BJob& B = hj[o];
+    B.n = n;
+    B.rowptr = J.mat->rowptr;
+    B.col = J.mat->col;
+    B.val = f ? static_cast<const void*>(J.mat->val32) : static_cast<const void*>(J.mat->val);
+    B.coef = nullptr;  // device addresses below
+    B.xs = J.xscale;
+    B.colss = J.colss;
+    B.part = nullptr;
+    B.tab = tab;
+    B.tiles = tiles;
+    B.tile_rows = tile_rows;
+    B.ncols = J.ncols;
+    B.nch = nch;
+    B.vec = vec;
+    B.fp32 = f ? 1 : 0;
+    B.glog = glog;
+    B.degree = J.degree;
+    B.ldt = static_cast<int32_t>(ldw);
     // buffer rotation of the recurrence (as in the single-instance filter)
-    auto tabp = [&](int t, int which) -> const void* { return tab + ((3 * static_cast<size_t>(t) + which) * J.ncols) * es; };
     const int d = J.degree;
     const void* cur = nullptr;
     const void* prev = nullptr;
@@ -303,9 +481,6 @@ arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_j
       BPass P{};
       P.alpha = plan.alpha;
       P.beta = plan.beta;
-      P.sy = tabp(t, 0);
-      P.sx = tabp(t, 1);
-      P.sz = tabp(t, 2);
       const int jdx = d - 1 - t;
       const bool last = (t == d - 1);
       if (t == 0) {
@@ -313,7 +488,7 @@ arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_j
         P.ldy = J.ldx;
       } else {
         P.Yin = cur;
-        P.ldy = ldw[j];
+        P.ldy = ldw;
       }
       if (plan.coef[d == 1 ? 0 : jdx] != 0.0) {
         P.X = J.X;
@@ -322,7 +497,7 @@ arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_j
       if (t >= 1) {
         if (prev) {
           P.Z = prev;
-          P.ldz = ldw[j];
+          P.ldz = ldw;
         } else if (plan.coef[d] != 0.0) {
           P.Z = J.X;
           P.ldz = J.ldx;
@@ -333,97 +508,105 @@ arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_j
         P.ldo = J.ldy;
       } else {
         P.out = (t == 0) ? static_cast<void*>(W1) : (prev ? const_cast<void*>(prev) : static_cast<void*>(W2));
-        P.ldo = ldw[j];
+        P.ldo = ldw;
       }
-      hp[static_cast<size_t>(j) * dmax + t] = P;
+      hp[static_cast<size_t>(o) * dmax + t] = P;
       prev = (t == 0) ? nullptr : cur;
       cur = P.out;
     }
-    for (int t = 0; t < dmax; ++t) {
-      int64_t* off = hoff.data() + static_cast<size_t>(t) * (njobs + 1);
-      off[j + 1] = (t < d) ? static_cast<int64_t>(n) * nch : 0;
+  }
+  // per class: pass offsets over its tiles (dmax rows), the table prologue's offsets (one
+  // row) and column-sum offsets over its columns
+  std::vector<int64_t> hoff, hcs;
+  size_t off_at[4] = {0, 0, 0, 0}, cs_at[4] = {0, 0, 0, 0};
+  int first = 0;
+  for (int k = 0; k < 4; ++k) {
+    int count = 0;
+    while (first + count < njobs && cls[order[first + count]] == k) ++count;
+    out->cls[k].first = first;
+    out->cls[k].count = count;
+    off_at[k] = hoff.size();
+    cs_at[k] = hcs.size();
+    if (count > 0) {
+      for (int t = 0; t < dmax; ++t) {
+        int64_t acc = 0;
+        hoff.push_back(0);
+        for (int o = first; o < first + count; ++o) {
+          acc += (t < hj[o].degree) ? hj[o].tiles : 0;
+          hoff.push_back(acc);
+        }
+      }
+      int64_t acc = 0;
+      hoff.push_back(0);
+      for (int o = first; o < first + count; ++o) {
+        acc += static_cast<int64_t>(hj[o].degree) * hj[o].ncols;
+        hoff.push_back(acc);
+      }
+      acc = 0;
+      hcs.push_back(0);
+      for (int o = first; o < first + count; ++o) {
+        acc += jobs[order[o]].colss ? hj[o].ncols : 0;
+        hcs.push_back(acc);
+      }
     }
+    first += count;
   }
-  for (int t = 0; t < dmax; ++t) {
-    int64_t* off = hoff.data() + static_cast<size_t>(t) * (njobs + 1);
-    for (int j = 0; j < njobs; ++j) off[j + 1] += off[j];
-  }
-  // descriptors to the device
-  const size_t bj = hj.size() * sizeof(BJob), bp = hp.size() * sizeof(BPass), bo = hoff.size() * sizeof(int64_t);
+  double* part = nullptr;
+  if (part_total) ARB_TRY(ws<double>(ctx, WS_SS_PART, part_total, &part));
+  // descriptors to the device: jobs, passes, offsets, column-sum offsets, coefficients
+  const size_t bj = hj.size() * sizeof(BJob), bp = hp.size() * sizeof(BPass), bo = hoff.size() * sizeof(int64_t),
+               bc = hcs.size() * sizeof(int64_t), bf = hcoef.size() * sizeof(double);
+  const size_t bytes = bj + bp + bo + bc + bf;
   char* desc;
-  ARB_TRY(ws<char>(ctx, WS_BATCH_DESC, bj + bp + bo + 512, &desc));
+  ARB_TRY(ws<char>(ctx, WS_BATCH_DESC, bytes + 512, &desc));
+  const double* dcoef = reinterpret_cast<const double*>(desc + bj + bp + bo + bc);
+  for (int o = 0; o < njobs; ++o) {
+    hj[o].coef = dcoef + coef_at[o];
+    hj[o].part = jobs[order[o]].colss ? part + part_at[o] : nullptr;
+  }
   void* st;
-  ARB_TRY(host_stage(ctx, bj + bp + bo + 512, &st));
+  ARB_TRY(host_stage(ctx, bytes + 512, &st));
   ARB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // staging area free
   char* sp = static_cast<char*>(st);
   memcpy(sp, hj.data(), bj);
   memcpy(sp + bj, hp.data(), bp);
   memcpy(sp + bj + bp, hoff.data(), bo);
-  ARB_CUDA(ctx, cudaMemcpyAsync(desc, sp, bj + bp + bo, cudaMemcpyHostToDevice, ctx->stream));
-  const BJob* dj = reinterpret_cast<const BJob*>(desc);
-  const BPass* dp = reinterpret_cast<const BPass*>(desc + bj);
-  const int64_t* doff = reinterpret_cast<const int64_t*>(desc + bj + bp);
+  memcpy(sp + bj + bp + bo, hcs.data(), bc);
+  memcpy(sp + bj + bp + bo + bc, hcoef.data(), bf);
+  ARB_CUDA(ctx, cudaMemcpyAsync(desc, sp, bytes, cudaMemcpyHostToDevice, ctx->stream));
   out->dmax = dmax;
-  int per_sm = 0;
-  ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_filter_kernel, BT_THREADS, 0));
-  out->coop_grid = std::max(1, std::max(1, per_sm) * ctx->num_sms / std::max(1, ctx->coop_share));
-  out->dj = dj;
-  out->dp = dp;
-  out->doff = doff;
-  // column-sum partials: the largest any job needs
-  size_t part_max = 0;
-  for (int j = 0; j < njobs; ++j) {
-    if (!jobs[j].colss) continue;
-    const int64_t n = jobs[j].mat->n;
-    const int64_t rows = std::max<int64_t>(256, (n + 4 * ctx->num_sms - 1) / (4 * ctx->num_sms));
-    part_max = std::max(part_max, static_cast<size_t>((n + rows - 1) / rows) * jobs[j].ncols);
+  out->dj = desc;
+  out->dp = desc + bj;
+  for (int k = 0; k < 4; ++k) {
+    BatchPlan::Class& c = out->cls[k];
+    if (c.count == 0) continue;
+    c.doff = reinterpret_cast<const int64_t*>(desc + bj + bp) + off_at[k];
+    c.dcs = reinterpret_cast<const int64_t*>(desc + bj + bp + bo) + cs_at[k];
+    int per_sm = 0;
+    ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, class_kernel(k), BT_THREADS, 0));
+    c.grid = std::max(1, std::max(1, per_sm) * ctx->num_sms / std::max(1, ctx->coop_share));
   }
-  if (part_max) ARB_TRY(ws<double>(ctx, WS_SS_PART, part_max, &out->part));
+  out->part = part;
   return ARB_OK;
 }
 
 arb_status filter_batched_launch(arb_ctx ctx, const BatchPlan& plan) {
-  const int32_t njobs = plan.njobs;
-  if (njobs <= 0) return ARB_OK;
-  for (const auto& tb : plan.tables) {
-    if (tb.fp32)
-      batched_table_kernel<float><<<tb.blocks, 256, 0, ctx->stream>>>(tb.d, tb.cc, tb.xscale, tb.ncols,
-                                                                      static_cast<float*>(tb.table));
-    else
-      batched_table_kernel<double><<<tb.blocks, 256, 0, ctx->stream>>>(tb.d, tb.cc, tb.xscale, tb.ncols,
-                                                                       static_cast<double*>(tb.table));
-    ARB_LAUNCHED(ctx);
-  }
-  const BJob* dj = static_cast<const BJob*>(plan.dj);
-  const BPass* dp = static_cast<const BPass*>(plan.dp);
-  const int64_t* doff = plan.doff;
-  int dmax = plan.dmax;
-  const arb_filter_job* jobs = plan.jobs.data();
-  const int grid = plan.coop_grid;
-  int nj = njobs;
-  void* args[] = {&dj, &dp, &doff, &nj, &dmax};
-  ARB_CUDA(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(batched_filter_kernel), dim3(grid),
-                                            dim3(BT_THREADS), args, 0, ctx->stream));
-  ARB_LAUNCHED(ctx);
-  // column sums of squares of each result (the MPM normalisation)
-  for (int j = 0; j < njobs; ++j) {
-    const arb_filter_job& J = jobs[j];
-    if (!J.colss) continue;
-    const int64_t n = J.mat->n;
-    const int64_t rows = std::max<int64_t>(256, (n + 4 * ctx->num_sms - 1) / (4 * ctx->num_sms));
-    const int nb = static_cast<int>((n + rows - 1) / rows);
-    double* part = plan.part;
-    if (J.fp32)
-      colss_kernel<float><<<nb, 128, 0, ctx->stream>>>(n, static_cast<const float*>(J.Y), J.ldy, J.ncols, rows, part);
-    else
-      colss_kernel<double><<<nb, 128, 0, ctx->stream>>>(n, static_cast<const double*>(J.Y), J.ldy, J.ncols, rows, part);
-    ARB_LAUNCHED(ctx);
-    colss_reduce_kernel<<<(J.ncols + 127) / 128, 128, 0, ctx->stream>>>(part, nb, J.ncols, J.colss);
+  if (plan.njobs <= 0) return ARB_OK;
+  for (int k = 0; k < 4; ++k) {
+    const BatchPlan::Class& c = plan.cls[k];
+    if (c.count == 0) continue;
+    const BJob* dj = static_cast<const BJob*>(plan.dj) + c.first;
+    const BPass* dp = static_cast<const BPass*>(plan.dp) + static_cast<size_t>(c.first) * plan.dmax;
+    const int64_t* doff = c.doff;
+    const int64_t* dcs = c.dcs;
+    int dmax = plan.dmax;
+    int nj = c.count;
+    void* args[] = {&dj, &dp, &doff, &nj, &dmax, &dcs};
+    ARB_CUDA(ctx, cudaLaunchCooperativeKernel(class_kernel(k), dim3(c.grid), dim3(BT_THREADS), args, 0, ctx->stream));
     ARB_LAUNCHED(ctx);
   }
   return ARB_OK;
 }
-
 
 arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs) {
   BatchPlan plan;

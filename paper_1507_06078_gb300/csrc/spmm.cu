@@ -213,9 +213,16 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
     csx[u] = P.X ? static_cast<T>(P.sx[cu]) : T(0);
     csz[u] = P.Z ? static_cast<T>(P.sz[cu]) : T(0);
   }
+  // column reductions: FP64 for FP64 blocks; for FP32 blocks double-float pairs (FP32 hi,
+  // lo with error-free product and sum transforms), which keep the FP64 pipe (a small
+  // fraction of the FP32 rate on this GPU) out of the row loop
   double red[VEC];
+  float rhi[VEC], rlo[VEC];
 #pragma unroll
-  for (int u = 0; u < VEC; ++u) red[u] = 0.0;
+  for (int u = 0; u < VEC; ++u) {
+    red[u] = 0.0;
+    rhi[u] = rlo[u] = 0.f;
+  }
   // SHORT pipeline state: indices of the next row, row pointers of the one after
   int n_jc = 0, n_cnt = 0, p_beg = 0, p_end = 0;
   T n_av = T(0);
@@ -360,13 +367,27 @@ __global__ void __launch_bounds__(SPMM_THREADS, ARB_SPMM_MIN_BLOCKS) spmm_fused_
       if constexpr (RED) {
 #pragma unroll
         for (int u = 0; u < VEC; ++u) {
-          const double od = static_cast<double>(o[u]);
-          red[u] += P.dot_with_yin ? od * static_cast<double>(yi[u]) : od * od;
+          if constexpr (std::is_same<T, float>::value) {
+            const float b = P.dot_with_yin ? yi[u] : o[u];
+            const float pr = o[u] * b;
+            const float pe = fmaf(o[u], b, -pr);
+            const float sm = rhi[u] + pr;
+            const float bp = sm - rhi[u];
+            rlo[u] += ((rhi[u] - (sm - bp)) + (pr - bp)) + pe;
+            rhi[u] = sm;
+          } else {
+            const double od = static_cast<double>(o[u]);
+            red[u] += P.dot_with_yin ? od * static_cast<double>(yi[u]) : od * od;
+          }
         }
       }
     }
   }
   if constexpr (RED) {
+    if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) red[u] = static_cast<double>(rhi[u]) + static_cast<double>(rlo[u]);
+    }
     if (act)
 #pragma unroll
       for (int u = 0; u < VEC; ++u) s_red[static_cast<size_t>(warp) * ncols + c + u] = red[u];
