@@ -1708,6 +1708,7 @@ std::string round_key(const BatchPlan& plan) {
     put(&c.grid, sizeof(c.grid));
     put(&c.doff, sizeof(c.doff));
     put(&c.dcs, sizeof(c.dcs));
+    put(&c.tickets, sizeof(c.tickets));
   }
   return key;
 }

@@ -361,6 +361,7 @@ struct BatchPlan {
     int grid = 0;
     const int64_t* doff = nullptr;  // pass and table-prologue offsets over the class's jobs
     const int64_t* dcs = nullptr;   // column-sum offsets over the class's columns
+    unsigned long long* tickets = nullptr;  // per-pass tile counters
   };
   int32_t njobs = 0;
   int dmax = 0;

@@ -74,10 +74,19 @@ struct BPass {
   double alpha, beta;
 };
 
-// VEC consecutive elements of a row; those at or past `valid` are left alone / zero
+// element offset r * ld of row r in a block of leading dimension ld (both below 2^31)
+__device__ __forceinline__ int64_t roff(int64_t r, int64_t ld) {
+  return static_cast<int64_t>(static_cast<int32_t>(r)) * static_cast<int32_t>(ld);
+}
+
+// VEC consecutive elements of a row.  For VEC > 1 the whole vector is read even where the
+// row's last vector is ragged (valid < VEC), except in a block's last row (tail = true),
+// which may end at the block's last column: the vector classes have leading dimensions
+// that are multiples of VEC, so such a read stays inside the row's leading dimension, and
+// the extra lanes' results are never stored.  For VEC == 1, valid <= 0 reads nothing.
 template <typename T, int VEC>
-__device__ __forceinline__ void vload(const T* p, int valid, T (&r)[VEC]) {
-  if (valid >= VEC) {
+__device__ __forceinline__ void vload(const T* p, int valid, T (&r)[VEC], bool tail = false) {
+  if (valid >= VEC || (VEC > 1 && !tail)) {
     if constexpr (VEC == 4 && sizeof(T) == 4) {
       const float4 t = *reinterpret_cast<const float4*>(p);
       r[0] = t.x;
@@ -164,6 +173,7 @@ __device__ void batched_tile(const BJob& J, const BPass& P, int t, int64_t tile,
   T* out = static_cast<T*>(P.out);
   const T* val = static_cast<const T*>(J.val);
   const T alpha = static_cast<T>(P.alpha), beta = static_cast<T>(P.beta);
+  const int nlast = static_cast<int>(J.n - 1);
   // column sums of squares of the tile's rows: FP64 for FP64 instances, double-float
   // (hi, lo) for FP32 ones
   using Acc = typename std::conditional<sizeof(T) == 4, float, double>::type;
@@ -207,10 +217,11 @@ __device__ void batched_tile(const BJob& J, const BPass& P, int t, int64_t tile,
           nj[q] = in ? J.col[nb + q] : 0;
           nv[q] = in ? val[nb + q] : T(0);
         }
+        const bool tail = row == nlast;
         T xv[VEC], zv[VEC], yi[VEC];
-        if (X) vload<T, VEC>(X + row * P.ldx + c, valid, xv);
-        if (Z) vload<T, VEC>(Z + row * P.ldz + c, valid, zv);
-        if (beta != T(0)) vload<T, VEC>(Yin + row * P.ldy + c, valid, yi);
+        if (X) vload<T, VEC>(X + roff(row, P.ldx) + c, valid, xv, tail);
+        if (Z) vload<T, VEC>(Z + roff(row, P.ldz) + c, valid, zv, tail);
+        if (beta != T(0)) vload<T, VEC>(Yin + roff(row, P.ldy) + c, valid, yi, tail);
         T acc[VEC];
 #pragma unroll
         for (int u = 0; u < VEC; ++u) acc[u] = T(0);
@@ -218,7 +229,7 @@ __device__ void batched_tile(const BJob& J, const BPass& P, int t, int64_t tile,
           T y[BT_PF][VEC];
 #pragma unroll
           for (int q = 0; q < BT_PF; ++q)
-            if (cb + q < ce) vload<T, VEC>(Yin + static_cast<int64_t>(cj[q]) * P.ldy + c, valid, y[q]);
+            if (cb + q < ce) vload<T, VEC>(Yin + roff(cj[q], P.ldy) + c, valid, y[q], cj[q] == nlast);
 #pragma unroll
           for (int q = 0; q < BT_PF; ++q)
             if (cb + q < ce)
@@ -237,7 +248,7 @@ __device__ void batched_tile(const BJob& J, const BPass& P, int t, int64_t tile,
           T y[4][VEC];
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            if (e + q < ce) vload<T, VEC>(Yin + static_cast<int64_t>(jj[q]) * P.ldy + c, valid, y[q]);
+            if (e + q < ce) vload<T, VEC>(Yin + roff(jj[q], P.ldy) + c, valid, y[q], jj[q] == nlast);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             if (e + q < ce)
@@ -257,7 +268,7 @@ __device__ void batched_tile(const BJob& J, const BPass& P, int t, int64_t tile,
           if (X) o[u] = fma(mx[u], xv[u], o[u]);
           if (Z) o[u] = fma(mz[u], zv[u], o[u]);
         }
-        vstore<T, VEC>(out + row * P.ldo + c, valid, o);
+        vstore<T, VEC>(out + roff(row, P.ldo) + c, valid, o);
         if (want_ss) {
 #pragma unroll
           for (int u = 0; u < VEC; ++u) {
@@ -305,7 +316,7 @@ template <typename T, int VEC>
 __global__ void __launch_bounds__(BT_THREADS, ARB_BATCH_MIN_BLOCKS)
     batched_filter_kernel(const BJob* __restrict__ jobs, const BPass* __restrict__ passes,
                           const int64_t* __restrict__ offsets, int njobs, int dmax,
-                          const int64_t* __restrict__ csoff) {
+                          const int64_t* __restrict__ csoff, unsigned long long* __restrict__ tickets) {
   cg::grid_group g = cg::this_grid();
   const int lane = threadIdx.x & 31;
   const int64_t gw = static_cast<int64_t>(blockIdx.x) * BT_WARPS + (threadIdx.x >> 5);
@@ -319,7 +330,9 @@ __global__ void __launch_bounds__(BT_THREADS, ARB_BATCH_MIN_BLOCKS)
     }
     return lo;
   };
-  // prologue: every job's multiplier table, then a barrier
+  // prologue: every job's multiplier table and the passes' tile tickets, then a barrier
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < dmax; i += blockDim.x) tickets[i] = 0ull;
   {
     const int64_t gt = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nt = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -341,11 +354,19 @@ __global__ void __launch_bounds__(BT_THREADS, ARB_BATCH_MIN_BLOCKS)
   for (int t = 0; t < dmax; ++t) {
     const int64_t* off = offsets + static_cast<int64_t>(t) * (njobs + 1);
     const int64_t total = off[njobs];
-    for (int64_t item = gw; item < total; item += nw) {
+    // tiles handed out in order by a ticket counter, so warps that drew short tiles take
+    // more and the pass ends within about one tile of its average; the next ticket is
+    // drawn before the current tile runs
+    unsigned long long tk = 0;
+    if (lane == 0) tk = atomicAdd(tickets + t, 1ull);
+    int64_t item = static_cast<int64_t>(__shfl_sync(0xffffffffu, tk, 0));
+    while (item < total) {
+      if (lane == 0) tk = atomicAdd(tickets + t, 1ull);
       const int j = job_of(off, item);
       const BJob& J = jobs[j];
       const BPass& P = passes[static_cast<int64_t>(j) * dmax + t];
       batched_tile<T, VEC>(J, P, t, item - off[j], lane, t == J.degree - 1);
+      item = static_cast<int64_t>(__shfl_sync(0xffffffffu, tk, 0));
     }
     g.sync();
   }
@@ -556,7 +577,8 @@ arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_j
   // descriptors to the device: jobs, passes, offsets, column-sum offsets, coefficients
   const size_t bj = hj.size() * sizeof(BJob), bp = hp.size() * sizeof(BPass), bo = hoff.size() * sizeof(int64_t),
                bc = hcs.size() * sizeof(int64_t), bf = hcoef.size() * sizeof(double);
-  const size_t bytes = bj + bp + bo + bc + bf;
+  const size_t bt = 4 * static_cast<size_t>(dmax) * sizeof(unsigned long long);  // tile tickets, zeroed
+  const size_t bytes = bj + bp + bo + bc + bf + bt;
   char* desc;
   ARB_TRY(ws<char>(ctx, WS_BATCH_DESC, bytes + 512, &desc));
   const double* dcoef = reinterpret_cast<const double*>(desc + bj + bp + bo + bc);
@@ -573,6 +595,7 @@ arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_j
   memcpy(sp + bj + bp, hoff.data(), bo);
   memcpy(sp + bj + bp + bo, hcs.data(), bc);
   memcpy(sp + bj + bp + bo + bc, hcoef.data(), bf);
+  memset(sp + bj + bp + bo + bc + bf, 0, bt);
   ARB_CUDA(ctx, cudaMemcpyAsync(desc, sp, bytes, cudaMemcpyHostToDevice, ctx->stream));
   out->dmax = dmax;
   out->dj = desc;
@@ -582,6 +605,7 @@ arb_status filter_batched_prepare(arb_ctx ctx, int32_t njobs, const arb_filter_j
     if (c.count == 0) continue;
     c.doff = reinterpret_cast<const int64_t*>(desc + bj + bp) + off_at[k];
     c.dcs = reinterpret_cast<const int64_t*>(desc + bj + bp + bo) + cs_at[k];
+    c.tickets = reinterpret_cast<unsigned long long*>(desc + bj + bp + bo + bc + bf) + static_cast<size_t>(k) * dmax;
     int per_sm = 0;
     ARB_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, class_kernel(k), BT_THREADS, 0));
     c.grid = std::max(1, std::max(1, per_sm) * ctx->num_sms / std::max(1, ctx->coop_share));
@@ -599,9 +623,10 @@ arb_status filter_batched_launch(arb_ctx ctx, const BatchPlan& plan) {
     const BPass* dp = static_cast<const BPass*>(plan.dp) + static_cast<size_t>(c.first) * plan.dmax;
     const int64_t* doff = c.doff;
     const int64_t* dcs = c.dcs;
+    unsigned long long* tk = c.tickets;
     int dmax = plan.dmax;
     int nj = c.count;
-    void* args[] = {&dj, &dp, &doff, &nj, &dmax, &dcs};
+    void* args[] = {&dj, &dp, &doff, &nj, &dmax, &dcs, &tk};
     ARB_CUDA(ctx, cudaLaunchCooperativeKernel(class_kernel(k), dim3(c.grid), dim3(BT_THREADS), args, 0, ctx->stream));
     ARB_LAUNCHED(ctx);
   }
