@@ -2,6 +2,8 @@
 // built from the kernels of spmm.cu, dense.cu and jacobi.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <type_traits>
 #include <vector>
 
@@ -189,7 +191,7 @@ arb_status project_out(arb_ctx ctx, int64_t n, const T* Q, int64_t ldq, int32_t 
 // Z -> Z D W_r Theta_r^{-1/2}.
 template <typename T>
 static arb_status svqb_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* out, int64_t ldo,
-                            int32_t* rank) {
+                            int32_t* rank, bool have_gram = false) {
   double *G, *Gh, *W, *d, *theta;
   int32_t* r_dev;
   const size_t mm = static_cast<size_t>(m) * m;
@@ -199,7 +201,7 @@ static arb_status svqb_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int
   ARB_TRY(ws<double>(ctx, WS_VEC0, m, &d));
   ARB_TRY(ws<double>(ctx, WS_VEC1, m, &theta));
   ARB_TRY(ws<int32_t>(ctx, WS_INT0, 4, &r_dev));
-  ARB_TRY(gram<T>(ctx, n, Z, ldz, m, Z, ldz, m, G, m));
+  if (!have_gram) ARB_TRY(gram<T>(ctx, n, Z, ldz, m, Z, ldz, m, G, m));  // else G = Z^T Z already
   ARB_TRY(svqb_prep(ctx, m, G, m, Gh, d));
   ARB_TRY(syevj(ctx, m, Gh, m, theta, W, m, nullptr, jac_tol<T>(ctx), jac_df<T>(ctx)));
   ARB_TRY(svqb_finish(ctx, m, theta, W, m, d, orth_tau<T>(m), Gh, r_dev));
@@ -210,12 +212,22 @@ static arb_status svqb_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int
   return ARB_OK;
 }
 
+// ARB_TRACE set in the environment: one line per orthonormalisation on stderr
+inline bool orth_trace() {
+  static const bool on = getenv("ARB_TRACE") != nullptr;
+  return on;
+}
+
 // One CholeskyQR pass: G = Z^T Z, D = diag(G)^{-1/2}, D G D = R^T R (FP64 Cholesky whose
-// pivots must exceed thr), out = Z D R^{-1}.  *ok = false when the factorisation broke
-// down; out is then not written.
+// pivots must exceed thr), out = Z D R^{-1}.  With rank_test the pass also requires the
+// 1-norm reciprocal condition number of D G D, from its Cholesky factor, to exceed thr: a
+// symmetric matrix's 2-norm condition number is at most its 1-norm one, so the block is then
+// one whose eigen-truncated Gram pass would keep every direction.  *ok = false when the
+// factorisation broke down or the test failed; out is then not written, and G (the
+// WS_SMALL0 workspace) still holds Z^T Z.
 template <typename T>
 static arb_status cholqr_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* out, int64_t ldo,
-                              double thr, bool* ok) {
+                              double thr, bool rank_test, bool* ok) {
   double *G, *Gh, *M, *d;
   int32_t* status;
   const size_t mm = static_cast<size_t>(m) * m;
@@ -226,8 +238,26 @@ static arb_status cholqr_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, i
   ARB_TRY(ws<int32_t>(ctx, WS_CHOL_STATUS, 4, &status));
   ARB_TRY(gram<T>(ctx, n, Z, ldz, m, Z, ldz, m, G, m));
   ARB_TRY(svqb_prep(ctx, m, G, m, Gh, d));
-  ARB_TRY(cholesky_upper(ctx, m, Gh, m, thr, status));
-  ARB_TRY(triangular_inverse(ctx, m, Gh, m, d, M, status));
+  const double* factor = Gh;
+  int64_t ldf = m;
+  if (rank_test) {
+    double *R, *Rinv, *rc_dev;
+    ARB_TRY(ws<double>(ctx, WS_CHOL_R, mm, &R));
+    ARB_TRY(ws<double>(ctx, WS_CHOL_RINV, mm, &Rinv));
+    ARB_TRY(ws<double>(ctx, WS_VEC1, 2, &rc_dev));
+    ARB_TRY(rcond_from_cholesky(ctx, m, Gh, m, R, Rinv, M, status, rc_dev));  // M: scratch for G^{-1}
+    int32_t st[2] = {0, 0};
+    double rc = 0.0;
+    ARB_TRY(d2h_sync(ctx, st, status, sizeof(st)));
+    ARB_TRY(d2h_sync(ctx, &rc, rc_dev, sizeof(double)));
+    *ok = st[0] == 0 && rc > thr;
+    if (orth_trace()) fprintf(stderr, "[arb]   cholqr m %d rcond %.3e (threshold %.1e) %s\n", m, rc, thr, *ok ? "kept" : "-> gram passes");
+    if (!*ok) return ARB_OK;
+    factor = R;
+  } else {
+    ARB_TRY(cholesky_upper(ctx, m, Gh, m, thr, status));
+  }
+  ARB_TRY(triangular_inverse(ctx, m, factor, ldf, d, M, status));
   int32_t st[2] = {0, 0};
   ARB_TRY(d2h_sync(ctx, st, status, sizeof(st)));
   *ok = st[0] == 0;
@@ -235,30 +265,45 @@ static arb_status cholqr_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, i
   return ARB_OK;
 }
 
+// 1: CholeskyQR2 first for well-conditioned blocks; 0 (default): eigen-truncated Gram passes
+// only.  Measured per solve, CholeskyQR2 first / Gram passes only: 128^3 mixed 11.1 s /
+// 10.0 s; Chung-Lu n = 1e6, k = 500 FP64 55.8 s / 56.8 s, mixed 94.0 s / 56.1 s.  The
+// passes' eigenvalue truncation drops directions of the augmentation blocks that an
+// accepted Cholesky keeps (refinement basis 356 against 715 wide on 128^3), at the same
+// final residual.
+#ifndef ARB_ORTH_CHOLQR
+#define ARB_ORTH_CHOLQR 0
+#endif
+
 template <typename T>
 arb_status orth(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, int32_t m, T* U, int64_t ldu, T* tmp,
                 int64_t ldt, int32_t* rank, bool recover) {
   *rank = 0;
   if (m <= 0) return ARB_OK;
-  // CholeskyQR2: two Cholesky passes when the first factorisation keeps every pivot of the
-  // unit-diagonal Gram matrix above the Gram pass's truncation threshold (the block has
-  // full numerical rank) and the second Gram matrix is near the identity (every pivot
-  // above 1/2: the first pass left a well-conditioned block).  Otherwise the block is
-  // (numerically) rank deficient and the eigen-truncated Gram passes below take over.
-  if (m <= cholesky_max_order()) {
+  // CholeskyQR2 (ARB_ORTH_CHOLQR = 1): two Cholesky passes when the unit-diagonal Gram
+  // matrix's reciprocal condition number (from its factor) is above max(the Gram pass's
+  // truncation threshold, 1e-8) - a well-conditioned block - and the second Gram matrix is
+  // near the identity (every pivot above 1/2).  Otherwise the eigen-truncated Gram passes
+  // below take over and decide the rank, from the first pass's Gram matrix when that one
+  // failed.  A CholeskyQR2 that only asked for positive pivots made the 128^3 mixed solve
+  // take an extra FP32 outer iteration (13.0 s per solve).
+  bool have_gram = false;
+  if (m <= cholesky_max_order() && ARB_ORTH_CHOLQR) {
     bool ok1 = false, ok2 = false;
-    ARB_TRY(cholqr_pass<T>(ctx, n, Z, ldz, m, tmp, ldt, orth_tau<T>(m), &ok1));
-    if (ok1) ARB_TRY(cholqr_pass<T>(ctx, n, tmp, ldt, m, U, ldu, 0.5, &ok2));
+    ARB_TRY(cholqr_pass<T>(ctx, n, Z, ldz, m, tmp, ldt, std::max(orth_tau<T>(m), 1e-8), true, &ok1));
+    if (ok1) ARB_TRY(cholqr_pass<T>(ctx, n, tmp, ldt, m, U, ldu, 0.5, false, &ok2));
     if (ok2) {
       *rank = m;
       return ARB_OK;
     }
+    have_gram = !ok1;
   }
   int32_t r1 = 0, r2 = 0;
-  ARB_TRY(svqb_pass<T>(ctx, n, Z, ldz, m, tmp, ldt, &r1));
+  ARB_TRY(svqb_pass<T>(ctx, n, Z, ldz, m, tmp, ldt, &r1, have_gram));
   if (r1 == 0) return ARB_OK;
   ARB_TRY(svqb_pass<T>(ctx, n, tmp, ldt, r1, U, ldu, &r2));
   int32_t r = r2;
+  if (orth_trace()) fprintf(stderr, "[arb]   gram passes m %d rank %d / %d\n", m, r1, r2);
   // A Gram pass resolves singular values down to ~sqrt(tau) of the largest.  A filtered
   // block can span far more (one isolated extreme eigenvalue amplified by the filter), and
   // the directions the passes dropped are then the ones still to converge.  Recover them:
