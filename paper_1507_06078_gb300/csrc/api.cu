@@ -885,13 +885,6 @@ arb_status gn_step(arb_ctx ctx, arb_mat mat, SolveState& S, BlockSet<T>& B, cons
 // The phase is resumable at the points the lock-step batched driver needs: the start of an
 // outer iteration, every inner step (whose filter the caller may have applied for many
 // instances at once), the inner stop check, and the ARR / stop-rule tail.
-// > 0: the FP64 phase of a mixed solve takes the FP32 rcond of its inner stop rule whenever
-// that value is at least this large (resolved by an FP32 Gram matrix); 0: only while the
-// threshold itself is >= 1e-4
-#ifndef ARB_RCOND_F32_RESOLVED
-#define ARB_RCOND_F32_RESOLVED 0.0
-#endif
-
 template <typename T>
 struct Phase {
   arb_ctx ctx;
@@ -1024,10 +1017,10 @@ struct Phase {
     const double rcp = rc;
     bool done_rc = false;
     if constexpr (std::is_same<T, double>::value) {
-      if (S->x32 && (rc_thr >= 1e-4 || ARB_RCOND_F32_RESOLVED > 0.0)) {
+      if (S->x32 && rc_thr >= 1e-4) {
         ARB_TRY((copy_block<double, float>(ctx, n, B->X, B->ld, S->w, S->x32, S->ld32)));
         ARB_TRY(rcond_gram<float>(ctx, n, S->x32, S->ld32, S->w, S->xs, &rc));
-        done_rc = rc_thr >= 1e-4 || (ARB_RCOND_F32_RESOLVED > 0.0 && rc >= ARB_RCOND_F32_RESOLVED);
+        done_rc = true;
       }
     }
     if (!done_rc) ARB_TRY(rcond_gram<T>(ctx, n, B->X, B->ld, S->w, S->xs, &rc));
