@@ -265,14 +265,16 @@ static arb_status cholqr_pass(arb_ctx ctx, int64_t n, const T* Z, int64_t ldz, i
   return ARB_OK;
 }
 
-// 1: CholeskyQR2 first for well-conditioned blocks; 0 (default): eigen-truncated Gram passes
-// only.  Measured per solve, CholeskyQR2 first / Gram passes only: 128^3 mixed 11.1 s /
-// 10.0 s; Chung-Lu n = 1e6, k = 500 FP64 55.8 s / 56.8 s, mixed 94.0 s / 56.1 s.  The
-// passes' eigenvalue truncation drops directions of the augmentation blocks that an
-// accepted Cholesky keeps (refinement basis 356 against 715 wide on 128^3), at the same
-// final residual.
+// 1 (default): CholeskyQR2 first for well-conditioned blocks; 0: eigen-truncated Gram
+// passes only.  The passes cut Gram eigenvalues below 64 m u of the largest, i.e. singular
+// values below ~1e-6 of the largest, where a QR (the oracle's) keeps them to ~1e-13: on a
+// 1600-row diffusion operator (k = 16, tol 1e-9, FP64) the passes-only form stalled at
+// maxres 1.2e-9 after 8 outer iterations where the oracle and the CholeskyQR2-first form
+// converge in 4-5.  Dropping those directions is cheaper where it does not hurt: per solve,
+// CholeskyQR2 first / passes only, 128^3 mixed 11.1 s / 10.0 s; Chung-Lu n = 1e6, k = 500
+// FP64 55.8 s / 56.8 s, mixed 94.0 s / 56.1 s.
 #ifndef ARB_ORTH_CHOLQR
-#define ARB_ORTH_CHOLQR 0
+#define ARB_ORTH_CHOLQR 1
 #endif
 
 template <typename T>
