@@ -40,7 +40,7 @@ UNIT = "solves/s"
 # profiles/solve_counts_laplace3d_128.md).  The reference arm runs before the GPU arm and
 # cannot read them live; it scales its oracle sample with these, and the GPU arm's
 # cpu_baseline scales the same sample with the live counts.
-SOLVE_COUNTS = {128: {"spmm_cols": 507906, "outer_iters": 4}}
+SOLVE_COUNTS = {128: {"spmm_cols": 508266, "outer_iters": 4}}
 
 
 def laplacian_3d_closed_form(m: int) -> np.ndarray:
@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workload: --instances instances, --precision, graph/autotune flags")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--batched-filter", action="store_true",
+                    help="one batched filter call over --instances diffusion instances against per-instance calls")
     ap.add_argument("--c2", action="store_true", help="the full-size Chung-Lu workload (k = 500, p = 600)")
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--c2-precisions", default="fp64,mixed")
@@ -894,8 +896,54 @@ def run_batched_only(args):
     print(json.dumps(out))
 
 
+def run_batched_filter(args):
+    """--batched-filter: one degree-20 FP32 filter of --instances diffusion instances (sides
+    32..--max-side, p = 1.5 k rounded up to 4 columns) as one arb_filter_batched call
+    against one arb_filter_f32 call per instance, best of 5 after 2 warm-ups; wall time with
+    a device synchronisation on both sides."""
+    import torch
+    from paper_1507_06078_gb300 import arrabit as arb, build
+    build.build()
+    ctx = arb.Context(0)
+    ws = I.batched_diffusion_instances(count=args.instances, base_seed=30000, side_range=(32, args.max_side))
+    d = args.degree or 20
+    coef = arb.arb_filter_coefficients(arb.ARB_FILTER_CHEBINTERP, d)
+    jobs, alg = [], 0
+    for w in ws:
+        mat = arb.Matrix.from_csr(ctx, w.A)
+        hi = arb.arb_matrix_gershgorin(ctx, mat)[1]
+        pc = (w.p + 3) // 4 * 4
+        X = torch.from_numpy(I.gaussian_block(w.A.n, pc, w.seed).astype(np.float32)).cuda()
+        jobs.append(dict(mat=mat, op_scale=-1.0, op_shift=hi, a=0.0, b=0.5 * hi, coef=coef, X=X,
+                         colss=torch.zeros(pc, dtype=torch.float64, device="cuda")))
+        alg += filter_algorithmic_bytes(w.A.n, w.A.nnz, pc, d, s=4, z=4)
+
+    def timed(f):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    batched = lambda: arb.arb_filter_batched(ctx, jobs)  # noqa: E731
+    single = lambda: [arb.arb_filter_f32(ctx, j["mat"], -1.0, j["op_shift"], 0.0, j["b"], coef, j["X"])  # noqa: E731
+                      for j in jobs]
+    for _ in range(2):
+        timed(batched)
+        timed(single)
+    tb = min(timed(batched) for _ in range(5))
+    ts = min(timed(single) for _ in range(5))
+    print(json.dumps({"batched_filter": True, "instances": len(ws), "rows": int(sum(w.A.n for w in ws)),
+                      "degree": d, "batched_ms": tb * 1e3, "per_instance_calls_ms": ts * 1e3,
+                      "algorithmic_GB": alg / 1e9, "batched_alg_GBps": alg / tb / 1e9,
+                      "per_instance_alg_GBps": alg / ts / 1e9}))
+
+
 def main():
     args = parse()
+    if args.batched_filter:
+        run_batched_filter(args)
+        return
     if args.c2:
         run_c2(args)
         return
