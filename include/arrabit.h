@@ -284,10 +284,15 @@ typedef struct {
   double* colss;         /* device float64[ncols] or NULL: column sums of squares of Y */
 } arb_filter_job;
 
-/* Filter many instances (different matrices, widths, degrees, precisions) in ONE
- * persistent cooperative launch: all d_max passes of all instances, a grid-wide barrier
- * between passes.  Results equal per-instance arb_filter / arb_filter_f32 up to the order
- * of the FP operations within a row (none: the arithmetic is the same). */
+/* Filter many instances (different matrices, widths, degrees, precisions) in persistent
+ * cooperative launches, one per element type and vector width present (FP32 with 16-byte
+ * rows, FP32 otherwise, FP64 likewise): all d_max passes of all instances of a class, a
+ * grid-wide barrier between passes, tiles of rows handed to warps by per-pass ticket
+ * counters.  Y equals the per-instance arb_filter / arb_filter_f32 result bit for bit (the
+ * same operations in the same order per element); colss equals the column sums of squares
+ * of Y to ~1e-14 relative (FP32 jobs sum in double-float pairs, FP64 jobs in FP64; the
+ * order differs from the single-instance filter's).  X and Y are n rows of ldx / ldy
+ * elements; rows of a 16-byte class may be read up to their leading dimension. */
 arb_status arb_filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs);
 
 /* Host-side coefficients c_0..c_d (float64[degree+1]) of the degree-d Chebyshev
@@ -459,16 +464,18 @@ enum { ARB_BATCH_GRAPHS = 1, ARB_BATCH_AUTOTUNE = 2 };
 /* Solve nb independent problems (Algorithm 8 each, uneven sizes, widths and degrees) in
  * lock step: every instance runs its own outer iterations, stop rules and precision
  * phases, but in each round every instance that is in its inner loop takes one
- * multi-power step, and the filters of all those steps run as ONE persistent cooperative
- * launch (the batched filter of arb_filter_batched: all passes of all instances, a
- * grid-wide barrier between passes).  Instances whose step cannot join the batch (the GN
- * inner solver, the double-float refinement filter of ARB_MIXED_DF) take it alone in the
- * same round.  flags: ARB_BATCH_GRAPHS captures the device work of a round into a CUDA
- * graph the second time the same round shape occurs (the same instances, buffers and
- * degrees) and replays it afterwards, with the round's descriptors re-uploaded before
- * each replay; ARB_BATCH_AUTOTUNE runs arb_matrix_autotune on every distinct matrix first
- * (width p of its first problem).  The work runs on a stream of its own, ordered after the
- * context's stream; each instance has workspaces of its own for the duration of the call.
+ * multi-power step, and the filters of all those steps run as one batched filter
+ * (arb_filter_batched: one persistent cooperative launch per element type present, all
+ * passes of all instances, a grid-wide barrier between passes).  Instances whose step
+ * cannot join the batch (the GN inner solver, the double-float refinement filter of
+ * ARB_MIXED_DF) take it alone in the same round.
+ * flags: ARB_BATCH_GRAPHS captures the device work of a round into a CUDA graph the second
+ * time the same launch shape occurs (the same descriptor addresses, job counts per class
+ * and maximum degree; everything else is read from the descriptors) and replays it
+ * afterwards, with the round's descriptors re-uploaded before each replay;
+ * ARB_BATCH_AUTOTUNE runs arb_matrix_autotune on every distinct matrix first (width p of
+ * its first problem).  The work runs on a stream of its own, ordered after the context's
+ * stream; each instance has workspaces of its own for the duration of the call.
  * Arguments and outputs per instance as for arb_solve (x0[i] host n_i x p_i or NULL;
  * evecs[i] host column-major or NULL; ldq may be NULL for ldq[i] = n_i; opts, info and
  * stats may be NULL).  Returns ARB_OK when every instance converged, else the first
