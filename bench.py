@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched workload: --instances instances, --precision, graph/autotune flags")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--c0", action="store_true", help="the 2D 64^2 workload: milliseconds per solve, FP64 and mixed")
     ap.add_argument("--batched-filter", action="store_true",
                     help="one batched filter call over --instances diffusion instances against per-instance calls")
     ap.add_argument("--c2", action="store_true", help="the full-size Chung-Lu workload (k = 500, p = 600)")
@@ -939,8 +940,48 @@ def run_batched_filter(args):
                       "per_instance_alg_GBps": alg / ts / 1e9}))
 
 
+def run_c0(args):
+    """--c0: the 2D 64^2 workload (k = 20, p = 30, d = 10, q = 1, b after every ARR) solved
+    to its relative residual 1e-10 in FP64 and in mixed precision: milliseconds per solve (wall
+    time around each arb_solve with a device synchronisation, --warmup untimed solves, then
+    --steps timed ones), kernel launches per solve and the work counts.  Problems of this
+    size are latency bound: the metric is the time per solve."""
+    import torch
+    from paper_1507_06078_gb300 import arrabit as arb, build
+    build.build()
+    ctx = arb.Context(0)
+    w = I.workload_2d64()
+    mat = arb.Matrix.from_csr(ctx, w.A)
+    X0 = I.gaussian_block(w.A.n, w.p, 20150722)
+    out = {"c0": True, "workload": w.name, "tol": w.tol}
+    for name, prec in (("fp64", arb.ARB_FP64), ("mixed", arb.ARB_MIXED)):
+        o = arb.arb_options_default(w.k)
+        o.p, o.q, o.degree, o.precision, o.b_update = w.p, 1, 10, prec, 1
+        for _ in range(args.warmup):
+            arb.arb_solve(ctx, mat, w.k, arb.ARB_SMALLEST, w.tol, o, x0=X0)
+        ts, r, l0 = [], None, ctx.launches()
+        for _ in range(max(args.steps, 1)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = arb.arb_solve(ctx, mat, w.k, arb.ARB_SMALLEST, w.tol, o, x0=X0)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        c = 2.0 - 2.0 * np.cos(np.pi * np.arange(1, 65) / 65.0)
+        lam = np.sort((c[:, None] + c[None, :]).ravel())[:w.k]
+        out[name] = {"ms_per_solve": 1e3 * float(np.median(ts)), "ms_min": 1e3 * min(ts),
+                     "launches_per_solve": (ctx.launches() - l0) // max(args.steps, 1),
+                     "outer_iters": r.info["outer_iters"], "n_filters": r.info["n_filters"],
+                     "maxres": r.info["maxres"], "stop": r.info["stop_reason"],
+                     "t_filter_s": r.info["t_filter"], "t_arr_s": r.info["t_arr"]}
+        out[name]["eig_err_vs_closed_form"] = float(np.max(np.abs(r.evals - lam)))
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.c0:
+        run_c0(args)
+        return
     if args.batched_filter:
         run_batched_filter(args)
         return

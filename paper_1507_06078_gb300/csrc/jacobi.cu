@@ -743,6 +743,15 @@ __global__ void __launch_bounds__(JAC_THREADS, 3) jacobi_block_df_kernel(JacPara
 
 }  // namespace
 
+// orders up to this take the one-CTA kernel; above, the cooperative block kernel.  One SM's
+// FP64 pipe bounds the one-CTA kernel (2.2 ms at order 60 on GB300), so from order 33 the
+// block kernel's few CTAs (or its double-float form) win: the 64^2 solve took 29.8 ms
+// instead of 35.3 ms in FP64 and 24.7 ms instead of 31.0 ms in mixed precision
+#ifndef ARB_JAC_ONE_CTA_M
+#define ARB_JAC_ONE_CTA_M 32
+#endif
+static_assert(ARB_JAC_ONE_CTA_M <= JAC_SMALL_M, "the one-CTA kernel holds at most JAC_SMALL_M");
+
 arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w, double* V,
                  int64_t ldv, int32_t* sweeps, double tol, bool df) {
   if (m <= 0) {
@@ -752,7 +761,7 @@ arb_status syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w
   if (m > 8192) return set_error(ctx, ARB_INVALID_ARG, "syevj: matrix too large");
   const int M = (m % 2 == 0) ? m : m + 1;
   const int half = M / 2;
-  if (M <= JAC_SMALL_M) {
+  if (M <= ARB_JAC_ONE_CTA_M) {
     const size_t smem = (2 * static_cast<size_t>(M) * M + 2 * half + JAC_SMALL_THREADS) * sizeof(double);
     int32_t* sw;
     ARB_TRY(ws<int32_t>(ctx, WS_JACOBI, 4, &sw));

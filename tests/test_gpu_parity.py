@@ -356,9 +356,9 @@ def test_gram_df_extreme_magnitudes(arb, ctx_df):
     assert np.all(np.abs(G - X.T @ X) <= 1e-13 * np.outer(nrm, nrm))
 
 
-@pytest.mark.parametrize("m", [97, 200, 256, 720])
+@pytest.mark.parametrize("m", [33, 60, 96, 97, 200, 256, 720])
 def test_syevj_double_float_matches_numpy(arb, ctx_df, m):
-    # orders above 96 on a double-float context: the rotations and block products carry
+    # orders above 32 on a double-float context: the rotations and block products carry
     # ~2^-48 relative error per step and the sweeps stop at off(H) <= 1e-13 ||H||_F
     rng = np.random.default_rng(1000 + m)
     H = rng.standard_normal((m, m))
