@@ -604,8 +604,9 @@ class Server:
 
 def arb_filter_batched(ctx: Context, jobs: list[dict]):
     """Filter several instances in one launch.  Each job: dict(mat, op_scale, op_shift, a, b,
-    coef (numpy), X (torch CUDA float32/float64, row-major), xscale=None, colss=None);
-    returns the list of outputs Y."""
+    coef (numpy), X (torch CUDA float32/float64, row-major, any leading dimension),
+    xscale=None, colss=None, Y=None (preallocated output of X's shape)); returns the list
+    of outputs Y."""
     import torch
     arr = (arb_filter_job * len(jobs))()
     keep, outs = [], []
@@ -614,7 +615,11 @@ def arb_filter_batched(ctx: Context, jobs: list[dict]):
         if not (X.is_cuda and X.dim() == 2 and X.stride(1) == 1 and X.dtype in (torch.float32, torch.float64)):
             raise ValueError("X: row-major 2D float32/float64 CUDA tensor expected")
         coef = np.ascontiguousarray(j["coef"], dtype=np.float64)
-        Y = torch.empty_like(X)
+        Y = j.get("Y")
+        if Y is None:
+            Y = torch.empty_like(X)
+        elif not (Y.is_cuda and Y.dim() == 2 and Y.stride(1) == 1 and Y.dtype == X.dtype and Y.shape == X.shape):
+            raise ValueError("Y: row-major 2D CUDA tensor of X's shape and type expected")
         keep += [coef, X, Y]
         outs.append(Y)
         arr[i] = arb_filter_job(j["mat"].handle, j["op_scale"], j["op_shift"], j["a"], j["b"], len(coef) - 1,

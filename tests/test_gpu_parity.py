@@ -711,6 +711,37 @@ def test_solve_b_every_arr_against_oracle(arb, ctx, precision):
     np.testing.assert_allclose(r.evals, laplacian_3d_eigs(12)[:20], atol=1e-9)
 
 
+def test_filter_batched_padded_rows(arb, ctx):
+    # blocks whose leading dimension is a multiple of the 16-byte vector but whose width is
+    # not: the batched kernel reads whole vectors inside the leading dimension (never past
+    # the block's last row) and writes only the block's columns
+    specs = [(I.diffusion_2d(30, 5), 13, 6, True), (I.laplacian_3d(9), 30, 12, True), (I.laplacian_2d(17), 7, 5, True),
+             (I.diffusion_2d(21, 6), 7, 4, False), (I.laplacian_2d(19), 65, 7, False)]
+    jobs, singles, pads = [], [], []
+    for i, (A, ncols, d, f32) in enumerate(specs):
+        mat = arb.Matrix.from_csr(ctx, A)
+        sigma = O.gershgorin_bounds(O.csr_to_scipy(A.n, A.rowptr, A.col, A.val))[1]
+        ld = (ncols + 3) // 4 * 4 + 4
+        dt = torch.float32 if f32 else torch.float64
+        Xf = torch.full((A.n, ld), 3.0, dtype=dt, device="cuda")
+        Xf[:, :ncols] = dev(I.gaussian_block(A.n, ncols, 70 + i)).to(dt)
+        Yf = torch.full((A.n, ld), 7.0, dtype=dt, device="cuda")
+        coef = O.interpolant_cheb_coeffs(d)
+        colss = torch.zeros(ncols, dtype=torch.float64, device="cuda")
+        jobs.append(dict(mat=mat, op_scale=-1.0, op_shift=sigma, a=0.0, b=0.6 * sigma, coef=coef, X=Xf[:, :ncols],
+                         Y=Yf[:, :ncols], colss=colss))
+        Xc = Xf[:, :ncols].contiguous()
+        singles.append(host((arb.arb_filter_f32 if f32 else arb.arb_filter)(ctx, mat, -1.0, sigma, 0.0, 0.6 * sigma,
+                                                                          coef, Xc)))
+        pads.append((Yf, ncols))
+    arb.arb_filter_batched(ctx, jobs)
+    for single, (Yf, ncols), job in zip(singles, pads, jobs):
+        Yh = host(Yf)
+        np.testing.assert_array_equal(Yh[:, :ncols], single)
+        assert np.all(Yh[:, ncols:] == 7.0)  # the padding is never written
+        np.testing.assert_allclose(host(job["colss"]), np.sum(single.astype(np.float64) ** 2, axis=0), rtol=1e-10)
+
+
 def test_filter_batched_matches_single_instance_filters(arb, ctx):
     # uneven instances (sizes, widths, degrees, both precisions) in one persistent launch,
     # each compared with its own single-instance filter and with the oracle
