@@ -167,3 +167,38 @@ def test_gram_bindings_refuse_mismatched_shapes_before_any_launch(fn):
         f(None, X, torch.zeros((100, 3), dtype=dt), torch.zeros((4, 2), dtype=torch.float64))
     with pytest.raises(ValueError, match="C_out"):
         f(None, X, torch.zeros((100, 3), dtype=dt), torch.zeros((3, 4), dtype=torch.float64))
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the binding's ctypes structures against the C compiler's layout of include/arrabit.h:
+    # size and the offset of every field, for every structure the calls pass by pointer
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [arb.arb_options, arb.arb_info, arb.arb_filter_job, arb.arb_batch_stats]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "arrabit.h"', "int main(void) {"]
+    for s in structs:
+        name = s.__name__
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in s._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, field, value = line.split()
+            got[(name, field)] = int(value)
+    for s in structs:
+        name = s.__name__
+        assert got[(name, "size")] == ctypes.sizeof(s), name
+        for f, _ in s._fields_:
+            assert got[(name, f)] == getattr(s, f).offset, (name, f)
