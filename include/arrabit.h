@@ -133,7 +133,7 @@ arb_status arb_ctx_destroy(arb_ctx ctx);
  * steps inside arb_solve) take FP64 operands, split them into hi + lo FP32 pairs and
  * multiply-add in double-float arithmetic on the FP32 pipe (compensated Dot2 sums, about
  * 2^-44 relative per term), returning FP64; the Jacobi eigensolver (arb_syevj and the
- * same step inside those calls) then runs orders above 96 in double-float arithmetic too
+ * same step inside those calls) then runs orders above 32 in double-float arithmetic too
  * and stops at off(H) <= 1e-13 ||H||_F.  Off by default (plain FP64).  ARB_MIXED_DF
  * solves switch it on for their refinement phase and restore the setting afterwards.  The
  * paper computes in FP64 throughout; this mode is the library's.  Errors:
@@ -357,7 +357,7 @@ arb_status arb_gemm_tall_f32(arb_ctx ctx, int64_t n, const float* In, int64_t ld
  * parallel cyclic Jacobi on the device (Alg. 1 step 3, reading H = V Sigma V^T).
  * w: float64[m] descending; V: m x m row-major (ldv), column j the eigenvector of w[j].
  * H is not modified.  sweeps (host, may be NULL) receives the sweep count.  Sweeps stop at
- * off(H) <= 1e-15 ||H||_F (FP64), or 1e-13 ||H||_F for orders above 96 on a context with
+ * off(H) <= 1e-15 ||H||_F (FP64), or 1e-13 ||H||_F for orders above 32 on a context with
  * double-float dense arithmetic (arb_ctx_set_dense_df). */
 arb_status arb_syevj(arb_ctx ctx, int32_t m, const double* H, int64_t ldh, double* w,
                      double* V, int64_t ldv, int32_t* sweeps);
