@@ -383,7 +383,7 @@ arb_status filter_batched(arb_ctx ctx, int32_t njobs, const arb_filter_job* jobs
 void matrix_free_sell(arb_mat m);
 // frees a matrix's bulk-copy group table (spmm_bulk.cu)
 void matrix_free_bulk(arb_mat m);
-// df: orders above 96 in double-float arithmetic on the FP32 pipe (stops at <= 1e-13).
+// df: orders above 32 in double-float arithmetic on the FP32 pipe (stops at <= 1e-13).
 // jac_df / jac_tol: the Jacobi arithmetic and tolerance for matrices formed from element
 // type T: FP32 bases (accurate to ~1e-7) and double-float dense products take the
 // double-float kernel; plain FP64 keeps FP64 throughout.

@@ -9,8 +9,9 @@
 // commute and are applied together.  Sweeps stop when off(A) <= tol ||H||_F (1e-15 for
 // FP64 data; callers whose matrices carry FP32-level errors pass 1e-10) or after 60.
 //
-// m <= 96: one CTA holds A and V in shared memory and rotates single indices.
-// m > 96: block Jacobi.  The indices are cut into NB blocks of 16 (NB even; padding
+// m <= ARB_JAC_ONE_CTA_M (32; the kernel holds up to 96): one CTA holds A and V in shared
+// memory and rotates single indices.
+// Above: block Jacobi.  The indices are cut into NB blocks of 16 (NB even; padding
 // indices have zero rows and columns, so no rotation ever couples them to real ones).  A
 // round of the tournament on the NB blocks pairs blocks (I, J); for each pair the 32 x 32
 // subproblem A[I+J, I+J] gets one cyclic Jacobi sweep in shared memory, accumulating the
