@@ -475,9 +475,14 @@ def run_ours(args):
                   "p99_speedup_vs_fp64": mix64["p99_s"] / mix["p99_s"],
                   "solves_per_s_speedup_vs_fp64": mix["solves_per_s"] / max(mix64["solves_per_s"], 1e-30)}
 
+    small = None
+    if rank == 0 and world == 1:
+        small = _guarded(lambda: c0_timings(steps=5, warmup=2))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_sample(W, {"spmm_cols": int(np.mean([i["spmm_cols"] for i in infos]))})
+        cpu["full_solves"] = _guarded(lambda: cpu_full_solves(budget_s=20.0))
 
     if rank == 0:
         info = infos[-1]
@@ -492,7 +497,7 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
                 "gpu_launches": int(launches), "fp64_path": fp64_cmp, "strict_1e-8": strict, "served": served,
-                "batched_c3": batched,
+                "batched_c3": batched, "small_c0": small,
                 "solve": {"eig_rel_err_vs_closed_form": eig_err, "maxres": info["maxres"],
                           "outer_iters": info["outer_iters"], "n_filters": info["n_filters"],
                           "spmm_cols": info["spmm_cols"], "t_filter_s": info["t_filter"],
@@ -940,40 +945,83 @@ def run_batched_filter(args):
                       "per_instance_alg_GBps": alg / ts / 1e9}))
 
 
-def run_c0(args):
-    """--c0: the 2D 64^2 workload (k = 20, p = 30, d = 10, q = 1, b after every ARR) solved
-    to its relative residual 1e-10 in FP64 and in mixed precision: milliseconds per solve (wall
-    time around each arb_solve with a device synchronisation, --warmup untimed solves, then
-    --steps timed ones), kernel launches per solve and the work counts.  Problems of this
+def c0_timings(steps=5, warmup=2):
+    """The 2D 64^2 workload (k = 20, p = 30, d = 10, q = 1, b after every ARR) solved to its
+    relative residual 1e-10 in FP64 and in mixed precision: milliseconds per solve (wall
+    time around each arb_solve with a device synchronisation, `warmup` untimed solves, then
+    `steps` timed ones), kernel launches per solve and the work counts.  Problems of this
     size are latency bound: the metric is the time per solve."""
     import torch
-    from paper_1507_06078_gb300 import arrabit as arb, build
-    build.build()
+    from paper_1507_06078_gb300 import arrabit as arb
     ctx = arb.Context(0)
     w = I.workload_2d64()
     mat = arb.Matrix.from_csr(ctx, w.A)
     X0 = I.gaussian_block(w.A.n, w.p, 20150722)
-    out = {"c0": True, "workload": w.name, "tol": w.tol}
+    out = {"workload": w.name, "tol": w.tol}
+    c = 2.0 - 2.0 * np.cos(np.pi * np.arange(1, 65) / 65.0)
+    lam = np.sort((c[:, None] + c[None, :]).ravel())[:w.k]
     for name, prec in (("fp64", arb.ARB_FP64), ("mixed", arb.ARB_MIXED)):
         o = arb.arb_options_default(w.k)
         o.p, o.q, o.degree, o.precision, o.b_update = w.p, 1, 10, prec, 1
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             arb.arb_solve(ctx, mat, w.k, arb.ARB_SMALLEST, w.tol, o, x0=X0)
         ts, r, l0 = [], None, ctx.launches()
-        for _ in range(max(args.steps, 1)):
+        for _ in range(max(steps, 1)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             r = arb.arb_solve(ctx, mat, w.k, arb.ARB_SMALLEST, w.tol, o, x0=X0)
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
-        c = 2.0 - 2.0 * np.cos(np.pi * np.arange(1, 65) / 65.0)
-        lam = np.sort((c[:, None] + c[None, :]).ravel())[:w.k]
         out[name] = {"ms_per_solve": 1e3 * float(np.median(ts)), "ms_min": 1e3 * min(ts),
-                     "launches_per_solve": (ctx.launches() - l0) // max(args.steps, 1),
+                     "launches_per_solve": (ctx.launches() - l0) // max(steps, 1),
                      "outer_iters": r.info["outer_iters"], "n_filters": r.info["n_filters"],
                      "maxres": r.info["maxres"], "stop": r.info["stop_reason"],
-                     "t_filter_s": r.info["t_filter"], "t_arr_s": r.info["t_arr"]}
-        out[name]["eig_err_vs_closed_form"] = float(np.max(np.abs(r.evals - lam)))
+                     "t_filter_s": r.info["t_filter"], "t_arr_s": r.info["t_arr"],
+                     "eig_err_vs_closed_form": float(np.max(np.abs(r.evals - lam)))}
+    mat.close()
+    ctx.close()
+    return out
+
+
+def cpu_full_solves(budget_s=20.0):
+    """The oracle (oracle.arrabit_mpm, FP64, unchanged) solving whole problems end to end on
+    the host: the 2D 64^2 workload (k = 20, tol 1e-10) and the smallest instances of the
+    batched diffusion family (seeds 30000 + i, sides 32-128, q = 1, d = 20, tol 1e-8), each
+    with the same options as the GPU runs, until about budget_s seconds are spent.  Seconds
+    per solve, measured, not extrapolated."""
+    from oracle import arrabit_oracle as O
+    t_start = time.perf_counter()
+    out = []
+    w = I.workload_2d64()
+    probs = [(w.name, w.A, w.k, I.gaussian_block(w.A.n, w.p, 20150722), w.tol, 10)]
+    for inst in sorted(I.batched_diffusion_instances(count=8, base_seed=30000, side_range=(32, 128)),
+                       key=lambda v: v.A.n)[:3]:
+        probs.append((inst.name, inst.A, inst.k, I.gaussian_block(inst.A.n, inst.p, inst.seed), 1e-8, 20))
+    for name, A, k, X0, tol, d in probs:
+        if time.perf_counter() - t_start > budget_s:
+            break
+        B = O.csr_to_scipy(A.n, A.rowptr, A.col, A.val)
+        t0 = time.perf_counter()
+        r = O.arrabit_mpm(B, k, X0, which="smallest", tol=tol, q=1, degree=d, b_update="every_arr")
+        out.append({"problem": name, "n": int(A.n), "k": int(k), "seconds": time.perf_counter() - t0,
+                    "converged": bool(r.converged), "outer_iters": int(r.outer_iters)})
+    return out
+
+
+def _guarded(f):
+    """Run one optional part of the bench line; an exception becomes an error entry."""
+    try:
+        return f()
+    except Exception as e:  # noqa: BLE001 - the line must still be printed
+        return {"error": repr(e)[:300]}
+
+
+def run_c0(args):
+    """--c0: the small workload's time per solve (c0_timings), FP64 and mixed."""
+    from paper_1507_06078_gb300 import build
+    build.build()
+    out = c0_timings(args.steps, args.warmup)
+    out["c0"] = True
     print(json.dumps(out))
 
 
